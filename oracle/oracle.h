@@ -1,0 +1,133 @@
+/*
+ * oracle.h -- plain FP64 CPU oracle for the Heston / Longstaff-Schwartz /
+ * bump-and-revalue Greeks path of "Low-power option Greeks" (Klaisoongnoen,
+ * Brown, Thomson Brown, HEART '22).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes
+ * or calls this code; only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load it.  It shares no header, table or
+ * helper with the CUDA path.
+ *
+ * Every function follows the definition of the step it implements, in the
+ * order the method states it, in double precision, compiled without FMA
+ * contraction.  The paper itself prints no formulas: it names the method
+ * (Heston model, Andersen quadratic-exponential discretisation, two
+ * double-precision random inputs per path/asset/step, exponential of the log
+ * price, Longstaff-Schwartz regression with a quadratic curve fit; Sec. 2.2
+ * and Sec. 2.2.1) and cites the original papers for the formulas.  The
+ * readings taken where it is silent are listed per function below.
+ *
+ * Pins (tests/test_oracle_*.py): Philox against the cuRAND host generator;
+ * the normal quantile against scipy's ndtri; the QE variance step against its
+ * exact first two conditional moments; the FT-Euler step against its xi = 0
+ * closed form; path prices against the Heston characteristic-function price
+ * and Black-Scholes; the backward induction against a least-squares solve by
+ * QR on tiny path sets and against a stopping-time reconstruction; American
+ * prices against a CRR tree restricted to the same exercise dates; Greeks
+ * against Black-Scholes Greeks.  No function here is unpinned.
+ */
+#ifndef LSMC_ORACLE_H
+#define LSMC_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_PUT = 0, ORC_CALL = 1 };
+enum { ORC_AMERICAN = 0, ORC_EUROPEAN = 1 };
+enum { ORC_QE = 0, ORC_FT_EULER = 1 };
+enum { ORC_BASIS_S2 = 0, ORC_BASIS_SV2 = 1 };
+/* uniform grid: 52-bit (double) or 23-bit (single-precision) mantissa */
+enum { ORC_GRID_F64 = 0, ORC_GRID_F32 = 1 };
+enum { ORC_GREEK_DELTA = 1, ORC_GREEK_GAMMA = 2, ORC_GREEK_VEGA = 4,
+       ORC_GREEK_RHO = 8, ORC_GREEK_THETA = 16 };
+/* scenario kinds, in the order scenarios are laid out */
+enum { ORC_SC_BASE = 0, ORC_SC_S_UP, ORC_SC_S_DN, ORC_SC_SG_UP, ORC_SC_SG_DN,
+       ORC_SC_V_UP, ORC_SC_V_DN, ORC_SC_R_UP, ORC_SC_R_DN, ORC_SC_T_DN,
+       ORC_SC_T_UP, ORC_SC_COUNT };
+
+typedef struct {
+  double S0, r, q, v0, kappa, theta, xi, rho;
+} orc_heston;
+
+typedef struct {
+  double rel_dS, rel_dS_gamma, rel_dv0, abs_dr, abs_dT;
+  uint32_t greek_mask;
+  uint32_t pad_;
+} orc_bumps;
+
+typedef struct {
+  double price, price_se, delta, gamma, vega, rho, theta, european_price;
+  uint32_t n_singular, n_revaluations;
+  int32_t status;
+  int32_t pad_;
+} orc_result;
+
+/* Philox4x32-10 (Salmon et al., SC'11): 10 rounds on a 128-bit counter
+ * under a 64-bit key. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                       uint32_t out[4]);
+
+/* (m + 1/2) 2^-52 with m = the top 52 bits of (hi:lo); never 0 or 1. */
+double orc_uniform_f64(uint32_t hi, uint32_t lo);
+/* (m + 1/2) 2^-23 with m = the top 23 bits of w; never 0 or 1. */
+double orc_uniform_f32(uint32_t w);
+
+/* Standard normal quantile: the root z of (1/2) erfc(-z / sqrt 2) = u. */
+double orc_norm_inv(double u);
+
+/* The random inputs of one path step: Philox of counter
+ * (path, step, stream, 0) under key (seed lo, seed hi) gives (U_V, Z_V, Z_X),
+ * Z = quantile(U).  out = {U_V, Z_V, Z_X}. */
+void orc_draws(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
+               int grid, double out[3]);
+
+/* Andersen QE step: out = {x1, v1}. */
+void orc_qe_step(const orc_heston* m, double dt, double x, double v,
+                 double uV, double zV, double zX, double out[2]);
+/* Full-truncation Euler step: out = {x1, v1 (raw), max(v1, 0)}. */
+void orc_ft_step(const orc_heston* m, double dt, double x, double v,
+                 double zV, double zX, double out[3]);
+
+/* Path matrices S[n*P + p], V[n*P + p] for n = 0..N (row 0 = S0, v0). */
+int orc_paths(const orc_heston* m, double T, int scheme, int grid,
+              uint32_t P, uint32_t N, uint64_t seed, uint32_t stream,
+              double* S, double* V, int n_threads);
+
+/* Longstaff-Schwartz backward induction over given paths.
+ * out = {price, price_se, european_price, continuation}.
+ * beta (optional): N*6 doubles, row n holds the step-n coefficients (NaN if
+ * no regression at n).  exercise (optional): N*P bytes, 1 where path p
+ * exercises at step n.  Returns 0 or a negative error. */
+int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
+             double S0, double K, double T, double r, double theta, int type,
+             int style, int basis, double out[4], uint32_t* n_singular,
+             double* beta, uint8_t* exercise);
+
+/* Scenario table of a bump specification: fills up to ORC_SC_COUNT models,
+ * maturities and kinds; returns the number of scenarios or a negative error. */
+int orc_scenarios(const orc_heston* m, double T, const orc_bumps* b,
+                  orc_heston* models, double* Ts, int* kinds);
+
+/* Price and Greeks of n_strikes contracts sharing one path set per scenario.
+ * scen_prices (optional): n_scen * n_strikes scenario values. */
+int orc_price_greeks(const orc_heston* m, int type, int style, double T,
+                     const double* strikes, uint32_t n_strikes, uint32_t P,
+                     uint32_t N, int scheme, int grid, int basis,
+                     const orc_bumps* b, uint64_t seed, uint32_t stream,
+                     int n_threads, orc_result* out, double* scen_prices);
+
+/* Array forms of the scalar functions above (plain loops). */
+void orc_philox_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out,
+                  size_t n);
+void orc_norm_inv_n(const double* u, double* z, size_t n);
+void orc_draws_n(uint64_t seed, uint32_t stream, const uint32_t* path,
+                 const uint32_t* step, size_t n, int grid, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
