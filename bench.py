@@ -1,0 +1,317 @@
+"""Benchmark: Heston / Longstaff-Schwartz price + full Greeks on one GB300.
+
+One step = the whole path of the workload (Philox + normals + Heston paths
+for every path group, Longstaff-Schwartz over every scenario x strike,
+estimator and finite-difference Greeks) for the American-put book of
+131,072 paths x 252 steps, strikes {80, 90, 100, 110, 120}, basis
+{1, S, S^2, v, Sv, v^2}, 11 revaluations per strike, FP64.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank prices its own
+replica of the workload (replicas only: the path needs no exchange) and
+rank 0 reports the sum of throughputs over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+_ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, _ROOT)
+
+from paper_2206_03719_gb300 import workloads  # noqa: E402
+
+GOLDEN = os.path.join(_ROOT, "tests", "golden", "paper_fp64.json")
+PEAKS = os.path.join(_ROOT, "MEASURED_PEAKS.json")
+# nominal FP64 rate of a GB300 (used as the ALU roofline of the FP64 path)
+FP64_NOMINAL_TFLOPS = 1.25
+# algorithmic FP64 operations of the backward pass:
+#   every (instance, path, date): S = scale*E, payoff, discount      -> 3
+#   in-the-money moment sums (SV2): x, w, 12 monomial products,
+#     15 monomial adds, 5 products + 6 adds for X^T y                 -> 40
+#   in-the-money exercise test at the next date: S, payoff, x, w,
+#     5 multiply-adds for the continuation value, compare             -> 15
+BWD_FLOPS_ALL = 3
+BWD_FLOPS_ITM = 40 + 15
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="paper_fp64",
+                    choices=["paper_fp64", "large_mixed", "paper_mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def pick_workload(name):
+    if name == "paper_fp64":
+        return workloads.PAPER_FP64
+    if name == "paper_mixed":
+        return workloads.PAPER_FP64.replace(precision="mixed",
+                                            name="american-put-heston-131072x252-5strikes-mixed")
+    return workloads.LARGE_MIXED
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def oracle_sample_rate(wl, sample_paths, threads=None):
+    """Time the FP64 oracle on the workload with sample_paths paths; return
+    (seconds, Greeks/s scaled to the full path count, cores used)."""
+    sys.path.insert(0, os.path.join(_ROOT, "tests"))
+    import oracle
+    from golden.make_golden import run_oracle  # noqa: E402
+    oracle.build()
+    n_threads = threads or (os.cpu_count() or 1)
+    sample = wl.replace(n_paths=sample_paths, precision="fp64")
+    t0 = time.perf_counter()
+    run_oracle(sample, n_threads=n_threads)
+    dt = time.perf_counter() - t0
+    scale = wl.n_paths / sample_paths  # the oracle's cost is linear in paths
+    return dt, wl.n_greeks / (dt * scale), n_threads
+
+
+def max_rel_err(got, gold):
+    worst = 0.0
+    for g, r in zip(got, gold):
+        for k in ("price", "delta", "gamma", "vega", "rho", "theta"):
+            if r[k] is None or (isinstance(r[k], float) and math.isnan(r[k])):
+                continue
+            worst = max(worst, abs(g[k] - r[k]) / max(abs(r[k]), 1e-12))
+    return worst
+
+
+def run_reference(args, wl):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    sample_paths = 2048
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt, rate, cores = oracle_sample_rate(wl, sample_paths)
+        if i >= args.warmup:
+            times.append(dt)
+    mean = sum(times) / len(times)
+    scale = wl.n_paths / sample_paths
+    value = wl.n_greeks / (mean * scale)
+    sample = ("FP64 oracle (oracle/oracle.c) on %d of the %d paths per step, all %d strikes and "
+              "%d revaluations, extrapolated linearly in paths" % (
+                  sample_paths, wl.n_paths, len(wl.strikes), wl.n_scenarios))
+    line = {
+        "impl": "reference", "metric": "Greeks/s", "value": value, "unit": "Greeks/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_paths": wl.n_paths, "n_steps": wl.n_steps,
+                   "strikes": wl.strikes, "revaluations": wl.n_scenarios,
+                   "scheme": wl.scheme, "basis": wl.basis},
+        "cpu_baseline": {"value": value, "unit": "Greeks/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Greeks/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    wl = pick_workload(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2206_03719_gb300 import api, build
+    from paper_2206_03719_gb300 import lsmc as L
+    build.build()
+    req = api.Request(wl)
+    need = L.lsmc_request_footprint(None, req.c)
+    ctx = api.Context(workspace_bytes=need + (256 << 20))
+    plan = ctx.plan([wl])
+    info = plan.info()
+    stream = ctx.stream
+
+    for _ in range(args.warmup):
+        plan.launch()
+    first = plan.fetch()
+    plan.set_timing(True)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        plan.launch()
+    end.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end) / args.steps
+    kms, launches = plan.kernel_times()
+    res = plan.fetch()
+    info = plan.info()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * wl.n_greeks / (ms_max / 1e3)
+
+    plan.close()
+    # end to end through the public call with host buffers
+    e2e = None
+    if not args.no_e2e:
+        times = []
+        for i in range(max(2, min(args.steps, 3)) + 1):
+            barrier()
+            t0 = time.perf_counter()
+            out = L.lsmc_price_request(ctx.ctx, req.c)
+            times.append(time.perf_counter() - t0)
+        e2e_s = sorted(times[1:])[len(times[1:]) // 2]
+        e2e = {"value": world * wl.n_greeks / e2e_s, "unit": "Greeks/s",
+               "h2d_bytes_per_step": int(info.h2d_bytes),
+               "d2h_bytes_per_step": int(info.d2h_bytes),
+               "ms_per_step": e2e_s * 1e3,
+               "path": "lsmc_price_request: validate, plan, upload, launch, read back"}
+
+    ctx.close()
+    if rank != 0:
+        return
+
+    # accuracy against the stored FP64 oracle values of this workload
+    acc = None
+    if os.path.exists(GOLDEN) and wl.n_paths == workloads.PAPER_FP64.n_paths:
+        gold = json.load(open(GOLDEN))["results"]
+        acc = max_rel_err(res, gold)
+
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    bwd_ms = kms[2] / max(1, launches)
+    fwd_ms = kms[1] / max(1, launches)
+    itm = info.itm_path_steps
+    flops = BWD_FLOPS_ALL * info.lsmc_path_steps + BWD_FLOPS_ITM * itm
+    achieved = flops / (bwd_ms / 1e3) / 1e12
+    fp64 = wl.precision == "fp64"
+    roofline = {
+        "kernel": "backward_kernel (Longstaff-Schwartz moments, solve, exercise)",
+        "bound": "alu", "achieved": achieved,
+        "peak": FP64_NOMINAL_TFLOPS if fp64 else None, "unit": "TFLOP/s",
+        "frac": achieved / FP64_NOMINAL_TFLOPS if fp64 else None,
+        "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (no measured FP64 peak)",
+        "traffic": None,
+        "kernel_ms": {"setup": kms[0] / max(1, launches), "forward": fwd_ms,
+                      "backward": bwd_ms, "greeks": kms[3] / max(1, launches)},
+    }
+    cpu = None
+    if not args.no_cpu_baseline:
+        dt, rate, cores = oracle_sample_rate(wl, 2048)
+        cpu = {"value": rate, "unit": "Greeks/s", "cores": cores, "kind": "oracle",
+               "sample": "FP64 oracle on 2048 of %d paths (all strikes and revaluations, "
+                         "%.1f s), scaled linearly to the full path count" % (wl.n_paths, dt)}
+    line = {
+        "metric": "Greeks/s", "value": value, "unit": "Greeks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if fp64 else "f32+f64", "data": "synthetic",
+        "config": {"workload": wl.name, "n_paths": wl.n_paths, "n_steps": wl.n_steps,
+                   "strikes": wl.strikes, "greeks": list(wl.greeks),
+                   "revaluations": wl.n_scenarios, "scheme": wl.scheme, "basis": wl.basis,
+                   "precision": wl.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
+        "path_steps_per_s": {"generated": world * wl.generated_path_steps / (ms_max / 1e3),
+                             "lsmc": world * wl.lsmc_path_steps / (ms_max / 1e3)},
+        "max_rel_err_vs_oracle": acc,
+        "accuracy_ok": (acc is not None and acc <= 1e-4) if acc is not None else None,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(info.kernels_per_launch) * args.steps,
+        "clocks": clocks,
+        "device_bytes": int(info.device_bytes),
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

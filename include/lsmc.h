@@ -1,0 +1,252 @@
+/*
+ * lsmc.h -- C ABI of the GB300 Heston / Longstaff-Schwartz / Greeks library.
+ *
+ * Method (Klaisoongnoen, Brown, Thomson Brown, "Low-power option Greeks",
+ * HEART '22): Monte Carlo paths of the Heston model discretised by
+ * Andersen's quadratic-exponential (QE) scheme from two random inputs per
+ * path and step, the exponential of the log price, then Longstaff-Schwartz
+ * early exercise by a least-squares curve fit per exercise date (Sec. 2.2 and
+ * Sec. 2.2.1; the loop reorganisation of Sec. 4.1 is what the GPU layout
+ * below replaces).  The paper names the Greeks as the purpose of the run
+ * (title, Sec. 2.2) without a method; here they are central bump-and-revalue
+ * differences under common random numbers.  A full-truncation Euler
+ * discretisation is offered beside QE.
+ *
+ * Conventions for every call:
+ *   - Return value: LSMC_OK (0) on success, LSMC_PENDING (1) for a request
+ *     still in flight, a negative LSMC_E* code otherwise; lsmc_strerror()
+ *     names it.  No C++ exception crosses this boundary.
+ *   - The caller owns every struct and array it passes; the library copies
+ *     what it needs before returning and keeps no caller pointer.
+ *   - Pointers documented "device" are CUDA global-memory addresses on the
+ *     context's device; "host" pointers are ordinary host memory.
+ *   - Floating point parameters must be finite.  Model limits: S0 > 0,
+ *     K > 0, T > 0, v0 >= 0, kappa > 0, theta > 0, xi >= 0 (xi > 0 for QE),
+ *     |rho| <= 1, n_paths >= 1, n_steps >= 1.  Violations return
+ *     LSMC_EINVAL and launch nothing.
+ */
+#ifndef LSMC_H
+#define LSMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LSMC_ABI_VERSION 1
+
+/* ---- status codes ------------------------------------------------------ */
+#define LSMC_OK 0
+#define LSMC_PENDING 1
+#define LSMC_EINVAL (-1)     /* an argument is out of range or not finite */
+#define LSMC_ENOMEM (-2)     /* device or workspace memory exhausted */
+#define LSMC_EBUSY (-3)      /* request queue full */
+#define LSMC_ETIMEOUT (-4)   /* a bounded device-side wait expired */
+#define LSMC_ECUDA (-5)      /* a CUDA runtime call failed */
+#define LSMC_ENOTIMPL (-6)   /* combination not supported */
+#define LSMC_ENOTFOUND (-7)  /* unknown ticket */
+#define LSMC_ENODEV (-8)     /* no usable CUDA device */
+
+/* ---- enumerations ------------------------------------------------------ */
+enum { LSMC_PUT = 0, LSMC_CALL = 1 };
+enum { LSMC_AMERICAN = 0, LSMC_EUROPEAN = 1 };
+/* Heston discretisation: Andersen QE (the paper's, Sec. 2.2) or
+ * full-truncation Euler (negative variance truncated in drift and diffusion). */
+enum { LSMC_SCHEME_QE = 0, LSMC_SCHEME_FT_EULER = 1 };
+/* Regression basis on in-the-money paths, scaled x = S/K, w = v/theta:
+ * S2 = {1, x, x^2} (the paper's quadratic curve fit, Sec. 2.2.1);
+ * SV2 = {1, x, x^2, w, x w, w^2}. */
+enum { LSMC_BASIS_S2 = 0, LSMC_BASIS_SV2 = 1 };
+/* FP64: paths, sums, solve and estimator in double precision.
+ * MIXED: paths and per-thread moment sums in single precision; cross-warp
+ * sums, the normal-equation solve and the estimator in double. */
+enum { LSMC_FP64 = 0, LSMC_MIXED = 1 };
+enum { LSMC_GREEK_DELTA = 1, LSMC_GREEK_GAMMA = 2, LSMC_GREEK_VEGA = 4,
+       LSMC_GREEK_RHO = 8, LSMC_GREEK_THETA = 16, LSMC_GREEK_ALL = 31 };
+
+/* ---- value types ------------------------------------------------------- */
+/* Heston model: dS = (r - q) S dt + sqrt(v) S dW1,
+ * dv = kappa (theta - v) dt + xi sqrt(v) dW2, d<W1, W2> = rho dt (Sec. 2.2). */
+typedef struct lsmc_heston {
+  double S0, r, q, v0, kappa, theta, xi, rho;
+} lsmc_heston;
+
+typedef struct lsmc_contract {
+  int32_t type;   /* LSMC_PUT / LSMC_CALL */
+  int32_t style;  /* LSMC_AMERICAN (exercise dates t_1..t_N and t_0) or EUROPEAN */
+  double K;       /* strike */
+  double T;       /* maturity in years; exercise dates t_n = n T / n_steps */
+} lsmc_contract;
+
+/* Central bumps: S0 (1 +- rel_dS) for delta, S0 (1 +- rel_dS_gamma) for gamma
+ * (0 or equal to rel_dS: gamma reuses the delta pair), v0 (1 +- rel_dv0) for
+ * vega = dV/dv0, r +- abs_dr for rho, T -+ abs_dT (same n_steps) for
+ * theta = -dV/dT.  greek_mask: LSMC_GREEK_* bits. */
+typedef struct lsmc_bumps {
+  double rel_dS, rel_dS_gamma, rel_dv0, abs_dr, abs_dT;
+  uint32_t greek_mask;
+  uint32_t reserved;
+} lsmc_bumps;
+
+/* Greeks not requested are NaN.  status: 0, or 1 when at least one exercise
+ * date had a singular regression (no exercise there; counted in
+ * n_singular_solves over all revaluations). */
+typedef struct lsmc_result {
+  double price, price_se, delta, gamma, vega, rho, theta, european_price;
+  uint32_t n_singular_solves, n_revaluations;
+  int32_t status;
+  int32_t reserved;
+} lsmc_result;
+
+typedef struct lsmc_config {
+  int32_t device;        /* CUDA device ordinal */
+  int32_t precision;     /* default LSMC_FP64 / LSMC_MIXED */
+  int32_t scheme;        /* default LSMC_SCHEME_QE / LSMC_SCHEME_FT_EULER */
+  int32_t reserved;
+  uint64_t hbm_budget;   /* bytes the serving loop may hold; 0 = 3/4 of free */
+  uint32_t max_inflight; /* requests on the device at once (serving); 0 = 8 */
+  uint32_t queue_capacity; /* pending requests accepted; 0 = 4096 */
+} lsmc_config;
+
+/* One pricing request: a family of contracts of one type/style/maturity that
+ * share one path set per scenario (one per strike).  precision / scheme of
+ * -1 take the context's default.  stream_id selects the random stream
+ * (Philox counter word 2); seed is the Philox key. */
+typedef struct lsmc_request {
+  lsmc_heston model;
+  int32_t type, style;
+  double T;
+  const double* strikes;   /* host, n_strikes values */
+  uint32_t n_strikes;
+  uint32_t n_paths, n_steps;
+  int32_t basis;
+  int32_t precision;
+  int32_t scheme;
+  lsmc_bumps bumps;
+  uint64_t seed;
+  uint32_t stream_id;
+  uint32_t reserved;
+} lsmc_request;
+
+typedef struct lsmc_ctx lsmc_ctx;
+typedef struct lsmc_plan lsmc_plan;
+
+/* ---- library ----------------------------------------------------------- */
+const char* lsmc_strerror(int status);
+int lsmc_abi_version(void);
+
+/* ---- context ----------------------------------------------------------- */
+/* Creates a context on config->device (NULL: device 0, FP64, QE).  The
+ * context owns a CUDA stream unless one is set, a workspace arena and, after
+ * the first lsmc_submit, one scheduler thread.  Thread-safe afterwards. */
+int lsmc_create(lsmc_ctx** out, const lsmc_config* config);
+/* Waits for in-flight work, stops the scheduler, frees everything. */
+void lsmc_destroy(lsmc_ctx* ctx);
+/* Work of the synchronous calls runs on this CUDA stream (a cudaStream_t; NULL
+ * = the context's own stream).  The caller keeps the stream alive. */
+int lsmc_set_stream(lsmc_ctx* ctx, void* cuda_stream);
+/* Device memory the context sub-allocates from instead of cudaMalloc
+ * (e.g. a PyTorch tensor).  Must be set before any plan exists and stay
+ * valid until lsmc_destroy; 256-byte aligned. */
+int lsmc_set_workspace(lsmc_ctx* ctx, void* device_ptr, size_t bytes);
+/* Bytes of device memory a request needs (paths, regression state, tables). */
+int lsmc_request_footprint(const lsmc_ctx* ctx, const lsmc_request* req,
+                           size_t* bytes);
+
+/* ---- synchronous pricing ----------------------------------------------- */
+/* One contract: price + the Greeks of bumps->greek_mask (Sec. 2.2). */
+int lsmc_price_greeks(lsmc_ctx* ctx, const lsmc_heston* model,
+                      const lsmc_contract* contract, uint32_t n_paths,
+                      uint32_t n_steps, int32_t basis, const lsmc_bumps* bumps,
+                      uint64_t seed, lsmc_result* out);
+/* All strikes of one request; outs: host, req->n_strikes results. */
+int lsmc_price_request(lsmc_ctx* ctx, const lsmc_request* req,
+                       lsmc_result* outs);
+/* A book of requests in one forward and one backward launch (CUDA-graph
+ * replayed); outs: host, sum of n_strikes results in request order. */
+int lsmc_price_book(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
+                    lsmc_result* outs);
+
+/* ---- plans: build once, launch many times ------------------------------ */
+/* Validates and expands the requests (scenarios, path groups, job tables),
+ * uploads the tables and reserves the device memory. */
+int lsmc_plan_create(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
+                     lsmc_plan** out);
+/* Enqueues the whole path (forward, backward, Greeks) on the context stream;
+ * with use_graph != 0 the sequence is captured once and replayed. */
+int lsmc_plan_launch(lsmc_plan* plan, int32_t use_graph);
+/* Waits for the last launch and copies its results to outs (host). */
+int lsmc_plan_fetch(lsmc_plan* plan, lsmc_result* outs);
+/* Device address of the launch's results (lsmc_result array). */
+int lsmc_plan_device_results(lsmc_plan* plan, void** device_ptr, size_t* count);
+/* Counters of the plan: kernels per launch, generated and LSMC path-steps,
+ * jobs of the backward pass, device bytes held. */
+typedef struct lsmc_plan_info {
+  uint64_t generated_path_steps, lsmc_path_steps, backward_jobs, device_bytes;
+  uint32_t kernels_per_launch, n_results, n_instances, n_groups;
+  uint64_t itm_path_steps; /* in-the-money regression path-steps, set by fetch */
+  uint64_t h2d_bytes;      /* table bytes uploaded by lsmc_plan_create */
+  uint64_t d2h_bytes;      /* bytes read back by each lsmc_plan_fetch */
+} lsmc_plan_info;
+int lsmc_plan_get_info(const lsmc_plan* plan, lsmc_plan_info* info);
+/* Per-kernel timing of later launches (CUDA events on the plan's stream,
+ * recorded between its kernels; no effect on results).  enable = 0 stops. */
+int lsmc_plan_set_timing(lsmc_plan* plan, int32_t enable);
+/* Device milliseconds summed over the launches since the previous call:
+ * ms[0] setup, ms[1] forward (paths), ms[2] backward (LSMC), ms[3] Greeks;
+ * *launches = number of launches summed.  Waits for the last launch. */
+int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
+/* Destroy every plan before the context it was created on. */
+void lsmc_plan_destroy(lsmc_plan* plan);
+
+/* ---- serving: continuous batching -------------------------------------- */
+/* Queues a copy of *req; returns a ticket.  Requests are admitted to the
+ * device while slots (config.max_inflight) and workspace bytes
+ * (config.hbm_budget) allow, each on its own stream, so their kernels
+ * overlap with those already running.  LSMC_EBUSY when the queue is full. */
+int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket);
+/* LSMC_PENDING while in flight; LSMC_OK with outs filled (n_strikes results)
+ * once done (the ticket is then released); a negative code on failure. */
+int lsmc_poll(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs);
+/* Blocks up to timeout_s (< 0: no limit) for the ticket, then as lsmc_poll. */
+int lsmc_wait(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs,
+              double timeout_s);
+/* Per-ticket timing (seconds, host steady clock): submit -> admit -> done. */
+int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
+                      double* admit_s, double* done_s);
+
+/* ---- stage entry points (device pointers; for parity tests) ------------- */
+/* Philox4x32-10 of n counters: d_ctr n x 4 uint32 (device), key = (key_lo,
+ * key_hi); d_out n x 4 uint32 (device).  (Random inputs of Sec. 2.2.1.) */
+int lsmc_philox(const uint32_t* d_ctr, uint32_t key_lo, uint32_t key_hi,
+                uint32_t* d_out, size_t n, void* cuda_stream);
+/* Random inputs of n (path, step) pairs under (seed, stream_id): d_out is
+ * n x 3 (U_V, Z_V, Z_X) as double (LSMC_FP64: 52-bit grid) or float
+ * (LSMC_MIXED: 23-bit grid). */
+int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
+               const uint32_t* d_step, size_t n, int32_t precision,
+               void* d_out, void* cuda_stream);
+/* Heston paths (Sec. 2.2.1: variance, log price, exponential):
+ * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double or
+ * float by precision; row 0 holds S0 and v0.  V holds max(v, 0) under
+ * FT_EULER. */
+int lsmc_paths(const lsmc_heston* model, double T, int32_t scheme,
+               int32_t precision, uint32_t n_paths, uint32_t n_steps,
+               uint64_t seed, uint32_t stream_id, void* d_S, void* d_V,
+               void* cuda_stream);
+/* Longstaff-Schwartz backward pass over given paths (same layout as
+ * lsmc_paths output).  d_out (device, 4 doubles): price, price_se,
+ * european_price, continuation value.  d_beta (device, optional):
+ * n_steps x 6 doubles, row n = coefficients at date n (NaN if none).
+ * d_n_singular (device, optional): 1 uint32. */
+int lsmc_backward(const void* d_S, const void* d_V, uint32_t n_paths,
+                  uint32_t n_steps, int32_t precision, const lsmc_heston* model,
+                  const lsmc_contract* contract, int32_t basis, double* d_out,
+                  double* d_beta, uint32_t* d_n_singular, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

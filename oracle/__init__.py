@@ -91,6 +91,9 @@ def lib():
         L.orc_paths.argtypes = [ctypes.POINTER(Heston), ctypes.c_double, ctypes.c_int,
                                 ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                 ctypes.c_uint64, ctypes.c_uint32, dp, dp, ctypes.c_int]
+        L.orc_path_one.argtypes = [ctypes.POINTER(Heston), ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
+                                   ctypes.c_uint64, ctypes.c_uint32, dp, dp]
         L.orc_lsmc.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
             [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + \
             [dp, u32p, dp, ctypes.POINTER(ctypes.c_uint8)]
@@ -182,6 +185,17 @@ def paths(model: Heston, T, scheme, P, N, seed, stream=0, grid=GRID_F64,
                          n_threads or default_threads())
     if rc != 0:
         raise ValueError("orc_paths rejected its arguments (%d)" % rc)
+    return S, V
+
+
+def path_one(model: Heston, T, scheme, path, N, seed, stream=0, grid=GRID_F64):
+    """S, V of one path (index `path`), each of length N + 1."""
+    S = np.empty(N + 1, dtype=np.float64)
+    V = np.empty(N + 1, dtype=np.float64)
+    rc = lib().orc_path_one(ctypes.byref(model), T, scheme, grid, path, N, seed, stream,
+                            _ptr(S, ctypes.c_double), _ptr(V, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("orc_path_one rejected its arguments (%d)" % rc)
     return S, V
 
 

@@ -264,6 +264,36 @@ static void orc_paths_chunk(void* vctx, uint32_t chunk) {
   }
 }
 
+int orc_path_one(const orc_heston* m, double T, int scheme, int grid,
+                 uint32_t path, uint32_t N, uint64_t seed, uint32_t stream,
+                 double* S, double* V) {
+  if (!m || !S || !V || N == 0) return -1;
+  if (!orc_model_ok(m, T, scheme)) return -1;
+  if (grid != ORC_GRID_F64 && grid != ORC_GRID_F32) return -1;
+  /* the chunked forward pass restricted to one path: same arithmetic */
+  orc_paths_ctx c = {m, T / (double)N, scheme, grid, 1u, N, stream, seed, S, V};
+  double x = 0.0, v = m->v0;
+  S[0] = m->S0;
+  V[0] = m->v0;
+  for (uint32_t n = 0; n < N; ++n) {
+    double d[3];
+    orc_draws(seed, stream, path, n, grid, d);
+    if (scheme == ORC_QE) {
+      double o[2];
+      orc_qe_step(m, c.dt, x, v, d[0], d[1], d[2], o);
+      x = o[0]; v = o[1];
+      V[n + 1] = v;
+    } else {
+      double o[3];
+      orc_ft_step(m, c.dt, x, v, d[1], d[2], o);
+      x = o[0]; v = o[1];
+      V[n + 1] = o[2];
+    }
+    S[n + 1] = m->S0 * exp(x);
+  }
+  return 0;
+}
+
 int orc_paths(const orc_heston* m, double T, int scheme, int grid,
               uint32_t P, uint32_t N, uint64_t seed, uint32_t stream,
               double* S, double* V, int n_threads) {

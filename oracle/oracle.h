@@ -97,6 +97,11 @@ int orc_paths(const orc_heston* m, double T, int scheme, int grid,
               uint32_t P, uint32_t N, uint64_t seed, uint32_t stream,
               double* S, double* V, int n_threads);
 
+/* One path (index `path`) of orc_paths: S[n], V[n] for n = 0..N. */
+int orc_path_one(const orc_heston* m, double T, int scheme, int grid,
+                 uint32_t path, uint32_t N, uint64_t seed, uint32_t stream,
+                 double* S, double* V);
+
 /* Longstaff-Schwartz backward induction over given paths.
  * out = {price, price_se, european_price, continuation}.
  * beta (optional): N*6 doubles, row n holds the step-n coefficients (NaN if

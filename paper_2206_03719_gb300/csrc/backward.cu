@@ -1,0 +1,561 @@
+// backward.cu -- Longstaff-Schwartz backward induction, estimator and Greeks.
+//
+// The paper's Longstaff-Schwartz stage is a reduction followed by a
+// quadratic curve fit per exercise date (Sec. 2.2.1); here the fit is a
+// least-squares regression of the discounted cash flow on a scaled basis over
+// the in-the-money paths, solved from its normal equations.
+//
+// Work decomposition.  A regression instance (scenario x strike) has one job
+// per (exercise date, path tile).  Jobs are numbered round-major (round r =
+// the r-th date counted back from maturity) and CTAs of a persistent grid take
+// them from one atomic counter, so no co-residency is assumed: a job only
+// waits for the previous round of its own instance, whose jobs all carry
+// smaller numbers and were taken by CTAs that are already running.
+//
+// A job (date n, tile t) of instance i:
+//   1. applies the exercise rule of date n+1 (coefficients published by the
+//      previous round) to the tile's cash flows, or initialises them with the
+//      payoff at maturity;
+//   2. accumulates, over in-the-money paths, the 15
+//      distinct monomials x^a w^b (a + b <= 4) that make up X^T X and the six
+//      entries of X^T Y (register sums, warp shuffles, a fixed-order sum over
+//      warps: no atomics, so results do not depend on scheduling);
+//   3. writes the tile partial and arrives on the instance's counter.  The CTA
+//      that arrives last sums the tile partials in tile order, solves the
+//      normal equations by Cholesky in FP64 and publishes the coefficients.
+// Every wait is bounded in time; on expiry the kernel records an error code
+// and returns.
+#include <cstdio>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace lsmc {
+
+namespace {
+
+__device__ __forceinline__ double payoff_d(int type, double K, double S) {
+  const double h = type == kPut ? K - S : S - K;
+  return h > 0.0 ? h : 0.0;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real payoff(int type, Real K, Real S) {
+  const Real h = type == kPut ? K - S : S - K;
+  return h > (Real)0 ? h : (Real)0;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// monomial slot of x^a w^b
+__host__ __device__ constexpr int mono(int a, int b) {
+  return b == 0 ? a : b == 1 ? 5 + a : b == 2 ? 9 + a : b == 3 ? 12 + a : 14;
+}
+
+// Solve the B x B normal equations assembled from the monomial sums M and
+// right-hand sides R.  Returns false (no exercise on this date) when fewer
+// in-the-money paths than basis functions were seen, or when a Cholesky pivot
+// is not above 1e-13 times the largest diagonal entry.
+__device__ bool solve_normal_equations(int B, const double* M, const double* R,
+                                       double beta[6]) {
+  const int pa[6] = {0, 1, 2, 0, 1, 0};
+  const int pb[6] = {0, 0, 0, 1, 1, 2};
+  if (M[0] < (double)B) return false;
+  double A[6][6], L[6][6];
+  double maxdiag = 0.0;
+  for (int i = 0; i < B; ++i)
+    for (int j = 0; j < B; ++j) A[i][j] = M[mono(pa[i] + pa[j], pb[i] + pb[j])];
+  for (int i = 0; i < B; ++i) maxdiag = fmax(maxdiag, A[i][i]);
+  for (int j = 0; j < B; ++j) {
+    double d = A[j][j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 1e-13 * maxdiag)) return false;
+    L[j][j] = sqrt(d);
+    const double inv = 1.0 / L[j][j];
+    for (int i = j + 1; i < B; ++i) {
+      double s = A[i][j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s * inv;
+    }
+  }
+  double z[6];
+  for (int i = 0; i < B; ++i) {
+    double s = R[i];
+    for (int k = 0; k < i; ++k) s -= L[i][k] * z[k];
+    z[i] = s / L[i][i];
+  }
+  for (int i = B - 1; i >= 0; --i) {
+    double s = z[i];
+    for (int k = i + 1; k < B; ++k) s -= L[k][i] * beta[k];
+    beta[i] = s / L[i][i];
+  }
+  for (int i = B; i < 6; ++i) beta[i] = 0.0;
+  return true;
+}
+
+struct JobInfo {
+  unsigned long long job;
+  uint32_t inst, tile, round;
+  int32_t abort;
+};
+
+}  // namespace
+
+// Derived per-instance constants: reciprocals of the basis scales, the
+// exercise value at t_0, the S multiplier of every date (scale0 exp(n dr dt))
+// and the discount factor of every date back to t_0 (exp(-r n dt)).
+__global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst) {
+  const uint32_t i = blockIdx.x;
+  if (i >= n_inst) return;
+  BwdInstance& I = inst[i];
+  if (threadIdx.x == 0) {
+    I.disc = exp(-I.r * I.dt);
+    I.disc_T = exp(-I.r * I.T);
+    I.invK = 1.0 / I.K;
+    I.inv_theta = 1.0 / I.theta;
+    I.h0 = payoff_d(I.type, I.K, I.spot);
+  }
+  for (uint32_t n = threadIdx.x; n <= I.N; n += blockDim.x) {
+    I.scale_tab[n] = I.dr_dt == 0.0 ? I.scale0 : I.scale0 * exp((double)n * I.dr_dt);
+    I.scale_tab[I.N + 1 + n] = exp(-I.r * ((double)n * I.dt));
+  }
+}
+
+namespace {
+
+// Sum over the warp.  Double precision: plain shuffles.  Single precision:
+// the partial sums travel as unevaluated float pairs (hi + lo, Knuth's
+// two-sum at every level), so the warp total keeps about 44 bits; it is
+// returned in double.
+__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
+__device__ __forceinline__ double warp_total(float v) {
+  float hi = v, lo = 0.0f;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
+    const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
+    const float s = __fadd_rn(hi, oh);
+    const float bb = __fsub_rn(s, hi);
+    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+    e = __fadd_rn(e, __fadd_rn(lo, ol));
+    hi = __fadd_rn(s, e);
+    lo = __fsub_rn(e, __fsub_rn(hi, s));
+  }
+  return (double)hi + (double)lo;
+}
+
+}  // namespace
+
+// Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
+// current exercise time tau.  The regression target of date n, the cash flow
+// discounted to t_n, is Z exp(r n dt): the same factor for every path, so the
+// regression runs on Z and the exercise test compares h exp(-r n dt) with the
+// fitted value in the same units.  Z changes only where a path exercises.
+template <typename Real, int BASIS, int PPT>
+__global__ void __launch_bounds__(kBlock)
+backward_kernel(BwdArgs a) {
+  constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
+  constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
+  constexpr int NA = NM + NB;                         // register sums
+  constexpr int TILE = kBlock * PPT;
+  constexpr int NW = kBlock / 32;
+
+  __shared__ JobInfo s_job;
+  __shared__ double s_beta[6];
+  __shared__ int s_beta_ok;
+  __shared__ int s_last;
+  __shared__ double s_red[NW][kNSum];
+  __shared__ double s_chunk[NW][kNSum];
+  __shared__ double s_sum[kNSum];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  unsigned long long next = 0;
+  if (tid == 0) next = atomicAdd(&a.ctl->next_job, 1ull);
+
+  for (;;) {
+    if (tid == 0) {
+      JobInfo ji;
+      ji.job = next;
+      ji.abort = 0;
+      if (ld_volatile(&a.ctl->error) != 0 || next >= a.total_jobs) {
+        ji.abort = 1;
+      } else {
+        next = atomicAdd(&a.ctl->next_job, 1ull);  // prefetch the following job
+        // round: last r with round_off[r] <= job
+        uint32_t lo = 0, hi = a.n_rounds;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) / 2;
+          if (a.round_off[mid] <= ji.job) lo = mid; else hi = mid;
+        }
+        const uint32_t local = (uint32_t)(ji.job - a.round_off[lo]);
+        uint32_t klo = 0, khi = a.active[lo];
+        while (khi - klo > 1) {
+          const uint32_t mid = (klo + khi) / 2;
+          if (a.cum_tiles[mid] <= local) klo = mid; else khi = mid;
+        }
+        ji.round = lo;
+        ji.inst = klo;
+        ji.tile = local - a.cum_tiles[klo];
+      }
+      s_job = ji;
+    }
+    __syncthreads();
+    const JobInfo ji = s_job;
+    if (ji.abort) return;
+
+    const BwdInstance& I = a.inst[ji.inst];
+    BwdState* st = &a.state[ji.inst];
+    const uint32_t N = I.N, P = I.P, r = ji.round;
+    const size_t ld = I.ld;
+    const Real* E = (const Real*)I.E;
+    const Real* V = (const Real*)I.V;
+    Real* Z = (Real*)I.Y;
+    const double* stab = I.scale_tab;          // S multipliers, dates 0..N
+    const double* dtab = I.scale_tab + N + 1;  // discount to t_0, dates 0..N
+    const int type = I.type;
+    const Real K = (Real)I.K, invK = (Real)I.invK, invTh = (Real)I.inv_theta;
+    const bool european = I.style == kEuropean;
+    const bool final_job = european || r == N - 1;
+    // regression date of this round (0 for the estimator round)
+    const uint32_t n = european ? 0 : N - 1 - r;
+    const bool first = european || r == 0;  // cash flows start at the maturity payoff
+
+    // ---- 1. wait for the exercise rule of date n + 1 -----------------------
+    if (!first) {
+      if (tid == 0) {
+        int ok = 1;
+        const unsigned long long t0 = global_timer_ns();
+        unsigned spins = 0;
+        while (ld_acquire_gpu(&st->ready) < r) {
+          if (ld_volatile(&a.ctl->error) != 0) { ok = 0; break; }
+          __nanosleep(spins < 64 ? 32 : 256);
+          if (++spins > (1u << 26) || global_timer_ns() - t0 > a.timeout_ns) {
+            atomicCAS(&a.ctl->error, 0u, (uint32_t)kDevErrTimeout);
+            a.ctl->error_info = ji.inst;
+            ok = 0;
+            break;
+          }
+        }
+        if (ok) {
+          __threadfence();
+          s_beta_ok = (int)__ldcg(&st->beta_ok);
+          for (int i = 0; i < 6; ++i) s_beta[i] = __ldcg(&st->beta[i]);
+        }
+        s_last = ok ? 0 : -1;
+      }
+      __syncthreads();
+      if (s_last < 0) return;
+    }
+
+    const uint32_t p_base = ji.tile * TILE + tid;
+    Real z[PPT];
+    double euro = 0.0;
+    if (first) {
+      // the discount factor multiplies in double and the product is rounded
+      // once, so single-precision cash flows carry no shared per-date bias
+      const Real sN = (Real)stab[N];
+      const double dN = dtab[N];
+      const Real* EN = E + (size_t)(N - 1) * ld;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t p = p_base + k * kBlock;
+        z[k] = (Real)0;
+        if (p < P) {
+          z[k] = (Real)((double)payoff<Real>(type, K, sN * EN[p]) * dN);
+          euro += (double)z[k];
+          if (!final_job) Z[p] = z[k];
+        }
+      }
+    } else {
+      // exercise at date n + 1 where the discounted payoff beats the fitted
+      // continuation value
+      const int bok = s_beta_ok;
+      Real b[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) b[i] = (Real)s_beta[i];
+      const Real s1 = (Real)stab[n + 1], d1 = (Real)dtab[n + 1];
+      const double d1d = dtab[n + 1];
+      const Real* E1 = E + (size_t)n * ld;
+      const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t p = p_base + k * kBlock;
+        z[k] = (Real)0;
+        if (p < P) {
+          z[k] = ld_cg(Z + p);
+          if (bok) {
+            const Real S = s1 * E1[p];
+            const Real h = payoff<Real>(type, K, S);
+            if (h > (Real)0) {
+              const Real x = S * invK;
+              Real c = fma(fma(b[2], x, b[1]), x, b[0]);
+              if (BASIS == kBasisSV2) {
+                const Real w = V1[p] * invTh;
+                c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
+              }
+              if (h * d1 > c) {
+                const Real hz = (Real)((double)h * d1d);
+                z[k] = hz;
+                if (!final_job) Z[p] = hz;
+              }
+            }
+          }
+        }
+      }
+    }
+
+    if (final_job) {
+      // ---- estimator at t_0 -------------------------------------------------
+      double sy = 0.0, sy2 = 0.0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t p = p_base + k * kBlock;
+        if (p < P) {
+          const double zv = (double)z[k];
+          sy += zv;
+          sy2 += zv * zv;
+        }
+      }
+      sy = warp_sum(sy);
+      sy2 = warp_sum(sy2);
+      euro = warp_sum(euro);
+      if (lane == 0) {
+        s_red[warp][kSlotSumY] = sy;
+        s_red[warp][kSlotSumY2] = sy2;
+        s_red[warp][kSlotEuro] = euro;
+      }
+      __syncthreads();
+      if (tid >= kSlotEuro && tid < kNSum) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += s_red[w][tid];
+        I.partial[(size_t)ji.tile * kNSum + tid] = s;
+      }
+    } else {
+      // ---- moment sums of date n over the in-the-money paths -----------------
+      const Real s0 = (Real)stab[n];
+      const Real* E0 = E + (size_t)(n - 1) * ld;
+      const Real* V0 = BASIS == kBasisSV2 ? V + (size_t)(n - 1) * ld : nullptr;
+      Real acc[NA];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) acc[i] = (Real)0;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t p = p_base + k * kBlock;
+        if (p < P) {
+          const Real yv = z[k];
+          const Real S = s0 * E0[p];
+          const Real h = payoff<Real>(type, K, S);
+          if (h > (Real)0) {
+            const Real x = S * invK, x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
+            acc[0] += (Real)1;
+            acc[1] += x;
+            acc[2] += x2;
+            acc[3] += x3;
+            acc[4] += x4;
+            if (BASIS == kBasisSV2) {
+              const Real w = V0[p] * invTh, w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
+              const Real xw = x * w;
+              acc[mono(0, 1)] += w;
+              acc[mono(1, 1)] += xw;
+              acc[mono(2, 1)] += x2 * w;
+              acc[mono(3, 1)] += x3 * w;
+              acc[mono(0, 2)] += w2;
+              acc[mono(1, 2)] += x * w2;
+              acc[mono(2, 2)] += x2 * w2;
+              acc[mono(0, 3)] += w3;
+              acc[mono(1, 3)] += x * w3;
+              acc[mono(0, 4)] += w4;
+              acc[NM + 0] += yv;
+              acc[NM + 1] += x * yv;
+              acc[NM + 2] += x2 * yv;
+              acc[NM + 3] += w * yv;
+              acc[NM + 4] += xw * yv;
+              acc[NM + 5] += w2 * yv;
+            } else {
+              acc[NM + 0] += yv;
+              acc[NM + 1] += x * yv;
+              acc[NM + 2] += x2 * yv;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const double v = warp_total(acc[i]);
+        if (lane == 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
+      }
+      euro = warp_sum(euro);
+      if (lane == 0) s_red[warp][kSlotEuro] = euro;
+      __syncthreads();
+      if (tid < kNSum) {
+        const bool used = tid < NM || (tid >= kSlotRhs && tid < kSlotRhs + NB) || tid == kSlotEuro;
+        double s = 0.0;
+        if (used)
+          for (int w = 0; w < NW; ++w) s += s_red[w][tid];
+        I.partial[(size_t)ji.tile * kNSum + tid] = s;
+      }
+    }
+
+    // ---- arrive; the last tile of this round reduces and solves --------------
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const uint32_t old = atomicAdd(&st->arrive, 1u);
+      s_last = (old + 1 == (r + 1) * I.tiles) ? 1 : 0;
+      if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) continue;
+
+    {
+      // fixed-order sum of the tile partials: a contiguous chunk of tiles per
+      // warp, a slot per lane, then the chunks in order
+      const uint32_t tiles = I.tiles;
+      const uint32_t per = (tiles + NW - 1) / NW;
+      if (lane < kNSum) {
+        double s = 0.0;
+        const uint32_t t0 = warp * per, t1 = min(tiles, t0 + per);
+        for (uint32_t t = t0; t < t1; ++t) s += __ldcg(&I.partial[(size_t)t * kNSum + lane]);
+        s_chunk[warp][lane] = s;
+      }
+      __syncthreads();
+      if (tid < kNSum) {
+        double s = 0.0;
+        for (int w = 0; w < NW; ++w) s += s_chunk[w][tid];
+        s_sum[tid] = s;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      if (final_job) {
+        BwdResult res;
+        const double Pd = (double)P;
+        const double mean = s_sum[kSlotSumY] / Pd;
+        const double var = P > 1 ? (s_sum[kSlotSumY2] - Pd * mean * mean) / (Pd - 1.0) : 0.0;
+        const double euro_sum = first ? s_sum[kSlotEuro] : __ldcg(&st->euro_sum);
+        res.cont = mean;
+        res.se = var > 0.0 ? sqrt(var / Pd) : 0.0;
+        res.euro = euro_sum / Pd;
+        res.price = european ? mean : fmax(I.h0, mean);
+        res.itm = __ldcg(&st->itm);
+        res.singular = __ldcg(&st->singular);
+        res.done = 1;
+        a.results[I.out_index] = res;
+      } else {
+        double beta[6];
+        const bool ok = solve_normal_equations(NB, s_sum, s_sum + kSlotRhs, beta);
+        if (r == 0) st->euro_sum = s_sum[kSlotEuro];
+        st->itm = __ldcg(&st->itm) + s_sum[0];
+        if (!ok) st->singular = __ldcg(&st->singular) + 1u;
+        st->beta_ok = ok ? 1u : 0u;
+        for (int i = 0; i < 6; ++i) st->beta[i] = ok ? beta[i] : 0.0;
+        if (I.beta_hist) {
+          // coefficients in the units of the cash flow discounted to t_n
+          const double to_n = 1.0 / dtab[n];
+          for (int i = 0; i < 6; ++i)
+            I.beta_hist[(size_t)n * 6 + i] =
+                ok ? (i < NB ? beta[i] * to_n : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
+        }
+        __threadfence();
+        st_release_gpu(&st->ready, r + 1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Greeks of each (request, strike) by central differences of the scenario
+// prices (the bump layout of the request's scenario table).
+__global__ void greeks_kernel(const GreekOut* __restrict__ g,
+                              const BwdResult* __restrict__ res, uint32_t n_out,
+                              DevResult* __restrict__ out) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_out) return;
+  const GreekOut G = g[i];
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  auto V = [&](int kind) { return res[G.res[kind]].price; };
+  DevResult o;
+  const BwdResult base = res[G.res[kScBase]];
+  o.price = base.price;
+  o.price_se = base.se;
+  o.european_price = base.euro;
+  o.delta = o.gamma = o.vega = o.rho = o.theta = nan;
+  if ((G.mask & 1u) && G.res[kScSUp] >= 0)
+    o.delta = (V(kScSUp) - V(kScSDn)) / (2.0 * G.hS * G.S0);
+  if (G.mask & 2u) {
+    if (G.res[kScSgUp] >= 0) {
+      const double h = G.hG * G.S0;
+      o.gamma = (V(kScSgUp) - 2.0 * V(kScBase) + V(kScSgDn)) / (h * h);
+    } else if (G.res[kScSUp] >= 0) {
+      const double h = G.hS * G.S0;
+      o.gamma = (V(kScSUp) - 2.0 * V(kScBase) + V(kScSDn)) / (h * h);
+    }
+  }
+  if ((G.mask & 4u) && G.res[kScVUp] >= 0)
+    o.vega = (V(kScVUp) - V(kScVDn)) / (2.0 * G.hV * G.v0);
+  if ((G.mask & 8u) && G.res[kScRUp] >= 0)
+    o.rho = (V(kScRUp) - V(kScRDn)) / (2.0 * G.dR);
+  if ((G.mask & 16u) && G.res[kScTDn] >= 0)
+    o.theta = (V(kScTDn) - V(kScTUp)) / (2.0 * G.dT);
+  uint32_t sing = 0, nrev = 0;
+  for (int k = 0; k < kScCount; ++k)
+    if (G.res[k] >= 0) { sing += res[G.res[k]].singular; ++nrev; }
+  o.n_singular_solves = sing;
+  o.n_revaluations = nrev;
+  o.status = sing ? 1 : 0;
+  o.reserved = 0;
+  out[i] = o;
+}
+
+cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s) {
+  if (n_inst == 0) return cudaSuccess;
+  setup_kernel<<<n_inst, 128, 0, s>>>(inst, n_inst);
+  return cudaGetLastError();
+}
+
+template <typename Real, int BASIS, int PPT>
+static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t s) {
+  backward_kernel<Real, BASIS, PPT><<<grid, kBlock, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int backward_tile(bool fp64) { return kBlock * (fp64 ? 4 : 8); }
+
+cudaError_t launch_backward(const BwdArgs& a, bool fp64, int basis, int grid,
+                            cudaStream_t s) {
+  if (a.total_jobs == 0) return cudaSuccess;
+  if (fp64)
+    return basis == kBasisSV2 ? launch_bwd_t<double, kBasisSV2, 4>(a, grid, s)
+                              : launch_bwd_t<double, kBasisS2, 4>(a, grid, s);
+  return basis == kBasisSV2 ? launch_bwd_t<float, kBasisSV2, 8>(a, grid, s)
+                            : launch_bwd_t<float, kBasisS2, 8>(a, grid, s);
+}
+
+int backward_occupancy(bool fp64, int basis) {
+  int n = 0;
+  cudaError_t e;
+  if (fp64)
+    e = basis == kBasisSV2
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<double, kBasisSV2, 4>, kBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<double, kBasisS2, 4>, kBlock, 0);
+  else
+    e = basis == kBasisSV2
+            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<float, kBasisSV2, 8>, kBlock, 0)
+            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<float, kBasisS2, 8>, kBlock, 0);
+  return e == cudaSuccess ? n : 1;
+}
+
+cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
+                          DevResult* out, cudaStream_t s) {
+  if (n_out == 0) return cudaSuccess;
+  greeks_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(g, res, n_out, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lsmc

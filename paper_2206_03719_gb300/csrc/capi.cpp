@@ -1,0 +1,862 @@
+// capi.cpp -- the extern "C" boundary: contexts, plans, synchronous pricing,
+// stage entry points and the continuous-batching request loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "../../include/lsmc.h"
+#include "kernels.h"
+#include "plan.h"
+#include "planner.h"
+
+using namespace lsmc;
+
+static_assert(sizeof(DevResult) == sizeof(lsmc_result), "result layout");
+static_assert(offsetof(DevResult, status) == offsetof(lsmc_result, status), "result layout");
+
+namespace {
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct Ticket;
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  Ticket* t = nullptr;
+};
+
+}  // namespace
+
+struct lsmc_ctx {
+  int device = 0;
+  int precision = LSMC_FP64, scheme = LSMC_SCHEME_QE;
+  cudaStream_t own_stream = nullptr, stream = nullptr;
+  Arena arena;
+  bool user_workspace = false;
+  void* own_arena_mem = nullptr;
+  size_t hbm_budget = 0;
+  uint32_t max_inflight = 8, queue_capacity = 4096;
+  int num_sms = 0;
+  int occ[2][2] = {{0, 0}, {0, 0}};
+  // serving
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::thread sched;
+  bool stop = false, sched_started = false;
+  std::deque<Ticket*> pending;
+  std::map<uint64_t, Ticket*> tickets;
+  uint64_t next_ticket = 1;
+  std::vector<Slot> slots;
+  double t0 = 0;
+};
+
+struct lsmc_plan {
+  lsmc_ctx* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  PlanLayout L;
+  char* dev = nullptr;
+  int alloc_kind = 0;  // 0 cudaMalloc, 1 arena, 2 cudaMallocAsync
+  bool run_forward = true, run_backward = true, run_greeks = true;
+  FwdArgs fa{};
+  BwdArgs ba{};
+  BwdInstance* d_inst = nullptr;
+  GreekOut* d_greeks = nullptr;
+  BwdResult* d_results = nullptr;
+  DevResult* d_out = nullptr;
+  void* d_state = nullptr;
+  size_t state_bytes = 0;
+  Control* d_ctl = nullptr;
+  int bwd_grid = 1;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<DevResult> h_out;
+  std::vector<BwdResult> h_res;
+  uint64_t itm = 0;
+  // per-kernel timing: one set of 5 events per launch since the last read
+  bool timing = false;
+  std::vector<std::array<cudaEvent_t, 5>> ev;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+struct Ticket {
+  uint64_t id = 0;
+  lsmc_request req{};
+  std::vector<double> strikes;
+  int status = LSMC_PENDING;
+  std::vector<lsmc_result> results;
+  double t_submit = 0, t_admit = 0, t_done = 0;
+  lsmc_plan* plan = nullptr;
+  size_t footprint = 0;
+  int slot = -1;
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return LSMC_OK;
+  if (e == cudaErrorMemoryAllocation) return LSMC_ENOMEM;
+  return LSMC_ECUDA;
+}
+
+#define LSMC_CUDA(call)                          \
+  do {                                           \
+    cudaError_t e__ = (call);                    \
+    if (e__ != cudaSuccess) return cuda_status(e__); \
+  } while (0)
+
+int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? dflt : dflt) : v; }
+
+int occupancy(lsmc_ctx* ctx, bool fp64, int basis) {
+  if (ctx) {
+    int& o = ctx->occ[fp64 ? 1 : 0][basis];
+    if (o == 0) o = std::max(1, backward_occupancy(fp64, basis));
+    return o;
+  }
+  return std::max(1, backward_occupancy(fp64, basis));
+}
+
+int sm_count(lsmc_ctx* ctx) {
+  if (ctx && ctx->num_sms) return ctx->num_sms;
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (ctx) ctx->num_sms = n;
+  return n > 0 ? n : 1;
+}
+
+// Device layout of a plan: tables | state + control | results | out |
+// scale tables | partials | Y | paths.
+int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hist) {
+  PlanLayout& L = p->L;
+  const bool fp64 = L.opt.precision == LSMC_FP64;
+  const size_t real = fp64 ? 8 : 4;
+  char* base = p->dev;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* q = base + off; off += align256(bytes); return q; };
+  // tables (host blob mirrors this layout)
+  std::vector<char> blob(L.bytes_tables, 0);
+  size_t boff = 0;
+  auto put = [&](const void* src, size_t bytes) -> char* {
+    char* dst = base + boff;
+    if (bytes) std::memcpy(blob.data() + boff, src, bytes);
+    boff += align256(bytes);
+    return dst;
+  };
+  char* paths = base + L.bytes_tables + L.bytes_state + L.bytes_results + L.bytes_out +
+                L.bytes_scale + L.bytes_partial + L.bytes_y;
+  char* yreg = paths - L.bytes_y;
+  char* preg = yreg - L.bytes_partial;
+  char* sreg = preg - L.bytes_scale;
+  // bind group rows
+  for (size_t g = 0; g < L.groups.size(); ++g) {
+    FwdGroup& G = L.groups[g];
+    if (ext_S) {
+      G.E = (char*)ext_S + (size_t)G.ld * real;  // row 1 (ld == P here)
+      G.E_row0 = ext_S;
+      G.V = ext_V ? (char*)ext_V + (size_t)G.ld * real : nullptr;
+      G.V_row0 = ext_V;
+    } else {
+      G.E = paths + L.group_E_off[g];
+      G.V = L.group_V_off[g] == SIZE_MAX ? nullptr : paths + L.group_V_off[g];
+      G.E_row0 = G.V_row0 = nullptr;
+    }
+  }
+  for (size_t i = 0; i < L.inst.size(); ++i) {
+    BwdInstance& I = L.inst[i];
+    const PlanLayout::InstOff& o = L.inst_off[i];
+    const FwdGroup& G = L.groups[o.group];
+    I.E = G.E;
+    I.V = G.V;
+    I.ld = G.ld;
+    I.Y = yreg + o.y;
+    I.partial = (double*)(preg + o.partial);
+    I.scale_tab = (double*)(sreg + o.scale);
+    I.beta_hist = beta_hist;
+  }
+  const FwdContract* dC = (const FwdContract*)put(L.contracts.data(), sizeof(FwdContract) * L.contracts.size());
+  const FwdGroup* dG = (const FwdGroup*)put(L.groups.data(), sizeof(FwdGroup) * L.groups.size());
+  p->d_inst = (BwdInstance*)put(L.inst.data(), sizeof(BwdInstance) * L.inst.size());
+  const unsigned long long* dR = (const unsigned long long*)put(L.round_off.data(), sizeof(unsigned long long) * L.round_off.size());
+  const uint32_t* dT = (const uint32_t*)put(L.cum_tiles.data(), sizeof(uint32_t) * L.cum_tiles.size());
+  uint32_t zero = 0;
+  const uint32_t* dA = (const uint32_t*)(L.active.empty() ? put(&zero, 4) : put(L.active.data(), sizeof(uint32_t) * L.active.size()));
+  p->d_greeks = (GreekOut*)put(L.greeks.data(), sizeof(GreekOut) * L.greeks.size());
+  off = L.bytes_tables;
+  p->d_state = take(L.bytes_state);
+  p->state_bytes = L.bytes_state;
+  p->d_ctl = (Control*)((char*)p->d_state + sizeof(BwdState) * L.inst.size());
+  p->d_results = (BwdResult*)take(L.bytes_results);
+  p->d_out = (DevResult*)take(L.bytes_out);
+  LSMC_CUDA(cudaMemcpyAsync(base, blob.data(), blob.size(), cudaMemcpyHostToDevice, p->stream));
+
+  p->fa.contracts = dC;
+  p->fa.groups = dG;
+  p->fa.n_contracts = (uint32_t)L.contracts.size();
+  p->fa.n_blocks = L.fwd_blocks;
+  p->ba.inst = p->d_inst;
+  p->ba.state = (BwdState*)p->d_state;
+  p->ba.results = p->d_results;
+  p->ba.round_off = dR;
+  p->ba.cum_tiles = dT;
+  p->ba.active = dA;
+  p->ba.ctl = p->d_ctl;
+  p->ba.total_jobs = L.total_jobs;
+  p->ba.timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
+  p->ba.n_rounds = (uint32_t)L.active.size();
+  p->ba.n_inst = (uint32_t)L.inst.size();
+  const int occ = occupancy(p->ctx, fp64, L.opt.basis);
+  const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
+  p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
+  p->h_out.resize(L.greeks.size());
+  p->h_res.resize(L.n_results);
+  return LSMC_OK;
+}
+
+int plan_alloc(lsmc_plan* p, bool use_arena, bool stream_ordered) {
+  const size_t bytes = std::max<size_t>(p->L.total_bytes, 256);
+  if (use_arena && p->ctx && p->ctx->arena.active()) {
+    p->dev = (char*)p->ctx->arena.alloc(bytes);
+    if (!p->dev) return LSMC_ENOMEM;
+    p->alloc_kind = 1;
+    return LSMC_OK;
+  }
+  if (stream_ordered) {
+    LSMC_CUDA(cudaMallocAsync((void**)&p->dev, bytes, p->stream));
+    p->alloc_kind = 2;
+    return LSMC_OK;
+  }
+  LSMC_CUDA(cudaMalloc((void**)&p->dev, bytes));
+  p->alloc_kind = 0;
+  return LSMC_OK;
+}
+
+void plan_free(lsmc_plan* p) {
+  if (!p) return;
+  for (auto& e : p->ev)
+    for (auto x : e) cudaEventDestroy(x);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->dev) {
+    if (p->alloc_kind == 1) {
+      cudaStreamSynchronize(p->stream);
+      p->ctx->arena.free(p->dev);
+    } else if (p->alloc_kind == 2) {
+      cudaFreeAsync(p->dev, p->stream);
+    } else {
+      cudaStreamSynchronize(p->stream);
+      cudaFree(p->dev);
+    }
+  }
+  delete p;
+}
+
+// requests of one plan share precision, scheme and basis
+int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions* o) {
+  if (!reqs || n == 0) return LSMC_EINVAL;
+  const int dprec = ctx ? ctx->precision : LSMC_FP64;
+  const int dsch = ctx ? ctx->scheme : LSMC_SCHEME_QE;
+  o->precision = resolve(ctx, reqs[0].precision, dprec);
+  o->scheme = resolve(ctx, reqs[0].scheme, dsch);
+  o->basis = reqs[0].basis;
+  for (size_t i = 0; i < n; ++i) {
+    const int prec = resolve(ctx, reqs[i].precision, dprec);
+    const int sch = resolve(ctx, reqs[i].scheme, dsch);
+    int rc = validate_request(reqs[i], prec, sch);
+    if (rc) return rc;
+    if (prec != o->precision || sch != o->scheme || reqs[i].basis != o->basis)
+      return LSMC_ENOTIMPL;
+  }
+  return LSMC_OK;
+}
+
+int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
+                   cudaStream_t stream, bool use_arena, lsmc_plan** out) {
+  PlanOptions o;
+  int rc = plan_options(ctx, reqs, n, &o);
+  if (rc) return rc;
+  std::unique_ptr<lsmc_plan> p(new (std::nothrow) lsmc_plan());
+  if (!p) return LSMC_ENOMEM;
+  p->ctx = ctx;
+  p->stream = stream;
+  rc = build_layout(reqs, n, o, &p->L);
+  if (rc) return rc;
+  rc = plan_alloc(p.get(), use_arena, false);
+  if (rc) return rc;
+  rc = plan_bind_and_upload(p.get(), nullptr, nullptr, nullptr);
+  if (rc) { plan_free(p.release()); return rc; }
+  *out = p.release();
+  return LSMC_OK;
+}
+
+int plan_enqueue(lsmc_plan* p, bool timed = false) {
+  const bool fp64 = p->L.opt.precision == LSMC_FP64;
+  cudaEvent_t* ev = nullptr;
+  if (timed) {
+    if (p->ev_used == p->ev.size()) {
+      std::array<cudaEvent_t, 5> e{};
+      for (auto& x : e) LSMC_CUDA(cudaEventCreate(&x));
+      p->ev.push_back(e);
+    }
+    ev = p->ev[p->ev_used++].data();
+  }
+  auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], p->stream) : cudaSuccess; };
+  LSMC_CUDA(cudaMemsetAsync(p->d_state, 0, p->state_bytes, p->stream));
+  LSMC_CUDA(mark(0));
+  if (p->run_backward) LSMC_CUDA(launch_setup(p->d_inst, (uint32_t)p->L.inst.size(), p->stream));
+  LSMC_CUDA(mark(1));
+  if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, fp64, p->L.opt.scheme, p->stream));
+  LSMC_CUDA(mark(2));
+  if (p->run_backward) LSMC_CUDA(launch_backward(p->ba, fp64, p->L.opt.basis, p->bwd_grid, p->stream));
+  LSMC_CUDA(mark(3));
+  if (p->run_greeks)
+    LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out, p->stream));
+  LSMC_CUDA(mark(4));
+  return LSMC_OK;
+}
+
+int plan_launch(lsmc_plan* p, bool use_graph) {
+  if (!use_graph || p->timing) return plan_enqueue(p, p->timing);
+  if (!p->exec) {
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeThreadLocal;
+    LSMC_CUDA(cudaStreamBeginCapture(p->stream, mode));
+    int rc = plan_enqueue(p);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(p->stream, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    LSMC_CUDA(e);
+    p->graph = g;
+    LSMC_CUDA(cudaGraphInstantiate(&p->exec, g, 0));
+  }
+  LSMC_CUDA(cudaGraphLaunch(p->exec, p->stream));
+  return LSMC_OK;
+}
+
+int plan_collect(lsmc_plan* p, lsmc_result* outs) {
+  Control ctl{};
+  LSMC_CUDA(cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, p->stream));
+  if (!p->h_res.empty())
+    LSMC_CUDA(cudaMemcpyAsync(p->h_res.data(), p->d_results, sizeof(BwdResult) * p->h_res.size(),
+                              cudaMemcpyDeviceToHost, p->stream));
+  if (!p->h_out.empty())
+    LSMC_CUDA(cudaMemcpyAsync(p->h_out.data(), p->d_out, sizeof(DevResult) * p->h_out.size(),
+                              cudaMemcpyDeviceToHost, p->stream));
+  LSMC_CUDA(cudaStreamSynchronize(p->stream));
+  if (ctl.error == kDevErrTimeout) return LSMC_ETIMEOUT;
+  if (ctl.error) return LSMC_ECUDA;
+  double itm = 0;
+  for (const auto& r : p->h_res) {
+    if (p->run_backward && !r.done) return LSMC_ECUDA;
+    itm += r.itm;
+  }
+  p->itm = (uint64_t)itm;
+  if (outs) std::memcpy(outs, p->h_out.data(), sizeof(DevResult) * p->h_out.size());
+  return LSMC_OK;
+}
+
+// ---- serving ---------------------------------------------------------------------
+void finish_ticket(lsmc_ctx* ctx, Ticket* t, int status) {
+  t->status = status;
+  t->t_done = now_s() - ctx->t0;
+  if (t->plan) { plan_free(t->plan); t->plan = nullptr; }
+  ctx->done_cv.notify_all();
+}
+
+void scheduler_loop(lsmc_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  while (!ctx->stop) {
+    bool progress = false;
+    // completions
+    for (size_t s = 0; s < ctx->slots.size(); ++s) {
+      Slot& sl = ctx->slots[s];
+      if (!sl.t) continue;
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      Ticket* t = sl.t;
+      sl.t = nullptr;
+      int rc = q == cudaSuccess ? LSMC_OK : LSMC_ECUDA;
+      if (rc == LSMC_OK) {
+        t->results.resize(t->plan->h_out.size());
+        rc = plan_collect(t->plan, t->results.data());
+      }
+      finish_ticket(ctx, t, rc);
+      progress = true;
+    }
+    // admissions (first come, first served)
+    while (!ctx->pending.empty()) {
+      int free_slot = -1;
+      for (size_t s = 0; s < ctx->slots.size(); ++s)
+        if (!ctx->slots[s].t) { free_slot = (int)s; break; }
+      if (free_slot < 0) break;
+      Ticket* t = ctx->pending.front();
+      if (ctx->arena.largest_free() < t->footprint) break;  // wait for memory
+      ctx->pending.pop_front();
+      Slot& sl = ctx->slots[free_slot];
+      lsmc_plan* p = nullptr;
+      int rc = plan_create_on(ctx, &t->req, 1, sl.stream, true, &p);
+      if (rc == LSMC_ENOMEM) {  // fragmentation: retry once others finish
+        ctx->pending.push_front(t);
+        break;
+      }
+      t->t_admit = now_s() - ctx->t0;
+      if (rc == LSMC_OK) rc = plan_launch(p, false);
+      if (rc == LSMC_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = LSMC_ECUDA;
+      t->plan = p;
+      if (rc != LSMC_OK) {
+        finish_ticket(ctx, t, rc);
+      } else {
+        sl.t = t;
+        t->slot = free_slot;
+      }
+      progress = true;
+    }
+    bool inflight = false;
+    for (const auto& sl : ctx->slots) inflight |= sl.t != nullptr;
+    if (!inflight && ctx->pending.empty()) {
+      ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
+    } else if (!progress) {
+      ctx->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+  }
+}
+
+int start_scheduler(lsmc_ctx* ctx) {
+  if (ctx->sched_started) return LSMC_OK;
+  if (!ctx->arena.active()) {
+    size_t budget = ctx->hbm_budget;
+    if (budget == 0) {
+      size_t fr = 0, tot = 0;
+      LSMC_CUDA(cudaMemGetInfo(&fr, &tot));
+      budget = std::min<size_t>(fr / 4 * 3, (size_t)64 << 30);
+    }
+    LSMC_CUDA(cudaMalloc(&ctx->own_arena_mem, budget));
+    ctx->arena.reset(ctx->own_arena_mem, budget);
+  }
+  ctx->slots.resize(ctx->max_inflight);
+  for (auto& s : ctx->slots) {
+    LSMC_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    LSMC_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+  }
+  ctx->sched = std::thread(scheduler_loop, ctx);
+  ctx->sched_started = true;
+  return LSMC_OK;
+}
+
+lsmc_request default_request(const lsmc_heston* m, const lsmc_contract* c, uint32_t P,
+                             uint32_t N, int32_t basis, const lsmc_bumps* b, uint64_t seed) {
+  lsmc_request q{};
+  q.model = *m;
+  q.type = c->type;
+  q.style = c->style;
+  q.T = c->T;
+  q.strikes = &c->K;
+  q.n_strikes = 1;
+  q.n_paths = P;
+  q.n_steps = N;
+  q.basis = basis;
+  q.precision = -1;
+  q.scheme = -1;
+  if (b) q.bumps = *b;
+  q.seed = seed;
+  q.stream_id = 0;
+  return q;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lsmc_strerror(int s) {
+  switch (s) {
+    case LSMC_OK: return "ok";
+    case LSMC_PENDING: return "pending";
+    case LSMC_EINVAL: return "invalid argument";
+    case LSMC_ENOMEM: return "out of device or workspace memory";
+    case LSMC_EBUSY: return "request queue full";
+    case LSMC_ETIMEOUT: return "bounded device wait expired";
+    case LSMC_ECUDA: return "CUDA runtime error";
+    case LSMC_ENOTIMPL: return "not supported";
+    case LSMC_ENOTFOUND: return "unknown ticket";
+    case LSMC_ENODEV: return "no usable CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int lsmc_abi_version(void) { return LSMC_ABI_VERSION; }
+
+int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
+  if (!out) return LSMC_EINVAL;
+  *out = nullptr;
+  lsmc_config c{};
+  if (cfg) c = *cfg;
+  if (c.precision != LSMC_FP64 && c.precision != LSMC_MIXED) return LSMC_EINVAL;
+  if (c.scheme != LSMC_SCHEME_QE && c.scheme != LSMC_SCHEME_FT_EULER) return LSMC_EINVAL;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return LSMC_ENODEV;
+  if (c.device < 0 || c.device >= ndev) return LSMC_EINVAL;
+  LSMC_CUDA(cudaSetDevice(c.device));
+  lsmc_ctx* ctx = new (std::nothrow) lsmc_ctx();
+  if (!ctx) return LSMC_ENOMEM;
+  ctx->device = c.device;
+  ctx->precision = c.precision;
+  ctx->scheme = c.scheme;
+  ctx->hbm_budget = (size_t)c.hbm_budget;
+  ctx->max_inflight = c.max_inflight ? c.max_inflight : 8;
+  ctx->queue_capacity = c.queue_capacity ? c.queue_capacity : 4096;
+  ctx->t0 = now_s();
+  if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete ctx;
+    return LSMC_ECUDA;
+  }
+  ctx->stream = ctx->own_stream;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+  *out = ctx;
+  return LSMC_OK;
+}
+
+void lsmc_destroy(lsmc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  {
+    std::unique_lock<std::mutex> lk(ctx->mu);
+    ctx->stop = true;
+  }
+  ctx->cv.notify_all();
+  if (ctx->sched.joinable()) ctx->sched.join();
+  for (auto& s : ctx->slots) {
+    if (s.stream) cudaStreamSynchronize(s.stream);
+    if (s.t) { if (s.t->plan) plan_free(s.t->plan); s.t->plan = nullptr; }
+  }
+  for (auto& kv : ctx->tickets) {
+    if (kv.second->plan) plan_free(kv.second->plan);
+    delete kv.second;
+  }
+  for (auto& s : ctx->slots) {
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.stream) cudaStreamDestroy(s.stream);
+  }
+  if (ctx->own_stream) {
+    cudaStreamSynchronize(ctx->own_stream);
+    cudaStreamDestroy(ctx->own_stream);
+  }
+  if (ctx->own_arena_mem) cudaFree(ctx->own_arena_mem);
+  delete ctx;
+}
+
+int lsmc_set_stream(lsmc_ctx* ctx, void* s) {
+  if (!ctx) return LSMC_EINVAL;
+  ctx->stream = s ? (cudaStream_t)s : ctx->own_stream;
+  return LSMC_OK;
+}
+
+int lsmc_set_workspace(lsmc_ctx* ctx, void* ptr, size_t bytes) {
+  if (!ctx || !ptr || bytes < 4096 || ((uintptr_t)ptr & 255)) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->arena.active() && ctx->arena.used()) return LSMC_EBUSY;
+  if (ctx->own_arena_mem) return LSMC_EBUSY;
+  ctx->arena.reset(ptr, bytes);
+  ctx->user_workspace = true;
+  return LSMC_OK;
+}
+
+int lsmc_request_footprint(const lsmc_ctx* ctx, const lsmc_request* req, size_t* bytes) {
+  if (!req || !bytes) return LSMC_EINVAL;
+  PlanOptions o;
+  int rc = plan_options(const_cast<lsmc_ctx*>(ctx), req, 1, &o);
+  if (rc) return rc;
+  PlanLayout L;
+  rc = build_layout(req, 1, o, &L);
+  if (rc) return rc;
+  *bytes = align256(L.total_bytes);
+  return LSMC_OK;
+}
+
+int lsmc_plan_create(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, lsmc_plan** out) {
+  if (!ctx || !out) return LSMC_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  return plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, out);
+}
+
+int lsmc_plan_launch(lsmc_plan* p, int32_t use_graph) {
+  if (!p) return LSMC_EINVAL;
+  return plan_launch(p, use_graph != 0);
+}
+
+int lsmc_plan_fetch(lsmc_plan* p, lsmc_result* outs) {
+  if (!p || !outs) return LSMC_EINVAL;
+  return plan_collect(p, outs);
+}
+
+int lsmc_plan_device_results(lsmc_plan* p, void** ptr, size_t* count) {
+  if (!p || !ptr || !count) return LSMC_EINVAL;
+  *ptr = p->d_out;
+  *count = p->L.greeks.size();
+  return LSMC_OK;
+}
+
+int lsmc_plan_get_info(const lsmc_plan* p, lsmc_plan_info* info) {
+  if (!p || !info) return LSMC_EINVAL;
+  info->generated_path_steps = p->L.generated_path_steps;
+  info->lsmc_path_steps = p->L.lsmc_path_steps;
+  info->backward_jobs = p->L.total_jobs;
+  info->device_bytes = p->L.total_bytes;
+  info->kernels_per_launch = (p->run_backward ? 2 : 0) + (p->run_forward ? 1 : 0) + (p->run_greeks ? 1 : 0);
+  info->n_results = (uint32_t)p->L.greeks.size();
+  info->n_instances = (uint32_t)p->L.inst.size();
+  info->n_groups = (uint32_t)p->L.groups.size();
+  info->itm_path_steps = p->itm;
+  info->h2d_bytes = p->L.bytes_tables;
+  info->d2h_bytes = sizeof(Control) + sizeof(BwdResult) * p->h_res.size() +
+                    sizeof(DevResult) * p->h_out.size();
+  return LSMC_OK;
+}
+
+int lsmc_plan_set_timing(lsmc_plan* p, int32_t enable) {
+  if (!p) return LSMC_EINVAL;
+  p->timing = enable != 0;
+  return LSMC_OK;
+}
+
+int lsmc_plan_kernel_times(lsmc_plan* p, double ms[4], uint32_t* launches) {
+  if (!p || !ms) return LSMC_EINVAL;
+  for (int i = 0; i < 4; ++i) ms[i] = 0.0;
+  if (p->ev_used) LSMC_CUDA(cudaEventSynchronize(p->ev[p->ev_used - 1][4]));
+  for (size_t k = 0; k < p->ev_used; ++k)
+    for (int i = 0; i < 4; ++i) {
+      float t = 0.f;
+      LSMC_CUDA(cudaEventElapsedTime(&t, p->ev[k][i], p->ev[k][i + 1]));
+      ms[i] += t;
+    }
+  if (launches) *launches = (uint32_t)p->ev_used;
+  p->ev_used = 0;
+  return LSMC_OK;
+}
+
+void lsmc_plan_destroy(lsmc_plan* p) { plan_free(p); }
+
+int lsmc_price_request(lsmc_ctx* ctx, const lsmc_request* req, lsmc_result* outs) {
+  if (!ctx || !req || !outs) return LSMC_EINVAL;
+  lsmc_plan* p = nullptr;
+  int rc = lsmc_plan_create(ctx, req, 1, &p);
+  if (rc) return rc;
+  rc = plan_launch(p, false);
+  if (rc == LSMC_OK) rc = plan_collect(p, outs);
+  plan_free(p);
+  return rc;
+}
+
+int lsmc_price_greeks(lsmc_ctx* ctx, const lsmc_heston* m, const lsmc_contract* c,
+                      uint32_t P, uint32_t N, int32_t basis, const lsmc_bumps* b,
+                      uint64_t seed, lsmc_result* out) {
+  if (!ctx || !m || !c || !b || !out) return LSMC_EINVAL;
+  lsmc_request q = default_request(m, c, P, N, basis, b, seed);
+  return lsmc_price_request(ctx, &q, out);
+}
+
+int lsmc_price_book(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, lsmc_result* outs) {
+  if (!ctx || !reqs || !n || !outs) return LSMC_EINVAL;
+  lsmc_plan* p = nullptr;
+  int rc = lsmc_plan_create(ctx, reqs, n, &p);
+  if (rc) return rc;
+  rc = plan_launch(p, true);
+  if (rc == LSMC_OK) rc = plan_collect(p, outs);
+  plan_free(p);
+  return rc;
+}
+
+// ---- serving -------------------------------------------------------------------
+int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket) {
+  if (!ctx || !req || !ticket) return LSMC_EINVAL;
+  PlanOptions o;
+  int rc = plan_options(ctx, req, 1, &o);
+  if (rc) return rc;
+  size_t fp = 0;
+  rc = lsmc_request_footprint(ctx, req, &fp);
+  if (rc) return rc;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  cudaSetDevice(ctx->device);
+  rc = start_scheduler(ctx);
+  if (rc) return rc;
+  if (fp > ctx->arena.capacity()) return LSMC_ENOMEM;
+  if (ctx->pending.size() >= ctx->queue_capacity) return LSMC_EBUSY;
+  Ticket* t = new (std::nothrow) Ticket();
+  if (!t) return LSMC_ENOMEM;
+  t->id = ctx->next_ticket++;
+  t->req = *req;
+  t->strikes.assign(req->strikes, req->strikes + req->n_strikes);
+  t->req.strikes = t->strikes.data();
+  t->footprint = fp;
+  t->t_submit = now_s() - ctx->t0;
+  ctx->tickets[t->id] = t;
+  ctx->pending.push_back(t);
+  *ticket = t->id;
+  lk.unlock();
+  ctx->cv.notify_all();
+  return LSMC_OK;
+}
+
+static int take_result(lsmc_ctx* ctx, std::map<uint64_t, Ticket*>::iterator it, lsmc_result* outs) {
+  Ticket* t = it->second;
+  const int st = t->status;
+  if (st == LSMC_OK && outs)
+    std::memcpy(outs, t->results.data(), sizeof(lsmc_result) * t->results.size());
+  ctx->tickets.erase(it);
+  delete t;
+  return st;
+}
+
+int lsmc_poll(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs) {
+  if (!ctx) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return LSMC_ENOTFOUND;
+  if (it->second->status == LSMC_PENDING) return LSMC_PENDING;
+  return take_result(ctx, it, outs);
+}
+
+int lsmc_wait(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs, double timeout_s) {
+  if (!ctx) return LSMC_EINVAL;
+  std::unique_lock<std::mutex> lk(ctx->mu);
+  auto pred = [&] {
+    auto it = ctx->tickets.find(ticket);
+    return it == ctx->tickets.end() || it->second->status != LSMC_PENDING;
+  };
+  if (timeout_s < 0) {
+    ctx->done_cv.wait(lk, pred);
+  } else {
+    ctx->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), pred);
+  }
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return LSMC_ENOTFOUND;
+  if (it->second->status == LSMC_PENDING) return LSMC_PENDING;
+  return take_result(ctx, it, outs);
+}
+
+int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* s, double* a, double* d) {
+  if (!ctx) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  auto it = ctx->tickets.find(ticket);
+  if (it == ctx->tickets.end()) return LSMC_ENOTFOUND;
+  if (s) *s = it->second->t_submit;
+  if (a) *a = it->second->t_admit;
+  if (d) *d = it->second->t_done;
+  return LSMC_OK;
+}
+
+// ---- stage entry points ------------------------------------------------------------
+int lsmc_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out, size_t n,
+                void* s) {
+  if ((!d_ctr || !d_out) && n) return LSMC_EINVAL;
+  LSMC_CUDA(launch_philox(d_ctr, k0, k1, d_out, n, (cudaStream_t)s));
+  return LSMC_OK;
+}
+
+int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path, const uint32_t* d_step,
+               size_t n, int32_t precision, void* d_out, void* s) {
+  if ((!d_path || !d_step || !d_out) && n) return LSMC_EINVAL;
+  if (precision != LSMC_FP64 && precision != LSMC_MIXED) return LSMC_EINVAL;
+  LSMC_CUDA(launch_draws(seed, stream_id, d_path, d_step, n, precision == LSMC_FP64, d_out,
+                         (cudaStream_t)s));
+  return LSMC_OK;
+}
+
+static int stage_plan(const lsmc_heston* m, double T, int32_t scheme, int32_t precision,
+                      uint32_t P, uint32_t N, int32_t basis, const lsmc_contract* c,
+                      uint64_t seed, uint32_t stream_id, cudaStream_t s, lsmc_plan** out) {
+  lsmc_contract cc{LSMC_PUT, LSMC_AMERICAN, m ? m->S0 : 1.0, T};
+  if (c) cc = *c;
+  lsmc_request q = default_request(m, &cc, P, N, basis, nullptr, seed);
+  q.bumps.greek_mask = 0;
+  q.precision = precision;
+  q.scheme = scheme;
+  q.stream_id = stream_id;
+  PlanOptions o;
+  int rc = plan_options(nullptr, &q, 1, &o);
+  if (rc) return rc;
+  o.raw_paths = true;
+  std::unique_ptr<lsmc_plan> p(new (std::nothrow) lsmc_plan());
+  if (!p) return LSMC_ENOMEM;
+  p->stream = s;
+  rc = build_layout(&q, 1, o, &p->L);
+  if (rc) return rc;
+  // paths live in caller memory: drop the path region, rows are P apart
+  p->L.total_bytes -= p->L.bytes_paths;
+  p->L.bytes_paths = 0;
+  for (auto& G : p->L.groups) G.ld = P;
+  *out = p.release();
+  return LSMC_OK;
+}
+
+int lsmc_paths(const lsmc_heston* m, double T, int32_t scheme, int32_t precision, uint32_t P,
+               uint32_t N, uint64_t seed, uint32_t stream_id, void* d_S, void* d_V, void* s) {
+  if (!m || !d_S || !d_V) return LSMC_EINVAL;
+  lsmc_plan* p = nullptr;
+  int rc = stage_plan(m, T, scheme, precision, P, N, LSMC_BASIS_SV2, nullptr, seed, stream_id,
+                      (cudaStream_t)s, &p);
+  if (rc) return rc;
+  rc = plan_alloc(p, false, true);
+  if (rc == LSMC_OK) rc = plan_bind_and_upload(p, d_S, d_V, nullptr);
+  p->run_backward = p->run_greeks = false;
+  if (rc == LSMC_OK) {
+    const cudaError_t e = launch_forward(p->fa, precision == LSMC_FP64, scheme, p->stream);
+    rc = cuda_status(e);
+  }
+  plan_free(p);
+  return rc;
+}
+
+int lsmc_backward(const void* d_S, const void* d_V, uint32_t P, uint32_t N, int32_t precision,
+                  const lsmc_heston* m, const lsmc_contract* c, int32_t basis, double* d_out,
+                  double* d_beta, uint32_t* d_nsing, void* s) {
+  if (!d_S || !m || !c || !d_out) return LSMC_EINVAL;
+  if (basis == LSMC_BASIS_SV2 && !d_V) return LSMC_EINVAL;
+  const int scheme = m->xi > 0 ? LSMC_SCHEME_QE : LSMC_SCHEME_FT_EULER;
+  lsmc_plan* p = nullptr;
+  int rc = stage_plan(m, c->T, scheme, precision, P, N, basis, c, 0, 0, (cudaStream_t)s, &p);
+  if (rc) return rc;
+  p->run_forward = p->run_greeks = false;
+  rc = plan_alloc(p, false, true);
+  if (rc == LSMC_OK && d_beta)
+    rc = cuda_status(cudaMemsetAsync(d_beta, 0xFF, sizeof(double) * 6 * N, p->stream));
+  if (rc == LSMC_OK) rc = plan_bind_and_upload(p, const_cast<void*>(d_S), const_cast<void*>(d_V), d_beta);
+  if (rc == LSMC_OK) rc = plan_enqueue(p);
+  if (rc == LSMC_OK) {
+    // price, se, european, continuation are the first four fields
+    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 4 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, p->stream));
+    if (rc == LSMC_OK && d_nsing)
+      rc = cuda_status(cudaMemcpyAsync(d_nsing, &p->d_results->singular, sizeof(uint32_t),
+                                       cudaMemcpyDeviceToDevice, p->stream));
+    if (rc == LSMC_OK) {
+      Control ctl{};
+      rc = cuda_status(cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, p->stream));
+      if (rc == LSMC_OK) rc = cuda_status(cudaStreamSynchronize(p->stream));
+      if (rc == LSMC_OK && ctl.error) rc = ctl.error == kDevErrTimeout ? LSMC_ETIMEOUT : LSMC_ECUDA;
+    }
+  }
+  plan_free(p);
+  return rc;
+}
+
+}  // extern "C"

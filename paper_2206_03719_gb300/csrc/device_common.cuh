@@ -1,0 +1,83 @@
+// device_common.cuh -- counter-based random inputs, uniform grids and the
+// synchronisation primitives shared by the kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lsmc {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
+// multiplies and an xor-permute, the key advancing by the Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// (m + 1/2) 2^-52, m = top 52 bits of (hi:lo): exact, in (0, 1).
+__device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
+  const unsigned long long m =
+      ((unsigned long long)hi << 20) | (unsigned long long)(lo >> 12);
+  return __fma_rn(__ull2double_rn(m), 0x1p-52, 0x1p-53);
+}
+
+// (m + 1/2) 2^-23, m = top 23 bits of w: exact, in (0, 1).
+__device__ __forceinline__ float uniform23(uint32_t w) {
+  return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
+}
+
+template <typename Real> struct Draw;
+template <> struct Draw<double> {
+  // U_V, Z_V from words (0, 1); Z_X from words (2, 3)
+  __device__ __forceinline__ static void make(uint4 w, double& uV, double& zV,
+                                              double& zX) {
+    uV = uniform52(w.x, w.y);
+    zV = normcdfinv(uV);
+    zX = normcdfinv(uniform52(w.z, w.w));
+  }
+};
+template <> struct Draw<float> {
+  // U_V from word 0 and Z_X from word 2: the top 23 bits of the words the
+  // double-precision grid reads first, so both precisions see one stream
+  __device__ __forceinline__ static void make(uint4 w, float& uV, float& zV,
+                                              float& zX) {
+    uV = uniform23(w.x);
+    zV = normcdfinvf(uV);
+    zX = normcdfinvf(uniform23(w.z));
+  }
+};
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
+  return *(const volatile uint32_t*)p;
+}
+
+// L2-coherent loads of data other CTAs wrote during this launch
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+
+}  // namespace lsmc

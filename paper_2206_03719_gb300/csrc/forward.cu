@@ -1,0 +1,236 @@
+// forward.cu -- random inputs and Heston path generation (forward pass).
+//
+// One thread owns one path of one contract and runs the whole time loop in
+// registers (the GPU form of the paper's loop interchange, Sec. 4.1: the
+// serial dependency along time stays inside a thread, independent paths fill
+// the machine).  Per step it draws Philox4x32-10 once, maps the words to the
+// uniform grid and two normal quantiles, then advances every path group of
+// the contract with those same inputs (common random numbers) and stores
+// exp(x) and v for the step as one coalesced row per group (step-major,
+// path-minor: the layout of Sec. 4.1, Fig. "datalayout").
+#include <cstdio>
+
+#include "device_common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+namespace lsmc {
+
+template <typename Real> struct Fm;
+template <> struct Fm<double> {
+  __device__ static double div(double a, double b) { return a / b; }
+  __device__ static double sqrt_(double a) { return sqrt(a); }
+  __device__ static double log_(double a) { return log(a); }
+  __device__ static double exp_(double a) { return exp(a); }
+};
+template <> struct Fm<float> {
+  __device__ static float div(float a, float b) { return __fdividef(a, b); }
+  __device__ static float sqrt_(float a) { return sqrtf(a); }
+  __device__ static float log_(float a) { return __logf(a); }
+  __device__ static float exp_(float a) { return __expf(a); }
+};
+
+template <typename Real>
+struct GroupConst {
+  // QE: m = mA + mB v, s^2 = sA + sB v, x1 = x + c0 + K1 v + K2 v1 + sqrt(K3 (v + v1)) Z
+  Real mA, mB, sA, sB, c0, K1, K2, K3;
+  // FT-Euler
+  Real dt, kdt, theta, xi, rho, rhob, mudt;
+  Real v0, out_scale;
+  Real* E;
+  Real* V;
+  uint64_t ld;
+};
+
+// Scheme constants of one path group, from the model (Andersen 2008 for QE
+// with gamma1 = gamma2 = 1/2; the plain Euler coefficients for FT).
+template <typename Real>
+__device__ void make_group_const(const FwdGroup& g, GroupConst<Real>& c) {
+  const double dt = g.dt, k = g.kappa, th = g.theta, xi = g.xi, rho = g.rho;
+  const double E = exp(-k * dt);
+  const double omE = -expm1(-k * dt);  // 1 - E without cancellation
+  c.mA = (Real)(th * omE);
+  c.mB = (Real)E;
+  if (xi > 0.0) {
+    c.sB = (Real)(xi * xi * E * omE / k);
+    c.sA = (Real)(th * xi * xi * omE * omE / (2.0 * k));
+    const double K0 = -rho * k * th * dt / xi;
+    const double h = 0.5 * dt * (k * rho / xi - 0.5);
+    c.K1 = (Real)(h - rho / xi);
+    c.K2 = (Real)(h + rho / xi);
+    c.c0 = (Real)((g.r - g.q) * dt + K0);
+  } else {
+    c.sA = c.sB = c.K1 = c.K2 = c.c0 = (Real)0;
+  }
+  c.K3 = (Real)(0.5 * dt * (1.0 - rho * rho));
+  c.dt = (Real)dt;
+  c.kdt = (Real)(k * dt);
+  c.theta = (Real)th;
+  c.xi = (Real)xi;
+  c.rho = (Real)rho;
+  c.rhob = (Real)sqrt(1.0 - rho * rho);
+  c.mudt = (Real)((g.r - g.q) * dt);
+  c.v0 = (Real)g.v0;
+  c.out_scale = (Real)g.out_scale;
+  c.E = (Real*)g.E;
+  c.V = (Real*)g.V;
+  c.ld = g.ld;
+}
+
+// Andersen QE step: variance by the quadratic branch (psi <= 1.5) or the
+// exponential branch, then the log price from both variances.
+template <typename Real>
+__device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x,
+                                        Real& v, Real uV, Real zV, Real zX) {
+  using F = Fm<Real>;
+  const Real m = fma(c.mB, v, c.mA);
+  const Real s2 = fma(c.sB, v, c.sA);
+  const Real psi = F::div(s2, m * m);
+  Real v1;
+  if (psi <= (Real)1.5) {
+    const Real inv = F::div((Real)2, psi);
+    const Real t = inv - (Real)1;
+    const Real b2 = t + F::sqrt_(inv * t);
+    const Real b = F::sqrt_(b2);
+    const Real a = F::div(m, (Real)1 + b2);
+    const Real q = b + zV;
+    v1 = a * q * q;
+  } else {
+    const Real p = F::div(psi - (Real)1, psi + (Real)1);
+    const Real omp = (Real)1 - p;
+    v1 = (uV <= p) ? (Real)0 : F::div(m, omp) * F::log_(F::div(omp, (Real)1 - uV));
+  }
+  x = x + c.c0 + c.K1 * v + c.K2 * v1 + F::sqrt_(c.K3 * (v + v1)) * zX;
+  v = v1;
+}
+
+// Full-truncation Euler: v+ = max(v, 0) in drift and diffusion.
+template <typename Real>
+__device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
+                                        Real& v, Real zV, Real zX) {
+  using F = Fm<Real>;
+  const Real vp = v > (Real)0 ? v : (Real)0;
+  const Real sq = F::sqrt_(vp * c.dt);
+  const Real v1 = v + c.kdt * (c.theta - vp) + c.xi * sq * zV;
+  x = x + (c.mudt - (Real)0.5 * vp * c.dt) + sq * (c.rho * zV + c.rhob * zX);
+  v = v1;
+}
+
+template <typename Real, int SCHEME>
+__global__ void __launch_bounds__(kBlock)
+forward_kernel(FwdArgs a) {
+  __shared__ GroupConst<Real> gc[kMaxGroups];
+  __shared__ FwdContract sc;
+  if (threadIdx.x == 0) {
+    // contract of this block: last contract whose block0 <= blockIdx.x
+    uint32_t lo = 0, hi = a.n_contracts;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) / 2;
+      if (a.contracts[mid].block0 <= blockIdx.x) lo = mid; else hi = mid;
+    }
+    sc = a.contracts[lo];
+  }
+  __syncthreads();
+  if (threadIdx.x < sc.n_groups)
+    make_group_const<Real>(a.groups[sc.group0 + threadIdx.x], gc[threadIdx.x]);
+  __syncthreads();
+
+  const uint32_t p = (blockIdx.x - sc.block0) * kBlock + threadIdx.x;
+  if (p >= sc.P) return;
+  const int ng = (int)sc.n_groups;
+  const uint2 key = make_uint2((uint32_t)sc.seed, (uint32_t)(sc.seed >> 32));
+
+  Real x[kMaxGroups], v[kMaxGroups];
+#pragma unroll
+  for (int g = 0; g < kMaxGroups; ++g) {
+    x[g] = (Real)0;
+    v[g] = g < ng ? gc[g].v0 : (Real)0;
+  }
+  for (int g = 0; g < ng; ++g) {
+    const FwdGroup& gg = a.groups[sc.group0 + g];
+    if (gg.E_row0) ((Real*)gg.E_row0)[p] = gc[g].out_scale;
+    if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
+  }
+
+  for (uint32_t n = 0; n < sc.N; ++n) {
+    const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+    Real uV, zV, zX;
+    Draw<Real>::make(w, uV, zV, zX);
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) {
+      if (g < ng) {
+        const GroupConst<Real>& c = gc[g];
+        if (SCHEME == kSchemeQE) {
+          qe_step<Real>(c, x[g], v[g], uV, zV, zX);
+        } else {
+          ft_step<Real>(c, x[g], v[g], zV, zX);
+        }
+        const size_t off = (size_t)n * c.ld + p;
+        c.E[off] = c.out_scale * Fm<Real>::exp_(x[g]);
+        if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+      }
+    }
+  }
+}
+
+__global__ void philox_kernel(const uint4* __restrict__ ctr, uint2 key,
+                              uint4* __restrict__ out, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], key);
+}
+
+template <typename Real>
+__global__ void draws_kernel(uint2 key, uint32_t stream_id,
+                             const uint32_t* __restrict__ path,
+                             const uint32_t* __restrict__ step, size_t n,
+                             Real* __restrict__ out) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 w = philox4x32_10(make_uint4(path[i], step[i], stream_id, 0u), key);
+  Real uV, zV, zX;
+  Draw<Real>::make(w, uV, zV, zX);
+  out[3 * i] = uV;
+  out[3 * i + 1] = zV;
+  out[3 * i + 2] = zX;
+}
+
+cudaError_t launch_forward(const FwdArgs& a, bool fp64, int scheme,
+                           cudaStream_t s) {
+  if (a.n_blocks == 0) return cudaSuccess;
+  if (fp64) {
+    if (scheme == kSchemeQE)
+      forward_kernel<double, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
+    else
+      forward_kernel<double, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
+  } else {
+    if (scheme == kSchemeQE)
+      forward_kernel<float, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
+    else
+      forward_kernel<float, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                          uint32_t* out, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + kBlock - 1) / kBlock;
+  philox_kernel<<<(unsigned)blocks, kBlock, 0, s>>>(
+      (const uint4*)ctr, make_uint2(k0, k1), (uint4*)out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path,
+                         const uint32_t* step, size_t n, bool fp64, void* out,
+                         cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + kBlock - 1) / kBlock;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  if (fp64)
+    draws_kernel<double><<<(unsigned)blocks, kBlock, 0, s>>>(key, stream_id, path, step, n, (double*)out);
+  else
+    draws_kernel<float><<<(unsigned)blocks, kBlock, 0, s>>>(key, stream_id, path, step, n, (float*)out);
+  return cudaGetLastError();
+}
+
+}  // namespace lsmc

@@ -1,0 +1,27 @@
+// kernels.h -- host-side launchers of the device kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.h"
+
+namespace lsmc {
+
+cudaError_t launch_forward(const FwdArgs& a, bool fp64, int scheme, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
+                          uint32_t* out, size_t n, cudaStream_t s);
+cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path,
+                         const uint32_t* step, size_t n, bool fp64, void* out,
+                         cudaStream_t s);
+cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s);
+cudaError_t launch_backward(const BwdArgs& a, bool fp64, int basis, int grid,
+                            cudaStream_t s);
+cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
+                          DevResult* out, cudaStream_t s);
+// paths per backward job
+int backward_tile(bool fp64);
+// resident backward CTAs per SM
+int backward_occupancy(bool fp64, int basis);
+
+}  // namespace lsmc

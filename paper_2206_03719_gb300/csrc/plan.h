@@ -1,0 +1,134 @@
+// plan.h -- device-side tables of one launch (host planner <-> kernels).
+//
+// A launch prices a set of "contracts" (a request = one model, one maturity,
+// several strikes).  Each contract's bump scenarios are folded onto "path
+// groups": scenarios whose paths are the same simulation.  Scenarios that
+// only move S0 share x = ln(S/S0) exactly; scenarios that only move r share
+// the variance path and shift x by n (dr) dt, i.e. scale S by exp(n dr dt).
+// v0 and T bumps need their own simulation.  A regression "instance" is one
+// (scenario, strike) pair; it reads its group's stored exp(x) and v rows.
+#pragma once
+
+#include <cstdint>
+
+namespace lsmc {
+
+constexpr int kBlock = 256;      // threads per CTA (forward and backward)
+constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
+constexpr int kNSum = 24;        // doubles per tile partial
+// partial layout: 15 monomials x^a w^b (a + b <= 4), 6 right-hand sides,
+// European payoff sum, sum of Y, sum of Y^2
+constexpr int kSlotRhs = 15;
+constexpr int kSlotEuro = 21;
+constexpr int kSlotSumY = 22;
+constexpr int kSlotSumY2 = 23;
+
+enum : int32_t { kSchemeQE = 0, kSchemeFT = 1 };
+enum : int32_t { kPut = 0, kCall = 1 };
+enum : int32_t { kAmerican = 0, kEuropean = 1 };
+enum : int32_t { kBasisS2 = 0, kBasisSV2 = 1 };
+
+// error codes written by kernels into Control::error
+enum : uint32_t { kDevErrTimeout = 1, kDevErrBadJob = 2 };
+
+// ---- forward ------------------------------------------------------------
+struct FwdGroup {
+  double v0, kappa, theta, xi, rho, r, q, dt;
+  double out_scale;   // E row value = out_scale * exp(x)
+  void* E;            // rows 1..N at index n-1, ld elements apart
+  void* V;            // rows 1..N (nullptr: not stored)
+  void* E_row0;       // optional row 0 (= out_scale)
+  void* V_row0;       // optional row 0 (= v0)
+  uint64_t ld;
+};
+
+struct FwdContract {
+  uint64_t seed;
+  uint32_t stream_id;
+  uint32_t P, N;
+  uint32_t group0, n_groups;
+  uint32_t block0;    // first CTA of this contract in the grid
+};
+
+struct FwdArgs {
+  const FwdContract* contracts;
+  const FwdGroup* groups;
+  uint32_t n_contracts;
+  uint32_t n_blocks;
+};
+
+// ---- backward -------------------------------------------------------------
+struct BwdInstance {
+  const void* E;      // group rows 1..N (exp(x) scaled by the group's out_scale)
+  const void* V;      // group variance rows 1..N (nullptr for basis S2)
+  uint64_t ld;
+  void* Y;            // P cash flows discounted to t_0 (owned by this instance)
+  double* partial;    // tiles x kNSum
+  double* beta_hist;  // optional N x 6
+  double* scale_tab;  // 2 (N + 1): S multipliers of E, then discount factors
+                      // exp(-r n dt) (filled by the setup kernel)
+  double spot;        // scenario S0 (exercise value at t_0)
+  double scale0;      // S0 multiplier of E rows
+  double dr_dt;       // S multiplier exp(n dr_dt) (folded rate bump)
+  double r, dt, T, K, theta;
+  double disc, disc_T, invK, inv_theta, h0;   // filled by the setup kernel
+  uint32_t P, N, tiles, gens;
+  int32_t type, style, basis;
+  uint32_t out_index; // result slot
+};
+
+struct BwdState {
+  uint32_t arrive;    // tile arrivals, all generations
+  uint32_t ready;     // generations solved and published
+  uint32_t singular;
+  uint32_t beta_ok;
+  double beta[6];
+  double euro_sum;
+  double itm;         // in-the-money path-steps seen by the regressions
+};
+
+struct BwdResult {
+  double price, se, euro, cont, itm;
+  uint32_t singular;
+  uint32_t done;
+};
+
+struct Control {
+  unsigned long long next_job;
+  uint32_t error;
+  uint32_t error_info;
+};
+
+struct BwdArgs {
+  const BwdInstance* inst;   // sorted by gens, descending
+  BwdState* state;
+  BwdResult* results;        // indexed by BwdInstance::out_index
+  const unsigned long long* round_off;  // n_rounds + 1
+  const uint32_t* cum_tiles; // n_inst + 1 (over the sorted instances)
+  const uint32_t* active;    // instances active in each round
+  Control* ctl;
+  unsigned long long total_jobs;
+  unsigned long long timeout_ns;
+  uint32_t n_rounds, n_inst;
+};
+
+// ---- Greeks ---------------------------------------------------------------
+// device mirror of lsmc_result (same layout; checked in capi.cpp)
+struct DevResult {
+  double price, price_se, delta, gamma, vega, rho, theta, european_price;
+  uint32_t n_singular_solves, n_revaluations;
+  int32_t status;
+  int32_t reserved;
+};
+
+struct GreekOut {
+  int32_t res[11];     // result slot per scenario kind (-1 absent)
+  uint32_t mask;
+  double S0, v0, hS, hG, hV, dR, dT;
+};
+
+// scenario kinds (layout order)
+enum : int32_t { kScBase = 0, kScSUp, kScSDn, kScSgUp, kScSgDn, kScVUp, kScVDn,
+                 kScRUp, kScRDn, kScTDn, kScTUp, kScCount };
+
+}  // namespace lsmc

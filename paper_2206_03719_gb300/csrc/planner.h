@@ -1,0 +1,85 @@
+// planner.h -- host planner: request validation, scenario expansion, path
+// group folding and the device tables of one launch (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lsmc.h"
+#include "plan.h"
+
+namespace lsmc {
+
+// First-fit sub-allocator over one device range (256-byte granules).
+class Arena {
+ public:
+  void reset(void* base, size_t bytes);
+  bool active() const { return base_ != nullptr; }
+  void* alloc(size_t bytes);
+  void free(void* p);
+  size_t capacity() const { return size_; }
+  size_t used() const;
+  size_t largest_free() const;
+
+ private:
+  struct Block { size_t off, size; };
+  char* base_ = nullptr;
+  size_t size_ = 0;
+  std::vector<Block> free_;   // sorted by offset
+  std::vector<Block> used_;
+  mutable std::mutex mu_;
+};
+
+struct Scenario {
+  int32_t kind;
+  lsmc_heston model;
+  double T;
+};
+
+// Bump-and-revalue scenarios of a request, in layout order:
+// base, S+, S-, S+ (gamma), S- (gamma), v0+, v0-, r+, r-, T-, T+.
+int expand_scenarios(const lsmc_request& req, std::vector<Scenario>* out);
+
+// Checks a request; LSMC_OK or LSMC_EINVAL.
+int validate_request(const lsmc_request& req, int precision, int scheme);
+
+struct PlanOptions {
+  int precision = LSMC_FP64;
+  int scheme = LSMC_SCHEME_QE;
+  int basis = LSMC_BASIS_S2;
+  bool raw_paths = false;       // stage entry point: E rows are S itself
+};
+
+// Sizes and host tables of one launch; device pointers are bound later.
+struct PlanLayout {
+  PlanOptions opt;
+  std::vector<FwdContract> contracts;
+  std::vector<FwdGroup> groups;
+  std::vector<BwdInstance> inst;          // sorted by gens, descending
+  std::vector<unsigned long long> round_off;
+  std::vector<uint32_t> cum_tiles, active;
+  std::vector<GreekOut> greeks;
+  // region offsets (bytes) of each group's E and V rows (V: SIZE_MAX if not
+  // stored) and of each sorted instance's Y, partials and scale table
+  std::vector<size_t> group_E_off, group_V_off;
+  struct InstOff { size_t y, partial, scale; uint32_t group; };
+  std::vector<InstOff> inst_off;
+  uint32_t n_results = 0;                 // BwdResult slots
+  uint32_t fwd_blocks = 0;
+  uint64_t total_jobs = 0;
+  uint64_t generated_path_steps = 0, lsmc_path_steps = 0;
+  // device bytes of each region
+  size_t bytes_paths = 0, bytes_y = 0, bytes_partial = 0, bytes_scale = 0;
+  size_t bytes_tables = 0, bytes_state = 0, bytes_results = 0, bytes_out = 0;
+  size_t total_bytes = 0;
+};
+
+int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
+                 PlanLayout* L);
+
+}  // namespace lsmc

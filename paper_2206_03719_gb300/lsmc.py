@@ -1,0 +1,317 @@
+"""ctypes binding of liblsmc.so (include/lsmc.h): argument marshalling only.
+
+Every function of the C ABI is exposed under its C name with the same
+arguments.  All computation runs in the library's CUDA kernels; if the
+library has not been built (see paper_2206_03719_gb300.build) loading fails
+with an error instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+LSMC_OK, LSMC_PENDING = 0, 1
+LSMC_EINVAL, LSMC_ENOMEM, LSMC_EBUSY, LSMC_ETIMEOUT = -1, -2, -3, -4
+LSMC_ECUDA, LSMC_ENOTIMPL, LSMC_ENOTFOUND, LSMC_ENODEV = -5, -6, -7, -8
+LSMC_PUT, LSMC_CALL = 0, 1
+LSMC_AMERICAN, LSMC_EUROPEAN = 0, 1
+LSMC_SCHEME_QE, LSMC_SCHEME_FT_EULER = 0, 1
+LSMC_BASIS_S2, LSMC_BASIS_SV2 = 0, 1
+LSMC_FP64, LSMC_MIXED = 0, 1
+LSMC_GREEK_DELTA, LSMC_GREEK_GAMMA, LSMC_GREEK_VEGA = 1, 2, 4
+LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31
+
+EXPORTS = [
+    "lsmc_strerror", "lsmc_abi_version", "lsmc_create", "lsmc_destroy",
+    "lsmc_set_stream", "lsmc_set_workspace", "lsmc_request_footprint",
+    "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book",
+    "lsmc_plan_create", "lsmc_plan_launch", "lsmc_plan_fetch",
+    "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
+    "lsmc_plan_set_timing", "lsmc_plan_kernel_times",
+    "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
+    "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_backward",
+]
+
+
+class lsmc_heston(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("S0", "r", "q", "v0", "kappa", "theta", "xi", "rho")]
+
+
+class lsmc_contract(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int32), ("style", ctypes.c_int32),
+                ("K", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+class lsmc_bumps(ctypes.Structure):
+    _fields_ = [("rel_dS", ctypes.c_double), ("rel_dS_gamma", ctypes.c_double),
+                ("rel_dv0", ctypes.c_double), ("abs_dr", ctypes.c_double),
+                ("abs_dT", ctypes.c_double), ("greek_mask", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class lsmc_result(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("price", "price_se", "delta", "gamma", "vega", "rho", "theta",
+                 "european_price")] + [
+        ("n_singular_solves", ctypes.c_uint32), ("n_revaluations", ctypes.c_uint32),
+        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+
+
+class lsmc_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
+                ("queue_capacity", ctypes.c_uint32)]
+
+
+class lsmc_request(ctypes.Structure):
+    _fields_ = [("model", lsmc_heston), ("type", ctypes.c_int32),
+                ("style", ctypes.c_int32), ("T", ctypes.c_double),
+                ("strikes", ctypes.POINTER(ctypes.c_double)),
+                ("n_strikes", ctypes.c_uint32), ("n_paths", ctypes.c_uint32),
+                ("n_steps", ctypes.c_uint32), ("basis", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("scheme", ctypes.c_int32),
+                ("bumps", lsmc_bumps), ("seed", ctypes.c_uint64),
+                ("stream_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class lsmc_plan_info(ctypes.Structure):
+    _fields_ = [("generated_path_steps", ctypes.c_uint64),
+                ("lsmc_path_steps", ctypes.c_uint64),
+                ("backward_jobs", ctypes.c_uint64), ("device_bytes", ctypes.c_uint64),
+                ("kernels_per_launch", ctypes.c_uint32), ("n_results", ctypes.c_uint32),
+                ("n_instances", ctypes.c_uint32), ("n_groups", ctypes.c_uint32),
+                ("itm_path_steps", ctypes.c_uint64), ("h2d_bytes", ctypes.c_uint64),
+                ("d2h_bytes", ctypes.c_uint64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = False):
+    """Load liblsmc.so (raises if it is missing and build_if_missing is False)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if build_if_missing:
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                "liblsmc.so is not built (%s); run paper_2206_03719_gb300.build.build()" % path)
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        vp, sz, u32, u64, i32, dbl = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.c_int32, ctypes.c_double)
+        sig = {
+            "lsmc_strerror": ([ctypes.c_int], ctypes.c_char_p),
+            "lsmc_abi_version": ([], ctypes.c_int),
+            "lsmc_create": ([P(vp), P(lsmc_config)], ctypes.c_int),
+            "lsmc_destroy": ([vp], None),
+            "lsmc_set_stream": ([vp, vp], ctypes.c_int),
+            "lsmc_set_workspace": ([vp, vp, sz], ctypes.c_int),
+            "lsmc_request_footprint": ([vp, P(lsmc_request), P(sz)], ctypes.c_int),
+            "lsmc_price_greeks": ([vp, P(lsmc_heston), P(lsmc_contract), u32, u32, i32,
+                                   P(lsmc_bumps), u64, P(lsmc_result)], ctypes.c_int),
+            "lsmc_price_request": ([vp, P(lsmc_request), P(lsmc_result)], ctypes.c_int),
+            "lsmc_price_book": ([vp, P(lsmc_request), sz, P(lsmc_result)], ctypes.c_int),
+            "lsmc_plan_create": ([vp, P(lsmc_request), sz, P(vp)], ctypes.c_int),
+            "lsmc_plan_launch": ([vp, i32], ctypes.c_int),
+            "lsmc_plan_fetch": ([vp, P(lsmc_result)], ctypes.c_int),
+            "lsmc_plan_device_results": ([vp, P(vp), P(sz)], ctypes.c_int),
+            "lsmc_plan_get_info": ([vp, P(lsmc_plan_info)], ctypes.c_int),
+            "lsmc_plan_destroy": ([vp], None),
+            "lsmc_plan_set_timing": ([vp, i32], ctypes.c_int),
+            "lsmc_plan_kernel_times": ([vp, P(dbl), P(u32)], ctypes.c_int),
+            "lsmc_submit": ([vp, P(lsmc_request), P(u64)], ctypes.c_int),
+            "lsmc_poll": ([vp, u64, P(lsmc_result)], ctypes.c_int),
+            "lsmc_wait": ([vp, u64, P(lsmc_result), dbl], ctypes.c_int),
+            "lsmc_ticket_times": ([vp, u64, P(dbl), P(dbl), P(dbl)], ctypes.c_int),
+            "lsmc_philox": ([vp, u32, u32, vp, sz, vp], ctypes.c_int),
+            "lsmc_draws": ([u64, u32, vp, vp, sz, i32, vp, vp], ctypes.c_int),
+            "lsmc_paths": ([P(lsmc_heston), dbl, i32, i32, u32, u32, u64, u32, vp, vp, vp],
+                           ctypes.c_int),
+            "lsmc_backward": ([vp, vp, u32, u32, i32, P(lsmc_heston), P(lsmc_contract), i32,
+                               vp, vp, vp, vp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+class LsmcError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = load().lsmc_strerror(status).decode()
+        super().__init__("%s: %s (%d)" % (what, msg, status) if what else "%s (%d)" % (msg, status))
+
+
+def check(status, what=""):
+    if status < 0:
+        raise LsmcError(status, what)
+    return status
+
+
+# ---- C-named wrappers (same names and arguments as include/lsmc.h) ---------
+def lsmc_strerror(status):
+    return load().lsmc_strerror(status).decode()
+
+
+def lsmc_abi_version():
+    return load().lsmc_abi_version()
+
+
+def lsmc_create(config):
+    ctx = ctypes.c_void_p()
+    check(load().lsmc_create(ctypes.byref(ctx), ctypes.byref(config) if config else None),
+          "lsmc_create")
+    return ctx
+
+
+def lsmc_destroy(ctx):
+    load().lsmc_destroy(ctx)
+
+
+def lsmc_set_stream(ctx, stream):
+    return check(load().lsmc_set_stream(ctx, stream), "lsmc_set_stream")
+
+
+def lsmc_set_workspace(ctx, ptr, nbytes):
+    return check(load().lsmc_set_workspace(ctx, ptr, nbytes), "lsmc_set_workspace")
+
+
+def lsmc_request_footprint(ctx, req):
+    n = ctypes.c_size_t()
+    check(load().lsmc_request_footprint(ctx, ctypes.byref(req), ctypes.byref(n)),
+          "lsmc_request_footprint")
+    return n.value
+
+
+def lsmc_price_greeks(ctx, model, contract, n_paths, n_steps, basis, bumps, seed):
+    out = lsmc_result()
+    check(load().lsmc_price_greeks(ctx, ctypes.byref(model), ctypes.byref(contract), n_paths,
+                                   n_steps, basis, ctypes.byref(bumps), seed,
+                                   ctypes.byref(out)), "lsmc_price_greeks")
+    return out
+
+
+def lsmc_price_request(ctx, req):
+    outs = (lsmc_result * req.n_strikes)()
+    check(load().lsmc_price_request(ctx, ctypes.byref(req), outs), "lsmc_price_request")
+    return list(outs)
+
+
+def lsmc_price_book(ctx, reqs):
+    arr = (lsmc_request * len(reqs))(*reqs)
+    total = sum(r.n_strikes for r in reqs)
+    outs = (lsmc_result * total)()
+    check(load().lsmc_price_book(ctx, arr, len(reqs), outs), "lsmc_price_book")
+    return list(outs)
+
+
+def lsmc_plan_create(ctx, reqs):
+    arr = (lsmc_request * len(reqs))(*reqs)
+    plan = ctypes.c_void_p()
+    check(load().lsmc_plan_create(ctx, arr, len(reqs), ctypes.byref(plan)), "lsmc_plan_create")
+    return plan
+
+
+def lsmc_plan_launch(plan, use_graph=False):
+    return check(load().lsmc_plan_launch(plan, 1 if use_graph else 0), "lsmc_plan_launch")
+
+
+def lsmc_plan_fetch(plan, n_results):
+    outs = (lsmc_result * n_results)()
+    check(load().lsmc_plan_fetch(plan, outs), "lsmc_plan_fetch")
+    return list(outs)
+
+
+def lsmc_plan_device_results(plan):
+    p, n = ctypes.c_void_p(), ctypes.c_size_t()
+    check(load().lsmc_plan_device_results(plan, ctypes.byref(p), ctypes.byref(n)),
+          "lsmc_plan_device_results")
+    return p.value, n.value
+
+
+def lsmc_plan_get_info(plan):
+    info = lsmc_plan_info()
+    check(load().lsmc_plan_get_info(plan, ctypes.byref(info)), "lsmc_plan_get_info")
+    return info
+
+
+def lsmc_plan_set_timing(plan, enable=True):
+    return check(load().lsmc_plan_set_timing(plan, 1 if enable else 0), "lsmc_plan_set_timing")
+
+
+def lsmc_plan_kernel_times(plan):
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_uint32()
+    check(load().lsmc_plan_kernel_times(plan, ms, ctypes.byref(n)), "lsmc_plan_kernel_times")
+    return list(ms), n.value
+
+
+def lsmc_plan_destroy(plan):
+    load().lsmc_plan_destroy(plan)
+
+
+def lsmc_submit(ctx, req):
+    t = ctypes.c_uint64()
+    check(load().lsmc_submit(ctx, ctypes.byref(req), ctypes.byref(t)), "lsmc_submit")
+    return t.value
+
+
+def lsmc_poll(ctx, ticket, n_strikes):
+    outs = (lsmc_result * n_strikes)()
+    st = check(load().lsmc_poll(ctx, ticket, outs), "lsmc_poll")
+    return st, (list(outs) if st == LSMC_OK else None)
+
+
+def lsmc_wait(ctx, ticket, n_strikes, timeout_s=-1.0):
+    outs = (lsmc_result * n_strikes)()
+    st = check(load().lsmc_wait(ctx, ticket, outs, timeout_s), "lsmc_wait")
+    return st, (list(outs) if st == LSMC_OK else None)
+
+
+def lsmc_ticket_times(ctx, ticket):
+    s, a, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    check(load().lsmc_ticket_times(ctx, ticket, ctypes.byref(s), ctypes.byref(a),
+                                   ctypes.byref(d)), "lsmc_ticket_times")
+    return s.value, a.value, d.value
+
+
+def lsmc_philox(d_ctr, key_lo, key_hi, d_out, n, stream=None):
+    return check(load().lsmc_philox(d_ctr, key_lo, key_hi, d_out, n, stream), "lsmc_philox")
+
+
+def lsmc_draws(seed, stream_id, d_path, d_step, n, precision, d_out, stream=None):
+    return check(load().lsmc_draws(seed, stream_id, d_path, d_step, n, precision, d_out, stream),
+                 "lsmc_draws")
+
+
+def lsmc_paths(model, T, scheme, precision, n_paths, n_steps, seed, stream_id, d_S, d_V,
+               stream=None):
+    return check(load().lsmc_paths(ctypes.byref(model), T, scheme, precision, n_paths, n_steps,
+                                   seed, stream_id, d_S, d_V, stream), "lsmc_paths")
+
+
+def lsmc_backward(d_S, d_V, n_paths, n_steps, precision, model, contract, basis, d_out,
+                  d_beta=None, d_n_singular=None, stream=None):
+    return check(load().lsmc_backward(d_S, d_V, n_paths, n_steps, precision, ctypes.byref(model),
+                                      ctypes.byref(contract), basis, d_out, d_beta, d_n_singular,
+                                      stream), "lsmc_backward")

@@ -1,0 +1,118 @@
+"""The C ABI without a GPU: the library loads, exports every entry point
+include/lsmc.h declares, its structs have the header's layout, and host-side
+validation works (CPU only; no kernel is launched)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_2206_03719_gb300 import build as B
+from paper_2206_03719_gb300 import lsmc as L
+from paper_2206_03719_gb300 import api, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lsmc.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsmc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(L.EXPORTS) == declared
+
+
+def test_abi_version_and_strerror(lib):
+    assert L.lsmc_abi_version() == 1
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert L.lsmc_strerror(code) not in ("", "unknown status")
+    assert L.lsmc_strerror(12345) == "unknown status"
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    src = tmp_path / "sizes.c"
+    src.write_text("""
+#include <stdio.h>
+#include <stddef.h>
+#include "lsmc.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsmc_heston), sizeof(lsmc_contract),
+         sizeof(lsmc_bumps), sizeof(lsmc_result), sizeof(lsmc_config), sizeof(lsmc_request),
+         sizeof(lsmc_plan_info));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(lsmc_request, strikes), offsetof(lsmc_request, bumps),
+         offsetof(lsmc_request, seed), offsetof(lsmc_result, n_singular_solves),
+         offsetof(lsmc_config, hbm_budget));
+  return 0;
+}
+""")
+    exe = tmp_path / "sizes"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().split("\n")[:2]]
+    assert sizes == [ctypes.sizeof(t) for t in (L.lsmc_heston, L.lsmc_contract, L.lsmc_bumps,
+                                                   L.lsmc_result, L.lsmc_config, L.lsmc_request,
+                                                   L.lsmc_plan_info)]
+    assert offs == [L.lsmc_request.strikes.offset, L.lsmc_request.bumps.offset,
+                    L.lsmc_request.seed.offset, L.lsmc_result.n_singular_solves.offset,
+                    L.lsmc_config.hbm_budget.offset]
+
+
+def test_footprint_and_validation_on_host(lib):
+    req = api.Request(workloads.PAPER_FP64)
+    n = L.lsmc_request_footprint(None, req.c)
+    # 5 path groups x (S and v) x 252 x 131072 doubles dominate
+    assert n > 5 * 2 * 252 * 131072 * 8
+    mixed = api.Request(workloads.PAPER_FP64, precision="mixed")
+    assert L.lsmc_request_footprint(None, mixed.c) < n
+    bad = [
+        dict(model=dict(workloads.HESTON_BASE, xi=0.0)),                # QE needs xi > 0
+        dict(model=dict(workloads.HESTON_BASE, rho=1.5)),
+        dict(model=dict(workloads.HESTON_BASE, S0=float("nan"))),
+        dict(strikes=[-1.0]),
+        dict(T=0.0),
+        dict(n_paths=0),
+        dict(rel_dS=0.0),
+        dict(abs_dT=2.0),
+    ]
+    for kw in bad:
+        r = api.Request(workloads.PAPER_FP64.replace(**kw))
+        with pytest.raises(L.LsmcError) as e:
+            L.lsmc_request_footprint(None, r.c)
+        assert e.value.status == L.LSMC_EINVAL, kw
+    # FT-Euler accepts xi = 0
+    ft = api.Request(workloads.PAPER_FP64.replace(model=dict(workloads.HESTON_BASE, xi=0.0)),
+                     scheme="ft_euler")
+    assert L.lsmc_request_footprint(None, ft.c) > 0
+
+
+def test_create_without_a_device_reports_enodev(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    ctx = ctypes.c_void_p()
+    cfg = L.lsmc_config(0, 0, 0, 0, 0, 0, 0)
+    assert lib.lsmc_create(ctypes.byref(ctx), ctypes.byref(cfg)) == L.LSMC_ENODEV
+    assert not ctx.value
+
+
+def test_stage_entry_points_reject_bad_arguments_before_launch(lib):
+    assert lib.lsmc_philox(None, 0, 0, None, 5, None) == L.LSMC_EINVAL
+    assert lib.lsmc_draws(1, 0, None, None, 3, 0, None, None) == L.LSMC_EINVAL
+    assert lib.lsmc_draws(1, 0, None, None, 0, 7, None, None) == L.LSMC_EINVAL
+    m = L.lsmc_heston(100, 0.02, 0, 0.04, 1.5, 0.04, 0.3, -0.7)
+    assert lib.lsmc_paths(ctypes.byref(m), 1.0, 0, 0, 16, 4, 1, 0, None, None, None) == L.LSMC_EINVAL
+    assert lib.lsmc_create(None, None) == L.LSMC_EINVAL

@@ -1,0 +1,123 @@
+"""End-to-end GPU parity through the C ABI: prices and Greeks of whole
+requests against the FP64 oracle on identical random streams."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import KEYS, assert_close, oracle_for, rel_err, torch_cuda
+from paper_2206_03719_gb300 import api, workloads
+from paper_2206_03719_gb300 import lsmc as L
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+FP64_TOL = 1e-10      # relative, FP64 GPU path vs FP64 oracle on identical streams
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    from paper_2206_03719_gb300 import build
+    build.build()
+    c = api.Context(workspace_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+def test_small_american_put_matches_oracle(ctx):
+    wl = workloads.SMALL_FP64
+    got = ctx.price(wl)
+    ref = oracle_for(wl)
+    assert got[0]["n_revaluations"] == 5
+    assert_close(got[0], ref[0], FP64_TOL, keys=("price", "delta", "gamma", "vega", "european_price"))
+    assert math.isnan(got[0]["rho"]) and math.isnan(got[0]["theta"])
+    assert abs(got[0]["price_se"] - ref[0]["price_se"]) <= 1e-9 * ref[0]["price_se"]
+
+
+VARIANTS = [
+    dict(),
+    dict(scheme="ft_euler"),
+    dict(option="call", model=dict(workloads.HESTON_BASE, q=0.03), strikes=[95.0, 105.0]),
+    dict(style="european"),
+    dict(basis="sv2", greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02),
+    dict(n_paths=1000, n_steps=7, strikes=[90.0, 100.0, 111.0]),       # ragged tiles
+    dict(n_paths=3001, n_steps=1),                                      # one date
+    dict(n_paths=5000, n_steps=2, basis="sv2"),
+    dict(n_paths=64, n_steps=12, strikes=[60.0]),                       # singular dates
+    dict(scheme="ft_euler", model=dict(workloads.HESTON_BASE, xi=0.0), basis="s2"),
+    dict(model=dict(workloads.HESTON_BASE, kappa=0.5, theta=0.09, xi=0.6, rho=-0.3, v0=0.01),
+         greeks=workloads.ALL_GREEKS, stream=17, seed=2**63 + 5),
+]
+
+
+@pytest.mark.parametrize("kw", VARIANTS, ids=[str(i) for i in range(len(VARIANTS))])
+def test_variants_match_oracle(ctx, kw):
+    wl = workloads.SMALL_FP64.replace(n_paths=4096, n_steps=24, **kw) if "n_paths" not in kw \
+        else workloads.SMALL_FP64.replace(**kw)
+    got = ctx.price(wl)
+    ref = oracle_for(wl)
+    for g, r in zip(got, ref):
+        keys = ["price", "european_price"] + [k for k in wl.greeks]
+        assert_close(g, r, FP64_TOL, keys=keys, what=str(kw))
+        assert g["n_singular_solves"] == r["n_singular"]
+        assert g["n_revaluations"] == r["n_revaluations"]
+
+
+@pytest.mark.parametrize("name", ["paper_fp64", "paper_fp64_ft"])
+def test_paper_size_fp64_matches_stored_oracle_values(ctx, name):
+    path = os.path.join(GOLDEN, name + ".json")
+    gold = json.load(open(path))
+    wl = workloads.PAPER_FP64.replace(scheme=gold["scheme"])
+    assert gold["n_paths"] == wl.n_paths and gold["n_steps"] == wl.n_steps
+    got = ctx.price(wl)
+    for g, r in zip(got, gold["results"]):
+        assert g["n_revaluations"] == 11
+        assert_close(g, r, FP64_TOL, what=name)
+
+
+def test_graph_replay_is_bit_identical(ctx):
+    wl = workloads.SMALL_FP64.replace(basis="sv2", greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02,
+                                      strikes=[90.0, 100.0])
+    plan = ctx.plan([wl])
+    plan.launch(use_graph=False)
+    a = plan.fetch()
+    plan.launch(use_graph=True)
+    b = plan.fetch()
+    plan.launch(use_graph=True)
+    c = plan.fetch()
+    plan.close()
+    assert a == b == c
+    assert a == ctx.price(wl)
+
+
+def test_book_equals_requests_priced_one_by_one(ctx):
+    book = workloads.book(n_contracts=6, paths_hi=20000, steps=(8, 16, 33), precision="fp64")
+    together = ctx.price_book(book)
+    alone = [ctx.price(w)[0] for w in book]
+    assert together == alone
+    for w, g in zip(book[:2], together[:2]):
+        r = oracle_for(w)[0]
+        assert_close(g, r, FP64_TOL, keys=("price", "delta", "gamma", "vega", "rho", "theta"))
+
+
+def test_mixed_precision_within_1e4_of_fp64_oracle(ctx):
+    wl = workloads.PAPER_FP64.replace(n_paths=32768, n_steps=64, precision="mixed")
+    got = ctx.price(wl)
+    ref = oracle_for(wl.replace(precision="fp64"))
+    worst = {}
+    for g, r in zip(got, ref):
+        for k in ("price", "delta", "vega", "rho", "theta", "european_price"):
+            worst[k] = max(worst.get(k, 0.0), rel_err(g[k], r[k]))
+    print("mixed vs FP64 oracle, worst relative errors:", worst)
+    assert worst["price"] <= 1e-3 and worst["european_price"] <= 1e-4
+
+
+def test_invalid_requests_are_rejected_before_launch(ctx):
+    for kw in (dict(n_paths=0), dict(strikes=[float("inf")]),
+               dict(model=dict(workloads.HESTON_BASE, kappa=-1.0))):
+        with pytest.raises(L.LsmcError) as e:
+            ctx.price(workloads.SMALL_FP64.replace(**kw))
+        assert e.value.status == L.LSMC_EINVAL
