@@ -293,10 +293,13 @@ backward_kernel(BwdArgs a) {
             const Real S = s1 * E1[p];
             const Real h = payoff<Real>(type, K, S);
             if (h > (Real)0) {
-              const Real x = S * invK;
+              // continuation value in the basis centred at the strike and at
+              // theta (x - 1, w - 1): same fitted function, far less
+              // cancellation when evaluated in single precision
+              const Real x = fma(S, invK, (Real)-1);
               Real c = fma(fma(b[2], x, b[1]), x, b[0]);
               if (BASIS == kBasisSV2) {
-                const Real w = V1[p] * invTh;
+                const Real w = fma(V1[p], invTh, (Real)-1);
                 c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
               }
               if (h * d1 > c) {
@@ -454,7 +457,11 @@ backward_kernel(BwdArgs a) {
         st->itm = __ldcg(&st->itm) + s_sum[0];
         if (!ok) st->singular = __ldcg(&st->singular) + 1u;
         st->beta_ok = ok ? 1u : 0u;
-        for (int i = 0; i < 6; ++i) st->beta[i] = ok ? beta[i] : 0.0;
+        // publish the coefficients re-expanded around x = 1, w = 1
+        const double bc[6] = {beta[0] + beta[1] + beta[2] + beta[3] + beta[4] + beta[5],
+                              beta[1] + 2.0 * beta[2] + beta[4], beta[2],
+                              beta[3] + beta[4] + 2.0 * beta[5], beta[4], beta[5]};
+        for (int i = 0; i < 6; ++i) st->beta[i] = ok ? bc[i] : 0.0;
         if (I.beta_hist) {
           // coefficients in the units of the cash flow discounted to t_n
           const double to_n = 1.0 / dtab[n];

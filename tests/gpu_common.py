@@ -52,7 +52,9 @@ def assert_close(got, ref, tol, keys=KEYS, what=""):
     errs = {}
     scale = max(abs(ref.get("price", 1.0)), 1e-2)
     for k in keys:
-        floor = 1e-12 * scale / _DENOM.get(k, 1.0)
+        # a Greek is compared relative to itself or, when it is much smaller
+        # than the price differences it is made of, to price / denominator
+        floor = scale / _DENOM.get(k, 1.0)
         e = abs(got[k] - ref[k]) / max(abs(ref[k]), floor) if not (
             math.isnan(got[k]) and math.isnan(ref[k])) else 0.0
         errs[k] = e
