@@ -246,6 +246,26 @@ int lsmc_backward(const void* d_S, const void* d_V, uint32_t n_paths,
                   const lsmc_contract* contract, int32_t basis, double* d_out,
                   double* d_beta, uint32_t* d_n_singular, void* cuda_stream);
 
+/* The backward pass of lsmc_backward for callers that cannot allocate device
+ * memory (another allocator owns the device, cudaMalloc/cudaFree would
+ * synchronise a latency-critical path, or the device is nearly full).  The
+ * paper has no counterpart; this is a deployment variant.  Same arguments,
+ * layouts and results as lsmc_backward; it calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Its scratch is a 16 MiB array that the library
+ * keeps in device memory on every device that loads it, until the process
+ * exits; a request needing more (about n_paths x 8 bytes plus n_steps x 64
+ * bytes in FP64) returns LSMC_ENOMEM before anything is launched.  The
+ * first call on a device looks up the array's device address (do that call
+ * before any stream capture).  All calls share the one array and leave their
+ * contents in it: calls whose work overlaps on the GPU (other streams, other
+ * host threads) race and must be serialised by the caller.  Returns after
+ * the work has finished (the call waits on cuda_stream). */
+int lsmc_backward_noalloc(const void* d_S, const void* d_V, uint32_t n_paths,
+                          uint32_t n_steps, int32_t precision,
+                          const lsmc_heston* model, const lsmc_contract* contract,
+                          int32_t basis, double* d_out, double* d_beta,
+                          uint32_t* d_n_singular, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -860,3 +860,40 @@ int lsmc_backward(const void* d_S, const void* d_V, uint32_t P, uint32_t N, int3
 }
 
 }  // extern "C"
+
+// ---- backward pass with caller-provided scratch ----------------------------------
+namespace lsmc {
+
+int backward_in_scratch(void* scratch, size_t scratch_bytes, const void* d_S, const void* d_V,
+                        uint32_t P, uint32_t N, int32_t precision, const lsmc_heston* m,
+                        const lsmc_contract* c, int32_t basis, double* d_out, double* d_beta,
+                        uint32_t* d_nsing, cudaStream_t s) {
+  if (!scratch || !d_S || !m || !c || !d_out) return LSMC_EINVAL;
+  if (basis == LSMC_BASIS_SV2 && !d_V) return LSMC_EINVAL;
+  const int scheme = m->xi > 0 ? LSMC_SCHEME_QE : LSMC_SCHEME_FT_EULER;
+  lsmc_plan* p = nullptr;
+  int rc = stage_plan(m, c->T, scheme, precision, P, N, basis, c, 0, 0, s, &p);
+  if (rc) return rc;
+  std::unique_ptr<lsmc_plan> owner(p);
+  if (p->L.total_bytes > scratch_bytes) return LSMC_ENOMEM;
+  p->run_forward = p->run_greeks = false;
+  p->dev = (char*)scratch;  // borrowed: never freed here
+  if (d_beta) rc = cuda_status(cudaMemsetAsync(d_beta, 0xFF, sizeof(double) * 6 * N, s));
+  if (rc == LSMC_OK) rc = plan_bind_and_upload(p, const_cast<void*>(d_S), const_cast<void*>(d_V), d_beta);
+  if (rc == LSMC_OK) rc = plan_enqueue(p);
+  if (rc == LSMC_OK)
+    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 4 * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, s));
+  if (rc == LSMC_OK && d_nsing)
+    rc = cuda_status(cudaMemcpyAsync(d_nsing, &p->d_results->singular, sizeof(uint32_t),
+                                     cudaMemcpyDeviceToDevice, s));
+  Control ctl{};
+  if (rc == LSMC_OK)
+    rc = cuda_status(cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+  if (rc == LSMC_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == LSMC_OK && ctl.error) rc = ctl.error == kDevErrTimeout ? LSMC_ETIMEOUT : LSMC_ECUDA;
+  p->dev = nullptr;
+  return rc;
+}
+
+}  // namespace lsmc

@@ -25,3 +25,14 @@ int backward_tile(bool fp64);
 int backward_occupancy(bool fp64, int basis);
 
 }  // namespace lsmc
+
+#include "../../include/lsmc.h"
+
+namespace lsmc {
+// Backward pass of lsmc_backward with every temporary placed in the given
+// device range instead of freshly allocated memory (capi.cpp).
+int backward_in_scratch(void* scratch, size_t scratch_bytes, const void* d_S, const void* d_V,
+                        uint32_t P, uint32_t N, int32_t precision, const lsmc_heston* m,
+                        const lsmc_contract* c, int32_t basis, double* d_out, double* d_beta,
+                        uint32_t* d_nsing, cudaStream_t s);
+}  // namespace lsmc

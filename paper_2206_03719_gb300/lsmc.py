@@ -32,7 +32,7 @@ EXPORTS = [
     "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
     "lsmc_plan_set_timing", "lsmc_plan_kernel_times",
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
-    "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_backward",
+    "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_backward", "lsmc_backward_noalloc",
 ]
 
 
@@ -146,6 +146,8 @@ def load(build_if_missing: bool = False):
                            ctypes.c_int),
             "lsmc_backward": ([vp, vp, u32, u32, i32, P(lsmc_heston), P(lsmc_contract), i32,
                                vp, vp, vp, vp], ctypes.c_int),
+            "lsmc_backward_noalloc": ([vp, vp, u32, u32, i32, P(lsmc_heston), P(lsmc_contract),
+                                       i32, vp, vp, vp, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -315,3 +317,11 @@ def lsmc_backward(d_S, d_V, n_paths, n_steps, precision, model, contract, basis,
     return check(load().lsmc_backward(d_S, d_V, n_paths, n_steps, precision, ctypes.byref(model),
                                       ctypes.byref(contract), basis, d_out, d_beta, d_n_singular,
                                       stream), "lsmc_backward")
+
+
+def lsmc_backward_noalloc(d_S, d_V, n_paths, n_steps, precision, model, contract, basis, d_out,
+                          d_beta=None, d_n_singular=None, stream=None):
+    return check(load().lsmc_backward_noalloc(d_S, d_V, n_paths, n_steps, precision,
+                                              ctypes.byref(model), ctypes.byref(contract), basis,
+                                              d_out, d_beta, d_n_singular, stream),
+                 "lsmc_backward_noalloc")
