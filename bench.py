@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="paper_fp64",
                     choices=["paper_fp64", "large_mixed", "paper_mixed"])
+    ap.add_argument("--paths", type=int, default=0,
+                    help="override the path count (profiling of a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -184,6 +186,8 @@ def run_reference(args, wl):
 def main():
     args = parse()
     wl = pick_workload(args.workload)
+    if args.paths:
+        wl = wl.replace(n_paths=args.paths, name=wl.name + "-paths%d" % args.paths)
     if args.impl == "reference":
         run_reference(args, wl)
         return

@@ -92,12 +92,15 @@ typedef struct lsmc_bumps {
 
 /* Greeks not requested are NaN.  status: 0, or 1 when at least one exercise
  * date had a singular regression (no exercise there; counted in
- * n_singular_solves over all revaluations). */
+ * n_singular_solves over all revaluations).  n_near_ties counts exercise
+ * decisions (over all revaluations) whose discounted payoff lay within a
+ * relative 1e-10 of the fitted continuation value: only such decisions can
+ * come out differently under another rounding of the same arithmetic. */
 typedef struct lsmc_result {
   double price, price_se, delta, gamma, vega, rho, theta, european_price;
   uint32_t n_singular_solves, n_revaluations;
   int32_t status;
-  int32_t reserved;
+  uint32_t n_near_ties;
 } lsmc_result;
 
 typedef struct lsmc_config {
@@ -237,8 +240,8 @@ int lsmc_paths(const lsmc_heston* model, double T, int32_t scheme,
                uint64_t seed, uint32_t stream_id, void* d_S, void* d_V,
                void* cuda_stream);
 /* Longstaff-Schwartz backward pass over given paths (same layout as
- * lsmc_paths output).  d_out (device, 4 doubles): price, price_se,
- * european_price, continuation value.  d_beta (device, optional):
+ * lsmc_paths output).  d_out (device, 5 doubles): price, price_se,
+ * european_price, continuation value, near-tie decisions (see lsmc_result).  d_beta (device, optional):
  * n_steps x 6 doubles, row n = coefficients at date n (NaN if none).
  * d_n_singular (device, optional): 1 uint32. */
 int lsmc_backward(const void* d_S, const void* d_V, uint32_t n_paths,

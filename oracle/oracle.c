@@ -311,7 +311,9 @@ int orc_paths(const orc_heston* m, double T, int scheme, int grid,
 /* for early exercise; Sec. 2.2.1: a reduction followed by a quadratic      */
 /* curve fit).  Readings: exercise dates t_1..t_N; in-the-money means a     */
 /* strictly positive payoff; only those paths enter the regression; the     */
-/* basis is scaled, x = S/K and w = v/theta; the regression target is the   */
+/* basis is scaled and centred, x = S/K - 1 and w = v/theta - 1 (the same   */
+/* fitted function as the raw monomials of S and v, with normal equations  */
+/* far better conditioned); the regression target is the                    */
 /* cash flow discounted to the current date; exercise when the payoff       */
 /* strictly exceeds the fitted continuation value; a date with fewer        */
 /* in-the-money paths than basis functions, or a Cholesky pivot at or       */
@@ -324,7 +326,7 @@ static double orc_payoff(int type, double K, double s) {
 
 static int orc_basis(int basis, double s, double v, double K, double theta,
                      double phi[6]) {
-  const double x = s / K, w = v / theta;
+  const double x = s / K - 1.0, w = v / theta - 1.0;
   phi[0] = 1.0;
   phi[1] = x;
   phi[2] = x * x;

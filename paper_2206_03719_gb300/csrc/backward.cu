@@ -129,13 +129,9 @@ __global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst) {
 
 namespace {
 
-// Sum over the warp.  Double precision: plain shuffles.  Single precision:
-// the partial sums travel as unevaluated float pairs (hi + lo, Knuth's
-// two-sum at every level), so the warp total keeps about 44 bits; it is
-// returned in double.
-__device__ __forceinline__ double warp_total(double v) { return warp_sum(v); }
-__device__ __forceinline__ double warp_total(float v) {
-  float hi = v, lo = 0.0f;
+// Sum over the warp of unevaluated float pairs (hi + lo, Knuth's two-sum at
+// every level): the total keeps about 44 bits and is returned in double.
+__device__ __forceinline__ double warp_total_pair(float hi, float lo) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
     const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
@@ -152,18 +148,61 @@ __device__ __forceinline__ double warp_total(float v) {
 
 }  // namespace
 
+namespace {
+
+// Per-thread moment sums across the sub-tiles of a job.  Double precision
+// adds into one double per sum.  Single precision sums at most PPT paths in
+// float, then folds that partial into an unevaluated pair (hi + lo) with
+// Knuth's two-sum, so a job of many sub-tiles keeps about 44 bits.
+template <typename Real, int NA> struct Acc;
+template <int NA> struct Acc<double, NA> {
+  double s[NA];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) s[i] = 0.0;
+  }
+  __device__ __forceinline__ double* target() { return s; }
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ double total(int i) const { return warp_sum(s[i]); }
+};
+template <int NA> struct Acc<float, NA> {
+  float hi[NA], lo[NA], t[NA];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) hi[i] = lo[i] = t[i] = 0.0f;
+  }
+  __device__ __forceinline__ float* target() { return t; }
+  __device__ __forceinline__ void fold() {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const float sum = __fadd_rn(hi[i], t[i]);
+      const float bb = __fsub_rn(sum, hi[i]);
+      const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(sum, bb)), __fsub_rn(t[i], bb));
+      hi[i] = sum;
+      lo[i] = __fadd_rn(lo[i], err);
+      t[i] = 0.0f;
+    }
+  }
+  __device__ __forceinline__ double total(int i) const { return warp_total_pair(hi[i], lo[i]); }
+};
+
+}  // namespace
+
 // Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
 // current exercise time tau.  The regression target of date n, the cash flow
 // discounted to t_n, is Z exp(r n dt): the same factor for every path, so the
 // regression runs on Z and the exercise test compares h exp(-r n dt) with the
 // fitted value in the same units.  Z changes only where a path exercises.
+//
+// A job covers `a.sub` sub-tiles of kBlock * PPT paths: the wait for the
+// previous round, the block reduction and the arrival are paid once per job.
 template <typename Real, int BASIS, int PPT>
 __global__ void __launch_bounds__(kBlock)
 backward_kernel(BwdArgs a) {
   constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
   constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
   constexpr int NA = NM + NB;                         // register sums
-  constexpr int TILE = kBlock * PPT;
+  constexpr int TILE0 = kBlock * PPT;
   constexpr int NW = kBlock / 32;
 
   __shared__ JobInfo s_job;
@@ -175,6 +214,7 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_sum[kNSum];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t sub = a.sub;
   unsigned long long next = 0;
   if (tid == 0) next = atomicAdd(&a.ctl->next_job, 1ull);
 
@@ -225,8 +265,9 @@ backward_kernel(BwdArgs a) {
     // regression date of this round (0 for the estimator round)
     const uint32_t n = european ? 0 : N - 1 - r;
     const bool first = european || r == 0;  // cash flows start at the maturity payoff
+    const uint32_t tile_base = ji.tile * (sub * TILE0);
 
-    // ---- 1. wait for the exercise rule of date n + 1 -----------------------
+    // ---- wait for the exercise rule of date n + 1 ---------------------------
     if (!first) {
       if (tid == 0) {
         int ok = 1;
@@ -253,159 +294,165 @@ backward_kernel(BwdArgs a) {
       if (s_last < 0) return;
     }
 
-    const uint32_t p_base = ji.tile * TILE + tid;
-    Real z[PPT];
-    double euro = 0.0;
-    if (first) {
-      // the discount factor multiplies in double and the product is rounded
-      // once, so single-precision cash flows carry no shared per-date bias
-      const Real sN = (Real)stab[N];
-      const double dN = dtab[N];
-      const Real* EN = E + (size_t)(N - 1) * ld;
+    // per-job constants
+    const int bok = first ? 0 : s_beta_ok;
+    Real b[6];
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const uint32_t p = p_base + k * kBlock;
-        z[k] = (Real)0;
-        if (p < P) {
-          z[k] = (Real)((double)payoff<Real>(type, K, sN * EN[p]) * dN);
-          euro += (double)z[k];
-          if (!final_job) Z[p] = z[k];
+    for (int i = 0; i < 6; ++i) b[i] = first ? (Real)0 : (Real)s_beta[i];
+    const Real s1 = (Real)stab[n + 1], d1 = (Real)dtab[n + 1];
+    const double d1d = dtab[n + 1];
+    const Real sN = (Real)stab[N];
+    const double dN = dtab[N];
+    const Real s0 = (Real)stab[n];
+    const Real* EN = E + (size_t)(N - 1) * ld;
+    const Real* E1 = E + (size_t)n * ld;                        // date n + 1
+    const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
+    const Real* E0 = final_job ? nullptr : E + (size_t)(n - 1) * ld;  // date n
+    const Real* V0 = (BASIS == kBasisSV2 && !final_job) ? V + (size_t)(n - 1) * ld : nullptr;
+
+    Acc<Real, NA> acc;
+    acc.zero();
+    double euro = 0.0, ties = 0.0, sy = 0.0, sy2 = 0.0;
+
+    for (uint32_t sb = 0; sb < sub; ++sb) {
+      const uint32_t p_base = tile_base + sb * TILE0 + tid;
+      if (p_base >= P) break;
+      Real z[PPT];
+      if (first) {
+        // the discount factor multiplies in double and the product is
+        // rounded once, so single-precision cash flows carry no shared
+        // per-date bias
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const uint32_t p = p_base + k * kBlock;
+          z[k] = (Real)0;
+          if (p < P) {
+            z[k] = (Real)((double)payoff<Real>(type, K, sN * EN[p]) * dN);
+            euro += (double)z[k];
+            if (!final_job) Z[p] = z[k];
+          }
+        }
+      } else {
+        // exercise at date n + 1 where the discounted payoff beats the
+        // fitted continuation value (basis centred at the strike and theta)
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const uint32_t p = p_base + k * kBlock;
+          z[k] = (Real)0;
+          if (p < P) {
+            z[k] = ld_cg(Z + p);
+            if (bok) {
+              const Real S = s1 * E1[p];
+              const Real h = payoff<Real>(type, K, S);
+              if (h > (Real)0) {
+                const Real x = fma(S, invK, (Real)-1);
+                Real c = fma(fma(b[2], x, b[1]), x, b[0]);
+                if (BASIS == kBasisSV2) {
+                  const Real w = fma(V1[p], invTh, (Real)-1);
+                  c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
+                }
+                const Real hd = h * d1;
+                if (fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd)) ties += 1.0;
+                if (hd > c) {
+                  const Real hz = (Real)((double)h * d1d);
+                  z[k] = hz;
+                  if (!final_job) Z[p] = hz;
+                }
+              }
+            }
+          }
         }
       }
-    } else {
-      // exercise at date n + 1 where the discounted payoff beats the fitted
-      // continuation value
-      const int bok = s_beta_ok;
-      Real b[6];
+
+      if (final_job) {
 #pragma unroll
-      for (int i = 0; i < 6; ++i) b[i] = (Real)s_beta[i];
-      const Real s1 = (Real)stab[n + 1], d1 = (Real)dtab[n + 1];
-      const double d1d = dtab[n + 1];
-      const Real* E1 = E + (size_t)n * ld;
-      const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
+        for (int k = 0; k < PPT; ++k) {
+          const uint32_t p = p_base + k * kBlock;
+          if (p < P) {
+            const double zv = (double)z[k];
+            sy += zv;
+            sy2 += zv * zv;
+          }
+        }
+      } else {
+        // moment sums of date n over the in-the-money paths
+        Real* t = acc.target();
 #pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const uint32_t p = p_base + k * kBlock;
-        z[k] = (Real)0;
-        if (p < P) {
-          z[k] = ld_cg(Z + p);
-          if (bok) {
-            const Real S = s1 * E1[p];
+        for (int k = 0; k < PPT; ++k) {
+          const uint32_t p = p_base + k * kBlock;
+          if (p < P) {
+            const Real yv = z[k];
+            const Real S = s0 * E0[p];
             const Real h = payoff<Real>(type, K, S);
             if (h > (Real)0) {
-              // continuation value in the basis centred at the strike and at
-              // theta (x - 1, w - 1): same fitted function, far less
-              // cancellation when evaluated in single precision
-              const Real x = fma(S, invK, (Real)-1);
-              Real c = fma(fma(b[2], x, b[1]), x, b[0]);
+              const Real x = fma(S, invK, (Real)-1), x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
+              t[0] += (Real)1;
+              t[1] += x;
+              t[2] += x2;
+              t[3] += x3;
+              t[4] += x4;
               if (BASIS == kBasisSV2) {
-                const Real w = fma(V1[p], invTh, (Real)-1);
-                c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
-              }
-              if (h * d1 > c) {
-                const Real hz = (Real)((double)h * d1d);
-                z[k] = hz;
-                if (!final_job) Z[p] = hz;
+                const Real w = fma(V0[p], invTh, (Real)-1), w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
+                const Real xw = x * w;
+                t[mono(0, 1)] += w;
+                t[mono(1, 1)] += xw;
+                t[mono(2, 1)] += x2 * w;
+                t[mono(3, 1)] += x3 * w;
+                t[mono(0, 2)] += w2;
+                t[mono(1, 2)] += x * w2;
+                t[mono(2, 2)] += x2 * w2;
+                t[mono(0, 3)] += w3;
+                t[mono(1, 3)] += x * w3;
+                t[mono(0, 4)] += w4;
+                t[NM + 0] += yv;
+                t[NM + 1] += x * yv;
+                t[NM + 2] += x2 * yv;
+                t[NM + 3] += w * yv;
+                t[NM + 4] += xw * yv;
+                t[NM + 5] += w2 * yv;
+              } else {
+                t[NM + 0] += yv;
+                t[NM + 1] += x * yv;
+                t[NM + 2] += x2 * yv;
               }
             }
           }
         }
+        acc.fold();
       }
     }
 
+    // ---- block reduction into the tile partial --------------------------------
     if (final_job) {
-      // ---- estimator at t_0 -------------------------------------------------
-      double sy = 0.0, sy2 = 0.0;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const uint32_t p = p_base + k * kBlock;
-        if (p < P) {
-          const double zv = (double)z[k];
-          sy += zv;
-          sy2 += zv * zv;
-        }
-      }
       sy = warp_sum(sy);
       sy2 = warp_sum(sy2);
-      euro = warp_sum(euro);
-      if (lane == 0) {
-        s_red[warp][kSlotSumY] = sy;
-        s_red[warp][kSlotSumY2] = sy2;
-        s_red[warp][kSlotEuro] = euro;
-      }
-      __syncthreads();
-      if (tid >= kSlotEuro && tid < kNSum) {
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += s_red[w][tid];
-        I.partial[(size_t)ji.tile * kNSum + tid] = s;
-      }
     } else {
-      // ---- moment sums of date n over the in-the-money paths -----------------
-      const Real s0 = (Real)stab[n];
-      const Real* E0 = E + (size_t)(n - 1) * ld;
-      const Real* V0 = BASIS == kBasisSV2 ? V + (size_t)(n - 1) * ld : nullptr;
-      Real acc[NA];
-#pragma unroll
-      for (int i = 0; i < NA; ++i) acc[i] = (Real)0;
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const uint32_t p = p_base + k * kBlock;
-        if (p < P) {
-          const Real yv = z[k];
-          const Real S = s0 * E0[p];
-          const Real h = payoff<Real>(type, K, S);
-          if (h > (Real)0) {
-            const Real x = S * invK, x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
-            acc[0] += (Real)1;
-            acc[1] += x;
-            acc[2] += x2;
-            acc[3] += x3;
-            acc[4] += x4;
-            if (BASIS == kBasisSV2) {
-              const Real w = V0[p] * invTh, w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
-              const Real xw = x * w;
-              acc[mono(0, 1)] += w;
-              acc[mono(1, 1)] += xw;
-              acc[mono(2, 1)] += x2 * w;
-              acc[mono(3, 1)] += x3 * w;
-              acc[mono(0, 2)] += w2;
-              acc[mono(1, 2)] += x * w2;
-              acc[mono(2, 2)] += x2 * w2;
-              acc[mono(0, 3)] += w3;
-              acc[mono(1, 3)] += x * w3;
-              acc[mono(0, 4)] += w4;
-              acc[NM + 0] += yv;
-              acc[NM + 1] += x * yv;
-              acc[NM + 2] += x2 * yv;
-              acc[NM + 3] += w * yv;
-              acc[NM + 4] += xw * yv;
-              acc[NM + 5] += w2 * yv;
-            } else {
-              acc[NM + 0] += yv;
-              acc[NM + 1] += x * yv;
-              acc[NM + 2] += x2 * yv;
-            }
-          }
-        }
-      }
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
-        const double v = warp_total(acc[i]);
+        const double v = acc.total(i);
         if (lane == 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
       }
-      euro = warp_sum(euro);
-      if (lane == 0) s_red[warp][kSlotEuro] = euro;
-      __syncthreads();
-      if (tid < kNSum) {
-        const bool used = tid < NM || (tid >= kSlotRhs && tid < kSlotRhs + NB) || tid == kSlotEuro;
-        double s = 0.0;
-        if (used)
-          for (int w = 0; w < NW; ++w) s += s_red[w][tid];
-        I.partial[(size_t)ji.tile * kNSum + tid] = s;
-      }
+    }
+    euro = warp_sum(euro);
+    ties = warp_sum(ties);
+    if (lane == 0) {
+      s_red[warp][kSlotEuro] = euro;
+      s_red[warp][kSlotTies] = ties;
+      s_red[warp][kSlotSumY] = sy;
+      s_red[warp][kSlotSumY2] = sy2;
+    }
+    __syncthreads();
+    if (tid < kNSum) {
+      const bool used = final_job ? tid >= kSlotEuro
+                                  : (tid < NM || (tid >= kSlotRhs && tid < kSlotRhs + NB) ||
+                                     tid == kSlotEuro || tid == kSlotTies);
+      double v = 0.0;
+      if (used)
+        for (int w = 0; w < NW; ++w) v += s_red[w][tid];
+      I.partial[(size_t)ji.tile * kNSum + tid] = v;
     }
 
-    // ---- arrive; the last tile of this round reduces and solves --------------
+    // ---- arrive; the last tile of this round reduces and solves ---------------
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -422,16 +469,16 @@ backward_kernel(BwdArgs a) {
       const uint32_t tiles = I.tiles;
       const uint32_t per = (tiles + NW - 1) / NW;
       if (lane < kNSum) {
-        double s = 0.0;
+        double v = 0.0;
         const uint32_t t0 = warp * per, t1 = min(tiles, t0 + per);
-        for (uint32_t t = t0; t < t1; ++t) s += __ldcg(&I.partial[(size_t)t * kNSum + lane]);
-        s_chunk[warp][lane] = s;
+        for (uint32_t t = t0; t < t1; ++t) v += __ldcg(&I.partial[(size_t)t * kNSum + lane]);
+        s_chunk[warp][lane] = v;
       }
       __syncthreads();
       if (tid < kNSum) {
-        double s = 0.0;
-        for (int w = 0; w < NW; ++w) s += s_chunk[w][tid];
-        s_sum[tid] = s;
+        double v = 0.0;
+        for (int w = 0; w < NW; ++w) v += s_chunk[w][tid];
+        s_sum[tid] = v;
       }
       __syncthreads();
     }
@@ -447,6 +494,7 @@ backward_kernel(BwdArgs a) {
         res.euro = euro_sum / Pd;
         res.price = european ? mean : fmax(I.h0, mean);
         res.itm = __ldcg(&st->itm);
+        res.ties = __ldcg(&st->ties) + s_sum[kSlotTies];
         res.singular = __ldcg(&st->singular);
         res.done = 1;
         a.results[I.out_index] = res;
@@ -455,13 +503,10 @@ backward_kernel(BwdArgs a) {
         const bool ok = solve_normal_equations(NB, s_sum, s_sum + kSlotRhs, beta);
         if (r == 0) st->euro_sum = s_sum[kSlotEuro];
         st->itm = __ldcg(&st->itm) + s_sum[0];
+        st->ties = __ldcg(&st->ties) + s_sum[kSlotTies];
         if (!ok) st->singular = __ldcg(&st->singular) + 1u;
         st->beta_ok = ok ? 1u : 0u;
-        // publish the coefficients re-expanded around x = 1, w = 1
-        const double bc[6] = {beta[0] + beta[1] + beta[2] + beta[3] + beta[4] + beta[5],
-                              beta[1] + 2.0 * beta[2] + beta[4], beta[2],
-                              beta[3] + beta[4] + 2.0 * beta[5], beta[4], beta[5]};
-        for (int i = 0; i < 6; ++i) st->beta[i] = ok ? bc[i] : 0.0;
+        for (int i = 0; i < 6; ++i) st->beta[i] = ok ? beta[i] : 0.0;
         if (I.beta_hist) {
           // coefficients in the units of the cash flow discounted to t_n
           const double to_n = 1.0 / dtab[n];
@@ -511,12 +556,17 @@ __global__ void greeks_kernel(const GreekOut* __restrict__ g,
   if ((G.mask & 16u) && G.res[kScTDn] >= 0)
     o.theta = (V(kScTDn) - V(kScTUp)) / (2.0 * G.dT);
   uint32_t sing = 0, nrev = 0;
+  double ties = 0.0;
   for (int k = 0; k < kScCount; ++k)
-    if (G.res[k] >= 0) { sing += res[G.res[k]].singular; ++nrev; }
+    if (G.res[k] >= 0) {
+      sing += res[G.res[k]].singular;
+      ties += res[G.res[k]].ties;
+      ++nrev;
+    }
   o.n_singular_solves = sing;
   o.n_revaluations = nrev;
   o.status = sing ? 1 : 0;
-  o.reserved = 0;
+  o.n_near_ties = (uint32_t)ties;
   out[i] = o;
 }
 

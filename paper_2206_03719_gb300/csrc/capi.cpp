@@ -27,6 +27,8 @@ using namespace lsmc;
 
 static_assert(sizeof(DevResult) == sizeof(lsmc_result), "result layout");
 static_assert(offsetof(DevResult, status) == offsetof(lsmc_result, status), "result layout");
+static_assert(offsetof(DevResult, n_near_ties) == offsetof(lsmc_result, n_near_ties), "result layout");
+static_assert(offsetof(BwdResult, ties) == 4 * sizeof(double), "stage output layout");
 
 namespace {
 
@@ -58,6 +60,7 @@ struct lsmc_ctx {
   uint32_t max_inflight = 8, queue_capacity = 4096;
   int num_sms = 0;
   int occ[2][2] = {{0, 0}, {0, 0}};
+  uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
   // serving
   std::mutex mu;
   std::condition_variable cv, done_cv;
@@ -224,6 +227,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
+  p->ba.sub = std::max<uint32_t>(1, L.opt.sub);
   const int occ = occupancy(p->ctx, fp64, L.opt.basis);
   const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
@@ -298,6 +302,11 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
   if (!p) return LSMC_ENOMEM;
   p->ctx = ctx;
   p->stream = stream;
+  {
+    const bool fp64 = o.precision == LSMC_FP64;
+    const uint32_t ctas = (uint32_t)occupancy(ctx, fp64, o.basis) * (uint32_t)sm_count(ctx);
+    o.sub = ctx && ctx->sub_override ? ctx->sub_override : choose_sub(reqs, n, fp64, ctas);
+  }
   rc = build_layout(reqs, n, o, &p->L);
   if (rc) return rc;
   rc = plan_alloc(p.get(), use_arena, false);
@@ -842,8 +851,8 @@ int lsmc_backward(const void* d_S, const void* d_V, uint32_t P, uint32_t N, int3
   if (rc == LSMC_OK) rc = plan_bind_and_upload(p, const_cast<void*>(d_S), const_cast<void*>(d_V), d_beta);
   if (rc == LSMC_OK) rc = plan_enqueue(p);
   if (rc == LSMC_OK) {
-    // price, se, european, continuation are the first four fields
-    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 4 * sizeof(double),
+    // price, se, european, continuation, near ties are the first five fields
+    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 5 * sizeof(double),
                                      cudaMemcpyDeviceToDevice, p->stream));
     if (rc == LSMC_OK && d_nsing)
       rc = cuda_status(cudaMemcpyAsync(d_nsing, &p->d_results->singular, sizeof(uint32_t),
@@ -882,7 +891,7 @@ int backward_in_scratch(void* scratch, size_t scratch_bytes, const void* d_S, co
   if (rc == LSMC_OK) rc = plan_bind_and_upload(p, const_cast<void*>(d_S), const_cast<void*>(d_V), d_beta);
   if (rc == LSMC_OK) rc = plan_enqueue(p);
   if (rc == LSMC_OK)
-    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 4 * sizeof(double),
+    rc = cuda_status(cudaMemcpyAsync(d_out, p->d_results, 5 * sizeof(double),
                                      cudaMemcpyDeviceToDevice, s));
   if (rc == LSMC_OK && d_nsing)
     rc = cuda_status(cudaMemcpyAsync(d_nsing, &p->d_results->singular, sizeof(uint32_t),

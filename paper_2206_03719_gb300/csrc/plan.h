@@ -15,13 +15,18 @@ namespace lsmc {
 
 constexpr int kBlock = 256;      // threads per CTA (forward and backward)
 constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
-constexpr int kNSum = 24;        // doubles per tile partial
+constexpr int kNSum = 25;        // doubles per tile partial
 // partial layout: 15 monomials x^a w^b (a + b <= 4), 6 right-hand sides,
-// European payoff sum, sum of Y, sum of Y^2
+// European payoff sum, sum of Y, sum of Y^2, near-tie count
 constexpr int kSlotRhs = 15;
 constexpr int kSlotEuro = 21;
 constexpr int kSlotSumY = 22;
 constexpr int kSlotSumY2 = 23;
+constexpr int kSlotTies = 24;
+// an exercise decision whose discounted payoff lies within this relative
+// distance of the fitted continuation value is counted as a near tie: two
+// correct implementations that round differently may decide it differently
+constexpr double kTieRel = 1e-10;
 
 enum : int32_t { kSchemeQE = 0, kSchemeFT = 1 };
 enum : int32_t { kPut = 0, kCall = 1 };
@@ -85,10 +90,11 @@ struct BwdState {
   double beta[6];
   double euro_sum;
   double itm;         // in-the-money path-steps seen by the regressions
+  double ties;        // near-tie exercise decisions
 };
 
 struct BwdResult {
-  double price, se, euro, cont, itm;
+  double price, se, euro, cont, ties, itm;
   uint32_t singular;
   uint32_t done;
 };
@@ -110,6 +116,7 @@ struct BwdArgs {
   unsigned long long total_jobs;
   unsigned long long timeout_ns;
   uint32_t n_rounds, n_inst;
+  uint32_t sub;              // sub-tiles of kBlock * PPT paths per job
 };
 
 // ---- Greeks ---------------------------------------------------------------
@@ -118,7 +125,7 @@ struct DevResult {
   double price, price_se, delta, gamma, vega, rho, theta, european_price;
   uint32_t n_singular_solves, n_revaluations;
   int32_t status;
-  int32_t reserved;
+  uint32_t n_near_ties;
 };
 
 struct GreekOut {

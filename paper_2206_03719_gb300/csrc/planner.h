@@ -53,7 +53,13 @@ struct PlanOptions {
   int scheme = LSMC_SCHEME_QE;
   int basis = LSMC_BASIS_S2;
   bool raw_paths = false;       // stage entry point: E rows are S itself
+  uint32_t sub = 1;             // sub-tiles per backward job
 };
+
+// Sub-tiles per backward job so that the busiest round has about
+// jobs_per_cta jobs for each of `ctas` resident CTAs.
+uint32_t choose_sub(const lsmc_request* reqs, size_t n, bool fp64, uint32_t ctas,
+                    uint32_t jobs_per_cta = 4);
 
 // Sizes and host tables of one launch; device pointers are bound later.
 struct PlanLayout {

@@ -58,10 +58,10 @@ class lsmc_result(ctypes.Structure):
                 ("price", "price_se", "delta", "gamma", "vega", "rho", "theta",
                  "european_price")] + [
         ("n_singular_solves", ctypes.c_uint32), ("n_revaluations", ctypes.c_uint32),
-        ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+        ("status", ctypes.c_int32), ("n_near_ties", ctypes.c_uint32)]
 
     def as_dict(self):
-        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
 class lsmc_config(ctypes.Structure):

@@ -34,6 +34,18 @@ def oracle_for(wl, grid=oracle.GRID_F64, n_threads=None):
         stream=wl.stream, n_threads=n_threads)
 
 
+FP64_TOL = 1e-10     # FP64 GPU vs FP64 oracle on identical streams
+FLIP_TOL = 1e-4      # the same when near-tie exercise decisions occurred
+
+
+def parity_tol(n_near_ties):
+    """1e-10 when no exercise decision was within rounding reach of its
+    threshold (then both implementations must take the same decisions);
+    otherwise decisions may legitimately differ and each difference moves a
+    price at first order: the bound falls back to 1e-4."""
+    return FP64_TOL if int(n_near_ties) == 0 else FLIP_TOL
+
+
 def rel_err(a, b):
     """|a - b| / max(|b|, 1e-12); NaN on both sides counts as equal."""
     if math.isnan(b) and math.isnan(a):

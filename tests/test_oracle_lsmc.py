@@ -27,8 +27,8 @@ def _payoff(S, K, put):
     return np.maximum(K - S, 0.0) if put else np.maximum(S - K, 0.0)
 
 
-def _basis(S, V, K, theta, basis):
-    x, w = S / K, V / theta
+def _basis(S, V, K, theta, basis, centre=1.0):
+    x, w = S / K - centre, V / theta - centre
     cols = [np.ones_like(x), x, x * x]
     if basis == oracle.BASIS_SV2:
         cols += [w, x * w, w * w]
@@ -95,7 +95,7 @@ def test_regression_invariant_under_basis_scaling():
     n = 3
     itm = S[n] < 100.0
     X = _basis(S[n][itm], V[n][itm], 100.0, 0.04, oracle.BASIS_SV2)
-    Xu = _basis(S[n][itm], V[n][itm], 1.0, 1.0, oracle.BASIS_SV2)
+    Xu = _basis(S[n][itm], V[n][itm], 1.0, 1.0, oracle.BASIS_SV2, centre=0.0)
     fitted = X @ d["beta"][n]
     # regression target at date n rebuilt from the stopping times
     ex = d["exercise"]

@@ -37,7 +37,7 @@ def _paths(torch, model, P, N, precision, seed):
 
 
 def _run(torch, fn, S, V, P, N, precision, model, K, basis):
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
     beta = torch.zeros((N, 6), dtype=torch.float64, device="cuda")
     ns = torch.zeros(1, dtype=torch.int32, device="cuda")
     c = L.lsmc_contract(L.LSMC_PUT, L.LSMC_AMERICAN, K, 1.0)
@@ -79,7 +79,7 @@ def test_noalloc_rejects_requests_beyond_its_scratch(torch):
     P, N = 1 << 22, 1
     S = torch.full((N + 1, P), 100.0, dtype=torch.float64, device="cuda")
     V = torch.full((N + 1, P), 0.04, dtype=torch.float64, device="cuda")
-    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
     c = L.lsmc_contract(L.LSMC_PUT, L.LSMC_AMERICAN, 100.0, 1.0)
     with pytest.raises(L.LsmcError) as e:
         L.lsmc_backward_noalloc(S.data_ptr(), V.data_ptr(), P, N, L.LSMC_FP64,
