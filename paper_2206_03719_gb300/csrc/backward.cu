@@ -129,21 +129,31 @@ __global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst) {
 
 namespace {
 
-// Sum over the warp of unevaluated float pairs (hi + lo, Knuth's two-sum at
-// every level): the total keeps about 44 bits and is returned in double.
-__device__ __forceinline__ double warp_total_pair(float hi, float lo) {
+// Knuth's two-sum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Sum of unevaluated float pairs (hi + lo): two-sum of the high parts, the
+// low parts added to the error, renormalised.  About 44 bits survive.
+__device__ __forceinline__ float2 pair_add(float2 x, float2 y) {
+  float s, e;
+  two_sum(x.x, y.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(x.y, y.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+
+__device__ __forceinline__ float2 warp_pair_sum(float2 v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, hi, off);
-    const float ol = __shfl_xor_sync(0xffffffffu, lo, off);
-    const float s = __fadd_rn(hi, oh);
-    const float bb = __fsub_rn(s, hi);
-    float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
-    e = __fadd_rn(e, __fadd_rn(lo, ol));
-    hi = __fadd_rn(s, e);
-    lo = __fsub_rn(e, __fsub_rn(hi, s));
+    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, off),
+                                 __shfl_xor_sync(0xffffffffu, v.y, off));
+    v = pair_add(v, o);
   }
-  return (double)hi + (double)lo;
+  return v;
 }
 
 }  // namespace
@@ -163,7 +173,6 @@ template <int NA> struct Acc<double, NA> {
   }
   __device__ __forceinline__ double* target() { return s; }
   __device__ __forceinline__ void fold() {}
-  __device__ __forceinline__ double total(int i) const { return warp_sum(s[i]); }
 };
 template <int NA> struct Acc<float, NA> {
   float hi[NA], lo[NA], t[NA];
@@ -175,15 +184,13 @@ template <int NA> struct Acc<float, NA> {
   __device__ __forceinline__ void fold() {
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const float sum = __fadd_rn(hi[i], t[i]);
-      const float bb = __fsub_rn(sum, hi[i]);
-      const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(sum, bb)), __fsub_rn(t[i], bb));
+      float sum, err;
+      two_sum(hi[i], t[i], sum, err);
       hi[i] = sum;
       lo[i] = __fadd_rn(lo[i], err);
       t[i] = 0.0f;
     }
   }
-  __device__ __forceinline__ double total(int i) const { return warp_total_pair(hi[i], lo[i]); }
 };
 
 }  // namespace
@@ -210,11 +217,14 @@ backward_kernel(BwdArgs a) {
   __shared__ int s_beta_ok;
   __shared__ int s_last;
   __shared__ double s_red[NW][kNSum];
+  __shared__ float2 s_redf[NW][NA];   // single precision: per-warp pair sums
   __shared__ double s_chunk[NW][kNSum];
   __shared__ double s_sum[kNSum];
+  __shared__ Real s_c[16];            // per-job constants, converted once
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sub = a.sub;
+  constexpr bool kSingle = sizeof(Real) == 4;
   unsigned long long next = 0;
   if (tid == 0) next = atomicAdd(&a.ctl->next_job, 1ull);
 
@@ -259,7 +269,6 @@ backward_kernel(BwdArgs a) {
     const double* stab = I.scale_tab;          // S multipliers, dates 0..N
     const double* dtab = I.scale_tab + N + 1;  // discount to t_0, dates 0..N
     const int type = I.type;
-    const Real K = (Real)I.K, invK = (Real)I.invK, invTh = (Real)I.inv_theta;
     const bool european = I.style == kEuropean;
     const bool final_job = european || r == N - 1;
     // regression date of this round (0 for the estimator round)
@@ -294,16 +303,30 @@ backward_kernel(BwdArgs a) {
       if (s_last < 0) return;
     }
 
-    // per-job constants
+    // per-job constants, converted to the working precision once per job
+    if (tid < 13) {
+      double v;
+      switch (tid) {
+        case 6: v = stab[n + 1]; break;
+        case 7: v = dtab[n + 1]; break;
+        case 8: v = stab[N]; break;
+        case 9: v = stab[n]; break;
+        case 10: v = I.K; break;
+        case 11: v = I.invK; break;
+        case 12: v = I.inv_theta; break;
+        default: v = first ? 0.0 : s_beta[tid]; break;
+      }
+      s_c[tid] = (Real)v;
+    }
+    __syncthreads();
     const int bok = first ? 0 : s_beta_ok;
     Real b[6];
 #pragma unroll
-    for (int i = 0; i < 6; ++i) b[i] = first ? (Real)0 : (Real)s_beta[i];
-    const Real s1 = (Real)stab[n + 1], d1 = (Real)dtab[n + 1];
+    for (int i = 0; i < 6; ++i) b[i] = s_c[i];
+    const Real s1 = s_c[6], d1 = s_c[7], sN = s_c[8], s0 = s_c[9];
+    const Real K = s_c[10], invK = s_c[11], invTh = s_c[12];
     const double d1d = dtab[n + 1];
-    const Real sN = (Real)stab[N];
     const double dN = dtab[N];
-    const Real s0 = (Real)stab[n];
     const Real* EN = E + (size_t)(N - 1) * ld;
     const Real* E1 = E + (size_t)n * ld;                        // date n + 1
     const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
@@ -312,11 +335,36 @@ backward_kernel(BwdArgs a) {
 
     Acc<Real, NA> acc;
     acc.zero();
-    double euro = 0.0, ties = 0.0, sy = 0.0, sy2 = 0.0;
+    double euro = 0.0, sy = 0.0, sy2 = 0.0;
+    uint32_t ties = 0;
 
     for (uint32_t sb = 0; sb < sub; ++sb) {
       const uint32_t p_base = tile_base + sb * TILE0 + tid;
       if (p_base >= P) break;
+      // every load of the sub-tile is issued before any arithmetic, so each
+      // thread has up to 5 * PPT independent loads in flight
+      Real zr[PPT], e1[PPT], v1[PPT], e0[PPT], v0[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const uint32_t p = p_base + k * kBlock;
+        const bool valid = p < P;
+        zr[k] = e1[k] = v1[k] = e0[k] = v0[k] = (Real)0;
+        if (valid) {
+          if (first) {
+            e1[k] = EN[p];
+          } else {
+            zr[k] = ld_cg(Z + p);
+            if (bok) {
+              e1[k] = E1[p];
+              if (BASIS == kBasisSV2) v1[k] = V1[p];
+            }
+          }
+          if (!final_job) {
+            e0[k] = E0[p];
+            if (BASIS == kBasisSV2) v0[k] = V0[p];
+          }
+        }
+      }
       Real z[PPT];
       if (first) {
         // the discount factor multiplies in double and the product is
@@ -327,7 +375,7 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           z[k] = (Real)0;
           if (p < P) {
-            z[k] = (Real)((double)payoff<Real>(type, K, sN * EN[p]) * dN);
+            z[k] = (Real)((double)payoff<Real>(type, K, sN * e1[k]) * dN);
             euro += (double)z[k];
             if (!final_job) Z[p] = z[k];
           }
@@ -338,26 +386,23 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
-          z[k] = (Real)0;
-          if (p < P) {
-            z[k] = ld_cg(Z + p);
-            if (bok) {
-              const Real S = s1 * E1[p];
-              const Real h = payoff<Real>(type, K, S);
-              if (h > (Real)0) {
-                const Real x = fma(S, invK, (Real)-1);
-                Real c = fma(fma(b[2], x, b[1]), x, b[0]);
-                if (BASIS == kBasisSV2) {
-                  const Real w = fma(V1[p], invTh, (Real)-1);
-                  c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
-                }
-                const Real hd = h * d1;
-                if (fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd)) ties += 1.0;
-                if (hd > c) {
-                  const Real hz = (Real)((double)h * d1d);
-                  z[k] = hz;
-                  if (!final_job) Z[p] = hz;
-                }
+          z[k] = zr[k];
+          if (bok && p < P) {
+            const Real S = s1 * e1[k];
+            const Real h = payoff<Real>(type, K, S);
+            if (h > (Real)0) {
+              const Real x = fma(S, invK, (Real)-1);
+              Real c = fma(fma(b[2], x, b[1]), x, b[0]);
+              if (BASIS == kBasisSV2) {
+                const Real w = fma(v1[k], invTh, (Real)-1);
+                c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
+              }
+              const Real hd = h * d1;
+              if (fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd)) ++ties;
+              if (hd > c) {
+                const Real hz = (Real)((double)h * d1d);
+                z[k] = hz;
+                if (!final_job) Z[p] = hz;
               }
             }
           }
@@ -382,7 +427,7 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           if (p < P) {
             const Real yv = z[k];
-            const Real S = s0 * E0[p];
+            const Real S = s0 * e0[k];
             const Real h = payoff<Real>(type, K, S);
             if (h > (Real)0) {
               const Real x = fma(S, invK, (Real)-1), x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
@@ -392,7 +437,7 @@ backward_kernel(BwdArgs a) {
               t[3] += x3;
               t[4] += x4;
               if (BASIS == kBasisSV2) {
-                const Real w = fma(V0[p], invTh, (Real)-1), w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
+                const Real w = fma(v0[k], invTh, (Real)-1), w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
                 const Real xw = x * w;
                 t[mono(0, 1)] += w;
                 t[mono(1, 1)] += xw;
@@ -429,26 +474,39 @@ backward_kernel(BwdArgs a) {
     } else {
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
-        const double v = acc.total(i);
-        if (lane == 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
+        if constexpr (kSingle) {
+          const float2 v = warp_pair_sum(make_float2(acc.hi[i], acc.lo[i]));
+          if (lane == 0) s_redf[warp][i] = v;
+        } else {
+          const double v = warp_sum(acc.s[i]);
+          if (lane == 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
+        }
       }
     }
-    euro = warp_sum(euro);
-    ties = warp_sum(ties);
+    if (first) euro = warp_sum(euro);
+    ties = __reduce_add_sync(0xffffffffu, ties);
     if (lane == 0) {
       s_red[warp][kSlotEuro] = euro;
-      s_red[warp][kSlotTies] = ties;
+      s_red[warp][kSlotTies] = (double)ties;
       s_red[warp][kSlotSumY] = sy;
       s_red[warp][kSlotSumY2] = sy2;
     }
     __syncthreads();
     if (tid < kNSum) {
+      const bool moment = tid < NM || (tid >= kSlotRhs && tid < kSlotRhs + NB);
       const bool used = final_job ? tid >= kSlotEuro
-                                  : (tid < NM || (tid >= kSlotRhs && tid < kSlotRhs + NB) ||
-                                     tid == kSlotEuro || tid == kSlotTies);
+                                  : (moment || tid == kSlotEuro || tid == kSlotTies);
       double v = 0.0;
-      if (used)
-        for (int w = 0; w < NW; ++w) v += s_red[w][tid];
+      if (used) {
+        if (kSingle && moment) {
+          const int i = tid < NM ? tid : NM + (tid - kSlotRhs);
+          float2 pr = make_float2(0.0f, 0.0f);
+          for (int w = 0; w < NW; ++w) pr = pair_add(pr, s_redf[w][i]);
+          v = (double)pr.x + (double)pr.y;
+        } else {
+          for (int w = 0; w < NW; ++w) v += s_red[w][tid];
+        }
+      }
       I.partial[(size_t)ji.tile * kNSum + tid] = v;
     }
 

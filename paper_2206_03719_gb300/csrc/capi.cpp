@@ -9,6 +9,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -533,6 +534,10 @@ int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   ctx->max_inflight = c.max_inflight ? c.max_inflight : 8;
   ctx->queue_capacity = c.queue_capacity ? c.queue_capacity : 4096;
   ctx->t0 = now_s();
+  if (const char* e = std::getenv("LSMC_BACKWARD_SUB")) {  // tuning sweeps
+    const long v = std::strtol(e, nullptr, 10);
+    if (v > 0 && v <= 1024) ctx->sub_override = (uint32_t)v;
+  }
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete ctx;
     return LSMC_ECUDA;
