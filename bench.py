@@ -55,6 +55,8 @@ def parse():
                     help="override the path count (profiling of a smaller case)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the precision-split, book and serving measurements")
     return ap.parse_args()
 
 
@@ -183,6 +185,127 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+
+def measure_mixed_large(api, L, torch):
+    """Precision split at 1,048,576 paths: Greeks/s of the MIXED path and its
+    error against the FP64 GPU path on the same random stream."""
+    wl = workloads.LARGE_MIXED
+    need = L.lsmc_request_footprint(None, api.Request(wl).c)
+    need64 = L.lsmc_request_footprint(None, api.Request(wl, precision="fp64").c)
+    out = {"workload": wl.name}
+    with api.Context(workspace_bytes=max(need, need64) + (256 << 20)) as ctx:
+        plan = ctx.plan([wl])
+        for _ in range(3):
+            plan.launch()
+        plan.fetch()
+        plan.set_timing(True)
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            plan.launch()
+        mixed = plan.fetch()
+        wall = (time.perf_counter() - t0) / reps
+        kms, launches = plan.kernel_times()
+        plan.close()
+        ref = ctx.price(wl, precision="fp64")
+    errs = {}
+    for g, r in zip(mixed, ref):
+        for k in ("price", "delta", "gamma", "vega", "rho", "theta"):
+            e = abs(g[k] - r[k]) / max(abs(r[k]), 1e-12)
+            errs[k] = max(errs.get(k, 0.0), e)
+    ms = sum(kms) / max(1, launches)
+    out.update({"greeks_per_s": wl.n_greeks / (ms / 1e3), "ms_per_step": ms,
+                "wall_ms_per_step": wall * 1e3,
+                "generated_path_steps_per_s": wl.generated_path_steps / (ms / 1e3),
+                "lsmc_path_steps_per_s": wl.lsmc_path_steps / (ms / 1e3),
+                "kernel_ms": {"forward": kms[1] / max(1, launches),
+                              "backward": kms[2] / max(1, launches)},
+                "max_rel_err_vs_fp64_gpu": errs,
+                "within_1e-4": {k: v <= 1e-4 for k, v in errs.items()}})
+    return out
+
+
+def measure_book(api, L, torch, n_contracts=512, chunk=128):
+    """Uneven book (512 contracts, all bump scenarios, FP32 paths / FP64
+    reductions) in launches of `chunk` contracts, each captured once in a CUDA
+    graph and replayed; device time summed over the chunks (each chunk holds
+    its own paths, so chunks run one after another within a workspace of the
+    largest chunk's size)."""
+    book = workloads.book(n_contracts=n_contracts, precision="mixed")
+    chunks = [book[i:i + chunk] for i in range(0, len(book), chunk)]
+    need = max(sum(L.lsmc_request_footprint(None, api.Request(w).c) for w in c) for c in chunks)
+    greeks = sum(w.n_greeks for w in book)
+    gen = sum(w.generated_path_steps for w in book)
+    lsmc = sum(w.lsmc_path_steps for w in book)
+    total_ms = 0.0
+    with api.Context(workspace_bytes=need + (512 << 20)) as ctx:
+        for c in chunks:
+            p = ctx.plan(c)
+            p.launch(use_graph=True)  # capture and warm
+            p.fetch()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(ctx.stream)
+            p.launch(use_graph=True)
+            ev1.record(ctx.stream)
+            p.fetch()
+            total_ms += ev0.elapsed_time(ev1)
+            p.close()
+    return {"contracts": n_contracts, "launch_chunks": len(chunks), "device_ms": total_ms,
+            "greeks_per_s": greeks / (total_ms / 1e3),
+            "generated_path_steps_per_s": gen / (total_ms / 1e3),
+            "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
+            "precision": "mixed", "graph": True}
+
+
+def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32):
+    """Poisson stream of book-distributed requests with continuous batching
+    (MIXED; up to 16 requests on the device at once, admitted by workspace
+    bytes), and the first `serial_n` of the same requests solved one at a
+    time in plain FP64 on the same GPU."""
+    arrivals = workloads.poisson_arrivals(rate, warm_s + window_s, seed=11)
+    reqs = workloads.book(n_contracts=len(arrivals), seed=99, precision="mixed")
+    with api.Context(workspace_bytes=48 << 30, max_inflight=16, precision="mixed") as srv:
+        t0 = time.perf_counter()
+        tickets = []
+        for t_arr, w in zip(arrivals, reqs):
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            tickets.append((t_arr, w, srv.submit(w)))
+        ok = 0
+        for _, w, t in tickets:
+            st, _ = srv.wait(t, len(w.strikes), 300.0)
+            ok += st == L.LSMC_OK
+        wall = time.perf_counter() - t0
+        times = [L.lsmc_ticket_times(srv.ctx, t) for _, _, t in tickets]
+    lat = [d - s for (t_arr, _, _), (s, a, d) in zip(tickets, times) if t_arr >= warm_s]
+    lat.sort()
+    pct = lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] * 1e3 if lat else None
+    greeks = sum(w.n_greeks for t_arr, w, _ in tickets if t_arr >= warm_s)
+    first_done = min(s for s, a, d in times)
+    last_done = max(d for s, a, d in times)
+    served = {"rate_per_s": rate, "window_s": window_s, "requests": len(tickets), "ok": ok,
+              "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
+              "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
+              "precision": "mixed", "max_inflight": 16}
+    # the same requests, one at a time, plain FP64
+    serial = reqs[:serial_n]
+    need = max(L.lsmc_request_footprint(None, api.Request(w, precision="fp64").c) for w in serial)
+    with api.Context(workspace_bytes=need + (256 << 20)) as ctx:
+        ctx.price(serial[0], precision="fp64")
+        t0 = time.perf_counter()
+        per = []
+        for w in serial:
+            t1 = time.perf_counter()
+            ctx.price(w, precision="fp64")
+            per.append(time.perf_counter() - t1)
+        dt = time.perf_counter() - t0
+    per.sort()
+    served["serial_fp64"] = {"requests": len(serial), "greeks_per_s": sum(w.n_greeks for w in serial) / dt,
+                             "p50_ms": per[len(per) // 2] * 1e3, "p99_ms": per[-1] * 1e3}
+    return served
+
+
 def main():
     args = parse()
     wl = pick_workload(args.workload)
@@ -259,6 +382,15 @@ def main():
                "path": "lsmc_price_request: validate, plan, upload, launch, read back"}
 
     ctx.close()
+    extras = {}
+    if not args.no_extras and not args.paths and args.workload == "paper_fp64":
+        for name, fn in (("precision_split", measure_mixed_large), ("book", measure_book),
+                         ("serving", measure_serving)):
+            torch.cuda.empty_cache()
+            try:
+                extras[name] = fn(api, L, torch)
+            except Exception as e:  # report, do not hide, a failed extra
+                extras[name] = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank != 0:
         return
 
@@ -312,6 +444,7 @@ def main():
         "clocks": clocks,
         "device_bytes": int(info.device_bytes),
     }
+    line.update(extras)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -216,7 +216,9 @@ int lsmc_poll(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs);
 /* Blocks up to timeout_s (< 0: no limit) for the ticket, then as lsmc_poll. */
 int lsmc_wait(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs,
               double timeout_s);
-/* Per-ticket timing (seconds, host steady clock): submit -> admit -> done. */
+/* Per-ticket timing (seconds since lsmc_create, host steady clock): submit,
+ * admission to the device and completion.  Also answers for released
+ * tickets (the last 2^20 are remembered). */
 int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
                       double* admit_s, double* done_s);
 

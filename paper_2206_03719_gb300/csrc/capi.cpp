@@ -72,6 +72,8 @@ struct lsmc_ctx {
   uint64_t next_ticket = 1;
   std::vector<Slot> slots;
   double t0 = 0;
+  // submit / admit / done times of released tickets (bounded history)
+  std::map<uint64_t, std::array<double, 3>> history;
 };
 
 struct lsmc_plan {
@@ -733,6 +735,8 @@ int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket) {
 static int take_result(lsmc_ctx* ctx, std::map<uint64_t, Ticket*>::iterator it, lsmc_result* outs) {
   Ticket* t = it->second;
   const int st = t->status;
+  ctx->history[t->id] = {t->t_submit, t->t_admit, t->t_done};
+  while (ctx->history.size() > (1u << 20)) ctx->history.erase(ctx->history.begin());
   if (st == LSMC_OK && outs)
     std::memcpy(outs, t->results.data(), sizeof(lsmc_result) * t->results.size());
   ctx->tickets.erase(it);
@@ -771,7 +775,14 @@ int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* s, double* a, doub
   if (!ctx) return LSMC_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   auto it = ctx->tickets.find(ticket);
-  if (it == ctx->tickets.end()) return LSMC_ENOTFOUND;
+  if (it == ctx->tickets.end()) {
+    auto h = ctx->history.find(ticket);
+    if (h == ctx->history.end()) return LSMC_ENOTFOUND;
+    if (s) *s = h->second[0];
+    if (a) *a = h->second[1];
+    if (d) *d = h->second[2];
+    return LSMC_OK;
+  }
   if (s) *s = it->second->t_submit;
   if (a) *a = it->second->t_admit;
   if (d) *d = it->second->t_done;
