@@ -204,7 +204,7 @@ template <int NA> struct Acc<float, NA> {
 // A job covers `a.sub` sub-tiles of kBlock * PPT paths: the wait for the
 // previous round, the block reduction and the arrival are paid once per job.
 template <typename Real, int BASIS, int PPT>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, 2)
 backward_kernel(BwdArgs a) {
   constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
   constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
@@ -304,7 +304,7 @@ backward_kernel(BwdArgs a) {
     }
 
     // per-job constants, converted to the working precision once per job
-    if (tid < 13) {
+    if (tid < 16) {
       double v;
       switch (tid) {
         case 6: v = stab[n + 1]; break;
@@ -314,6 +314,12 @@ backward_kernel(BwdArgs a) {
         case 10: v = I.K; break;
         case 11: v = I.invK; break;
         case 12: v = I.inv_theta; break;
+        // discount factors as unevaluated pairs (hi + lo): a cash flow is
+        // h * hi + h * lo, one rounding, with no bias shared by the paths
+        // that exercise on the same date
+        case 13: v = dtab[n + 1] - (double)(Real)dtab[n + 1]; break;
+        case 14: v = dtab[N]; break;
+        case 15: v = dtab[N] - (double)(Real)dtab[N]; break;
         default: v = first ? 0.0 : s_beta[tid]; break;
       }
       s_c[tid] = (Real)v;
@@ -325,8 +331,7 @@ backward_kernel(BwdArgs a) {
     for (int i = 0; i < 6; ++i) b[i] = s_c[i];
     const Real s1 = s_c[6], d1 = s_c[7], sN = s_c[8], s0 = s_c[9];
     const Real K = s_c[10], invK = s_c[11], invTh = s_c[12];
-    const double d1d = dtab[n + 1];
-    const double dN = dtab[N];
+    const Real d1lo = s_c[13], dNhi = s_c[14], dNlo = s_c[15];
     const Real* EN = E + (size_t)(N - 1) * ld;
     const Real* E1 = E + (size_t)n * ld;                        // date n + 1
     const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
@@ -367,15 +372,13 @@ backward_kernel(BwdArgs a) {
       }
       Real z[PPT];
       if (first) {
-        // the discount factor multiplies in double and the product is
-        // rounded once, so single-precision cash flows carry no shared
-        // per-date bias
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
           z[k] = (Real)0;
           if (p < P) {
-            z[k] = (Real)((double)payoff<Real>(type, K, sN * e1[k]) * dN);
+            const Real h = payoff<Real>(type, K, sN * e1[k]);
+            z[k] = fma(h, dNhi, h * dNlo);
             euro += (double)z[k];
             if (!final_job) Z[p] = z[k];
           }
@@ -400,7 +403,7 @@ backward_kernel(BwdArgs a) {
               const Real hd = h * d1;
               if (fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd)) ++ties;
               if (hd > c) {
-                const Real hz = (Real)((double)h * d1d);
+                const Real hz = fma(h, d1, h * d1lo);
                 z[k] = hz;
                 if (!final_job) Z[p] = hz;
               }

@@ -140,34 +140,69 @@ forward_kernel(FwdArgs a) {
   const int ng = (int)sc.n_groups;
   const uint2 key = make_uint2((uint32_t)sc.seed, (uint32_t)(sc.seed >> 32));
 
-  Real x[kMaxGroups], v[kMaxGroups];
-#pragma unroll
-  for (int g = 0; g < kMaxGroups; ++g) {
-    x[g] = (Real)0;
-    v[g] = g < ng ? gc[g].v0 : (Real)0;
-  }
   for (int g = 0; g < ng; ++g) {
     const FwdGroup& gg = a.groups[sc.group0 + g];
     if (gg.E_row0) ((Real*)gg.E_row0)[p] = gc[g].out_scale;
     if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
   }
 
-  for (uint32_t n = 0; n < sc.N; ++n) {
-    const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
-    Real uV, zV, zX;
-    Draw<Real>::make(w, uV, zV, zX);
+  if constexpr (sizeof(Real) == 8) {
+    // double precision is bound by the FP64 pipe: keep every group's state
+    // and constants in registers (one CTA per SM is enough to fill it)
+    Real x[kMaxGroups], v[kMaxGroups];
 #pragma unroll
     for (int g = 0; g < kMaxGroups; ++g) {
-      if (g < ng) {
-        const GroupConst<Real>& c = gc[g];
-        if (SCHEME == kSchemeQE) {
-          qe_step<Real>(c, x[g], v[g], uV, zV, zX);
-        } else {
-          ft_step<Real>(c, x[g], v[g], zV, zX);
+      x[g] = (Real)0;
+      v[g] = g < ng ? gc[g].v0 : (Real)0;
+    }
+    for (uint32_t n = 0; n < sc.N; ++n) {
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      Real uV, zV, zX;
+      Draw<Real>::make(w, uV, zV, zX);
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g) {
+        if (g < ng) {
+          const GroupConst<Real>& c = gc[g];
+          if (SCHEME == kSchemeQE) {
+            qe_step<Real>(c, x[g], v[g], uV, zV, zX);
+          } else {
+            ft_step<Real>(c, x[g], v[g], zV, zX);
+          }
+          const size_t off = (size_t)n * c.ld + p;
+          c.E[off] = c.out_scale * Fm<Real>::exp_(x[g]);
+          if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
         }
+      }
+    }
+  } else {
+    // single precision is bound by latency and issue: the group loop is not
+    // unrolled, so the constants are read from shared memory where they are
+    // used and the per-group state lives in shared memory too; the kernel
+    // then needs few registers and many warps fit on an SM
+    __shared__ Real xs[kMaxGroups][kBlock], vs[kMaxGroups][kBlock];
+    const int t = threadIdx.x;
+    for (int g = 0; g < ng; ++g) {
+      xs[g][t] = (Real)0;
+      vs[g][t] = gc[g].v0;
+    }
+    for (uint32_t n = 0; n < sc.N; ++n) {
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      Real uV, zV, zX;
+      Draw<Real>::make(w, uV, zV, zX);
+#pragma unroll 1
+      for (int g = 0; g < ng; ++g) {
+        const GroupConst<Real>& c = gc[g];
+        Real xg = xs[g][t], vg = vs[g][t];
+        if (SCHEME == kSchemeQE) {
+          qe_step<Real>(c, xg, vg, uV, zV, zX);
+        } else {
+          ft_step<Real>(c, xg, vg, zV, zX);
+        }
+        xs[g][t] = xg;
+        vs[g][t] = vg;
         const size_t off = (size_t)n * c.ld + p;
-        c.E[off] = c.out_scale * Fm<Real>::exp_(x[g]);
-        if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+        c.E[off] = c.out_scale * Fm<Real>::exp_(xg);
+        if (c.V) c.V[off] = (SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg;
       }
     }
   }
