@@ -61,8 +61,14 @@ enum { LSMC_SCHEME_QE = 0, LSMC_SCHEME_FT_EULER = 1 };
 enum { LSMC_BASIS_S2 = 0, LSMC_BASIS_SV2 = 1 };
 /* FP64: paths, sums, solve and estimator in double precision.
  * MIXED: paths and per-thread moment sums in single precision; cross-warp
- * sums, the normal-equation solve and the estimator in double. */
-enum { LSMC_FP64 = 0, LSMC_MIXED = 1 };
+ * sums (compensated float pairs), the normal-equation solve and the
+ * estimator in double.
+ * DF: paths, regression features, sums and exercise decisions in
+ * unevaluated pairs of floats (about 48 significant bits, computed on the
+ * FP32 pipes; the normal quantiles, the solve and the estimator in double):
+ * FP64-grade results at single-precision pipe rates.  Stored values are
+ * float pairs, as wide as doubles. */
+enum { LSMC_FP64 = 0, LSMC_MIXED = 1, LSMC_DF = 2 };
 enum { LSMC_GREEK_DELTA = 1, LSMC_GREEK_GAMMA = 2, LSMC_GREEK_VEGA = 4,
        LSMC_GREEK_RHO = 8, LSMC_GREEK_THETA = 16, LSMC_GREEK_ALL = 31 };
 
@@ -228,14 +234,14 @@ int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
 int lsmc_philox(const uint32_t* d_ctr, uint32_t key_lo, uint32_t key_hi,
                 uint32_t* d_out, size_t n, void* cuda_stream);
 /* Random inputs of n (path, step) pairs under (seed, stream_id): d_out is
- * n x 3 (U_V, Z_V, Z_X) as double (LSMC_FP64: 52-bit grid) or float
- * (LSMC_MIXED: 23-bit grid). */
+ * n x 3 (U_V, Z_V, Z_X) as double (LSMC_FP64: 52-bit grid), float
+ * (LSMC_MIXED: 23-bit grid) or float pairs (LSMC_DF: the FP64 values split). */
 int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
                const uint32_t* d_step, size_t n, int32_t precision,
                void* d_out, void* cuda_stream);
 /* Heston paths (Sec. 2.2.1: variance, log price, exponential):
- * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double or
- * float by precision; row 0 holds S0 and v0.  V holds max(v, 0) under
+ * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double, float
+ * or float pairs by precision; row 0 holds S0 and v0.  V holds max(v, 0) under
  * FT_EULER. */
 int lsmc_paths(const lsmc_heston* model, double T, int32_t scheme,
                int32_t precision, uint32_t n_paths, uint32_t n_steps,

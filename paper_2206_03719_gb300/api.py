@@ -17,7 +17,7 @@ _OPTION = {"put": L.LSMC_PUT, "call": L.LSMC_CALL}
 _STYLE = {"american": L.LSMC_AMERICAN, "european": L.LSMC_EUROPEAN}
 _BASIS = {"s2": L.LSMC_BASIS_S2, "sv2": L.LSMC_BASIS_SV2}
 _SCHEME = {"qe": L.LSMC_SCHEME_QE, "ft_euler": L.LSMC_SCHEME_FT_EULER}
-_PREC = {"fp64": L.LSMC_FP64, "mixed": L.LSMC_MIXED}
+_PREC = {"fp64": L.LSMC_FP64, "mixed": L.LSMC_MIXED, "df": L.LSMC_DF}
 _GREEK = {"delta": L.LSMC_GREEK_DELTA, "gamma": L.LSMC_GREEK_GAMMA,
           "vega": L.LSMC_GREEK_VEGA, "rho": L.LSMC_GREEK_RHO, "theta": L.LSMC_GREEK_THETA}
 

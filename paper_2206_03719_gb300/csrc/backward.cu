@@ -26,8 +26,10 @@
 // Every wait is bounded in time; on expiry the kernel records an error code
 // and returns.
 #include <cstdio>
+#include <type_traits>
 
 #include "device_common.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "plan.h"
 
@@ -174,8 +176,19 @@ template <int NA> struct Acc<double, NA> {
   __device__ __forceinline__ double* target() { return s; }
   __device__ __forceinline__ void fold() {}
 };
+template <int NA> struct Acc<df, NA> {
+  df s[NA];  // float-pair accumulation needs no folding
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) s[i] = df(0.0f, 0.0f);
+  }
+  __device__ __forceinline__ df* target() { return s; }
+  __device__ __forceinline__ void fold() {}
+  __device__ __forceinline__ float2 pair(int i) const { return make_float2(s[i].hi, s[i].lo); }
+};
 template <int NA> struct Acc<float, NA> {
   float hi[NA], lo[NA], t[NA];
+  __device__ __forceinline__ float2 pair(int i) const { return make_float2(hi[i], lo[i]); }
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int i = 0; i < NA; ++i) hi[i] = lo[i] = t[i] = 0.0f;
@@ -224,7 +237,9 @@ backward_kernel(BwdArgs a) {
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sub = a.sub;
-  constexpr bool kSingle = sizeof(Real) == 4;
+  // single precision and float pairs reduce through float pairs; double
+  // precision through doubles
+  constexpr bool kSingle = !std::is_same<Real, double>::value;
   unsigned long long next = 0;
   if (tid == 0) next = atomicAdd(&a.ctl->next_job, 1ull);
 
@@ -478,7 +493,7 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
         if constexpr (kSingle) {
-          const float2 v = warp_pair_sum(make_float2(acc.hi[i], acc.lo[i]));
+          const float2 v = warp_pair_sum(acc.pair(i));
           if (lane == 0) s_redf[warp][i] = v;
         } else {
           const double v = warp_sum(acc.s[i]);
@@ -643,30 +658,35 @@ static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-int backward_tile(bool fp64) { return kBlock * (fp64 ? 4 : 8); }
+// paths per thread in a sub-tile: 4 for double and float pairs, 8 for float
+int backward_tile(int precision) { return kBlock * (precision == kPrecMixed ? 8 : 4); }
 
-cudaError_t launch_backward(const BwdArgs& a, bool fp64, int basis, int grid,
+cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int grid,
                             cudaStream_t s) {
   if (a.total_jobs == 0) return cudaSuccess;
-  if (fp64)
-    return basis == kBasisSV2 ? launch_bwd_t<double, kBasisSV2, 4>(a, grid, s)
-                              : launch_bwd_t<double, kBasisS2, 4>(a, grid, s);
-  return basis == kBasisSV2 ? launch_bwd_t<float, kBasisSV2, 8>(a, grid, s)
-                            : launch_bwd_t<float, kBasisS2, 8>(a, grid, s);
+  const bool sv2 = basis == kBasisSV2;
+  if (precision == kPrecFP64)
+    return sv2 ? launch_bwd_t<double, kBasisSV2, 4>(a, grid, s)
+               : launch_bwd_t<double, kBasisS2, 4>(a, grid, s);
+  if (precision == kPrecDF)
+    return sv2 ? launch_bwd_t<df, kBasisSV2, 4>(a, grid, s)
+               : launch_bwd_t<df, kBasisS2, 4>(a, grid, s);
+  return sv2 ? launch_bwd_t<float, kBasisSV2, 8>(a, grid, s)
+             : launch_bwd_t<float, kBasisS2, 8>(a, grid, s);
 }
 
-int backward_occupancy(bool fp64, int basis) {
+template <typename Real, int BASIS, int PPT>
+static int occ_t() {
   int n = 0;
-  cudaError_t e;
-  if (fp64)
-    e = basis == kBasisSV2
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<double, kBasisSV2, 4>, kBlock, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<double, kBasisS2, 4>, kBlock, 0);
-  else
-    e = basis == kBasisSV2
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<float, kBasisSV2, 8>, kBlock, 0)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<float, kBasisS2, 8>, kBlock, 0);
-  return e == cudaSuccess ? n : 1;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<Real, BASIS, PPT>,
+                                                       kBlock, 0) == cudaSuccess ? n : 1;
+}
+
+int backward_occupancy(int precision, int basis) {
+  const bool sv2 = basis == kBasisSV2;
+  if (precision == kPrecFP64) return sv2 ? occ_t<double, kBasisSV2, 4>() : occ_t<double, kBasisS2, 4>();
+  if (precision == kPrecDF) return sv2 ? occ_t<df, kBasisSV2, 4>() : occ_t<df, kBasisS2, 4>();
+  return sv2 ? occ_t<float, kBasisSV2, 8>() : occ_t<float, kBasisS2, 8>();
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,

@@ -60,7 +60,7 @@ struct lsmc_ctx {
   size_t hbm_budget = 0;
   uint32_t max_inflight = 8, queue_capacity = 4096;
   int num_sms = 0;
-  int occ[2][2] = {{0, 0}, {0, 0}};
+  int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
   // serving
   std::mutex mu;
@@ -132,13 +132,13 @@ int cuda_status(cudaError_t e) {
 
 int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? dflt : dflt) : v; }
 
-int occupancy(lsmc_ctx* ctx, bool fp64, int basis) {
+int occupancy(lsmc_ctx* ctx, int precision, int basis) {
   if (ctx) {
-    int& o = ctx->occ[fp64 ? 1 : 0][basis];
-    if (o == 0) o = std::max(1, backward_occupancy(fp64, basis));
+    int& o = ctx->occ[precision][basis];
+    if (o == 0) o = std::max(1, backward_occupancy(precision, basis));
     return o;
   }
-  return std::max(1, backward_occupancy(fp64, basis));
+  return std::max(1, backward_occupancy(precision, basis));
 }
 
 int sm_count(lsmc_ctx* ctx) {
@@ -154,8 +154,8 @@ int sm_count(lsmc_ctx* ctx) {
 // scale tables | partials | Y | paths.
 int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hist) {
   PlanLayout& L = p->L;
-  const bool fp64 = L.opt.precision == LSMC_FP64;
-  const size_t real = fp64 ? 8 : 4;
+  const int prec = L.opt.precision;
+  const size_t real = value_bytes(prec);
   char* base = p->dev;
   size_t off = 0;
   auto take = [&](size_t bytes) { char* q = base + off; off += align256(bytes); return q; };
@@ -231,7 +231,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
   p->ba.sub = std::max<uint32_t>(1, L.opt.sub);
-  const int occ = occupancy(p->ctx, fp64, L.opt.basis);
+  const int occ = occupancy(p->ctx, prec, L.opt.basis);
   const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
   p->h_out.resize(L.greeks.size());
@@ -306,9 +306,8 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
   p->ctx = ctx;
   p->stream = stream;
   {
-    const bool fp64 = o.precision == LSMC_FP64;
-    const uint32_t ctas = (uint32_t)occupancy(ctx, fp64, o.basis) * (uint32_t)sm_count(ctx);
-    o.sub = ctx && ctx->sub_override ? ctx->sub_override : choose_sub(reqs, n, fp64, ctas);
+    const uint32_t ctas = (uint32_t)occupancy(ctx, o.precision, o.basis) * (uint32_t)sm_count(ctx);
+    o.sub = ctx && ctx->sub_override ? ctx->sub_override : choose_sub(reqs, n, o.precision, ctas);
   }
   rc = build_layout(reqs, n, o, &p->L);
   if (rc) return rc;
@@ -321,7 +320,7 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
 }
 
 int plan_enqueue(lsmc_plan* p, bool timed = false) {
-  const bool fp64 = p->L.opt.precision == LSMC_FP64;
+  const int prec = p->L.opt.precision;
   cudaEvent_t* ev = nullptr;
   if (timed) {
     if (p->ev_used == p->ev.size()) {
@@ -336,9 +335,9 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
   LSMC_CUDA(mark(0));
   if (p->run_backward) LSMC_CUDA(launch_setup(p->d_inst, (uint32_t)p->L.inst.size(), p->stream));
   LSMC_CUDA(mark(1));
-  if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, fp64, p->L.opt.scheme, p->stream));
+  if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, prec, p->L.opt.scheme, p->stream));
   LSMC_CUDA(mark(2));
-  if (p->run_backward) LSMC_CUDA(launch_backward(p->ba, fp64, p->L.opt.basis, p->bwd_grid, p->stream));
+  if (p->run_backward) LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, p->bwd_grid, p->stream));
   LSMC_CUDA(mark(3));
   if (p->run_greeks)
     LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out, p->stream));
@@ -521,7 +520,8 @@ int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   *out = nullptr;
   lsmc_config c{};
   if (cfg) c = *cfg;
-  if (c.precision != LSMC_FP64 && c.precision != LSMC_MIXED) return LSMC_EINVAL;
+  if (c.precision != LSMC_FP64 && c.precision != LSMC_MIXED && c.precision != LSMC_DF)
+    return LSMC_EINVAL;
   if (c.scheme != LSMC_SCHEME_QE && c.scheme != LSMC_SCHEME_FT_EULER) return LSMC_EINVAL;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) return LSMC_ENODEV;
@@ -800,8 +800,9 @@ int lsmc_philox(const uint32_t* d_ctr, uint32_t k0, uint32_t k1, uint32_t* d_out
 int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path, const uint32_t* d_step,
                size_t n, int32_t precision, void* d_out, void* s) {
   if ((!d_path || !d_step || !d_out) && n) return LSMC_EINVAL;
-  if (precision != LSMC_FP64 && precision != LSMC_MIXED) return LSMC_EINVAL;
-  LSMC_CUDA(launch_draws(seed, stream_id, d_path, d_step, n, precision == LSMC_FP64, d_out,
+  if (precision != LSMC_FP64 && precision != LSMC_MIXED && precision != LSMC_DF)
+    return LSMC_EINVAL;
+  LSMC_CUDA(launch_draws(seed, stream_id, d_path, d_step, n, precision, d_out,
                          (cudaStream_t)s));
   return LSMC_OK;
 }
@@ -844,7 +845,7 @@ int lsmc_paths(const lsmc_heston* m, double T, int32_t scheme, int32_t precision
   if (rc == LSMC_OK) rc = plan_bind_and_upload(p, d_S, d_V, nullptr);
   p->run_backward = p->run_greeks = false;
   if (rc == LSMC_OK) {
-    const cudaError_t e = launch_forward(p->fa, precision == LSMC_FP64, scheme, p->stream);
+    const cudaError_t e = launch_forward(p->fa, precision, scheme, p->stream);
     rc = cuda_status(e);
   }
   plan_free(p);

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace lsmc {
 
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64-bit
@@ -56,6 +58,18 @@ template <> struct Draw<float> {
   }
 };
 
+template <> struct Draw<df> {
+  // the double-precision draws (same grid and quantile as FP64), split into
+  // float pairs: float-pair paths see exactly the FP64 random inputs
+  __device__ __forceinline__ static void make(uint4 w, df& uV, df& zV, df& zX) {
+    double u, a, b;
+    Draw<double>::make(w, u, a, b);
+    uV = df(u);
+    zV = df(a);
+    zX = df(b);
+  }
+};
+
 __device__ __forceinline__ unsigned long long global_timer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -79,5 +93,9 @@ __device__ __forceinline__ uint32_t ld_volatile(const uint32_t* p) {
 // L2-coherent loads of data other CTAs wrote during this launch
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ld_cg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ df ld_cg(const df* p) {
+  const float2 v = __ldcg((const float2*)p);
+  return df(v.x, v.y);
+}
 
 }  // namespace lsmc

@@ -1,0 +1,150 @@
+// dfloat.cuh -- unevaluated pairs of floats ("double-float", hi + lo with
+// |lo| <= ulp(hi) / 2): about 48 significant bits computed on the FP32
+// pipes.  On a GB300 the FP64 pipe issues at about 1/64 of the FP32 rate, so
+// this arithmetic carries the Longstaff-Schwartz path at close to double
+// precision for a fraction of the cost of native double.
+//
+// Algorithms: Knuth's two-sum and Dekker's fast two-sum for additions,
+// the FMA-based exact product for multiplications (as in Hida, Li and
+// Bailey's double-double library), Newton corrections for division and
+// square root, and for exp a reduction by a multiple of ln 2 and a power of
+// two, a Taylor polynomial and repeated squaring of exp(r) - 1.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lsmc {
+
+struct df;
+__device__ df df_abs(df a);
+__device__ df df_max(df a, df b);
+__device__ df df_fma(df a, df b, df c);
+
+struct df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  // exact split of a double into its top 24 bits and the next 24 (explicit:
+  // a double never turns into a pair, or back, without being asked to)
+  __host__ __device__ constexpr explicit df(double d)
+      : hi((float)d), lo((float)(d - (double)(float)d)) {}
+  __host__ __device__ constexpr explicit df(int i) : hi((float)i), lo(0.0f) {}
+  __host__ __device__ explicit operator double() const {
+    return (double)hi + (double)lo;
+  }
+  // found only by argument-dependent lookup, so these never hide the float
+  // and double overloads for code that calls fabs, fmax or fma on scalars
+  friend __device__ __forceinline__ df fabs(df a) { return df_abs(a); }
+  friend __device__ __forceinline__ df fmax(df a, df b) { return df_max(a, b); }
+  friend __device__ __forceinline__ df fma(df a, df b, df c) { return df_fma(a, b, c); }
+};
+
+__device__ __forceinline__ df quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+
+__device__ __forceinline__ df two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return df(p, __fmaf_rn(a, b, -p));
+}
+
+__device__ __forceinline__ df operator+(df a, df b) {
+  df s = two_sum(a.hi, b.hi);
+  const df t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+
+__device__ __forceinline__ df operator*(df a, df b) {
+  df p = two_prod(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.lo, p.lo);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return quick_two_sum(p.hi, e);
+}
+
+__device__ __forceinline__ df mul_f(df a, float b) {
+  df p = two_prod(a.hi, b);
+  return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+
+__device__ __forceinline__ df operator/(df a, df b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df r = a - mul_f(b, q1);
+  const float q2 = __fdiv_rn(r.hi, b.hi);
+  const df r2 = r - mul_f(b, q2);
+  const float q3 = __fdiv_rn(r2.hi, b.hi);
+  const df q = quick_two_sum(q1, q2);
+  return q + df(q3, 0.0f);
+}
+
+__device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
+__device__ __forceinline__ df& operator*=(df& a, df b) { return a = a * b; }
+
+__device__ __forceinline__ bool operator<(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ bool operator>(df a, df b) { return b < a; }
+__device__ __forceinline__ bool operator<=(df a, df b) { return !(b < a); }
+__device__ __forceinline__ bool operator>=(df a, df b) { return !(a < b); }
+
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.0f ? -a : a; }
+__device__ __forceinline__ df df_max(df a, df b) { return a < b ? b : a; }
+__device__ __forceinline__ df df_fma(df a, df b, df c) { return a * b + c; }
+
+// x * 2^k, exact
+__device__ __forceinline__ df ldexp_df(df a, int k) {
+  return df(ldexpf(a.hi, k), ldexpf(a.lo, k));
+}
+
+__device__ __forceinline__ df sqrt_df(df a) {
+  if (!(a.hi > 0.0f)) return df(0.0f, 0.0f);
+  // y ~ sqrt(a) in float, then y + (a - y^2) / (2 y)
+  const float x = rsqrtf(a.hi);
+  const float y = __fmul_rn(a.hi, x);
+  const df r = a - two_prod(y, y);
+  return quick_two_sum(y, __fmul_rn(r.hi, __fmul_rn(x, 0.5f)));
+}
+
+__device__ __forceinline__ df exp_df(df a) {
+  // a = k ln2 + r, |r| <= ln2 / 2; exp(r) = (1 + s)^(2^4) with s = exp(r/16) - 1
+  constexpr double kLn2 = 0.693147180559945309417232121458176568;
+  constexpr double kLog2e = 1.442695040888963407359924681001892137;
+  if (a.hi > 88.0f) return df(__int_as_float(0x7f800000), 0.0f);
+  if (a.hi < -87.0f) return df(0.0f, 0.0f);
+  const float k = rintf(__fmul_rn(a.hi, (float)kLog2e));
+  const df r = ldexp_df(a - mul_f(df(kLn2), k), -4);
+  // Taylor series of exp(r) - 1 to r^8 / 8! (|r| <= 0.0217: remainder < 1e-18)
+  df s = r * df(1.0 / 40320.0) + df(1.0 / 5040.0);
+  s = s * r + df(1.0 / 720.0);
+  s = s * r + df(1.0 / 120.0);
+  s = s * r + df(1.0 / 24.0);
+  s = s * r + df(1.0 / 6.0);
+  s = s * r + df(0.5);
+  s = s * r + df(1.0);
+  s = s * r;
+  // (1 + s)^2 - 1 = s (2 + s), four times
+#pragma unroll
+  for (int i = 0; i < 4; ++i) s = s * (s + df(2.0f, 0.0f));
+  return ldexp_df(s + df(1.0f, 0.0f), (int)k);
+}
+
+__device__ __forceinline__ df log_df(df a) {
+  // one Newton step on exp: y1 = y0 + a exp(-y0) - 1
+  if (!(a.hi > 0.0f)) return df(-__int_as_float(0x7f800000), 0.0f);
+  const df y0(logf(a.hi), 0.0f);
+  return y0 + (a * exp_df(-y0) - df(1.0f, 0.0f));
+}
+
+}  // namespace lsmc

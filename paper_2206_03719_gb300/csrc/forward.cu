@@ -10,7 +10,10 @@
 // path-minor: the layout of Sec. 4.1, Fig. "datalayout").
 #include <cstdio>
 
+#include <type_traits>
+
 #include "device_common.cuh"
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "plan.h"
 
@@ -28,6 +31,12 @@ template <> struct Fm<float> {
   __device__ static float sqrt_(float a) { return sqrtf(a); }
   __device__ static float log_(float a) { return __logf(a); }
   __device__ static float exp_(float a) { return __expf(a); }
+};
+template <> struct Fm<df> {
+  __device__ static df div(df a, df b) { return a / b; }
+  __device__ static df sqrt_(df a) { return sqrt_df(a); }
+  __device__ static df log_(df a) { return log_df(a); }
+  __device__ static df exp_(df a) { return exp_df(a); }
 };
 
 template <typename Real>
@@ -146,7 +155,7 @@ forward_kernel(FwdArgs a) {
     if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
   }
 
-  if constexpr (sizeof(Real) == 8) {
+  if constexpr (std::is_same<Real, double>::value) {
     // double precision is bound by the FP64 pipe: keep every group's state
     // and constants in registers (one CTA per SM is enough to fill it)
     Real x[kMaxGroups], v[kMaxGroups];
@@ -175,7 +184,7 @@ forward_kernel(FwdArgs a) {
       }
     }
   } else {
-    // single precision is bound by latency and issue: the group loop is not
+    // single precision and float pairs are bound by latency and issue: the group loop is not
     // unrolled, so the constants are read from shared memory where they are
     // used and the per-group state lives in shared memory too; the kernel
     // then needs few registers and many warps fit on an SM
@@ -229,20 +238,19 @@ __global__ void draws_kernel(uint2 key, uint32_t stream_id,
   out[3 * i + 2] = zX;
 }
 
-cudaError_t launch_forward(const FwdArgs& a, bool fp64, int scheme,
-                           cudaStream_t s) {
+template <typename Real>
+static void launch_forward_t(const FwdArgs& a, int scheme, cudaStream_t s) {
+  if (scheme == kSchemeQE)
+    forward_kernel<Real, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
+  else
+    forward_kernel<Real, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
+}
+
+cudaError_t launch_forward(const FwdArgs& a, int precision, int scheme, cudaStream_t s) {
   if (a.n_blocks == 0) return cudaSuccess;
-  if (fp64) {
-    if (scheme == kSchemeQE)
-      forward_kernel<double, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
-    else
-      forward_kernel<double, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
-  } else {
-    if (scheme == kSchemeQE)
-      forward_kernel<float, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
-    else
-      forward_kernel<float, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
-  }
+  if (precision == kPrecFP64) launch_forward_t<double>(a, scheme, s);
+  else if (precision == kPrecDF) launch_forward_t<df>(a, scheme, s);
+  else launch_forward_t<float>(a, scheme, s);
   return cudaGetLastError();
 }
 
@@ -256,13 +264,15 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
 }
 
 cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path,
-                         const uint32_t* step, size_t n, bool fp64, void* out,
+                         const uint32_t* step, size_t n, int precision, void* out,
                          cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const size_t blocks = (n + kBlock - 1) / kBlock;
   const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-  if (fp64)
+  if (precision == kPrecFP64)
     draws_kernel<double><<<(unsigned)blocks, kBlock, 0, s>>>(key, stream_id, path, step, n, (double*)out);
+  else if (precision == kPrecDF)
+    draws_kernel<df><<<(unsigned)blocks, kBlock, 0, s>>>(key, stream_id, path, step, n, (df*)out);
   else
     draws_kernel<float><<<(unsigned)blocks, kBlock, 0, s>>>(key, stream_id, path, step, n, (float*)out);
   return cudaGetLastError();

@@ -8,21 +8,23 @@
 
 namespace lsmc {
 
-cudaError_t launch_forward(const FwdArgs& a, bool fp64, int scheme, cudaStream_t s);
+cudaError_t launch_forward(const FwdArgs& a, int precision, int scheme, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1,
                           uint32_t* out, size_t n, cudaStream_t s);
 cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path,
-                         const uint32_t* step, size_t n, bool fp64, void* out,
+                         const uint32_t* step, size_t n, int precision, void* out,
                          cudaStream_t s);
 cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s);
-cudaError_t launch_backward(const BwdArgs& a, bool fp64, int basis, int grid,
+cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int grid,
                             cudaStream_t s);
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
                           DevResult* out, cudaStream_t s);
-// paths per backward job
-int backward_tile(bool fp64);
+// paths per backward sub-tile
+int backward_tile(int precision);
 // resident backward CTAs per SM
-int backward_occupancy(bool fp64, int basis);
+int backward_occupancy(int precision, int basis);
+// bytes of one stored path value (E, V, cash flow) in a precision
+inline size_t value_bytes(int precision) { return precision == kPrecMixed ? 4 : 8; }
 
 }  // namespace lsmc
 

@@ -29,6 +29,8 @@ constexpr int kSlotTies = 24;
 constexpr double kTieRel = 1e-10;
 
 enum : int32_t { kSchemeQE = 0, kSchemeFT = 1 };
+// precisions (values of lsmc_request.precision)
+enum : int32_t { kPrecFP64 = 0, kPrecMixed = 1, kPrecDF = 2 };
 enum : int32_t { kPut = 0, kCall = 1 };
 enum : int32_t { kAmerican = 0, kEuropean = 1 };
 enum : int32_t { kBasisS2 = 0, kBasisSV2 = 1 };

@@ -93,7 +93,7 @@ int validate_request(const lsmc_request& q, int precision, int scheme) {
     return LSMC_EINVAL;
   if (scheme != LSMC_SCHEME_QE && scheme != LSMC_SCHEME_FT_EULER) return LSMC_EINVAL;
   if (scheme == LSMC_SCHEME_QE && !(m.xi > 0)) return LSMC_EINVAL;
-  if (precision != LSMC_FP64 && precision != LSMC_MIXED) return LSMC_EINVAL;
+  if (precision != LSMC_FP64 && precision != LSMC_MIXED && precision != LSMC_DF) return LSMC_EINVAL;
   if (q.type != LSMC_PUT && q.type != LSMC_CALL) return LSMC_EINVAL;
   if (q.style != LSMC_AMERICAN && q.style != LSMC_EUROPEAN) return LSMC_EINVAL;
   if (q.basis != LSMC_BASIS_S2 && q.basis != LSMC_BASIS_SV2) return LSMC_EINVAL;
@@ -164,9 +164,9 @@ static bool same_path_group(const Scenario& a, const lsmc_heston& g, double gT) 
          m.xi == g.xi && m.rho == g.rho && m.q == g.q;
 }
 
-uint32_t choose_sub(const lsmc_request* reqs, size_t n, bool fp64, uint32_t ctas,
+uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, uint32_t ctas,
                     uint32_t jobs_per_cta) {
-  const uint64_t tile0 = (uint64_t)backward_tile(fp64);
+  const uint64_t tile0 = (uint64_t)backward_tile(precision);
   uint64_t tiles = 0;  // sub-tiles of the first round, over all instances
   for (size_t i = 0; i < n; ++i) {
     std::vector<Scenario> sc;
@@ -182,9 +182,8 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
                  PlanLayout* L) {
   *L = PlanLayout();
   L->opt = opt;
-  const bool fp64 = opt.precision == LSMC_FP64;
-  const size_t real = fp64 ? 8 : 4;
-  const uint32_t tile = (uint32_t)backward_tile(fp64) * std::max<uint32_t>(1, opt.sub);
+  const size_t real = value_bytes(opt.precision);
+  const uint32_t tile = (uint32_t)backward_tile(opt.precision) * std::max<uint32_t>(1, opt.sub);
   const bool store_v = opt.basis == LSMC_BASIS_SV2;
   // device offsets are relative to the region starts; the caller binds them
   size_t off_paths = 0, off_y = 0, off_partial = 0, off_scale = 0;

@@ -58,7 +58,7 @@ struct PlanOptions {
 
 // Sub-tiles per backward job so that the busiest round has about
 // jobs_per_cta jobs for each of `ctas` resident CTAs.
-uint32_t choose_sub(const lsmc_request* reqs, size_t n, bool fp64, uint32_t ctas,
+uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, uint32_t ctas,
                     uint32_t jobs_per_cta = 4);
 
 // Sizes and host tables of one launch; device pointers are bound later.

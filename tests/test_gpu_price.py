@@ -54,12 +54,14 @@ VARIANTS = [
 ]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df"])
 @pytest.mark.parametrize("kw", VARIANTS, ids=[str(i) for i in range(len(VARIANTS))])
-def test_variants_match_oracle(ctx, kw):
+def test_variants_match_oracle(ctx, kw, prec):
     wl = workloads.SMALL_FP64.replace(n_paths=4096, n_steps=24, **kw) if "n_paths" not in kw \
         else workloads.SMALL_FP64.replace(**kw)
+    wl = wl.replace(precision=prec)
     got = ctx.price(wl)
-    ref = oracle_for(wl)
+    ref = oracle_for(wl.replace(precision="fp64"))
     for g, r in zip(got, ref):
         keys = ["price", "european_price"] + [k for k in wl.greeks]
         assert_close(g, r, parity_tol(g["n_near_ties"]), keys=keys, what=str(kw))
@@ -67,17 +69,19 @@ def test_variants_match_oracle(ctx, kw):
         assert g["n_revaluations"] == r["n_revaluations"]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df"])
 @pytest.mark.parametrize("name", ["paper_fp64", "paper_fp64_ft"])
-def test_paper_size_fp64_matches_stored_oracle_values(ctx, name):
+def test_paper_size_matches_stored_oracle_values(ctx, name, prec):
     path = os.path.join(GOLDEN, name + ".json")
     gold = json.load(open(path))
-    wl = workloads.PAPER_FP64.replace(scheme=gold["scheme"])
+    wl = workloads.PAPER_FP64.replace(scheme=gold["scheme"], precision=prec)
     assert gold["n_paths"] == wl.n_paths and gold["n_steps"] == wl.n_steps
     got = ctx.price(wl)
     seen = []
     for g, r in zip(got, gold["results"]):
         assert g["n_revaluations"] == 11
-        print("%s K=%g near ties %d" % (name, wl.strikes[len(seen)], g["n_near_ties"]))
+        print("%s %s K=%g near ties %d price rel err %.3g" % (
+            name, prec, wl.strikes[len(seen)], g["n_near_ties"], rel_err(g["price"], r["price"])))
         seen.append(g)
         # Greeks are differences of revaluations: a flipped decision in one of
         # them is divided by the bump, so only the price falls back to 1e-4

@@ -70,6 +70,19 @@ def test_draws_fp64_grid_exact_quantiles_close(torch):
     assert np.all(err <= 4e-15 * np.maximum(1.0, np.abs(ref[:, 1:])))
 
 
+def test_draws_pairs_are_the_fp64_draws(torch):
+    n = 20001
+    path, step = _pairs(n, 2)
+    d_path = torch.from_numpy(path.view(np.int32)).cuda()
+    d_step = torch.from_numpy(step.view(np.int32)).cuda()
+    out = torch.empty((n, 3, 2), dtype=torch.float32, device="cuda")
+    L.lsmc_draws(77, 4, d_path.data_ptr(), d_step.data_ptr(), n, L.LSMC_DF, out.data_ptr())
+    got = _pairs_to_f64(out.cpu().numpy())
+    ref = oracle.draws(77, 4, path, step, oracle.GRID_F64)
+    err = np.abs(got - ref)
+    assert np.all(err <= 2e-14 * np.maximum(1.0, np.abs(ref)))
+
+
 def test_draws_fp32_grid_exact_quantiles_close(torch):
     n = 50001
     path, step = _pairs(n, 1)
@@ -84,24 +97,41 @@ def test_draws_fp32_grid_exact_quantiles_close(torch):
     assert np.all(err <= 2e-6 * np.maximum(1.0, np.abs(ref[:, 1:])))
 
 
+def _pairs_to_f64(a):
+    """(..., 2) float32 pairs (hi, lo) -> float64 hi + lo."""
+    return a[..., 0].astype(np.float64) + a[..., 1].astype(np.float64)
+
+
+def _f64_to_pairs(x):
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    return np.stack([hi, lo], axis=-1)
+
+
 def _gpu_paths(torch, model, T, scheme, precision, P, N, seed, stream_id):
+    shape = (N + 1, P, 2) if precision == L.LSMC_DF else (N + 1, P)
     dt = torch.float64 if precision == L.LSMC_FP64 else torch.float32
-    S = torch.full((N + 1, P), float("nan"), dtype=dt, device="cuda")
-    V = torch.full((N + 1, P), float("nan"), dtype=dt, device="cuda")
+    S = torch.full(shape, float("nan"), dtype=dt, device="cuda")
+    V = torch.full(shape, float("nan"), dtype=dt, device="cuda")
     L.lsmc_paths(L.lsmc_heston(**model), T, scheme, precision, P, N, seed, stream_id,
                  S.data_ptr(), V.data_ptr())
     torch.cuda.synchronize()
+    if precision == L.LSMC_DF:
+        return _pairs_to_f64(S.cpu().numpy()), _pairs_to_f64(V.cpu().numpy())
     return S.cpu().numpy().astype(np.float64), V.cpu().numpy().astype(np.float64)
 
 
+@pytest.mark.parametrize("prec", [L.LSMC_FP64, L.LSMC_DF])
 @pytest.mark.parametrize("scheme", [L.LSMC_SCHEME_QE, L.LSMC_SCHEME_FT_EULER])
 @pytest.mark.parametrize("P,N", [(1000, 40), (257, 3), (1, 1)])
-def test_paths_fp64_match_oracle(torch, scheme, P, N):
+def test_paths_fp64_and_pairs_match_oracle(torch, prec, scheme, P, N):
     model = dict(H, xi=0.5, v0=0.02)  # both QE branches are visited
-    S, V = _gpu_paths(torch, model, 0.75, scheme, L.LSMC_FP64, P, N, 7, 3)
+    S, V = _gpu_paths(torch, model, 0.75, scheme, prec, P, N, 7, 3)
     So, Vo = oracle.paths(oracle.heston(**model), 0.75, scheme, P, N, 7, 3)
-    assert np.allclose(S, So, rtol=1e-12, atol=0)
-    assert np.allclose(V, Vo, rtol=1e-11, atol=1e-15)
+    # float pairs carry about 48 bits
+    rtol_s, rtol_v = (1e-12, 1e-11) if prec == L.LSMC_FP64 else (1e-11, 1e-10)
+    assert np.allclose(S, So, rtol=rtol_s, atol=0)
+    assert np.allclose(V, Vo, rtol=rtol_v, atol=1e-14)
 
 
 @pytest.mark.parametrize("scheme", [L.LSMC_SCHEME_QE, L.LSMC_SCHEME_FT_EULER])
@@ -117,9 +147,13 @@ def test_paths_fp32_match_oracle_on_the_same_stream(torch, scheme):
 
 def _backward(torch, S, V, precision, model, K, T, type_, style, basis):
     N, P = S.shape[0] - 1, S.shape[1]
-    dt = torch.float64 if precision == L.LSMC_FP64 else torch.float32
-    dS = torch.from_numpy(S).to(dt).cuda()
-    dV = torch.from_numpy(V).to(dt).cuda()
+    if precision == L.LSMC_DF:
+        dS = torch.from_numpy(_f64_to_pairs(S)).cuda()
+        dV = torch.from_numpy(_f64_to_pairs(V)).cuda()
+    else:
+        dt = torch.float64 if precision == L.LSMC_FP64 else torch.float32
+        dS = torch.from_numpy(S).to(dt).cuda()
+        dV = torch.from_numpy(V).to(dt).cuda()
     out = torch.zeros(5, dtype=torch.float64, device="cuda")
     beta = torch.zeros((N, 6), dtype=torch.float64, device="cuda")
     ns = torch.zeros(1, dtype=torch.int32, device="cuda")
@@ -130,14 +164,18 @@ def _backward(torch, S, V, precision, model, K, T, type_, style, basis):
     return out.cpu().numpy(), beta.cpu().numpy(), int(ns.cpu().numpy()[0])
 
 
+@pytest.mark.parametrize("prec", [L.LSMC_FP64, L.LSMC_DF])
 @pytest.mark.parametrize("basis", [L.LSMC_BASIS_S2, L.LSMC_BASIS_SV2])
 @pytest.mark.parametrize("type_,K", [(L.LSMC_PUT, 100.0), (L.LSMC_CALL, 95.0), (L.LSMC_PUT, 70.0)])
 @pytest.mark.parametrize("style", [L.LSMC_AMERICAN, L.LSMC_EUROPEAN])
-def test_backward_fp64_matches_oracle_on_oracle_paths(torch, basis, type_, K, style):
+def test_backward_fp64_and_pairs_match_oracle_on_oracle_paths(torch, prec, basis, type_, K, style):
     model = dict(H, q=0.01)
     P, N, T = 3000, 20, 1.0
     S, V = oracle.paths(oracle.heston(**model), T, oracle.QE, P, N, 99, 0)
-    got, beta, ns = _backward(torch, S, V, L.LSMC_FP64, model, K, T, type_, style, basis)
+    if prec == L.LSMC_DF:  # the oracle sees the paths the pairs hold
+        S = _pairs_to_f64(_f64_to_pairs(S))
+        V = _pairs_to_f64(_f64_to_pairs(V))
+    got, beta, ns = _backward(torch, S, V, prec, model, K, T, type_, style, basis)
     ref = oracle.lsmc(S, V, 100.0, K, T, model["r"], model["theta"], type_=type_, style=style,
                       basis=basis, want_detail=True)
     tol = parity_tol(got[4])
@@ -149,7 +187,7 @@ def test_backward_fp64_matches_oracle_on_oracle_paths(torch, basis, type_, K, st
         assert np.array_equal(np.isnan(beta[1:, 0]), np.isnan(rb[1:, 0]))
         ok = ~np.isnan(rb[1:, 0])
         scale = np.abs(rb[1:][ok]).max() if ok.any() else 1.0
-        assert np.allclose(beta[1:][ok], rb[1:][ok], rtol=0, atol=1e-6 * scale)
+        assert np.allclose(beta[1:][ok], rb[1:][ok], rtol=0, atol=(1e-6 if prec == L.LSMC_FP64 else 1e-4) * scale)
 
 
 @pytest.mark.parametrize("basis", [L.LSMC_BASIS_S2, L.LSMC_BASIS_SV2])
