@@ -189,52 +189,48 @@ def run_reference(args, wl):
 
 
 
-def measure_mixed_large(api, L, torch):
-    """Precision split at 1,048,576 paths: Greeks/s of the MIXED path and its
-    error against the FP64 GPU path on the same random stream."""
-    wl = workloads.LARGE_MIXED
+def measure_precision(api, L, torch, wl, reps=3):
+    """Greeks/s of a workload in a reduced or emulated precision and its
+    error against the FP64 GPU path (itself checked against the oracle) on
+    the same random stream."""
     need = L.lsmc_request_footprint(None, api.Request(wl).c)
     need64 = L.lsmc_request_footprint(None, api.Request(wl, precision="fp64").c)
-    out = {"workload": wl.name}
+    out = {"workload": wl.name, "precision": wl.precision, "n_paths": wl.n_paths}
     with api.Context(workspace_bytes=max(need, need64) + (256 << 20)) as ctx:
         plan = ctx.plan([wl])
         for _ in range(3):
             plan.launch()
         plan.fetch()
         plan.set_timing(True)
-        t0 = time.perf_counter()
-        reps = 3
         for _ in range(reps):
             plan.launch()
-        mixed = plan.fetch()
-        wall = (time.perf_counter() - t0) / reps
+        got = plan.fetch()
         kms, launches = plan.kernel_times()
         plan.close()
         ref = ctx.price(wl, precision="fp64")
     errs = {}
-    for g, r in zip(mixed, ref):
+    for g, r in zip(got, ref):
         for k in ("price", "delta", "gamma", "vega", "rho", "theta"):
             e = abs(g[k] - r[k]) / max(abs(r[k]), 1e-12)
             errs[k] = max(errs.get(k, 0.0), e)
     ms = sum(kms) / max(1, launches)
     out.update({"greeks_per_s": wl.n_greeks / (ms / 1e3), "ms_per_step": ms,
-                "wall_ms_per_step": wall * 1e3,
                 "generated_path_steps_per_s": wl.generated_path_steps / (ms / 1e3),
                 "lsmc_path_steps_per_s": wl.lsmc_path_steps / (ms / 1e3),
                 "kernel_ms": {"forward": kms[1] / max(1, launches),
                               "backward": kms[2] / max(1, launches)},
                 "max_rel_err_vs_fp64_gpu": errs,
-                "within_1e-4": {k: v <= 1e-4 for k, v in errs.items()}})
+                "all_within_1e-4": all(v <= 1e-4 for v in errs.values())})
     return out
 
 
-def measure_book(api, L, torch, n_contracts=512, chunk=128):
+def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     """Uneven book (512 contracts, all bump scenarios, FP32 paths / FP64
     reductions) in launches of `chunk` contracts, each captured once in a CUDA
     graph and replayed; device time summed over the chunks (each chunk holds
     its own paths, so chunks run one after another within a workspace of the
     largest chunk's size)."""
-    book = workloads.book(n_contracts=n_contracts, precision="mixed")
+    book = workloads.book(n_contracts=n_contracts, precision=precision)
     chunks = [book[i:i + chunk] for i in range(0, len(book), chunk)]
     need = max(sum(L.lsmc_request_footprint(None, api.Request(w).c) for w in c) for c in chunks)
     greeks = sum(w.n_greeks for w in book)
@@ -257,17 +253,18 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128):
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
-            "precision": "mixed", "graph": True}
+            "precision": precision, "graph": True}
 
 
-def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32):
+def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
+                    precision="mixed"):
     """Poisson stream of book-distributed requests with continuous batching
     (MIXED; up to 16 requests on the device at once, admitted by workspace
     bytes), and the first `serial_n` of the same requests solved one at a
     time in plain FP64 on the same GPU."""
     arrivals = workloads.poisson_arrivals(rate, warm_s + window_s, seed=11)
-    reqs = workloads.book(n_contracts=len(arrivals), seed=99, precision="mixed")
-    with api.Context(workspace_bytes=48 << 30, max_inflight=16, precision="mixed") as srv:
+    reqs = workloads.book(n_contracts=len(arrivals), seed=99, precision=precision)
+    with api.Context(workspace_bytes=48 << 30, max_inflight=16, precision=precision) as srv:
         t0 = time.perf_counter()
         tickets = []
         for t_arr, w in zip(arrivals, reqs):
@@ -290,7 +287,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     served = {"rate_per_s": rate, "window_s": window_s, "requests": len(tickets), "ok": ok,
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
-              "precision": "mixed", "max_inflight": 16}
+              "precision": precision, "max_inflight": 16}
     # the same requests, one at a time, plain FP64
     serial = reqs[:serial_n]
     need = max(L.lsmc_request_footprint(None, api.Request(w, precision="fp64").c) for w in serial)
@@ -387,8 +384,19 @@ def main():
     ctx.close()
     extras = {}
     if not args.no_extras and not args.paths and args.workload == "paper_fp64":
-        for name, fn in (("precision_split", measure_mixed_large), ("book", measure_book),
-                         ("serving", measure_serving)):
+        df_paper = workloads.PAPER_FP64.replace(
+            precision="df", name="american-put-heston-131072x252-5strikes-df")
+        df_large = workloads.LARGE_MIXED.replace(
+            precision="df", name="american-put-heston-1048576x252-5strikes-df")
+        jobs = (("precision_split", lambda *a: {
+                    "df_paper": measure_precision(*a, df_paper),
+                    "df_large": measure_precision(*a, df_large),
+                    "mixed_large": measure_precision(*a, workloads.LARGE_MIXED)}),
+                ("book", lambda *a: {"df": measure_book(*a, precision="df"),
+                                     "mixed": measure_book(*a, precision="mixed")}),
+                ("serving", lambda *a: {"df": measure_serving(*a, precision="df"),
+                                        "mixed": measure_serving(*a, precision="mixed")}))
+        for name, fn in jobs:
             torch.cuda.empty_cache()
             try:
                 extras[name] = fn(api, L, torch)

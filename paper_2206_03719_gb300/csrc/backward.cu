@@ -48,6 +48,30 @@ __device__ __forceinline__ Real payoff(int type, Real K, Real S) {
   return h > (Real)0 ? h : (Real)0;
 }
 
+// Inner-loop arithmetic: plain operators for float and double, the cheaper
+// unnormalised forms for float pairs.
+template <typename R> __device__ __forceinline__ R qmul(R a, R b) { return a * b; }
+template <> __device__ __forceinline__ df qmul<df>(df a, df b) { return mul_nr(a, b); }
+template <typename R> __device__ __forceinline__ void qacc(R& s, R t) { s += t; }
+template <> __device__ __forceinline__ void qacc<df>(df& s, df t) { acc_pair(s, t); }
+// a * b + c
+template <typename R> __device__ __forceinline__ R qfma(R a, R b, R c) { return fma(a, b, c); }
+template <> __device__ __forceinline__ df qfma<df>(df a, df b, df c) {
+  return add_sloppy(mul_nr(a, b), c);
+}
+// in-the-money payoff: h > 0 (for pairs, the sign of the unevaluated sum)
+template <typename R> __device__ __forceinline__ bool positive(R h) { return h > (R)0; }
+template <> __device__ __forceinline__ bool positive<df>(df h) {
+  return h.hi > 0.0f || (h.hi == 0.0f && h.lo > 0.0f);
+}
+template <typename R> __device__ __forceinline__ R qsub(R a, R b) { return a - b; }
+template <> __device__ __forceinline__ df qsub<df>(df a, df b) { return add_sloppy(a, -b); }
+// payoff without the max: put K - S, call S - K
+template <typename R>
+__device__ __forceinline__ R intrinsic(int type, R K, R S) {
+  return type == kPut ? qsub(K, S) : qsub(S, K);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -184,7 +208,10 @@ template <int NA> struct Acc<df, NA> {
   }
   __device__ __forceinline__ df* target() { return s; }
   __device__ __forceinline__ void fold() {}
-  __device__ __forceinline__ float2 pair(int i) const { return make_float2(s[i].hi, s[i].lo); }
+  __device__ __forceinline__ float2 pair(int i) const {
+    const df t = quick_two_sum(s[i].hi, s[i].lo);
+    return make_float2(t.hi, t.lo);
+  }
 };
 template <int NA> struct Acc<float, NA> {
   float hi[NA], lo[NA], t[NA];
@@ -406,19 +433,34 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           z[k] = zr[k];
           if (bok && p < P) {
-            const Real S = s1 * e1[k];
-            const Real h = payoff<Real>(type, K, S);
-            if (h > (Real)0) {
-              const Real x = fma(S, invK, (Real)-1);
-              Real c = fma(fma(b[2], x, b[1]), x, b[0]);
+            const Real S = qmul(s1, e1[k]);
+            const Real h = intrinsic<Real>(type, K, S);
+            if (positive(h)) {
+              const Real x = qfma(S, invK, (Real)-1);
+              Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
               if (BASIS == kBasisSV2) {
-                const Real w = fma(v1[k], invTh, (Real)-1);
-                c = fma(fma(b[5], w, fma(b[4], x, b[3])), w, c);
+                const Real w = qfma(v1[k], invTh, (Real)-1);
+                c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
               }
-              const Real hd = h * d1;
-              if (fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd)) ++ties;
-              if (hd > c) {
-                const Real hz = fma(h, d1, h * d1lo);
+              const Real hd = qmul(h, d1);
+              bool tie, exercise;
+              if constexpr (std::is_same<Real, df>::value) {
+                // the threshold only needs the leading floats
+                const df diff = qsub(hd, c);
+                tie = fabsf(diff.hi) <= (float)kTieRel * fmaxf(fabsf(c.hi), hd.hi);
+                exercise = positive(diff);
+              } else {
+                tie = fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd);
+                exercise = hd > c;
+              }
+              if (tie) ++ties;
+              if (exercise) {
+                Real hz;
+                if constexpr (std::is_same<Real, df>::value) {
+                  hz = quick_two_sum(hd.hi, hd.lo);
+                } else {
+                  hz = fma(h, d1, h * d1lo);
+                }
                 z[k] = hz;
                 if (!final_job) Z[p] = hz;
               }
@@ -445,38 +487,40 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           if (p < P) {
             const Real yv = z[k];
-            const Real S = s0 * e0[k];
-            const Real h = payoff<Real>(type, K, S);
-            if (h > (Real)0) {
-              const Real x = fma(S, invK, (Real)-1), x2 = x * x, x3 = x2 * x, x4 = x2 * x2;
-              t[0] += (Real)1;
-              t[1] += x;
-              t[2] += x2;
-              t[3] += x3;
-              t[4] += x4;
+            const Real S = qmul(s0, e0[k]);
+            const Real h = intrinsic<Real>(type, K, S);
+            if (positive(h)) {
+              const Real x = qfma(S, invK, (Real)-1);
+              const Real x2 = qmul(x, x), x3 = qmul(x2, x), x4 = qmul(x2, x2);
+              qacc(t[0], (Real)1);
+              qacc(t[1], x);
+              qacc(t[2], x2);
+              qacc(t[3], x3);
+              qacc(t[4], x4);
               if (BASIS == kBasisSV2) {
-                const Real w = fma(v0[k], invTh, (Real)-1), w2 = w * w, w3 = w2 * w, w4 = w2 * w2;
-                const Real xw = x * w;
-                t[mono(0, 1)] += w;
-                t[mono(1, 1)] += xw;
-                t[mono(2, 1)] += x2 * w;
-                t[mono(3, 1)] += x3 * w;
-                t[mono(0, 2)] += w2;
-                t[mono(1, 2)] += x * w2;
-                t[mono(2, 2)] += x2 * w2;
-                t[mono(0, 3)] += w3;
-                t[mono(1, 3)] += x * w3;
-                t[mono(0, 4)] += w4;
-                t[NM + 0] += yv;
-                t[NM + 1] += x * yv;
-                t[NM + 2] += x2 * yv;
-                t[NM + 3] += w * yv;
-                t[NM + 4] += xw * yv;
-                t[NM + 5] += w2 * yv;
+                const Real w = qfma(v0[k], invTh, (Real)-1);
+                const Real w2 = qmul(w, w), w3 = qmul(w2, w), w4 = qmul(w2, w2);
+                const Real xw = qmul(x, w);
+                qacc(t[mono(0, 1)], w);
+                qacc(t[mono(1, 1)], xw);
+                qacc(t[mono(2, 1)], qmul(x2, w));
+                qacc(t[mono(3, 1)], qmul(x3, w));
+                qacc(t[mono(0, 2)], w2);
+                qacc(t[mono(1, 2)], qmul(x, w2));
+                qacc(t[mono(2, 2)], qmul(x2, w2));
+                qacc(t[mono(0, 3)], w3);
+                qacc(t[mono(1, 3)], qmul(x, w3));
+                qacc(t[mono(0, 4)], w4);
+                qacc(t[NM + 0], yv);
+                qacc(t[NM + 1], qmul(x, yv));
+                qacc(t[NM + 2], qmul(x2, yv));
+                qacc(t[NM + 3], qmul(w, yv));
+                qacc(t[NM + 4], qmul(xw, yv));
+                qacc(t[NM + 5], qmul(w2, yv));
               } else {
-                t[NM + 0] += yv;
-                t[NM + 1] += x * yv;
-                t[NM + 2] += x2 * yv;
+                qacc(t[NM + 0], yv);
+                qacc(t[NM + 1], qmul(x, yv));
+                qacc(t[NM + 2], qmul(x2, yv));
               }
             }
           }

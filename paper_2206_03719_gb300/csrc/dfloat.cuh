@@ -103,6 +103,33 @@ __device__ __forceinline__ df df_abs(df a) { return a.hi < 0.0f ? -a : a; }
 __device__ __forceinline__ df df_max(df a, df b) { return a < b ? b : a; }
 __device__ __forceinline__ df df_fma(df a, df b, df c) { return a * b + c; }
 
+// ---- cheaper forms for inner loops ---------------------------------------
+// Product without the final renormalisation: hi is the float product, lo
+// carries the rest unnormalised (|lo| a few ulps of hi).  Fine as an input
+// to further products and sums.
+__device__ __forceinline__ df mul_nr(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df(p, e);
+}
+
+// Sum without cancellation guarantees (Dekker's "sloppy" addition): exact
+// two-sum of the high parts, low parts added; accurate unless a ~ -b.
+__device__ __forceinline__ df add_sloppy(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+// Running sum of pairs: two-sum of the high parts, the low parts collected
+// unnormalised (renormalise with quick_two_sum before using the total).
+__device__ __forceinline__ void acc_pair(df& s, df t) {
+  const df h = two_sum(s.hi, t.hi);
+  s.hi = h.hi;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(h.lo, t.lo));
+}
+
 // x * 2^k, exact
 __device__ __forceinline__ df ldexp_df(df a, int k) {
   return df(ldexpf(a.hi, k), ldexpf(a.lo, k));
