@@ -197,6 +197,7 @@ def measure_precision(api, L, torch, wl, reps=3):
     need64 = L.lsmc_request_footprint(None, api.Request(wl, precision="fp64").c)
     out = {"workload": wl.name, "precision": wl.precision, "n_paths": wl.n_paths}
     with api.Context(workspace_bytes=max(need, need64) + (256 << 20)) as ctx:
+        ctx.autotune([wl])
         plan = ctx.plan([wl])
         for _ in range(3):
             plan.launch()
@@ -238,7 +239,9 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     lsmc = sum(w.lsmc_path_steps for w in book)
     total_ms = 0.0
     with api.Context(workspace_bytes=need + (512 << 20)) as ctx:
+        subs = []
         for c in chunks:
+            subs.append(ctx.autotune(c)[0])
             p = ctx.plan(c)
             p.launch(use_graph=True)  # capture and warm
             p.fetch()
@@ -253,7 +256,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
-            "precision": precision, "graph": True}
+            "precision": precision, "graph": True, "autotuned_subtiles": subs}
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
@@ -330,6 +333,7 @@ def main():
     req = api.Request(wl)
     need = L.lsmc_request_footprint(None, req.c)
     ctx = api.Context(workspace_bytes=need + (256 << 20))
+    tuned_sub, tuned_ms = ctx.autotune([wl])
     plan = ctx.plan([wl])
     info = plan.info()
     stream = ctx.stream
@@ -443,6 +447,7 @@ def main():
                    "strikes": wl.strikes, "greeks": list(wl.greeks),
                    "revaluations": wl.n_scenarios, "scheme": wl.scheme, "basis": wl.basis,
                    "precision": wl.precision, "parallelism": "replicas" if world > 1 else "single",
+                   "backward_subtiles_per_job": tuned_sub,
                    "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
         "path_steps_per_s": {"generated": world * wl.generated_path_steps / (ms_max / 1e3),
                              "lsmc": world * wl.lsmc_path_steps / (ms_max / 1e3)},

@@ -106,6 +106,11 @@ class Context:
         reqs = [Request(w, **kw) for w in wls]
         return [r.as_dict() for r in L.lsmc_price_book(self.ctx, [q.c for q in reqs])]
 
+    def autotune(self, wls: Sequence[Workload], **kw):
+        """(sub-tiles per backward job, backward ms) chosen for these requests."""
+        reqs = [Request(w, **kw) for w in wls]
+        return L.lsmc_autotune(self.ctx, [q.c for q in reqs])
+
     def plan(self, wls: Sequence[Workload], **kw) -> "Plan":
         return Plan(self, wls, **kw)
 

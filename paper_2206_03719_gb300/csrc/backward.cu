@@ -267,37 +267,43 @@ backward_kernel(BwdArgs a) {
   // single precision and float pairs reduce through float pairs; double
   // precision through doubles
   constexpr bool kSingle = !std::is_same<Real, double>::value;
+  // Job decoding by thread 0: the job number `next` was taken from the
+  // counter one job earlier, so the atomic's latency is hidden.
   unsigned long long next = 0;
-  if (tid == 0) next = atomicAdd(&a.ctl->next_job, 1ull);
+  auto decode = [&]() {
+    JobInfo ji;
+    ji.job = next;
+    ji.abort = 0;
+    ji.round = ji.inst = ji.tile = 0;
+    if (ld_volatile(&a.ctl->error) != 0 || next >= a.total_jobs) {
+      ji.abort = 1;
+    } else {
+      next = atomicAdd(&a.ctl->next_job, 1ull);
+      // round: last r with round_off[r] <= job
+      uint32_t lo = 0, hi = a.n_rounds;
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) / 2;
+        if (a.round_off[mid] <= ji.job) lo = mid; else hi = mid;
+      }
+      const uint32_t local = (uint32_t)(ji.job - a.round_off[lo]);
+      uint32_t klo = 0, khi = a.active[lo];
+      while (khi - klo > 1) {
+        const uint32_t mid = (klo + khi) / 2;
+        if (a.cum_tiles[mid] <= local) klo = mid; else khi = mid;
+      }
+      ji.round = lo;
+      ji.inst = klo;
+      ji.tile = local - a.cum_tiles[klo];
+    }
+    s_job = ji;
+  };
+  if (tid == 0) {
+    next = atomicAdd(&a.ctl->next_job, 1ull);
+    decode();
+  }
+  __syncthreads();
 
   for (;;) {
-    if (tid == 0) {
-      JobInfo ji;
-      ji.job = next;
-      ji.abort = 0;
-      if (ld_volatile(&a.ctl->error) != 0 || next >= a.total_jobs) {
-        ji.abort = 1;
-      } else {
-        next = atomicAdd(&a.ctl->next_job, 1ull);  // prefetch the following job
-        // round: last r with round_off[r] <= job
-        uint32_t lo = 0, hi = a.n_rounds;
-        while (hi - lo > 1) {
-          const uint32_t mid = (lo + hi) / 2;
-          if (a.round_off[mid] <= ji.job) lo = mid; else hi = mid;
-        }
-        const uint32_t local = (uint32_t)(ji.job - a.round_off[lo]);
-        uint32_t klo = 0, khi = a.active[lo];
-        while (khi - klo > 1) {
-          const uint32_t mid = (klo + khi) / 2;
-          if (a.cum_tiles[mid] <= local) klo = mid; else khi = mid;
-        }
-        ji.round = lo;
-        ji.inst = klo;
-        ji.tile = local - a.cum_tiles[klo];
-      }
-      s_job = ji;
-    }
-    __syncthreads();
     const JobInfo ji = s_job;
     if (ji.abort) return;
 
@@ -318,55 +324,58 @@ backward_kernel(BwdArgs a) {
     const bool first = european || r == 0;  // cash flows start at the maturity payoff
     const uint32_t tile_base = ji.tile * (sub * TILE0);
 
-    // ---- wait for the exercise rule of date n + 1 ---------------------------
-    if (!first) {
+    // ---- warp 0: wait for the exercise rule of date n + 1, then convert the
+    // per-job constants to the working precision once ------------------------
+    if (warp == 0) {
       if (tid == 0) {
         int ok = 1;
-        const unsigned long long t0 = global_timer_ns();
-        unsigned spins = 0;
-        while (ld_acquire_gpu(&st->ready) < r) {
-          if (ld_volatile(&a.ctl->error) != 0) { ok = 0; break; }
-          __nanosleep(spins < 64 ? 32 : 256);
-          if (++spins > (1u << 26) || global_timer_ns() - t0 > a.timeout_ns) {
-            atomicCAS(&a.ctl->error, 0u, (uint32_t)kDevErrTimeout);
-            a.ctl->error_info = ji.inst;
-            ok = 0;
-            break;
+        if (!first) {
+          const unsigned long long t0 = global_timer_ns();
+          unsigned spins = 0;
+          while (ld_acquire_gpu(&st->ready) < r) {
+            if (ld_volatile(&a.ctl->error) != 0) { ok = 0; break; }
+            __nanosleep(spins < 64 ? 32 : 256);
+            if (++spins > (1u << 26) || global_timer_ns() - t0 > a.timeout_ns) {
+              atomicCAS(&a.ctl->error, 0u, (uint32_t)kDevErrTimeout);
+              a.ctl->error_info = ji.inst;
+              ok = 0;
+              break;
+            }
           }
-        }
-        if (ok) {
-          __threadfence();
-          s_beta_ok = (int)__ldcg(&st->beta_ok);
-          for (int i = 0; i < 6; ++i) s_beta[i] = __ldcg(&st->beta[i]);
+          if (ok) {
+            __threadfence();
+            s_beta_ok = (int)__ldcg(&st->beta_ok);
+            for (int i = 0; i < 6; ++i) s_beta[i] = __ldcg(&st->beta[i]);
+          }
         }
         s_last = ok ? 0 : -1;
       }
-      __syncthreads();
-      if (s_last < 0) return;
-    }
-
-    // per-job constants, converted to the working precision once per job
-    if (tid < 16) {
-      double v;
-      switch (tid) {
-        case 6: v = stab[n + 1]; break;
-        case 7: v = dtab[n + 1]; break;
-        case 8: v = stab[N]; break;
-        case 9: v = stab[n]; break;
-        case 10: v = I.K; break;
-        case 11: v = I.invK; break;
-        case 12: v = I.inv_theta; break;
-        // discount factors as unevaluated pairs (hi + lo): a cash flow is
-        // h * hi + h * lo, one rounding, with no bias shared by the paths
-        // that exercise on the same date
-        case 13: v = dtab[n + 1] - (double)(Real)dtab[n + 1]; break;
-        case 14: v = dtab[N]; break;
-        case 15: v = dtab[N] - (double)(Real)dtab[N]; break;
-        default: v = first ? 0.0 : s_beta[tid]; break;
+      __syncwarp();
+      if (lane < 16) {
+        double v;
+        switch (lane) {
+          case 6: v = stab[n + 1]; break;
+          case 7: v = dtab[n + 1]; break;
+          case 8: v = stab[N]; break;
+          case 9: v = stab[n]; break;
+          case 10: v = I.K; break;
+          case 11: v = I.invK; break;
+          case 12: v = I.inv_theta; break;
+          // discount factors as unevaluated pairs (hi + lo): a cash flow is
+          // h * hi + h * lo, one rounding, with no bias shared by the paths
+          // that exercise on the same date
+          case 13: v = dtab[n + 1] - (double)(Real)dtab[n + 1]; break;
+          case 14: v = dtab[N]; break;
+          case 15: v = dtab[N] - (double)(Real)dtab[N]; break;
+          default: v = first ? 0.0 : s_beta[lane]; break;
+        }
+        s_c[lane] = (Real)v;
       }
-      s_c[tid] = (Real)v;
     }
     __syncthreads();
+    if (s_last < 0) return;
+    // every thread has read this job: thread 0 decodes the next one now
+    if (tid == 0) decode();
     const int bok = first ? 0 : s_beta_ok;
     Real b[6];
 #pragma unroll
@@ -573,12 +582,17 @@ backward_kernel(BwdArgs a) {
     }
 
     // ---- arrive; the last tile of this round reduces and solves ---------------
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const uint32_t old = atomicAdd(&st->arrive, 1u);
-      s_last = (old + 1 == (r + 1) * I.tiles) ? 1 : 0;
-      if (s_last) __threadfence();
+    // the partial was written by warp 0 alone and every other write of this
+    // job is ordered before the reduction barrier above, so a warp-level
+    // sync suffices before the fence and the arrival
+    if (warp == 0) {
+      __syncwarp();
+      if (tid == 0) {
+        __threadfence();
+        const uint32_t old = atomicAdd(&st->arrive, 1u);
+        s_last = (old + 1 == (r + 1) * I.tiles) ? 1 : 0;
+        if (s_last) __threadfence();
+      }
     }
     __syncthreads();
     if (!s_last) continue;

@@ -62,6 +62,9 @@ struct lsmc_ctx {
   int num_sms = 0;
   int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
+  // autotuned sub-tiles per job, keyed by (precision, basis, log2 of the
+  // first round's sub-tile count)
+  std::map<uint64_t, uint32_t> tuned;
   // serving
   std::mutex mu;
   std::condition_variable cv, done_cv;
@@ -296,6 +299,20 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
   return LSMC_OK;
 }
 
+uint64_t tune_key(const lsmc_request* reqs, size_t n, const PlanOptions& o) {
+  // sub-tiles of the first round over all instances, as a power of two
+  const uint64_t tile0 = (uint64_t)backward_tile(o.precision);
+  uint64_t tiles = 0;
+  for (size_t i = 0; i < n; ++i) {
+    std::vector<Scenario> sc;
+    if (expand_scenarios(reqs[i], &sc) < 0) continue;
+    tiles += (uint64_t)sc.size() * reqs[i].n_strikes * ((reqs[i].n_paths + tile0 - 1) / tile0);
+  }
+  uint64_t lg = 0;
+  while ((2ull << lg) <= tiles) ++lg;
+  return ((uint64_t)o.precision << 40) | ((uint64_t)o.basis << 32) | lg;
+}
+
 int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
                    cudaStream_t stream, bool use_arena, lsmc_plan** out) {
   PlanOptions o;
@@ -307,7 +324,12 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
   p->stream = stream;
   {
     const uint32_t ctas = (uint32_t)occupancy(ctx, o.precision, o.basis) * (uint32_t)sm_count(ctx);
-    o.sub = ctx && ctx->sub_override ? ctx->sub_override : choose_sub(reqs, n, o.precision, ctas);
+    o.sub = choose_sub(reqs, n, o.precision, ctas);
+    if (ctx) {
+      auto it = ctx->tuned.find(tune_key(reqs, n, o));
+      if (it != ctx->tuned.end()) o.sub = it->second;
+      if (ctx->sub_override) o.sub = ctx->sub_override;
+    }
   }
   rc = build_layout(reqs, n, o, &p->L);
   if (rc) return rc;
@@ -786,6 +808,46 @@ int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* s, double* a, doub
   if (s) *s = it->second->t_submit;
   if (a) *a = it->second->t_admit;
   if (d) *d = it->second->t_done;
+  return LSMC_OK;
+}
+
+// ---- autotuner ----------------------------------------------------------------
+int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* best_sub,
+                  double* best_ms) {
+  if (!ctx || !reqs || !n) return LSMC_EINVAL;
+  cudaSetDevice(ctx->device);
+  PlanOptions o;
+  int rc = plan_options(ctx, reqs, n, &o);
+  if (rc) return rc;
+  const uint64_t key = tune_key(reqs, n, o);
+  const uint64_t tiles0 = std::max<uint64_t>(1, 1ull << (key & 0xffffffffu));
+  const uint32_t saved = ctx->sub_override;
+  uint32_t best = 0;
+  double best_t = 1e300;
+  for (uint32_t cand = 1; cand <= 64; cand *= 2) {
+    if (cand > 1 && (uint64_t)cand * 16 > tiles0 * 2) break;  // keep >= 8 jobs a round
+    ctx->sub_override = cand;
+    lsmc_plan* p = nullptr;
+    rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);
+    if (rc) break;
+    p->timing = true;
+    double ms[4] = {0, 0, 0, 0};
+    uint32_t launches = 0;
+    rc = plan_enqueue(p, true);  // warm-up launch, then the timed one
+    if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+    if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+    if (rc == LSMC_OK) rc = plan_enqueue(p, true);
+    if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+    if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+    plan_free(p);
+    if (rc) break;
+    if (ms[2] < best_t) { best_t = ms[2]; best = cand; }
+  }
+  ctx->sub_override = saved;
+  if (rc && !best) return rc;
+  ctx->tuned[key] = best;
+  if (best_sub) *best_sub = best;
+  if (best_ms) *best_ms = best_t;
   return LSMC_OK;
 }
 

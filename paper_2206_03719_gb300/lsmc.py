@@ -30,7 +30,7 @@ EXPORTS = [
     "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book",
     "lsmc_plan_create", "lsmc_plan_launch", "lsmc_plan_fetch",
     "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
-    "lsmc_plan_set_timing", "lsmc_plan_kernel_times",
+    "lsmc_plan_set_timing", "lsmc_plan_kernel_times", "lsmc_autotune",
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_backward", "lsmc_backward_noalloc",
 ]
@@ -136,6 +136,7 @@ def load(build_if_missing: bool = False):
             "lsmc_plan_destroy": ([vp], None),
             "lsmc_plan_set_timing": ([vp, i32], ctypes.c_int),
             "lsmc_plan_kernel_times": ([vp, P(dbl), P(u32)], ctypes.c_int),
+            "lsmc_autotune": ([vp, P(lsmc_request), sz, P(u32), P(dbl)], ctypes.c_int),
             "lsmc_submit": ([vp, P(lsmc_request), P(u64)], ctypes.c_int),
             "lsmc_poll": ([vp, u64, P(lsmc_result)], ctypes.c_int),
             "lsmc_wait": ([vp, u64, P(lsmc_result), dbl], ctypes.c_int),
@@ -266,6 +267,14 @@ def lsmc_plan_kernel_times(plan):
     n = ctypes.c_uint32()
     check(load().lsmc_plan_kernel_times(plan, ms, ctypes.byref(n)), "lsmc_plan_kernel_times")
     return list(ms), n.value
+
+
+def lsmc_autotune(ctx, reqs):
+    arr = (lsmc_request * len(reqs))(*reqs)
+    sub, ms = ctypes.c_uint32(), ctypes.c_double()
+    check(load().lsmc_autotune(ctx, arr, len(reqs), ctypes.byref(sub), ctypes.byref(ms)),
+          "lsmc_autotune")
+    return sub.value, ms.value
 
 
 def lsmc_plan_destroy(plan):

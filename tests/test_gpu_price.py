@@ -140,3 +140,14 @@ def test_invalid_requests_are_rejected_before_launch(ctx):
         with pytest.raises(L.LsmcError) as e:
             ctx.price(workloads.SMALL_FP64.replace(**kw))
         assert e.value.status == L.LSMC_EINVAL
+
+
+def test_autotuned_plans_still_match_oracle(ctx):
+    wl = workloads.SMALL_FP64.replace(n_paths=20000, n_steps=20, basis="sv2",
+                                      greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02)
+    sub, ms = ctx.autotune([wl])
+    assert sub >= 1 and ms > 0
+    got = ctx.price(wl)
+    ref = oracle_for(wl)
+    for g, r in zip(got, ref):
+        assert_close(g, r, parity_tol(g["n_near_ties"]), keys=("price", "delta", "gamma", "vega"))
