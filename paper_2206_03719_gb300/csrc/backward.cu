@@ -72,6 +72,45 @@ __device__ __forceinline__ R intrinsic(int type, R K, R S) {
   return type == kPut ? qsub(K, S) : qsub(S, K);
 }
 
+// In the money (payoff strictly positive) without forming the payoff: for
+// positive doubles the bit patterns order like the values, so the test runs
+// on the integer pipe instead of the narrow FP64 one.
+template <typename R>
+__device__ __forceinline__ bool in_money(int type, R K, R S) {
+  return type == kPut ? S < K : K < S;
+}
+template <>
+__device__ __forceinline__ bool in_money<double>(int type, double K, double S) {
+  const long long s = __double_as_longlong(S), k = __double_as_longlong(K);
+  return type == kPut ? s < k : k < s;
+}
+
+// Exercise decision (discounted payoff hd against fitted value c) and the
+// near-tie flag (|hd - c| within about 1e-10 of max(|c|, hd)).
+template <typename R>
+__device__ __forceinline__ void decide(R hd, R c, bool& exercise, bool& tie) {
+  tie = fabs(hd - c) <= (R)kTieRel * fmax(fabs(c), hd);
+  exercise = hd > c;
+}
+template <>
+__device__ __forceinline__ void decide<double>(double hd, double c, bool& exercise, bool& tie) {
+  // one FP64 subtraction; sign and exponents compared as integers
+  // (2^-33 = 1.16e-10 relative)
+  const double d = hd - c;
+  const long long bd = __double_as_longlong(d);
+  exercise = bd > 0;
+  const int ed = (int)((bd >> 52) & 0x7ff);
+  const int ec = (int)((__double_as_longlong(c) >> 52) & 0x7ff);
+  const int eh = (int)((__double_as_longlong(hd) >> 52) & 0x7ff);
+  tie = ed + 33 <= max(ec, eh);
+}
+template <>
+__device__ __forceinline__ void decide<df>(df hd, df c, bool& exercise, bool& tie) {
+  const df d = add_sloppy(hd, -c);
+  tie = fabsf(d.hi) <= (float)kTieRel * fmaxf(fabsf(c.hi), hd.hi);
+  exercise = d.hi > 0.0f || (d.hi == 0.0f && d.lo > 0.0f);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -235,6 +274,46 @@ template <int NA> struct Acc<float, NA> {
 
 }  // namespace
 
+// Adds one in-the-money path to the per-thread moment sums: the 15
+// monomials x^a w^b (a + b <= 4) of the centred basis variables
+// x = S/K - 1, w = v/theta - 1 and the six products with the cash flow y.
+template <typename Real, int BASIS, int NM>
+__device__ __forceinline__ void accumulate_moments(Real* t, Real S, Real v, Real yv, Real invK,
+                                                   Real invTh) {
+  const Real x = qfma(S, invK, (Real)-1);
+  const Real x2 = qmul(x, x), x3 = qmul(x2, x), x4 = qmul(x2, x2);
+  qacc(t[0], (Real)1);
+  qacc(t[1], x);
+  qacc(t[2], x2);
+  qacc(t[3], x3);
+  qacc(t[4], x4);
+  if (BASIS == kBasisSV2) {
+    const Real w = qfma(v, invTh, (Real)-1);
+    const Real w2 = qmul(w, w), w3 = qmul(w2, w), w4 = qmul(w2, w2);
+    const Real xw = qmul(x, w);
+    qacc(t[mono(0, 1)], w);
+    qacc(t[mono(1, 1)], xw);
+    qacc(t[mono(2, 1)], qmul(x2, w));
+    qacc(t[mono(3, 1)], qmul(x3, w));
+    qacc(t[mono(0, 2)], w2);
+    qacc(t[mono(1, 2)], qmul(x, w2));
+    qacc(t[mono(2, 2)], qmul(x2, w2));
+    qacc(t[mono(0, 3)], w3);
+    qacc(t[mono(1, 3)], qmul(x, w3));
+    qacc(t[mono(0, 4)], w4);
+    qacc(t[NM + 0], yv);
+    qacc(t[NM + 1], qmul(x, yv));
+    qacc(t[NM + 2], qmul(x2, yv));
+    qacc(t[NM + 3], qmul(w, yv));
+    qacc(t[NM + 4], qmul(xw, yv));
+    qacc(t[NM + 5], qmul(w2, yv));
+  } else {
+    qacc(t[NM + 0], yv);
+    qacc(t[NM + 1], qmul(x, yv));
+    qacc(t[NM + 2], qmul(x2, yv));
+  }
+}
+
 // Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
 // current exercise time tau.  The regression target of date n, the cash flow
 // discounted to t_n, is Z exp(r n dt): the same factor for every path, so the
@@ -261,12 +340,23 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_chunk[NW][kNSum];
   __shared__ double s_sum[kNSum];
   __shared__ Real s_c[16];            // per-job constants, converted once
+  // per-warp compaction of in-the-money paths: the heavy arithmetic runs on
+  // dense lists instead of on lanes that are mostly out of the money
+  constexpr int CAP = 32 * PPT;
+  __shared__ Real s_cs[NW][CAP];      // S
+  __shared__ Real s_cv[NW][CAP];      // v (basis SV2)
+  __shared__ Real s_cy[NW][CAP];      // cash flow (moment sums)
+  __shared__ unsigned short s_co[NW][CAP];  // origin k * 32 + lane (exercise)
+  __shared__ Real s_zn[NW][PPT][32];  // cash flows after the exercise test
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t sub = a.sub;
   // single precision and float pairs reduce through float pairs; double
   // precision through doubles
   constexpr bool kSingle = !std::is_same<Real, double>::value;
+  // compaction pays where the in-the-money arithmetic is heavy (double and
+  // float pairs); plain floats are bound by loads and stay uncompacted
+  constexpr bool kCompact = !std::is_same<Real, float>::value;
   // Job decoding by thread 0: the job number `next` was taken from the
   // counter one job earlier, so the atomic's latency is hidden.
   unsigned long long next = 0;
@@ -394,9 +484,15 @@ backward_kernel(BwdArgs a) {
     double euro = 0.0, sy = 0.0, sy2 = 0.0;
     uint32_t ties = 0;
 
+    const unsigned lane_lt = (1u << lane) - 1u;
+    Real* cs = s_cs[warp];
+    Real* cv = s_cv[warp];
+    Real* cy = s_cy[warp];
+    unsigned short* co = s_co[warp];
     for (uint32_t sb = 0; sb < sub; ++sb) {
-      const uint32_t p_base = tile_base + sb * TILE0 + tid;
-      if (p_base >= P) break;
+      const uint32_t sub_base = tile_base + sb * TILE0;
+      if (sub_base >= P) break;  // uniform across the CTA
+      const uint32_t p_base = sub_base + tid;
       // every load of the sub-tile is issued before any arithmetic, so each
       // thread has up to 5 * PPT independent loads in flight
       Real zr[PPT], e1[PPT], v1[PPT], e0[PPT], v0[PPT];
@@ -435,16 +531,17 @@ backward_kernel(BwdArgs a) {
           }
         }
       } else {
-        // exercise at date n + 1 where the discounted payoff beats the
-        // fitted continuation value (basis centred at the strike and theta)
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) {
-          const uint32_t p = p_base + k * kBlock;
-          z[k] = zr[k];
-          if (bok && p < P) {
-            const Real S = qmul(s1, e1[k]);
-            const Real h = intrinsic<Real>(type, K, S);
-            if (positive(h)) {
+        for (int k = 0; k < PPT; ++k) z[k] = zr[k];
+        if (bok && !kCompact) {
+          // exercise at date n + 1 where the discounted payoff beats the
+          // fitted continuation value (basis centred at the strike and theta)
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            const Real S = s1 * e1[k];
+            if (p < P && in_money<Real>(type, K, S)) {
+              const Real h = intrinsic<Real>(type, K, S);
               const Real x = qfma(S, invK, (Real)-1);
               Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
               if (BASIS == kBasisSV2) {
@@ -452,29 +549,66 @@ backward_kernel(BwdArgs a) {
                 c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
               }
               const Real hd = qmul(h, d1);
-              bool tie, exercise;
-              if constexpr (std::is_same<Real, df>::value) {
-                // the threshold only needs the leading floats
-                const df diff = qsub(hd, c);
-                tie = fabsf(diff.hi) <= (float)kTieRel * fmaxf(fabsf(c.hi), hd.hi);
-                exercise = positive(diff);
-              } else {
-                tie = fabs(hd - c) <= (Real)kTieRel * fmax(fabs(c), hd);
-                exercise = hd > c;
-              }
+              bool exercise, tie;
+              decide<Real>(hd, c, exercise, tie);
               if (tie) ++ties;
               if (exercise) {
-                Real hz;
-                if constexpr (std::is_same<Real, df>::value) {
-                  hz = quick_two_sum(hd.hi, hd.lo);
-                } else {
-                  hz = fma(h, d1, h * d1lo);
-                }
+                const Real hz = fma(h, d1, h * d1lo);
                 z[k] = hz;
                 if (!final_job) Z[p] = hz;
               }
             }
           }
+        } else if (bok) {
+          // the same with the in-the-money paths compacted per warp, so the
+          // heavy arithmetic runs on dense lists instead of on lanes that are
+          // mostly out of the money
+          int cnt = 0;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            const Real S = s1 * e1[k];  // normalised: the comparison reads hi first
+            const bool itm = p < P && in_money<Real>(type, K, S);
+            const unsigned m = __ballot_sync(0xffffffffu, itm);
+            if (itm) {
+              const int pos = cnt + __popc(m & lane_lt);
+              cs[pos] = S;
+              if (BASIS == kBasisSV2) cv[pos] = v1[k];
+              co[pos] = (unsigned short)(k * 32 + lane);
+            }
+            cnt += __popc(m);
+            s_zn[warp][k][lane] = z[k];
+          }
+          __syncwarp();
+          for (int j = lane; j < cnt; j += 32) {
+            const Real S = cs[j];
+            const Real h = intrinsic<Real>(type, K, S);
+            const Real x = qfma(S, invK, (Real)-1);
+            Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+            if (BASIS == kBasisSV2) {
+              const Real w = qfma(cv[j], invTh, (Real)-1);
+              c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+            }
+            const Real hd = qmul(h, d1);
+            bool exercise, tie;
+            decide<Real>(hd, c, exercise, tie);
+            if (tie) ++ties;
+            if (exercise) {
+              Real hz;
+              if constexpr (std::is_same<Real, df>::value) {
+                hz = quick_two_sum(hd.hi, hd.lo);
+              } else {
+                hz = fma(h, d1, h * d1lo);
+              }
+              const int o = co[j], kk = o >> 5, ll = o & 31;
+              s_zn[warp][kk][ll] = hz;
+              if (!final_job) Z[sub_base + warp * 32 + ll + kk * kBlock] = hz;
+            }
+          }
+          __syncwarp();
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) z[k] = s_zn[warp][k][lane];
+          __syncwarp();
         }
       }
 
@@ -488,52 +622,40 @@ backward_kernel(BwdArgs a) {
             sy2 += zv * zv;
           }
         }
-      } else {
+      } else if (!kCompact) {
         // moment sums of date n over the in-the-money paths
         Real* t = acc.target();
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
-          if (p < P) {
-            const Real yv = z[k];
-            const Real S = qmul(s0, e0[k]);
-            const Real h = intrinsic<Real>(type, K, S);
-            if (positive(h)) {
-              const Real x = qfma(S, invK, (Real)-1);
-              const Real x2 = qmul(x, x), x3 = qmul(x2, x), x4 = qmul(x2, x2);
-              qacc(t[0], (Real)1);
-              qacc(t[1], x);
-              qacc(t[2], x2);
-              qacc(t[3], x3);
-              qacc(t[4], x4);
-              if (BASIS == kBasisSV2) {
-                const Real w = qfma(v0[k], invTh, (Real)-1);
-                const Real w2 = qmul(w, w), w3 = qmul(w2, w), w4 = qmul(w2, w2);
-                const Real xw = qmul(x, w);
-                qacc(t[mono(0, 1)], w);
-                qacc(t[mono(1, 1)], xw);
-                qacc(t[mono(2, 1)], qmul(x2, w));
-                qacc(t[mono(3, 1)], qmul(x3, w));
-                qacc(t[mono(0, 2)], w2);
-                qacc(t[mono(1, 2)], qmul(x, w2));
-                qacc(t[mono(2, 2)], qmul(x2, w2));
-                qacc(t[mono(0, 3)], w3);
-                qacc(t[mono(1, 3)], qmul(x, w3));
-                qacc(t[mono(0, 4)], w4);
-                qacc(t[NM + 0], yv);
-                qacc(t[NM + 1], qmul(x, yv));
-                qacc(t[NM + 2], qmul(x2, yv));
-                qacc(t[NM + 3], qmul(w, yv));
-                qacc(t[NM + 4], qmul(xw, yv));
-                qacc(t[NM + 5], qmul(w2, yv));
-              } else {
-                qacc(t[NM + 0], yv);
-                qacc(t[NM + 1], qmul(x, yv));
-                qacc(t[NM + 2], qmul(x2, yv));
-              }
-            }
+          const Real S = s0 * e0[k];
+          if (p < P && in_money<Real>(type, K, S)) {
+            accumulate_moments<Real, BASIS, NM>(t, S, v0[k], z[k], invK, invTh);
           }
         }
+        acc.fold();
+      } else {
+        // moment sums of date n over the in-the-money paths, compacted
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          const uint32_t p = p_base + k * kBlock;
+          const Real S = s0 * e0[k];  // normalised: the comparison reads hi first
+          const bool itm = p < P && in_money<Real>(type, K, S);
+          const unsigned m = __ballot_sync(0xffffffffu, itm);
+          if (itm) {
+            const int pos = cnt + __popc(m & lane_lt);
+            cs[pos] = S;
+            if (BASIS == kBasisSV2) cv[pos] = v0[k];
+            cy[pos] = z[k];
+          }
+          cnt += __popc(m);
+        }
+        __syncwarp();
+        Real* t = acc.target();
+        for (int j = lane; j < cnt; j += 32)
+          accumulate_moments<Real, BASIS, NM>(t, cs[j], cv[j], cy[j], invK, invTh);
+        __syncwarp();
         acc.fold();
       }
     }
