@@ -53,6 +53,8 @@ def parse():
                     choices=["paper_fp64", "large_mixed", "paper_mixed", "paper_df"])
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (profiling of a smaller case)")
+    ap.add_argument("--sub", type=int, default=0,
+                    help="backward sub-tiles per job; 0 = pick by the autotuner")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -332,8 +334,14 @@ def main():
     build.build()
     req = api.Request(wl)
     need = L.lsmc_request_footprint(None, req.c)
+    if args.sub:
+        # fixed shape (profiling runs): the context reads the override at creation
+        os.environ["LSMC_BACKWARD_SUB"] = str(args.sub)
     ctx = api.Context(workspace_bytes=need + (256 << 20))
-    tuned_sub, tuned_ms = ctx.autotune([wl])
+    if args.sub:
+        tuned_sub = args.sub
+    else:
+        tuned_sub, tuned_ms = ctx.autotune([wl])
     plan = ctx.plan([wl])
     info = plan.info()
     stream = ctx.stream

@@ -37,36 +37,31 @@ __device__ __forceinline__ float uniform23(uint32_t w) {
   return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
+// Random inputs of one path step from one Philox block: the uniform U_V,
+// 1 - U_V (exact in both grids), Z_V = Phi^-1(U_V) and Z_X.  The float-pair
+// specialisation is in df_math.cuh and uses the tables t stages in shared
+// memory; the others ignore t.
+struct DfTables;
 template <typename Real> struct Draw;
 template <> struct Draw<double> {
   // U_V, Z_V from words (0, 1); Z_X from words (2, 3)
-  __device__ __forceinline__ static void make(uint4 w, double& uV, double& zV,
-                                              double& zX) {
-    uV = uniform52(w.x, w.y);
-    zV = normcdfinv(uV);
+  __device__ __forceinline__ static void make(uint4 w, double& u, double& omu, double& zV,
+                                              double& zX, const DfTables*) {
+    u = uniform52(w.x, w.y);
+    omu = 1.0 - u;
+    zV = normcdfinv(u);
     zX = normcdfinv(uniform52(w.z, w.w));
   }
 };
 template <> struct Draw<float> {
   // U_V from word 0 and Z_X from word 2: the top 23 bits of the words the
   // double-precision grid reads first, so both precisions see one stream
-  __device__ __forceinline__ static void make(uint4 w, float& uV, float& zV,
-                                              float& zX) {
-    uV = uniform23(w.x);
-    zV = normcdfinvf(uV);
+  __device__ __forceinline__ static void make(uint4 w, float& u, float& omu, float& zV,
+                                              float& zX, const DfTables*) {
+    u = uniform23(w.x);
+    omu = 1.0f - u;
+    zV = normcdfinvf(u);
     zX = normcdfinvf(uniform23(w.z));
-  }
-};
-
-template <> struct Draw<df> {
-  // the double-precision draws (same grid and quantile as FP64), split into
-  // float pairs: float-pair paths see exactly the FP64 random inputs
-  __device__ __forceinline__ static void make(uint4 w, df& uV, df& zV, df& zX) {
-    double u, a, b;
-    Draw<double>::make(w, u, a, b);
-    uV = df(u);
-    zV = df(a);
-    zX = df(b);
   }
 };
 

@@ -6,9 +6,8 @@
 //
 // Algorithms: Knuth's two-sum and Dekker's fast two-sum for additions,
 // the FMA-based exact product for multiplications (as in Hida, Li and
-// Bailey's double-double library), Newton corrections for division and
-// square root, and for exp a reduction by a multiple of ln 2 and a power of
-// two, a Taylor polynomial and repeated squaring of exp(r) - 1.
+// Bailey's double-double library), residual corrections for division and
+// square root.  exp, log and the normal quantile are in df_math.cuh.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -79,14 +78,30 @@ __device__ __forceinline__ df mul_f(df a, float b) {
   return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
 }
 
+// a / b: q1 = a.hi r with r ~ 1 / b.hi (approximate reciprocal and one
+// Newton step), then two corrections from the residuals a - q b, each
+// formed exactly with the FMA product (Karp and Markstein's scheme)
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ df operator/(df a, df b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  const df r = a - mul_f(b, q1);
-  const float q2 = __fdiv_rn(r.hi, b.hi);
-  const df r2 = r - mul_f(b, q2);
-  const float q3 = __fdiv_rn(r2.hi, b.hi);
+  const float r0 = rcp_approx(b.hi);
+  const float r = __fmaf_rn(r0, __fmaf_rn(-b.hi, r0, 1.0f), r0);
+  const float q1 = __fmul_rn(a.hi, r);
+  const df p1 = two_prod(q1, b.hi);
+  // a.hi - p1.hi is exact (the two agree to a few ulps)
+  const df R = two_sum(__fsub_rn(a.hi, p1.hi),
+                       __fmaf_rn(-q1, b.lo, __fsub_rn(a.lo, p1.lo)));
+  const float q2 = __fmul_rn(R.hi, r);
+  const df p2 = two_prod(q2, b.hi);
+  const df s = two_sum(R.hi, -p2.hi);
+  const float R2 = __fadd_rn(s.hi, __fadd_rn(s.lo, __fsub_rn(R.lo, __fmaf_rn(q2, b.lo, p2.lo))));
+  const float q3 = __fmul_rn(R2, r);
   const df q = quick_two_sum(q1, q2);
-  return q + df(q3, 0.0f);
+  return quick_two_sum(q.hi, __fadd_rn(q.lo, q3));
 }
 
 __device__ __forceinline__ df& operator+=(df& a, df b) { return a = a + b; }
@@ -137,41 +152,12 @@ __device__ __forceinline__ df ldexp_df(df a, int k) {
 
 __device__ __forceinline__ df sqrt_df(df a) {
   if (!(a.hi > 0.0f)) return df(0.0f, 0.0f);
-  // y ~ sqrt(a) in float, then y + (a - y^2) / (2 y)
+  // y ~ sqrt(a.hi) from the approximate reciprocal square root, then
+  // y + (a - y^2) / (2 y) with a - y^2 formed by one FMA (Karp and Markstein)
   const float x = rsqrtf(a.hi);
   const float y = __fmul_rn(a.hi, x);
-  const df r = a - two_prod(y, y);
-  return quick_two_sum(y, __fmul_rn(r.hi, __fmul_rn(x, 0.5f)));
-}
-
-__device__ __forceinline__ df exp_df(df a) {
-  // a = k ln2 + r, |r| <= ln2 / 2; exp(r) = (1 + s)^(2^4) with s = exp(r/16) - 1
-  constexpr double kLn2 = 0.693147180559945309417232121458176568;
-  constexpr double kLog2e = 1.442695040888963407359924681001892137;
-  if (a.hi > 88.0f) return df(__int_as_float(0x7f800000), 0.0f);
-  if (a.hi < -87.0f) return df(0.0f, 0.0f);
-  const float k = rintf(__fmul_rn(a.hi, (float)kLog2e));
-  const df r = ldexp_df(a - mul_f(df(kLn2), k), -4);
-  // Taylor series of exp(r) - 1 to r^8 / 8! (|r| <= 0.0217: remainder < 1e-18)
-  df s = r * df(1.0 / 40320.0) + df(1.0 / 5040.0);
-  s = s * r + df(1.0 / 720.0);
-  s = s * r + df(1.0 / 120.0);
-  s = s * r + df(1.0 / 24.0);
-  s = s * r + df(1.0 / 6.0);
-  s = s * r + df(0.5);
-  s = s * r + df(1.0);
-  s = s * r;
-  // (1 + s)^2 - 1 = s (2 + s), four times
-#pragma unroll
-  for (int i = 0; i < 4; ++i) s = s * (s + df(2.0f, 0.0f));
-  return ldexp_df(s + df(1.0f, 0.0f), (int)k);
-}
-
-__device__ __forceinline__ df log_df(df a) {
-  // one Newton step on exp: y1 = y0 + a exp(-y0) - 1
-  if (!(a.hi > 0.0f)) return df(-__int_as_float(0x7f800000), 0.0f);
-  const df y0(logf(a.hi), 0.0f);
-  return y0 + (a * exp_df(-y0) - df(1.0f, 0.0f));
+  const float e = __fadd_rn(__fmaf_rn(-y, y, a.hi), a.lo);
+  return quick_two_sum(y, __fmul_rn(e, __fmul_rn(x, 0.5f)));
 }
 
 }  // namespace lsmc

@@ -13,30 +13,37 @@
 #include <type_traits>
 
 #include "device_common.cuh"
+#include "df_math.cuh"
 #include "dfloat.cuh"
 #include "kernels.h"
 #include "plan.h"
 
 namespace lsmc {
 
+// Elementary functions per precision; the float-pair ones read their
+// tables from shared memory (t), the others ignore it.
 template <typename Real> struct Fm;
 template <> struct Fm<double> {
   __device__ static double div(double a, double b) { return a / b; }
   __device__ static double sqrt_(double a) { return sqrt(a); }
-  __device__ static double log_(double a) { return log(a); }
-  __device__ static double exp_(double a) { return exp(a); }
+  __device__ static double log_(double a, const DfTables*) { return log(a); }
+  __device__ static double exp_(double a, const DfTables*) { return exp(a); }
 };
 template <> struct Fm<float> {
   __device__ static float div(float a, float b) { return __fdividef(a, b); }
-  __device__ static float sqrt_(float a) { return sqrtf(a); }
-  __device__ static float log_(float a) { return __logf(a); }
-  __device__ static float exp_(float a) { return __expf(a); }
+  __device__ static float sqrt_(float a) {
+    float r;  // approximate square root (MUFU), exact at 0
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+  }
+  __device__ static float log_(float a, const DfTables*) { return __logf(a); }
+  __device__ static float exp_(float a, const DfTables*) { return __expf(a); }
 };
 template <> struct Fm<df> {
   __device__ static df div(df a, df b) { return a / b; }
   __device__ static df sqrt_(df a) { return sqrt_df(a); }
-  __device__ static df log_(df a) { return log_df(a); }
-  __device__ static df exp_(df a) { return exp_df(a); }
+  __device__ static df log_(df a, const DfTables* t) { return log_df(a, t->exp2); }
+  __device__ static df exp_(df a, const DfTables* t) { return exp_df(a, t->exp2); }
 };
 
 template <typename Real>
@@ -87,27 +94,31 @@ __device__ void make_group_const(const FwdGroup& g, GroupConst<Real>& c) {
 }
 
 // Andersen QE step: variance by the quadratic branch (psi <= 1.5) or the
-// exponential branch, then the log price from both variances.
+// exponential branch, then the log price from both variances.  With
+// psi = s^2 / m^2 the branch quantities are written with one division
+// each: 2 / psi = 2 m^2 / s^2, p = (psi - 1) / (psi + 1) = (s^2 - m^2) /
+// (s^2 + m^2), 1 - p = 2 m^2 / (s^2 + m^2), 1 / beta = m / (1 - p); the
+// point mass is taken when U_V <= p, i.e. 1 - U_V >= 1 - p.
 template <typename Real>
-__device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x,
-                                        Real& v, Real uV, Real zV, Real zX) {
+__device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x, Real& v,
+                                        Real omu, Real zV, Real zX, const DfTables* t) {
   using F = Fm<Real>;
   const Real m = fma(c.mB, v, c.mA);
   const Real s2 = fma(c.sB, v, c.sA);
-  const Real psi = F::div(s2, m * m);
+  const Real m2 = m * m;
   Real v1;
-  if (psi <= (Real)1.5) {
-    const Real inv = F::div((Real)2, psi);
-    const Real t = inv - (Real)1;
-    const Real b2 = t + F::sqrt_(inv * t);
+  if (s2 <= (Real)1.5 * m2) {
+    const Real inv = F::div(m2 + m2, s2);
+    const Real tt = inv - (Real)1;
+    const Real b2 = tt + F::sqrt_(inv * tt);
     const Real b = F::sqrt_(b2);
     const Real a = F::div(m, (Real)1 + b2);
     const Real q = b + zV;
     v1 = a * q * q;
   } else {
-    const Real p = F::div(psi - (Real)1, psi + (Real)1);
-    const Real omp = (Real)1 - p;
-    v1 = (uV <= p) ? (Real)0 : F::div(m, omp) * F::log_(F::div(omp, (Real)1 - uV));
+    const Real rden = F::div((Real)1, s2 + m2);
+    const Real omp = (m2 + m2) * rden;
+    v1 = (omu >= omp) ? (Real)0 : F::div(m, omp) * F::log_(F::div(omp, omu), t);
   }
   x = x + c.c0 + c.K1 * v + c.K2 * v1 + F::sqrt_(c.K3 * (v + v1)) * zX;
   v = v1;
@@ -126,7 +137,7 @@ __device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
 }
 
 template <typename Real, int SCHEME>
-__global__ void __launch_bounds__(kBlock)
+__global__ void __launch_bounds__(kBlock, std::is_same<Real, double>::value ? 2 : 1)
 forward_kernel(FwdArgs a) {
   __shared__ GroupConst<Real> gc[kMaxGroups];
   __shared__ FwdContract sc;
@@ -142,6 +153,11 @@ forward_kernel(FwdArgs a) {
   __syncthreads();
   if (threadIdx.x < sc.n_groups)
     make_group_const<Real>(a.groups[sc.group0 + threadIdx.x], gc[threadIdx.x]);
+  // float pairs: exp and quantile tables in shared memory
+  constexpr bool kPair = std::is_same<Real, df>::value;
+  __shared__ __align__(16) unsigned char tab_raw[kPair ? sizeof(DfTables) : 16];
+  DfTables* tabs = reinterpret_cast<DfTables*>(tab_raw);
+  if constexpr (kPair) load_df_tables(tabs);
   __syncthreads();
 
   const uint32_t p = (blockIdx.x - sc.block0) * kBlock + threadIdx.x;
@@ -155,9 +171,9 @@ forward_kernel(FwdArgs a) {
     if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
   }
 
-  if constexpr (std::is_same<Real, double>::value) {
-    // double precision is bound by the FP64 pipe: keep every group's state
-    // and constants in registers (one CTA per SM is enough to fill it)
+  if constexpr (!kPair) {
+    // double and float: every group's state in registers, the group loop
+    // unrolled so the groups' independent chains interleave
     Real x[kMaxGroups], v[kMaxGroups];
 #pragma unroll
     for (int g = 0; g < kMaxGroups; ++g) {
@@ -166,28 +182,27 @@ forward_kernel(FwdArgs a) {
     }
     for (uint32_t n = 0; n < sc.N; ++n) {
       const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
-      Real uV, zV, zX;
-      Draw<Real>::make(w, uV, zV, zX);
+      Real u, omu, zV, zX;
+      Draw<Real>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll
       for (int g = 0; g < kMaxGroups; ++g) {
         if (g < ng) {
           const GroupConst<Real>& c = gc[g];
           if (SCHEME == kSchemeQE) {
-            qe_step<Real>(c, x[g], v[g], uV, zV, zX);
+            qe_step<Real>(c, x[g], v[g], omu, zV, zX, tabs);
           } else {
             ft_step<Real>(c, x[g], v[g], zV, zX);
           }
           const size_t off = (size_t)n * c.ld + p;
-          c.E[off] = c.out_scale * Fm<Real>::exp_(x[g]);
+          c.E[off] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
           if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
         }
       }
     }
   } else {
-    // single precision and float pairs are bound by latency and issue: the group loop is not
-    // unrolled, so the constants are read from shared memory where they are
-    // used and the per-group state lives in shared memory too; the kernel
-    // then needs few registers and many warps fit on an SM
+    // float pairs: a group step is several hundred instructions, so the
+    // group loop is not unrolled (the code stays in the instruction cache)
+    // and the per-group state lives in shared memory
     __shared__ Real xs[kMaxGroups][kBlock], vs[kMaxGroups][kBlock];
     const int t = threadIdx.x;
     for (int g = 0; g < ng; ++g) {
@@ -196,21 +211,21 @@ forward_kernel(FwdArgs a) {
     }
     for (uint32_t n = 0; n < sc.N; ++n) {
       const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
-      Real uV, zV, zX;
-      Draw<Real>::make(w, uV, zV, zX);
+      Real u, omu, zV, zX;
+      Draw<Real>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll 1
       for (int g = 0; g < ng; ++g) {
         const GroupConst<Real>& c = gc[g];
         Real xg = xs[g][t], vg = vs[g][t];
         if (SCHEME == kSchemeQE) {
-          qe_step<Real>(c, xg, vg, uV, zV, zX);
+          qe_step<Real>(c, xg, vg, omu, zV, zX, tabs);
         } else {
           ft_step<Real>(c, xg, vg, zV, zX);
         }
         xs[g][t] = xg;
         vs[g][t] = vg;
         const size_t off = (size_t)n * c.ld + p;
-        c.E[off] = c.out_scale * Fm<Real>::exp_(xg);
+        c.E[off] = c.out_scale * Fm<Real>::exp_(xg, tabs);
         if (c.V) c.V[off] = (SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg;
       }
     }
@@ -228,11 +243,18 @@ __global__ void draws_kernel(uint2 key, uint32_t stream_id,
                              const uint32_t* __restrict__ path,
                              const uint32_t* __restrict__ step, size_t n,
                              Real* __restrict__ out) {
+  constexpr bool kPair = std::is_same<Real, df>::value;
+  __shared__ __align__(16) unsigned char tab_raw[kPair ? sizeof(DfTables) : 16];
+  DfTables* tabs = reinterpret_cast<DfTables*>(tab_raw);
+  if constexpr (kPair) {
+    load_df_tables(tabs);
+    __syncthreads();
+  }
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint4 w = philox4x32_10(make_uint4(path[i], step[i], stream_id, 0u), key);
-  Real uV, zV, zX;
-  Draw<Real>::make(w, uV, zV, zX);
+  Real uV, omu, zV, zX;
+  Draw<Real>::make(w, uV, omu, zV, zX, tabs);
   out[3 * i] = uV;
   out[3 * i + 1] = zV;
   out[3 * i + 2] = zX;
