@@ -55,6 +55,8 @@ def parse():
                     help="override the path count (profiling of a smaller case)")
     ap.add_argument("--sub", type=int, default=0,
                     help="backward sub-tiles per job; 0 = pick by the autotuner")
+    ap.add_argument("--ppt", type=int, default=0,
+                    help="backward paths per lane with --sub (0 = the precision's default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -243,7 +245,8 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     with api.Context(workspace_bytes=need + (512 << 20)) as ctx:
         subs = []
         for c in chunks:
-            subs.append(ctx.autotune(c)[0])
+            sub, ppt, _ = ctx.autotune(c)
+            subs.append([sub, ppt])
             p = ctx.plan(c)
             p.launch(use_graph=True)  # capture and warm
             p.fetch()
@@ -258,7 +261,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
-            "precision": precision, "graph": True, "autotuned_subtiles": subs}
+            "precision": precision, "graph": True, "autotuned_shape_sub_ppt": subs}
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
@@ -337,11 +340,13 @@ def main():
     if args.sub:
         # fixed shape (profiling runs): the context reads the override at creation
         os.environ["LSMC_BACKWARD_SUB"] = str(args.sub)
+        if args.ppt:
+            os.environ["LSMC_BACKWARD_PPT"] = str(args.ppt)
     ctx = api.Context(workspace_bytes=need + (256 << 20))
     if args.sub:
-        tuned_sub = args.sub
+        tuned_sub, tuned_ppt = args.sub, args.ppt or None
     else:
-        tuned_sub, tuned_ms = ctx.autotune([wl])
+        tuned_sub, tuned_ppt, _ = ctx.autotune([wl])
     plan = ctx.plan([wl])
     info = plan.info()
     stream = ctx.stream
@@ -456,6 +461,7 @@ def main():
                    "revaluations": wl.n_scenarios, "scheme": wl.scheme, "basis": wl.basis,
                    "precision": wl.precision, "parallelism": "replicas" if world > 1 else "single",
                    "backward_subtiles_per_job": tuned_sub,
+                   "backward_paths_per_lane": tuned_ppt,
                    "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
         "path_steps_per_s": {"generated": world * wl.generated_path_steps / (ms_max / 1e3),
                              "lsmc": world * wl.lsmc_path_steps / (ms_max / 1e3)},

@@ -207,12 +207,14 @@ int lsmc_plan_set_timing(lsmc_plan* plan, int32_t enable);
  * ms[0] setup, ms[1] forward (paths), ms[2] backward (LSMC), ms[3] Greeks;
  * *launches = number of launches summed.  Waits for the last launch. */
 int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
-/* Autotuner: times the backward pass of a plan for these requests with job
- * sizes of 1, 2, 4, ... sub-tiles (one warm-up and one timed launch each),
- * remembers the fastest for later plans of the same precision, basis and
- * size class on this context, and returns it (best_sub, best_ms: optional). */
+/* Autotuner: times the backward pass of a plan for these requests over its
+ * tile shapes -- paths per thread of a sub-tile (2 or 4 for LSMC_FP64 and
+ * LSMC_DF, 4 or 8 for LSMC_MIXED) and jobs of 1, 2, 4, ... sub-tiles (one
+ * warm-up and one timed launch each) --, remembers the fastest for later
+ * plans of the same precision, basis and size class on this context, and
+ * returns it (best_sub, best_ppt, best_ms: optional). */
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
-                  uint32_t* best_sub, double* best_ms);
+                  uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
 /* Destroy every plan before the context it was created on. */
 void lsmc_plan_destroy(lsmc_plan* plan);
 

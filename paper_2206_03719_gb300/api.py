@@ -107,7 +107,8 @@ class Context:
         return [r.as_dict() for r in L.lsmc_price_book(self.ctx, [q.c for q in reqs])]
 
     def autotune(self, wls: Sequence[Workload], **kw):
-        """(sub-tiles per backward job, backward ms) chosen for these requests."""
+        """(sub-tiles per backward job, paths per lane, backward ms) chosen
+        for these requests."""
         reqs = [Request(w, **kw) for w in wls]
         return L.lsmc_autotune(self.ctx, [q.c for q in reqs])
 

@@ -211,15 +211,6 @@ __device__ __forceinline__ float2 pair_add(float2 x, float2 y) {
   return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
 }
 
-__device__ __forceinline__ float2 warp_pair_sum(float2 v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    const float2 o = make_float2(__shfl_xor_sync(0xffffffffu, v.x, off),
-                                 __shfl_xor_sync(0xffffffffu, v.y, off));
-    v = pair_add(v, o);
-  }
-  return v;
-}
 
 }  // namespace
 
@@ -343,9 +334,9 @@ backward_kernel(BwdArgs a) {
   // per-warp compaction of in-the-money paths: the heavy arithmetic runs on
   // dense lists instead of on lanes that are mostly out of the money
   constexpr int CAP = 32 * PPT;
-  __shared__ Real s_cs[NW][CAP];      // S
-  __shared__ Real s_cv[NW][CAP];      // v (basis SV2)
-  __shared__ Real s_cy[NW][CAP];      // cash flow (moment sums)
+  // per warp: S, v (basis SV2) and cash flow of the compacted paths; the
+  // job-end reduction reuses the same space
+  __shared__ Real s_cbuf[NW][3][CAP];
   __shared__ unsigned short s_co[NW][CAP];  // origin k * 32 + lane (exercise)
   __shared__ Real s_zn[NW][PPT][32];  // cash flows after the exercise test
 
@@ -421,15 +412,20 @@ backward_kernel(BwdArgs a) {
         int ok = 1;
         if (!first) {
           const unsigned long long t0 = global_timer_ns();
-          unsigned spins = 0;
+          unsigned spins = 0, ns = 32;
           while (ld_acquire_gpu(&st->ready) < r) {
-            if (ld_volatile(&a.ctl->error) != 0) { ok = 0; break; }
-            __nanosleep(spins < 64 ? 32 : 256);
-            if (++spins > (1u << 26) || global_timer_ns() - t0 > a.timeout_ns) {
-              atomicCAS(&a.ctl->error, 0u, (uint32_t)kDevErrTimeout);
-              a.ctl->error_info = ji.inst;
-              ok = 0;
-              break;
+            // back off (32 ns doubling to 512 ns); the error word and the
+            // clock are read every 32nd time
+            __nanosleep(ns);
+            ns = ns < 512 ? 2 * ns : 512;
+            if ((++spins & 31) == 0) {
+              if (ld_volatile(&a.ctl->error) != 0) { ok = 0; break; }
+              if (spins > (1u << 26) || global_timer_ns() - t0 > a.timeout_ns) {
+                atomicCAS(&a.ctl->error, 0u, (uint32_t)kDevErrTimeout);
+                a.ctl->error_info = ji.inst;
+                ok = 0;
+                break;
+              }
             }
           }
           if (ok) {
@@ -485,9 +481,9 @@ backward_kernel(BwdArgs a) {
     uint32_t ties = 0;
 
     const unsigned lane_lt = (1u << lane) - 1u;
-    Real* cs = s_cs[warp];
-    Real* cv = s_cv[warp];
-    Real* cy = s_cy[warp];
+    Real* cs = s_cbuf[warp][0];
+    Real* cv = s_cbuf[warp][1];
+    Real* cy = s_cbuf[warp][2];
     unsigned short* co = s_co[warp];
     for (uint32_t sb = 0; sb < sub; ++sb) {
       const uint32_t sub_base = tile_base + sb * TILE0;
@@ -661,19 +657,41 @@ backward_kernel(BwdArgs a) {
     }
 
     // ---- block reduction into the tile partial --------------------------------
+    // per warp, the lanes' sums go through shared memory transposed (a row per
+    // sum, padded against bank conflicts, in the warp's compaction buffers)
+    // and lane i adds row i in lane order: a fixed order, and one add per lane
+    // and sum instead of a five-level butterfly over every sum
     if (final_job) {
       sy = warp_sum(sy);
       sy2 = warp_sum(sy2);
     } else {
+      using RedT = typename std::conditional<kSingle, float2, double>::type;
+      // rows per pass: as many as the warp's compaction buffers hold
+      constexpr int RROWS = (int)((3 * CAP * sizeof(Real)) / (33 * sizeof(RedT)));
+      static_assert(RROWS >= 1 && RROWS <= 32, "reduction rows per pass");
+      RedT(*red)[33] = reinterpret_cast<RedT(*)[33]>(cs);
+      __syncwarp();
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        if constexpr (kSingle) {
-          const float2 v = warp_pair_sum(acc.pair(i));
-          if (lane == 0) s_redf[warp][i] = v;
-        } else {
-          const double v = warp_sum(acc.s[i]);
-          if (lane == 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
+      for (int a0 = 0; a0 < NA; a0 += RROWS) {
+#pragma unroll
+        for (int i = a0; i < NA && i < a0 + RROWS; ++i) {
+          if constexpr (kSingle) red[i - a0][lane] = acc.pair(i);
+          else red[i - a0][lane] = acc.s[i];
         }
+        __syncwarp();
+        const int i = a0 + lane;
+        if (lane < RROWS && i < NA) {
+          if constexpr (kSingle) {
+            float2 pr = red[lane][0];
+            for (int l = 1; l < 32; ++l) pr = pair_add(pr, red[lane][l]);
+            s_redf[warp][i] = pr;
+          } else {
+            double v = red[lane][0];
+            for (int l = 1; l < 32; ++l) v += red[lane][l];
+            s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
+          }
+        }
+        __syncwarp();
       }
     }
     if (first) euro = warp_sum(euro);
@@ -838,21 +856,31 @@ static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// paths per thread in a sub-tile: 4 for double and float pairs, 8 for float
-int backward_tile(int precision) { return kBlock * (precision == kPrecMixed ? 8 : 4); }
+// Paths per thread in a sub-tile: 2 or 4 for double and float pairs, 4 or 8
+// for float.
+int backward_ppt_default(int precision) { return precision == kPrecMixed ? 8 : 4; }
+bool backward_ppt_valid(int precision, int ppt) {
+  return precision == kPrecMixed ? (ppt == 4 || ppt == 8) : (ppt == 2 || ppt == 4);
+}
 
-cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int grid,
+template <typename Real, int PPT>
+static cudaError_t launch_bwd_basis(const BwdArgs& a, int basis, int grid, cudaStream_t s) {
+  return basis == kBasisSV2 ? launch_bwd_t<Real, kBasisSV2, PPT>(a, grid, s)
+                            : launch_bwd_t<Real, kBasisS2, PPT>(a, grid, s);
+}
+
+cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt, int grid,
                             cudaStream_t s) {
   if (a.total_jobs == 0) return cudaSuccess;
-  const bool sv2 = basis == kBasisSV2;
+  if (!backward_ppt_valid(precision, ppt)) return cudaErrorInvalidValue;
   if (precision == kPrecFP64)
-    return sv2 ? launch_bwd_t<double, kBasisSV2, 4>(a, grid, s)
-               : launch_bwd_t<double, kBasisS2, 4>(a, grid, s);
+    return ppt == 2 ? launch_bwd_basis<double, 2>(a, basis, grid, s)
+                    : launch_bwd_basis<double, 4>(a, basis, grid, s);
   if (precision == kPrecDF)
-    return sv2 ? launch_bwd_t<df, kBasisSV2, 4>(a, grid, s)
-               : launch_bwd_t<df, kBasisS2, 4>(a, grid, s);
-  return sv2 ? launch_bwd_t<float, kBasisSV2, 8>(a, grid, s)
-             : launch_bwd_t<float, kBasisS2, 8>(a, grid, s);
+    return ppt == 2 ? launch_bwd_basis<df, 2>(a, basis, grid, s)
+                    : launch_bwd_basis<df, 4>(a, basis, grid, s);
+  return ppt == 4 ? launch_bwd_basis<float, 4>(a, basis, grid, s)
+                  : launch_bwd_basis<float, 8>(a, basis, grid, s);
 }
 
 template <typename Real, int BASIS, int PPT>
@@ -862,11 +890,15 @@ static int occ_t() {
                                                        kBlock, 0) == cudaSuccess ? n : 1;
 }
 
-int backward_occupancy(int precision, int basis) {
-  const bool sv2 = basis == kBasisSV2;
-  if (precision == kPrecFP64) return sv2 ? occ_t<double, kBasisSV2, 4>() : occ_t<double, kBasisS2, 4>();
-  if (precision == kPrecDF) return sv2 ? occ_t<df, kBasisSV2, 4>() : occ_t<df, kBasisS2, 4>();
-  return sv2 ? occ_t<float, kBasisSV2, 8>() : occ_t<float, kBasisS2, 8>();
+template <typename Real, int PPT>
+static int occ_basis(int basis) {
+  return basis == kBasisSV2 ? occ_t<Real, kBasisSV2, PPT>() : occ_t<Real, kBasisS2, PPT>();
+}
+
+int backward_occupancy(int precision, int basis, int ppt) {
+  if (precision == kPrecFP64) return ppt == 2 ? occ_basis<double, 2>(basis) : occ_basis<double, 4>(basis);
+  if (precision == kPrecDF) return ppt == 2 ? occ_basis<df, 2>(basis) : occ_basis<df, 4>(basis);
+  return ppt == 4 ? occ_basis<float, 4>(basis) : occ_basis<float, 8>(basis);
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,

@@ -60,10 +60,11 @@ struct lsmc_ctx {
   size_t hbm_budget = 0;
   uint32_t max_inflight = 8, queue_capacity = 4096;
   int num_sms = 0;
-  int occ[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
-  // autotuned sub-tiles per job, keyed by (precision, basis, log2 of the
-  // first round's sub-tile count)
+  uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
+  // autotuned backward shape (ppt << 16 | sub-tiles per job), keyed by
+  // (precision, basis, log2 of the first round's sub-tile count)
   std::map<uint64_t, uint32_t> tuned;
   // serving
   std::mutex mu;
@@ -135,13 +136,13 @@ int cuda_status(cudaError_t e) {
 
 int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? dflt : dflt) : v; }
 
-int occupancy(lsmc_ctx* ctx, int precision, int basis) {
+int occupancy(lsmc_ctx* ctx, int precision, int basis, int ppt) {
   if (ctx) {
-    int& o = ctx->occ[precision][basis];
-    if (o == 0) o = std::max(1, backward_occupancy(precision, basis));
+    int& o = ctx->occ[(precision * 4 + basis) * 16 + ppt];
+    if (o == 0) o = std::max(1, backward_occupancy(precision, basis, ppt));
     return o;
   }
-  return std::max(1, backward_occupancy(precision, basis));
+  return std::max(1, backward_occupancy(precision, basis, ppt));
 }
 
 int sm_count(lsmc_ctx* ctx) {
@@ -234,7 +235,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
   p->ba.sub = std::max<uint32_t>(1, L.opt.sub);
-  const int occ = occupancy(p->ctx, prec, L.opt.basis);
+  const int occ = occupancy(p->ctx, prec, L.opt.basis, plan_ppt(L.opt));
   const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
   p->h_out.resize(L.greeks.size());
@@ -300,8 +301,9 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
 }
 
 uint64_t tune_key(const lsmc_request* reqs, size_t n, const PlanOptions& o) {
-  // sub-tiles of the first round over all instances, as a power of two
-  const uint64_t tile0 = (uint64_t)backward_tile(o.precision);
+  // sub-tiles (of the default shape) of the first round over all
+  // instances, as a power of two
+  const uint64_t tile0 = (uint64_t)backward_tile(backward_ppt_default(o.precision));
   uint64_t tiles = 0;
   for (size_t i = 0; i < n; ++i) {
     std::vector<Scenario> sc;
@@ -323,13 +325,22 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
   p->ctx = ctx;
   p->stream = stream;
   {
-    const uint32_t ctas = (uint32_t)occupancy(ctx, o.precision, o.basis) * (uint32_t)sm_count(ctx);
-    o.sub = choose_sub(reqs, n, o.precision, ctas);
+    // backward shape: autotuned if this kind of launch was tuned, else
+    // the precision's paths per thread and about four jobs per resident CTA
+    // in the busiest round; overrides (tuning sweeps) win
+    uint32_t tuned = 0;
     if (ctx) {
       auto it = ctx->tuned.find(tune_key(reqs, n, o));
-      if (it != ctx->tuned.end()) o.sub = it->second;
-      if (ctx->sub_override) o.sub = ctx->sub_override;
+      if (it != ctx->tuned.end()) tuned = it->second;
     }
+    o.ppt = tuned >> 16;
+    if (ctx && ctx->ppt_override) o.ppt = ctx->ppt_override;
+    const int ppt = plan_ppt(o);
+    const uint32_t ctas = (uint32_t)occupancy(ctx, o.precision, o.basis, ppt) *
+                          (uint32_t)sm_count(ctx);
+    o.sub = choose_sub(reqs, n, o.precision, ppt, ctas);
+    if (tuned & 0xffffu) o.sub = tuned & 0xffffu;
+    if (ctx && ctx->sub_override) o.sub = ctx->sub_override;
   }
   rc = build_layout(reqs, n, o, &p->L);
   if (rc) return rc;
@@ -359,7 +370,9 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
   LSMC_CUDA(mark(1));
   if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, prec, p->L.opt.scheme, p->stream));
   LSMC_CUDA(mark(2));
-  if (p->run_backward) LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, p->bwd_grid, p->stream));
+  if (p->run_backward)
+    LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, plan_ppt(p->L.opt), p->bwd_grid,
+                              p->stream));
   LSMC_CUDA(mark(3));
   if (p->run_greeks)
     LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out, p->stream));
@@ -561,6 +574,10 @@ int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   if (const char* e = std::getenv("LSMC_BACKWARD_SUB")) {  // tuning sweeps
     const long v = std::strtol(e, nullptr, 10);
     if (v > 0 && v <= 1024) ctx->sub_override = (uint32_t)v;
+  }
+  if (const char* e = std::getenv("LSMC_BACKWARD_PPT")) {
+    const long v = std::strtol(e, nullptr, 10);
+    if (v == 2 || v == 4 || v == 8) ctx->ppt_override = (uint32_t)v;
   }
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete ctx;
@@ -813,7 +830,7 @@ int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* s, double* a, doub
 
 // ---- autotuner ----------------------------------------------------------------
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* best_sub,
-                  double* best_ms) {
+                  uint32_t* best_ppt, double* best_ms) {
   if (!ctx || !reqs || !n) return LSMC_EINVAL;
   cudaSetDevice(ctx->device);
   PlanOptions o;
@@ -821,32 +838,41 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* b
   if (rc) return rc;
   const uint64_t key = tune_key(reqs, n, o);
   const uint64_t tiles0 = std::max<uint64_t>(1, 1ull << (key & 0xffffffffu));
-  const uint32_t saved = ctx->sub_override;
+  const int dppt = backward_ppt_default(o.precision);
+  const uint32_t saved_sub = ctx->sub_override, saved_ppt = ctx->ppt_override;
   uint32_t best = 0;
   double best_t = 1e300;
-  for (uint32_t cand = 1; cand <= 64; cand *= 2) {
-    if (cand > 1 && (uint64_t)cand * 16 > tiles0 * 2) break;  // keep >= 8 jobs a round
-    ctx->sub_override = cand;
-    lsmc_plan* p = nullptr;
-    rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);
-    if (rc) break;
-    p->timing = true;
-    double ms[4] = {0, 0, 0, 0};
-    uint32_t launches = 0;
-    rc = plan_enqueue(p, true);  // warm-up launch, then the timed one
-    if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
-    if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
-    if (rc == LSMC_OK) rc = plan_enqueue(p, true);
-    if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
-    if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
-    plan_free(p);
-    if (rc) break;
-    if (ms[2] < best_t) { best_t = ms[2]; best = cand; }
+  // each paths-per-lane choice compiled for the precision, and sub-tiles per
+  // job in powers of two while the busiest round keeps >= 8 jobs
+  for (int ppt = 2; ppt <= 8 && rc == LSMC_OK; ppt *= 2) {
+    if (!backward_ppt_valid(o.precision, ppt)) continue;
+    for (uint32_t cand = 1; cand <= kMaxSub; cand *= 2) {
+      if (cand > 1 && (uint64_t)cand * ppt * 8 > tiles0 * dppt) break;
+      ctx->sub_override = cand;
+      ctx->ppt_override = (uint32_t)ppt;
+      lsmc_plan* p = nullptr;
+      rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);
+      if (rc) break;
+      p->timing = true;
+      double ms[4] = {0, 0, 0, 0};
+      uint32_t launches = 0;
+      rc = plan_enqueue(p, true);  // warm-up launch, then the timed one
+      if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+      if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+      if (rc == LSMC_OK) rc = plan_enqueue(p, true);
+      if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+      if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+      plan_free(p);
+      if (rc) break;
+      if (ms[2] < best_t) { best_t = ms[2]; best = ((uint32_t)ppt << 16) | cand; }
+    }
   }
-  ctx->sub_override = saved;
+  ctx->sub_override = saved_sub;
+  ctx->ppt_override = saved_ppt;
   if (rc && !best) return rc;
   ctx->tuned[key] = best;
-  if (best_sub) *best_sub = best;
+  if (best_sub) *best_sub = best & 0xffffu;
+  if (best_ppt) *best_ppt = best >> 16;
   if (best_ms) *best_ms = best_t;
   return LSMC_OK;
 }

@@ -15,14 +15,18 @@ cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path
                          const uint32_t* step, size_t n, int precision, void* out,
                          cudaStream_t s);
 cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s);
-cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int grid,
+cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt, int grid,
                             cudaStream_t s);
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
                           DevResult* out, cudaStream_t s);
+// Paths per thread of a backward sub-tile (a sub-tile is kBlock * ppt
+// paths): the default for a precision and whether a value is compiled for it.
+int backward_ppt_default(int precision);
+bool backward_ppt_valid(int precision, int ppt);
 // paths per backward sub-tile
-int backward_tile(int precision);
+inline int backward_tile(int ppt) { return kBlock * ppt; }
 // resident backward CTAs per SM
-int backward_occupancy(int precision, int basis);
+int backward_occupancy(int precision, int basis, int ppt);
 // bytes of one stored path value (E, V, cash flow) in a precision
 inline size_t value_bytes(int precision) { return precision == kPrecMixed ? 4 : 8; }
 

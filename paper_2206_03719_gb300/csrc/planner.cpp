@@ -164,18 +164,23 @@ static bool same_path_group(const Scenario& a, const lsmc_heston& g, double gT) 
          m.xi == g.xi && m.rho == g.rho && m.q == g.q;
 }
 
-uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, uint32_t ctas,
-                    uint32_t jobs_per_cta) {
-  const uint64_t tile0 = (uint64_t)backward_tile(precision);
+int plan_ppt(const PlanOptions& o) {
+  return o.ppt && backward_ppt_valid(o.precision, (int)o.ppt) ? (int)o.ppt
+                                                             : backward_ppt_default(o.precision);
+}
+
+uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, int ppt,
+                    uint32_t workers, uint32_t jobs_per_worker) {
+  const uint64_t tile0 = (uint64_t)backward_tile(ppt);
   uint64_t tiles = 0;  // sub-tiles of the first round, over all instances
   for (size_t i = 0; i < n; ++i) {
     std::vector<Scenario> sc;
     if (expand_scenarios(reqs[i], &sc) < 0) continue;
     tiles += (uint64_t)sc.size() * reqs[i].n_strikes * ((reqs[i].n_paths + tile0 - 1) / tile0);
   }
-  const uint64_t want = (uint64_t)std::max<uint32_t>(1, ctas) * std::max<uint32_t>(1, jobs_per_cta);
+  const uint64_t want = (uint64_t)std::max<uint32_t>(1, workers) * std::max<uint32_t>(1, jobs_per_worker);
   const uint64_t sub = tiles / want;
-  return (uint32_t)std::min<uint64_t>(64, std::max<uint64_t>(1, sub));
+  return (uint32_t)std::min<uint64_t>(kMaxSub, std::max<uint64_t>(1, sub));
 }
 
 int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
@@ -183,7 +188,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
   *L = PlanLayout();
   L->opt = opt;
   const size_t real = value_bytes(opt.precision);
-  const uint32_t tile = (uint32_t)backward_tile(opt.precision) * std::max<uint32_t>(1, opt.sub);
+  const uint32_t tile = (uint32_t)backward_tile(plan_ppt(opt)) * std::max<uint32_t>(1, opt.sub);
   const bool store_v = opt.basis == LSMC_BASIS_SV2;
   // device offsets are relative to the region starts; the caller binds them
   size_t off_paths = 0, off_y = 0, off_partial = 0, off_scale = 0;

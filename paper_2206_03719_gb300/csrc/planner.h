@@ -54,12 +54,19 @@ struct PlanOptions {
   int basis = LSMC_BASIS_S2;
   bool raw_paths = false;       // stage entry point: E rows are S itself
   uint32_t sub = 1;             // sub-tiles per backward job
+  uint32_t ppt = 0;             // paths per thread of a sub-tile (0: the precision's default)
 };
 
+// Paths per lane of a plan's backward sub-tiles.
+int plan_ppt(const PlanOptions& o);
+
+// Largest number of sub-tiles per backward job.
+constexpr uint32_t kMaxSub = 64;
+
 // Sub-tiles per backward job so that the busiest round has about
-// jobs_per_cta jobs for each of `ctas` resident CTAs.
-uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, uint32_t ctas,
-                    uint32_t jobs_per_cta = 4);
+// jobs_per_worker jobs for each of `workers` resident CTAs.
+uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, int ppt,
+                    uint32_t workers, uint32_t jobs_per_worker = 4);
 
 // Sizes and host tables of one launch; device pointers are bound later.
 struct PlanLayout {

@@ -136,7 +136,7 @@ def load(build_if_missing: bool = False):
             "lsmc_plan_destroy": ([vp], None),
             "lsmc_plan_set_timing": ([vp, i32], ctypes.c_int),
             "lsmc_plan_kernel_times": ([vp, P(dbl), P(u32)], ctypes.c_int),
-            "lsmc_autotune": ([vp, P(lsmc_request), sz, P(u32), P(dbl)], ctypes.c_int),
+            "lsmc_autotune": ([vp, P(lsmc_request), sz, P(u32), P(u32), P(dbl)], ctypes.c_int),
             "lsmc_submit": ([vp, P(lsmc_request), P(u64)], ctypes.c_int),
             "lsmc_poll": ([vp, u64, P(lsmc_result)], ctypes.c_int),
             "lsmc_wait": ([vp, u64, P(lsmc_result), dbl], ctypes.c_int),
@@ -270,11 +270,12 @@ def lsmc_plan_kernel_times(plan):
 
 
 def lsmc_autotune(ctx, reqs):
+    """(sub-tiles per job, paths per lane, backward ms) of the fastest shape."""
     arr = (lsmc_request * len(reqs))(*reqs)
-    sub, ms = ctypes.c_uint32(), ctypes.c_double()
-    check(load().lsmc_autotune(ctx, arr, len(reqs), ctypes.byref(sub), ctypes.byref(ms)),
-          "lsmc_autotune")
-    return sub.value, ms.value
+    sub, ppt, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+    check(load().lsmc_autotune(ctx, arr, len(reqs), ctypes.byref(sub), ctypes.byref(ppt),
+                               ctypes.byref(ms)), "lsmc_autotune")
+    return sub.value, ppt.value, ms.value
 
 
 def lsmc_plan_destroy(plan):

@@ -145,8 +145,8 @@ def test_invalid_requests_are_rejected_before_launch(ctx):
 def test_autotuned_plans_still_match_oracle(ctx):
     wl = workloads.SMALL_FP64.replace(n_paths=20000, n_steps=20, basis="sv2",
                                       greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02)
-    sub, ms = ctx.autotune([wl])
-    assert sub >= 1 and ms > 0
+    sub, ppt, ms = ctx.autotune([wl])
+    assert sub >= 1 and ppt in (2, 4) and ms > 0
     got = ctx.price(wl)
     ref = oracle_for(wl)
     for g, r in zip(got, ref):
