@@ -265,14 +265,16 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
-                    precision="mixed"):
+                    precision="mixed", max_inflight=16):
     """Poisson stream of book-distributed requests with continuous batching
-    (MIXED; up to 16 requests on the device at once, admitted by workspace
-    bytes), and the first `serial_n` of the same requests solved one at a
-    time in plain FP64 on the same GPU."""
+    (up to `max_inflight` launches on the device at once, each pricing the
+    requests admitted together, admitted by workspace bytes), and the first
+    `serial_n` of the same requests solved one at a time in plain FP64 on the
+    same GPU."""
     arrivals = workloads.poisson_arrivals(rate, warm_s + window_s, seed=11)
     reqs = workloads.book(n_contracts=len(arrivals), seed=99, precision=precision)
-    with api.Context(workspace_bytes=48 << 30, max_inflight=16, precision=precision) as srv:
+    with api.Context(workspace_bytes=48 << 30, max_inflight=max_inflight,
+                     precision=precision) as srv:
         t0 = time.perf_counter()
         tickets = []
         for t_arr, w in zip(arrivals, reqs):
@@ -295,7 +297,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     served = {"rate_per_s": rate, "window_s": window_s, "requests": len(tickets), "ok": ok,
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
-              "precision": precision, "max_inflight": 16}
+              "precision": precision, "max_inflight": max_inflight}
     # the same requests, one at a time, plain FP64
     serial = reqs[:serial_n]
     need = max(L.lsmc_request_footprint(None, api.Request(w, precision="fp64").c) for w in serial)
@@ -411,8 +413,9 @@ def main():
                     "mixed_large": measure_precision(*a, workloads.LARGE_MIXED)}),
                 ("book", lambda *a: {"df": measure_book(*a, precision="df"),
                                      "mixed": measure_book(*a, precision="mixed")}),
-                ("serving", lambda *a: {"df": measure_serving(*a, precision="df"),
-                                        "mixed": measure_serving(*a, precision="mixed")}))
+                ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
+                                        "mixed": measure_serving(*a, precision="mixed",
+                                                                 max_inflight=4)}))
         for name, fn in jobs:
             torch.cuda.empty_cache()
             try:

@@ -219,10 +219,15 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
 void lsmc_plan_destroy(lsmc_plan* plan);
 
 /* ---- serving: continuous batching -------------------------------------- */
-/* Queues a copy of *req; returns a ticket.  Requests are admitted to the
- * device while slots (config.max_inflight) and workspace bytes
- * (config.hbm_budget) allow, each on its own stream, so their kernels
- * overlap with those already running.  LSMC_EBUSY when the queue is full. */
+/* Queues a copy of *req; returns a ticket.  Whenever a slot
+ * (config.max_inflight) is free, the oldest pending request and the pending
+ * requests right behind it that can share a launch (same precision, scheme
+ * and basis; up to 64, while the workspace bytes of config.hbm_budget allow)
+ * are admitted together as one batch: one launch of each kernel, on the
+ * slot's own stream, overlapping with the batches already running.  The
+ * backward job size of a request depends on the request alone, so its
+ * results are the same whichever batch it runs in.  LSMC_EBUSY when the
+ * queue is full. */
 int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket);
 /* LSMC_PENDING while in flight; LSMC_OK with outs filled (n_strikes results)
  * once done (the ticket is then released); a negative code on failure. */

@@ -311,7 +311,7 @@ __device__ __forceinline__ void accumulate_moments(Real* t, Real S, Real v, Real
 // regression runs on Z and the exercise test compares h exp(-r n dt) with the
 // fitted value in the same units.  Z changes only where a path exercises.
 //
-// A job covers `a.sub` sub-tiles of kBlock * PPT paths: the wait for the
+// A job covers `I.sub` sub-tiles of kBlock * PPT paths: the wait for the
 // previous round, the block reduction and the arrival are paid once per job.
 template <typename Real, int BASIS, int PPT>
 __global__ void __launch_bounds__(kBlock, 2)
@@ -341,7 +341,6 @@ backward_kernel(BwdArgs a) {
   __shared__ Real s_zn[NW][PPT][32];  // cash flows after the exercise test
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint32_t sub = a.sub;
   // single precision and float pairs reduce through float pairs; double
   // precision through doubles
   constexpr bool kSingle = !std::is_same<Real, double>::value;
@@ -403,6 +402,7 @@ backward_kernel(BwdArgs a) {
     // regression date of this round (0 for the estimator round)
     const uint32_t n = european ? 0 : N - 1 - r;
     const bool first = european || r == 0;  // cash flows start at the maturity payoff
+    const uint32_t sub = I.sub;
     const uint32_t tile_base = ji.tile * (sub * TILE0);
 
     // ---- warp 0: wait for the exercise rule of date n + 1, then convert the

@@ -42,10 +42,13 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct Ticket;
 
+// A serving slot: one stream and, while busy, one plan pricing a batch of
+// admitted tickets.
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  Ticket* t = nullptr;
+  std::vector<Ticket*> batch;
+  lsmc_plan* plan = nullptr;
 };
 
 }  // namespace
@@ -61,6 +64,7 @@ struct lsmc_ctx {
   uint32_t max_inflight = 8, queue_capacity = 4096;
   int num_sms = 0;
   std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
+  std::mutex occ_mu;          // guards occ (plans are built on several threads)
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
   uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
   // autotuned backward shape (ppt << 16 | sub-tiles per job), keyed by
@@ -117,9 +121,12 @@ struct Ticket {
   int status = LSMC_PENDING;
   std::vector<lsmc_result> results;
   double t_submit = 0, t_admit = 0, t_done = 0;
-  lsmc_plan* plan = nullptr;
   size_t footprint = 0;
   int slot = -1;
+  // backward shape of this request priced alone (a batch keeps it, so a
+  // result does not depend on the batch it ran in)
+  uint32_t ppt = 0, sub = 1;
+  int precision = 0, scheme = 0, basis = 0;
 };
 
 int cuda_status(cudaError_t e) {
@@ -138,6 +145,7 @@ int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? df
 
 int occupancy(lsmc_ctx* ctx, int precision, int basis, int ppt) {
   if (ctx) {
+    std::lock_guard<std::mutex> g(ctx->occ_mu);
     int& o = ctx->occ[(precision * 4 + basis) * 16 + ppt];
     if (o == 0) o = std::max(1, backward_occupancy(precision, basis, ppt));
     return o;
@@ -234,7 +242,6 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
-  p->ba.sub = std::max<uint32_t>(1, L.opt.sub);
   const int occ = occupancy(p->ctx, prec, L.opt.basis, plan_ppt(L.opt));
   const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
@@ -315,8 +322,30 @@ uint64_t tune_key(const lsmc_request* reqs, size_t n, const PlanOptions& o) {
   return ((uint64_t)o.precision << 40) | ((uint64_t)o.basis << 32) | lg;
 }
 
+// Backward shape of a plan: autotuned if this kind of launch was tuned, else
+// the precision's paths per thread and about four jobs per resident CTA in
+// the busiest round; overrides (tuning sweeps) win.
+void choose_shape(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions* o) {
+  uint32_t tuned = 0;
+  if (ctx) {
+    auto it = ctx->tuned.find(tune_key(reqs, n, *o));
+    if (it != ctx->tuned.end()) tuned = it->second;
+  }
+  o->ppt = tuned >> 16;
+  if (ctx && ctx->ppt_override) o->ppt = ctx->ppt_override;
+  const int ppt = plan_ppt(*o);
+  const uint32_t ctas = (uint32_t)occupancy(ctx, o->precision, o->basis, ppt) *
+                        (uint32_t)sm_count(ctx);
+  o->sub = choose_sub(reqs, n, o->precision, ppt, ctas);
+  if (tuned & 0xffffu) o->sub = tuned & 0xffffu;
+  if (ctx && ctx->sub_override) o->sub = ctx->sub_override;
+}
+
+// subs (optional): the sub-tiles per job of each request, with paths per
+// thread ppt, instead of the shape chosen for the whole plan.
 int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
-                   cudaStream_t stream, bool use_arena, lsmc_plan** out) {
+                   cudaStream_t stream, bool use_arena, lsmc_plan** out,
+                   const std::vector<uint32_t>* subs = nullptr, uint32_t ppt = 0) {
   PlanOptions o;
   int rc = plan_options(ctx, reqs, n, &o);
   if (rc) return rc;
@@ -324,23 +353,11 @@ int plan_create_on(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n,
   if (!p) return LSMC_ENOMEM;
   p->ctx = ctx;
   p->stream = stream;
-  {
-    // backward shape: autotuned if this kind of launch was tuned, else
-    // the precision's paths per thread and about four jobs per resident CTA
-    // in the busiest round; overrides (tuning sweeps) win
-    uint32_t tuned = 0;
-    if (ctx) {
-      auto it = ctx->tuned.find(tune_key(reqs, n, o));
-      if (it != ctx->tuned.end()) tuned = it->second;
-    }
-    o.ppt = tuned >> 16;
-    if (ctx && ctx->ppt_override) o.ppt = ctx->ppt_override;
-    const int ppt = plan_ppt(o);
-    const uint32_t ctas = (uint32_t)occupancy(ctx, o.precision, o.basis, ppt) *
-                          (uint32_t)sm_count(ctx);
-    o.sub = choose_sub(reqs, n, o.precision, ppt, ctas);
-    if (tuned & 0xffffu) o.sub = tuned & 0xffffu;
-    if (ctx && ctx->sub_override) o.sub = ctx->sub_override;
+  if (subs && subs->size() == n) {
+    o.ppt = ppt;
+    o.sub_req = *subs;
+  } else {
+    choose_shape(ctx, reqs, n, &o);
   }
   rc = build_layout(reqs, n, o, &p->L);
   if (rc) return rc;
@@ -423,61 +440,99 @@ int plan_collect(lsmc_plan* p, lsmc_result* outs) {
 void finish_ticket(lsmc_ctx* ctx, Ticket* t, int status) {
   t->status = status;
   t->t_done = now_s() - ctx->t0;
-  if (t->plan) { plan_free(t->plan); t->plan = nullptr; }
   ctx->done_cv.notify_all();
 }
+
+// Requests admitted together share one plan (one launch of each kernel).
+constexpr size_t kMaxBatch = 64;
+constexpr uint32_t kMaxServeSub = 32;
 
 void scheduler_loop(lsmc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   std::unique_lock<std::mutex> lk(ctx->mu);
   while (!ctx->stop) {
     bool progress = false;
-    // completions
+    // completions: a batch finishes together
     for (size_t s = 0; s < ctx->slots.size(); ++s) {
       Slot& sl = ctx->slots[s];
-      if (!sl.t) continue;
+      if (sl.batch.empty()) continue;
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
-      Ticket* t = sl.t;
-      sl.t = nullptr;
       int rc = q == cudaSuccess ? LSMC_OK : LSMC_ECUDA;
+      std::vector<lsmc_result> all;
       if (rc == LSMC_OK) {
-        t->results.resize(t->plan->h_out.size());
-        rc = plan_collect(t->plan, t->results.data());
+        all.resize(sl.plan->h_out.size());
+        rc = plan_collect(sl.plan, all.data());
       }
-      finish_ticket(ctx, t, rc);
+      size_t off = 0;
+      for (Ticket* t : sl.batch) {
+        const size_t k = t->req.n_strikes;
+        if (rc == LSMC_OK && off + k <= all.size())
+          t->results.assign(all.begin() + off, all.begin() + off + k);
+        off += k;
+        finish_ticket(ctx, t, rc);
+      }
+      plan_free(sl.plan);
+      sl.plan = nullptr;
+      sl.batch.clear();
       progress = true;
     }
-    // admissions (first come, first served)
+    // admissions, first come first served: the oldest pending request and
+    // the pending requests right behind it that can share its launch (same
+    // precision, scheme, basis and paths per thread) while the workspace
+    // has room for all of them
     while (!ctx->pending.empty()) {
       int free_slot = -1;
       for (size_t s = 0; s < ctx->slots.size(); ++s)
-        if (!ctx->slots[s].t) { free_slot = (int)s; break; }
+        if (ctx->slots[s].batch.empty()) { free_slot = (int)s; break; }
       if (free_slot < 0) break;
-      Ticket* t = ctx->pending.front();
-      if (ctx->arena.largest_free() < t->footprint) break;  // wait for memory
-      ctx->pending.pop_front();
+      Ticket* t0 = ctx->pending.front();
+      const size_t room = ctx->arena.largest_free();
+      if (room < t0->footprint) break;  // wait for memory
+      std::vector<Ticket*> batch{t0};
+      size_t need = t0->footprint;
+      for (size_t i = 1; i < ctx->pending.size() && batch.size() < kMaxBatch; ++i) {
+        Ticket* t = ctx->pending[i];
+        if (t->precision != t0->precision || t->scheme != t0->scheme ||
+            t->basis != t0->basis || t->ppt != t0->ppt || need + t->footprint > room)
+          break;
+        batch.push_back(t);
+        need += t->footprint;
+      }
       Slot& sl = ctx->slots[free_slot];
       lsmc_plan* p = nullptr;
-      int rc = plan_create_on(ctx, &t->req, 1, sl.stream, true, &p);
-      if (rc == LSMC_ENOMEM) {  // fragmentation: retry once others finish
-        ctx->pending.push_front(t);
-        break;
+      int rc = LSMC_ENOMEM;
+      while (!batch.empty()) {
+        std::vector<lsmc_request> reqs;
+        std::vector<uint32_t> subs;
+        for (Ticket* t : batch) {
+          reqs.push_back(t->req);
+          subs.push_back(t->sub);
+        }
+        rc = plan_create_on(ctx, reqs.data(), reqs.size(), sl.stream, true, &p, &subs, t0->ppt);
+        if (rc != LSMC_ENOMEM || batch.size() == 1) break;
+        batch.resize(batch.size() / 2);  // fragmentation: a smaller batch
       }
-      t->t_admit = now_s() - ctx->t0;
+      if (rc == LSMC_ENOMEM) break;  // retry once others finish
+      ctx->pending.erase(ctx->pending.begin(), ctx->pending.begin() + batch.size());
+      const double t_admit = now_s() - ctx->t0;
+      for (Ticket* t : batch) {
+        t->t_admit = t_admit;
+        t->slot = free_slot;
+      }
       if (rc == LSMC_OK) rc = plan_launch(p, false);
       if (rc == LSMC_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = LSMC_ECUDA;
-      t->plan = p;
       if (rc != LSMC_OK) {
-        finish_ticket(ctx, t, rc);
+        if (p) plan_free(p);
+        for (Ticket* t : batch) finish_ticket(ctx, t, rc);
       } else {
-        sl.t = t;
-        t->slot = free_slot;
+        sl.plan = p;
+        sl.batch = batch;
       }
       progress = true;
     }
     bool inflight = false;
-    for (const auto& sl : ctx->slots) inflight |= sl.t != nullptr;
+    for (const auto& sl : ctx->slots) inflight |= !sl.batch.empty();
     if (!inflight && ctx->pending.empty()) {
       ctx->cv.wait(lk, [&] { return ctx->stop || !ctx->pending.empty(); });
     } else if (!progress) {
@@ -600,12 +655,11 @@ void lsmc_destroy(lsmc_ctx* ctx) {
   if (ctx->sched.joinable()) ctx->sched.join();
   for (auto& s : ctx->slots) {
     if (s.stream) cudaStreamSynchronize(s.stream);
-    if (s.t) { if (s.t->plan) plan_free(s.t->plan); s.t->plan = nullptr; }
+    if (s.plan) plan_free(s.plan);
+    s.plan = nullptr;
+    s.batch.clear();
   }
-  for (auto& kv : ctx->tickets) {
-    if (kv.second->plan) plan_free(kv.second->plan);
-    delete kv.second;
-  }
+  for (auto& kv : ctx->tickets) delete kv.second;
   for (auto& s : ctx->slots) {
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
@@ -762,6 +816,17 @@ int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket) {
   t->strikes.assign(req->strikes, req->strikes + req->n_strikes);
   t->req.strikes = t->strikes.data();
   t->footprint = fp;
+  t->precision = o.precision;
+  t->scheme = o.scheme;
+  t->basis = o.basis;
+  // serving shape, a function of the request alone (so its result does not
+  // depend on the batch it runs in): the precision's paths per thread and
+  // about four jobs per regression and date, at most kMaxServeSub sub-tiles
+  o.ppt = ctx->ppt_override;
+  t->ppt = (uint32_t)plan_ppt(o);
+  const uint32_t tiles = (req->n_paths + backward_tile((int)t->ppt) - 1) / backward_tile((int)t->ppt);
+  t->sub = ctx->sub_override ? ctx->sub_override
+                             : std::min<uint32_t>(kMaxServeSub, std::max<uint32_t>(1, (tiles + 3) / 4));
   t->t_submit = now_s() - ctx->t0;
   ctx->tickets[t->id] = t;
   ctx->pending.push_back(t);

@@ -82,6 +82,7 @@ struct BwdInstance {
   uint32_t P, N, tiles, gens;
   int32_t type, style, basis;
   uint32_t out_index; // result slot
+  uint32_t sub;       // sub-tiles of kBlock * PPT paths per job (a tile)
 };
 
 struct BwdState {
@@ -118,7 +119,6 @@ struct BwdArgs {
   unsigned long long total_jobs;
   unsigned long long timeout_ns;
   uint32_t n_rounds, n_inst;
-  uint32_t sub;              // sub-tiles of kBlock * PPT paths per job
 };
 
 // ---- Greeks ---------------------------------------------------------------

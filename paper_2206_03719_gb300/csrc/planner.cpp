@@ -188,7 +188,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
   *L = PlanLayout();
   L->opt = opt;
   const size_t real = value_bytes(opt.precision);
-  const uint32_t tile = (uint32_t)backward_tile(plan_ppt(opt)) * std::max<uint32_t>(1, opt.sub);
+  const uint32_t tile0 = (uint32_t)backward_tile(plan_ppt(opt));
   const bool store_v = opt.basis == LSMC_BASIS_SV2;
   // device offsets are relative to the region starts; the caller binds them
   size_t off_paths = 0, off_y = 0, off_partial = 0, off_scale = 0;
@@ -248,6 +248,8 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
     L->generated_path_steps += (uint64_t)P * N * sc.size();
     L->lsmc_path_steps += (uint64_t)P * N * sc.size() * q.n_strikes;
 
+    const uint32_t sub = std::max<uint32_t>(1, ci < opt.sub_req.size() ? opt.sub_req[ci] : opt.sub);
+    const uint32_t tile = tile0 * sub;
     const uint32_t tiles = (P + tile - 1) / tile;
     if ((uint64_t)tiles * N >= (1ull << 31)) return LSMC_EINVAL;
     std::vector<GreekOut> gos(q.n_strikes);
@@ -288,6 +290,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         I.P = P;
         I.N = N;
         I.tiles = tiles;
+        I.sub = sub;
         I.gens = q.style == LSMC_EUROPEAN ? 1 : N;
         I.type = q.type;
         I.style = q.style;

@@ -54,6 +54,7 @@ struct PlanOptions {
   int basis = LSMC_BASIS_S2;
   bool raw_paths = false;       // stage entry point: E rows are S itself
   uint32_t sub = 1;             // sub-tiles per backward job
+  std::vector<uint32_t> sub_req; // per request (if not empty: overrides sub)
   uint32_t ppt = 0;             // paths per thread of a sub-tile (0: the precision's default)
 };
 
