@@ -100,11 +100,12 @@ __device__ void make_group_const(const FwdGroup& g, GroupConst<Real>& c) {
 // (s^2 + m^2), 1 - p = 2 m^2 / (s^2 + m^2), 1 / beta = m / (1 - p); the
 // point mass is taken when U_V <= p, i.e. 1 - U_V >= 1 - p.
 template <typename Real>
-__device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x, Real& v,
-                                        Real omu, Real zV, Real zX, const DfTables* t) {
+__device__ __forceinline__ void qe_core(Real mA, Real mB, Real sA, Real sB, Real c0, Real K1,
+                                        Real K2, Real K3, Real& x, Real& v, Real omu, Real zV,
+                                        Real zX, const DfTables* t) {
   using F = Fm<Real>;
-  const Real m = fma(c.mB, v, c.mA);
-  const Real s2 = fma(c.sB, v, c.sA);
+  const Real m = fma(mB, v, mA);
+  const Real s2 = fma(sB, v, sA);
   const Real m2 = m * m;
   Real v1;
   if (s2 <= (Real)1.5 * m2) {
@@ -120,8 +121,14 @@ __device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x, Real
     const Real omp = (m2 + m2) * rden;
     v1 = (omu >= omp) ? (Real)0 : F::div(m, omp) * F::log_(F::div(omp, omu), t);
   }
-  x = x + c.c0 + c.K1 * v + c.K2 * v1 + F::sqrt_(c.K3 * (v + v1)) * zX;
+  x = x + c0 + K1 * v + K2 * v1 + F::sqrt_(K3 * (v + v1)) * zX;
   v = v1;
+}
+
+template <typename Real>
+__device__ __forceinline__ void qe_step(const GroupConst<Real>& c, Real& x, Real& v,
+                                        Real omu, Real zV, Real zX, const DfTables* t) {
+  qe_core<Real>(c.mA, c.mB, c.sA, c.sB, c.c0, c.K1, c.K2, c.K3, x, v, omu, zV, zX, t);
 }
 
 // Full-truncation Euler: v+ = max(v, 0) in drift and diffusion.
@@ -137,7 +144,7 @@ __device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
 }
 
 template <typename Real, int SCHEME>
-__global__ void __launch_bounds__(kBlock, std::is_same<Real, double>::value ? 2 : 1)
+__global__ void __launch_bounds__(kBlock, std::is_same<Real, double>::value ? 2 : (std::is_same<Real, float>::value ? 4 : 1))
 forward_kernel(FwdArgs a) {
   __shared__ GroupConst<Real> gc[kMaxGroups];
   __shared__ FwdContract sc;
@@ -171,9 +178,48 @@ forward_kernel(FwdArgs a) {
     if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
   }
 
-  if constexpr (!kPair) {
-    // double and float: every group's state in registers, the group loop
-    // unrolled so the groups' independent chains interleave
+  if constexpr (std::is_same<Real, float>::value && SCHEME == kSchemeQE) {
+    // the single-precision QE stepper: state, scheme constants and row
+    // pointers of every group in registers, the group loop unrolled so the
+    // groups' independent chains interleave, one shared row offset
+    float x[kMaxGroups], v[kMaxGroups], mA[kMaxGroups], mB[kMaxGroups], sA[kMaxGroups],
+        sB[kMaxGroups], c0[kMaxGroups], K1[kMaxGroups], K2[kMaxGroups], K3[kMaxGroups],
+        os[kMaxGroups];
+    float* rowE[kMaxGroups];
+    float* rowV[kMaxGroups];
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) {
+      const GroupConst<float>& c = gc[g < ng ? g : 0];
+      x[g] = 0.0f;
+      v[g] = c.v0;
+      mA[g] = c.mA; mB[g] = c.mB; sA[g] = c.sA; sB[g] = c.sB;
+      c0[g] = c.c0; K1[g] = c.K1; K2[g] = c.K2; K3[g] = c.K3;
+      os[g] = c.out_scale;
+      rowE[g] = c.E + p;
+      rowV[g] = c.V ? c.V + p : nullptr;
+    }
+    const size_t ld = gc[0].ld;  // one row stride for the groups of a contract
+    size_t off = 0;
+    for (uint32_t n = 0; n < sc.N; ++n, off += ld) {
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      float u, omu, zV, zX;
+      Draw<float>::make(w, u, omu, zV, zX, tabs);
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g) {
+        if (g < ng) {
+          float xg = x[g], vg = v[g];
+          qe_core<float>(mA[g], mB[g], sA[g], sB[g], c0[g], K1[g], K2[g], K3[g], xg, vg, omu,
+                         zV, zX, tabs);
+          x[g] = xg;
+          v[g] = vg;
+          rowE[g][off] = os[g] * __expf(xg);
+          if (rowV[g]) rowV[g][off] = vg;
+        }
+      }
+    }
+  } else if constexpr (!kPair) {
+    // double (and the float Euler scheme): every group's state in registers,
+    // the group loop unrolled so the groups' independent chains interleave
     Real x[kMaxGroups], v[kMaxGroups];
 #pragma unroll
     for (int g = 0; g < kMaxGroups; ++g) {
