@@ -144,7 +144,9 @@ __device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
 }
 
 template <typename Real, int SCHEME>
-__global__ void __launch_bounds__(kBlock, std::is_same<Real, double>::value ? 2 : (std::is_same<Real, float>::value ? 4 : 1))
+// register budgets: 128 per thread for double, 64 for float (eight CTAs of
+// 128 threads per SM), unconstrained for float pairs
+__global__ void __launch_bounds__(kFwdBlock, std::is_same<Real, double>::value ? 4 : (std::is_same<Real, float>::value ? 8 : 1))
 forward_kernel(FwdArgs a) {
   __shared__ GroupConst<Real> gc[kMaxGroups];
   __shared__ FwdContract sc;
@@ -167,7 +169,7 @@ forward_kernel(FwdArgs a) {
   if constexpr (kPair) load_df_tables(tabs);
   __syncthreads();
 
-  const uint32_t p = (blockIdx.x - sc.block0) * kBlock + threadIdx.x;
+  const uint32_t p = (blockIdx.x - sc.block0) * kFwdBlock + threadIdx.x;
   if (p >= sc.P) return;
   const int ng = (int)sc.n_groups;
   const uint2 key = make_uint2((uint32_t)sc.seed, (uint32_t)(sc.seed >> 32));
@@ -249,7 +251,7 @@ forward_kernel(FwdArgs a) {
     // float pairs: a group step is several hundred instructions, so the
     // group loop is not unrolled (the code stays in the instruction cache)
     // and the per-group state lives in shared memory
-    __shared__ Real xs[kMaxGroups][kBlock], vs[kMaxGroups][kBlock];
+    __shared__ Real xs[kMaxGroups][kFwdBlock], vs[kMaxGroups][kFwdBlock];
     const int t = threadIdx.x;
     for (int g = 0; g < ng; ++g) {
       xs[g][t] = (Real)0;
@@ -309,9 +311,9 @@ __global__ void draws_kernel(uint2 key, uint32_t stream_id,
 template <typename Real>
 static void launch_forward_t(const FwdArgs& a, int scheme, cudaStream_t s) {
   if (scheme == kSchemeQE)
-    forward_kernel<Real, kSchemeQE><<<a.n_blocks, kBlock, 0, s>>>(a);
+    forward_kernel<Real, kSchemeQE><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
   else
-    forward_kernel<Real, kSchemeFT><<<a.n_blocks, kBlock, 0, s>>>(a);
+    forward_kernel<Real, kSchemeFT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
 }
 
 cudaError_t launch_forward(const FwdArgs& a, int precision, int scheme, cudaStream_t s) {

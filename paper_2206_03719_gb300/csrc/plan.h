@@ -13,7 +13,8 @@
 
 namespace lsmc {
 
-constexpr int kBlock = 256;      // threads per CTA (forward and backward)
+constexpr int kBlock = 256;      // threads per CTA of the backward pass
+constexpr int kFwdBlock = 128;   // threads (paths) per CTA of the forward pass
 constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
 constexpr int kNSum = 25;        // doubles per tile partial
 // partial layout: 15 monomials x^a w^b (a + b <= 4), 6 right-hand sides,

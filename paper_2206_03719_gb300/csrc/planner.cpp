@@ -243,7 +243,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
     C.group0 = group0;
     C.n_groups = (uint32_t)gT.size();
     C.block0 = L->fwd_blocks;
-    L->fwd_blocks += (P + kBlock - 1) / kBlock;
+    L->fwd_blocks += (P + kFwdBlock - 1) / kFwdBlock;
     L->contracts.push_back(C);
     L->generated_path_steps += (uint64_t)P * N * sc.size();
     L->lsmc_path_steps += (uint64_t)P * N * sc.size() * q.n_strikes;
