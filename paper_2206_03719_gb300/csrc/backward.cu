@@ -268,30 +268,70 @@ template <int NA> struct Acc<float, NA> {
 // Adds one in-the-money path to the per-thread moment sums: the 15
 // monomials x^a w^b (a + b <= 4) of the centred basis variables
 // x = S/K - 1, w = v/theta - 1 and the six products with the cash flow y.
+// Every monomial of degree 3 or 4 is the product of two basis functions
+// (x^3 = x^2 x, x^3 w = x^2 (x w), ...), so it is added as one fused
+// multiply-add; the path count (monomial 1) is an integer.
 template <typename Real, int BASIS, int NM>
-__device__ __forceinline__ void accumulate_moments(Real* t, Real S, Real v, Real yv, Real invK,
-                                                   Real invTh) {
+__device__ __forceinline__ void accumulate_moments(Real* t, uint32_t& cnt, Real S, Real v, Real yv,
+                                                   Real invK, Real invTh) {
+  if constexpr (std::is_same<Real, float>::value) {
+    // single precision (uncompacted, predicated loop): the count as a float
+    // sum and the monomials as separate products schedule better there
+    const Real x = qfma(S, invK, (Real)-1);
+    const Real x2 = qmul(x, x), x3 = qmul(x2, x), x4 = qmul(x2, x2);
+    qacc(t[0], (Real)1);
+    qacc(t[1], x);
+    qacc(t[2], x2);
+    qacc(t[3], x3);
+    qacc(t[4], x4);
+    if (BASIS == kBasisSV2) {
+      const Real w = qfma(v, invTh, (Real)-1);
+      const Real w2 = qmul(w, w), w3 = qmul(w2, w), w4 = qmul(w2, w2);
+      const Real xw = qmul(x, w);
+      qacc(t[mono(0, 1)], w);
+      qacc(t[mono(1, 1)], xw);
+      qacc(t[mono(2, 1)], qmul(x2, w));
+      qacc(t[mono(3, 1)], qmul(x3, w));
+      qacc(t[mono(0, 2)], w2);
+      qacc(t[mono(1, 2)], qmul(x, w2));
+      qacc(t[mono(2, 2)], qmul(x2, w2));
+      qacc(t[mono(0, 3)], w3);
+      qacc(t[mono(1, 3)], qmul(x, w3));
+      qacc(t[mono(0, 4)], w4);
+      qacc(t[NM + 0], yv);
+      qacc(t[NM + 1], qmul(x, yv));
+      qacc(t[NM + 2], qmul(x2, yv));
+      qacc(t[NM + 3], qmul(w, yv));
+      qacc(t[NM + 4], qmul(xw, yv));
+      qacc(t[NM + 5], qmul(w2, yv));
+    } else {
+      qacc(t[NM + 0], yv);
+      qacc(t[NM + 1], qmul(x, yv));
+      qacc(t[NM + 2], qmul(x2, yv));
+    }
+    return;
+  }
+  ++cnt;
   const Real x = qfma(S, invK, (Real)-1);
-  const Real x2 = qmul(x, x), x3 = qmul(x2, x), x4 = qmul(x2, x2);
-  qacc(t[0], (Real)1);
+  const Real x2 = qmul(x, x);
   qacc(t[1], x);
   qacc(t[2], x2);
-  qacc(t[3], x3);
-  qacc(t[4], x4);
+  qacc(t[3], qmul(x2, x));
+  qacc(t[4], qmul(x2, x2));
   if (BASIS == kBasisSV2) {
     const Real w = qfma(v, invTh, (Real)-1);
-    const Real w2 = qmul(w, w), w3 = qmul(w2, w), w4 = qmul(w2, w2);
+    const Real w2 = qmul(w, w);
     const Real xw = qmul(x, w);
     qacc(t[mono(0, 1)], w);
     qacc(t[mono(1, 1)], xw);
     qacc(t[mono(2, 1)], qmul(x2, w));
-    qacc(t[mono(3, 1)], qmul(x3, w));
+    qacc(t[mono(3, 1)], qmul(x2, xw));
     qacc(t[mono(0, 2)], w2);
-    qacc(t[mono(1, 2)], qmul(x, w2));
+    qacc(t[mono(1, 2)], qmul(xw, w));
     qacc(t[mono(2, 2)], qmul(x2, w2));
-    qacc(t[mono(0, 3)], w3);
-    qacc(t[mono(1, 3)], qmul(x, w3));
-    qacc(t[mono(0, 4)], w4);
+    qacc(t[mono(0, 3)], qmul(w2, w));
+    qacc(t[mono(1, 3)], qmul(xw, w2));
+    qacc(t[mono(0, 4)], qmul(w2, w2));
     qacc(t[NM + 0], yv);
     qacc(t[NM + 1], qmul(x, yv));
     qacc(t[NM + 2], qmul(x2, yv));
@@ -477,6 +517,7 @@ backward_kernel(BwdArgs a) {
 
     Acc<Real, NA> acc;
     acc.zero();
+    uint32_t n_itm = 0;  // in-the-money paths of this thread (monomial 1)
     double euro = 0.0, sy = 0.0, sy2 = 0.0;
     uint32_t ties = 0;
 
@@ -626,7 +667,7 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           const Real S = s0 * e0[k];
           if (p < P && in_money<Real>(type, K, S)) {
-            accumulate_moments<Real, BASIS, NM>(t, S, v0[k], z[k], invK, invTh);
+            accumulate_moments<Real, BASIS, NM>(t, n_itm, S, v0[k], z[k], invK, invTh);
           }
         }
         acc.fold();
@@ -650,7 +691,7 @@ backward_kernel(BwdArgs a) {
         __syncwarp();
         Real* t = acc.target();
         for (int j = lane; j < cnt; j += 32)
-          accumulate_moments<Real, BASIS, NM>(t, cs[j], cv[j], cy[j], invK, invTh);
+          accumulate_moments<Real, BASIS, NM>(t, n_itm, cs[j], cv[j], cy[j], invK, invTh);
         __syncwarp();
         acc.fold();
       }
@@ -675,8 +716,13 @@ backward_kernel(BwdArgs a) {
       for (int a0 = 0; a0 < NA; a0 += RROWS) {
 #pragma unroll
         for (int i = a0; i < NA && i < a0 + RROWS; ++i) {
-          if constexpr (kSingle) red[i - a0][lane] = acc.pair(i);
-          else red[i - a0][lane] = acc.s[i];
+          // the path count: an integer, except in single precision
+          if constexpr (std::is_same<Real, float>::value)
+            red[i - a0][lane] = acc.pair(i);
+          else if constexpr (kSingle)
+            red[i - a0][lane] = i == 0 ? make_float2((float)n_itm, 0.0f) : acc.pair(i);
+          else
+            red[i - a0][lane] = i == 0 ? (double)n_itm : acc.s[i];
         }
         __syncwarp();
         const int i = a0 + lane;
