@@ -15,6 +15,7 @@ rank 0 reports the sum of throughputs over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -33,7 +34,8 @@ GOLDEN = os.path.join(_ROOT, "tests", "golden", "paper_fp64.json")
 PEAKS = os.path.join(_ROOT, "MEASURED_PEAKS.json")
 # nominal FP64 rate of a GB300 (used as the ALU roofline of the FP64 path)
 FP64_NOMINAL_TFLOPS = 1.25
-# algorithmic FP64 operations of the backward pass:
+# algorithmic FP64 operations of the backward pass (a fused multiply-add
+# counts as two):
 #   every (instance, path, date): S = scale*E, payoff, discount      -> 3
 #   in-the-money moment sums (SV2): x, w, 12 monomial products,
 #     15 monomial adds, 5 products + 6 adds for X^T y                 -> 40
@@ -41,6 +43,15 @@ FP64_NOMINAL_TFLOPS = 1.25
 #     5 multiply-adds for the continuation value, compare             -> 15
 BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
+# DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
+# kernel at 98,304 paths (2.612595e9 + 0.288776e9 bytes) scaled by the path
+# count (the path store and cash flows grow in proportion).  Valid only for
+# the kernel source it was taken from: reported as null once backward.cu
+# changes.
+BWD_TRAFFIC = {"bytes": (2.612595e9 + 0.288776448e9) * 131072 / 98304,
+               "source_sha256_16": "2e608630d8b5508e",
+               "capture": "profiles/backward_kernel_fp64_98304x252.md, scaled by 131072/98304"}
 
 
 def parse():
@@ -219,7 +230,12 @@ def measure_precision(api, L, torch, wl, reps=3):
             e = abs(g[k] - r[k]) / max(abs(r[k]), 1e-12)
             errs[k] = max(errs.get(k, 0.0), e)
     ms = sum(kms) / max(1, launches)
+    fwd_ms = kms[1] / max(1, launches)
+    # simulations after folding the bumps onto path groups: base, v0 +/- and
+    # T -/+ (S and r bumps share the base simulation)
+    groups = 1 + 2 * ("vega" in wl.greeks) + 2 * ("theta" in wl.greeks)
     out.update({"greeks_per_s": wl.n_greeks / (ms / 1e3), "ms_per_step": ms,
+                "forward_simulated_path_steps_per_s": wl.n_paths * wl.n_steps * groups / (fwd_ms / 1e3),
                 "generated_path_steps_per_s": wl.generated_path_steps / (ms / 1e3),
                 "lsmc_path_steps_per_s": wl.lsmc_path_steps / (ms / 1e3),
                 "kernel_ms": {"forward": kms[1] / max(1, launches),
@@ -230,8 +246,8 @@ def measure_precision(api, L, torch, wl, reps=3):
 
 
 def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
-    """Uneven book (512 contracts, all bump scenarios, FP32 paths / FP64
-    reductions) in launches of `chunk` contracts, each captured once in a CUDA
+    """Uneven book (512 contracts, all bump scenarios, in the given precision)
+    in launches of `chunk` contracts, each captured once in a CUDA
     graph and replayed; device time summed over the chunks (each chunk holds
     its own paths, so chunks run one after another within a workspace of the
     largest chunk's size)."""
@@ -402,7 +418,7 @@ def main():
 
     ctx.close()
     extras = {}
-    if not args.no_extras and not args.paths and args.workload == "paper_fp64":
+    if not args.no_extras and not args.paths and args.workload == "paper_fp64" and world == 1:
         df_paper = workloads.PAPER_FP64.replace(
             precision="df", name="american-put-heston-131072x252-5strikes-df")
         df_large = workloads.LARGE_MIXED.replace(
@@ -412,7 +428,8 @@ def main():
                     "df_large": measure_precision(*a, df_large),
                     "mixed_large": measure_precision(*a, workloads.LARGE_MIXED)}),
                 ("book", lambda *a: {"df": measure_book(*a, precision="df"),
-                                     "mixed": measure_book(*a, precision="mixed")}),
+                                     "mixed": measure_book(*a, precision="mixed"),
+                                     "fp64": measure_book(*a, precision="fp64")}),
                 ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
                                         "mixed": measure_serving(*a, precision="mixed",
                                                                  max_inflight=4)}))
@@ -438,13 +455,23 @@ def main():
     flops = BWD_FLOPS_ALL * info.lsmc_path_steps + BWD_FLOPS_ITM * itm
     achieved = flops / (bwd_ms / 1e3) / 1e12
     fp64 = wl.precision == "fp64"
+    traffic = None
+    src = os.path.join(_ROOT, "paper_2206_03719_gb300", "csrc", "backward.cu")
+    if fp64 and wl.n_paths == workloads.PAPER_FP64.n_paths and os.path.exists(src):
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] == BWD_TRAFFIC["source_sha256_16"]:
+                traffic = BWD_TRAFFIC["bytes"]
     roofline = {
         "kernel": "backward_kernel (Longstaff-Schwartz moments, solve, exercise)",
         "bound": "alu", "achieved": achieved,
         "peak": FP64_NOMINAL_TFLOPS if fp64 else None, "unit": "TFLOP/s",
         "frac": achieved / FP64_NOMINAL_TFLOPS if fp64 else None,
         "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (no measured FP64 peak)",
-        "traffic": None,
+        "traffic": traffic,
+        "traffic_source": BWD_TRAFFIC["capture"] if traffic else None,
+        # the path store read once (E and v rows of every path group and date)
+        "path_store_bytes": wl.n_paths * wl.n_steps * 2 * 8 *
+                            (1 + 2 * ("vega" in wl.greeks) + 2 * ("theta" in wl.greeks)),
         "kernel_ms": {"setup": kms[0] / max(1, launches), "forward": fwd_ms,
                       "backward": bwd_ms, "greeks": kms[3] / max(1, launches)},
     }
