@@ -94,6 +94,14 @@ def lib():
         L.orc_path_one.argtypes = [ctypes.POINTER(Heston), ctypes.c_double, ctypes.c_int,
                                    ctypes.c_int, ctypes.c_uint32, ctypes.c_uint32,
                                    ctypes.c_uint64, ctypes.c_uint32, dp, dp]
+        L.orc_multi_max.argtypes = [ctypes.POINTER(Heston), ctypes.c_uint32, ctypes.c_double,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                    ctypes.c_uint32, dp, ctypes.c_int]
+        L.orc_asset_path.argtypes = [ctypes.POINTER(Heston), ctypes.c_uint32, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                     ctypes.c_uint32, dp]
         L.orc_lsmc.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
             [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + \
             [dp, u32p, dp, ctypes.POINTER(ctypes.c_uint8)]
@@ -186,6 +194,30 @@ def paths(model: Heston, T, scheme, P, N, seed, stream=0, grid=GRID_F64,
     if rc != 0:
         raise ValueError("orc_paths rejected its arguments (%d)" % rc)
     return S, V
+
+
+def multi_max(models, T, scheme, P, N, seed, stream=0, rho_assets=0.0, grid=GRID_F64,
+              n_threads=None):
+    """STAC-A2 path reduction: M of shape (N + 1, P), the largest of the
+    assets' values per path and date (models: a sequence of Heston)."""
+    arr = (Heston * len(models))(*models)
+    M = np.empty((N + 1, P), dtype=np.float64)
+    rc = lib().orc_multi_max(arr, len(models), T, scheme, grid, rho_assets, P, N, seed, stream,
+                             _ptr(M, ctypes.c_double), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("orc_multi_max rejected its arguments (%d)" % rc)
+    return M
+
+
+def asset_path(model: Heston, asset, T, scheme, path, N, seed, stream=0, rho_assets=0.0,
+               grid=GRID_F64):
+    """S of one asset of one multi-asset path, length N + 1."""
+    S = np.empty(N + 1, dtype=np.float64)
+    rc = lib().orc_asset_path(ctypes.byref(model), asset, T, scheme, grid, rho_assets, path, N,
+                              seed, stream, _ptr(S, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("orc_asset_path rejected its arguments (%d)" % rc)
+    return S
 
 
 def path_one(model: Heston, T, scheme, path, N, seed, stream=0, grid=GRID_F64):

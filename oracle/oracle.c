@@ -100,7 +100,12 @@ double orc_norm_inv(double u) {
  * U_V feeds both branches of the QE variance step; Z_X drives the log price. */
 void orc_draws(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
                int grid, double out[3]) {
-  uint32_t ctr[4] = {path, step, stream, 0u};
+  orc_draws_asset(seed, stream, path, step, 0u, grid, out);
+}
+
+void orc_draws_asset(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
+                     uint32_t asset, int grid, double out[3]) {
+  uint32_t ctr[4] = {path, step, stream, asset};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t w[4];
   orc_philox4x32_10(ctr, key, w);
@@ -303,6 +308,111 @@ int orc_paths(const orc_heston* m, double T, int scheme, int grid,
   orc_paths_ctx c = {m, T / (double)N, scheme, grid, P, N, stream, seed, S, V};
   uint32_t chunks = (P + ORC_CHUNK - 1) / ORC_CHUNK;
   orc_parallel_for(chunks, n_threads, orc_paths_chunk, &c);
+  return 0;
+}
+
+/* ---- STAC-A2 multi-asset path reduction (Sec. 2.2.1, Sec. 4.1) --------- */
+/* Each asset of a path follows its own Heston model with its own random     */
+/* inputs (two per path, asset and date); the Longstaff-Schwartz path        */
+/* reduction keeps, for every path and date, the largest asset value.        */
+
+/* common factor of the log-price shocks of path `path` at date `step` */
+static double orc_common_shock(uint64_t seed, uint32_t stream, uint32_t path,
+                               uint32_t step, int grid) {
+  uint32_t ctr[4] = {path, step, stream, 0xFFFFFFFFu};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t w[4];
+  orc_philox4x32_10(ctr, key, w);
+  const double u = grid == ORC_GRID_F32 ? orc_uniform_f32(w[2]) : orc_uniform_f64(w[2], w[3]);
+  return orc_norm_inv(u);
+}
+
+/* one date of one asset: x, v advanced in place, returns S */
+static double orc_asset_step(const orc_heston* m, double dt, int scheme, int grid,
+                             double rho_assets, uint64_t seed, uint32_t stream,
+                             uint32_t path, uint32_t n, uint32_t asset, double* x,
+                             double* v) {
+  double d[3];
+  orc_draws_asset(seed, stream, path, n, asset, grid, d);
+  double zX = d[2];
+  if (rho_assets > 0.0) {
+    const double zc = orc_common_shock(seed, stream, path, n, grid);
+    zX = sqrt(rho_assets) * zc + sqrt(1.0 - rho_assets) * d[2];
+  }
+  if (scheme == ORC_QE) {
+    double o[2];
+    orc_qe_step(m, dt, *x, *v, d[0], d[1], zX, o);
+    *x = o[0]; *v = o[1];
+  } else {
+    double o[3];
+    orc_ft_step(m, dt, *x, *v, d[1], zX, o);
+    *x = o[0]; *v = o[1];
+  }
+  return m->S0 * exp(*x);
+}
+
+typedef struct {
+  const orc_heston* models;
+  uint32_t A, P, N, stream;
+  double dt, rho;
+  int scheme, grid;
+  uint64_t seed;
+  double* M;
+} orc_multi_ctx;
+
+static void orc_multi_chunk(void* vctx, uint32_t chunk) {
+  const orc_multi_ctx* c = (const orc_multi_ctx*)vctx;
+  uint32_t p0 = chunk * ORC_CHUNK;
+  uint32_t p1 = p0 + ORC_CHUNK < c->P ? p0 + ORC_CHUNK : c->P;
+  double* x = (double*)malloc(sizeof(double) * c->A);
+  double* v = (double*)malloc(sizeof(double) * c->A);
+  for (uint32_t p = p0; p < p1; ++p) {
+    double m0 = c->models[0].S0;
+    for (uint32_t a = 0; a < c->A; ++a) {
+      x[a] = 0.0;
+      v[a] = c->models[a].v0;
+      if (c->models[a].S0 > m0) m0 = c->models[a].S0;
+    }
+    c->M[p] = m0;
+    for (uint32_t n = 0; n < c->N; ++n) {
+      double mx = 0.0;
+      for (uint32_t a = 0; a < c->A; ++a) {
+        const double S = orc_asset_step(&c->models[a], c->dt, c->scheme, c->grid, c->rho,
+                                        c->seed, c->stream, p, n, a, &x[a], &v[a]);
+        if (a == 0 || S > mx) mx = S;
+      }
+      c->M[(size_t)(n + 1) * c->P + p] = mx;
+    }
+  }
+  free(x);
+  free(v);
+}
+
+int orc_multi_max(const orc_heston* models, uint32_t A, double T, int scheme, int grid,
+                  double rho_assets, uint32_t P, uint32_t N, uint64_t seed,
+                  uint32_t stream, double* M, int n_threads) {
+  if (!models || !M || A == 0 || P == 0 || N == 0) return -1;
+  if (!(rho_assets >= 0.0 && rho_assets <= 1.0)) return -1;
+  if (grid != ORC_GRID_F64 && grid != ORC_GRID_F32) return -1;
+  for (uint32_t a = 0; a < A; ++a)
+    if (!orc_model_ok(&models[a], T, scheme)) return -1;
+  orc_multi_ctx c = {models, A, P, N, stream, T / (double)N, rho_assets, scheme, grid, seed, M};
+  uint32_t chunks = (P + ORC_CHUNK - 1) / ORC_CHUNK;
+  orc_parallel_for(chunks, n_threads, orc_multi_chunk, &c);
+  return 0;
+}
+
+int orc_asset_path(const orc_heston* m, uint32_t asset, double T, int scheme, int grid,
+                   double rho_assets, uint32_t path, uint32_t N, uint64_t seed,
+                   uint32_t stream, double* S) {
+  if (!m || !S || N == 0) return -1;
+  if (!(rho_assets >= 0.0 && rho_assets <= 1.0)) return -1;
+  if (!orc_model_ok(m, T, scheme)) return -1;
+  double x = 0.0, v = m->v0;
+  S[0] = m->S0;
+  for (uint32_t n = 0; n < N; ++n)
+    S[n + 1] = orc_asset_step(m, T / (double)N, scheme, grid, rho_assets, seed, stream, path,
+                              n, asset, &x, &v);
   return 0;
 }
 

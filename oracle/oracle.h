@@ -85,6 +85,11 @@ double orc_norm_inv(double u);
 void orc_draws(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
                int grid, double out[3]);
 
+/* orc_draws for asset `asset` of a multi-asset path: counter
+ * (path, step, stream, asset); orc_draws is asset 0. */
+void orc_draws_asset(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
+                     uint32_t asset, int grid, double out[3]);
+
 /* Andersen QE step: out = {x1, v1}. */
 void orc_qe_step(const orc_heston* m, double dt, double x, double v,
                  double uV, double zV, double zX, double out[2]);
@@ -101,6 +106,24 @@ int orc_paths(const orc_heston* m, double T, int scheme, int grid,
 int orc_path_one(const orc_heston* m, double T, int scheme, int grid,
                  uint32_t path, uint32_t N, uint64_t seed, uint32_t stream,
                  double* S, double* V);
+
+/* STAC-A2 path reduction (Sec. 2.2.1, Sec. 4.1): A Heston assets per path,
+ * asset a with model models[a]; M[n*P + p] = max over assets of S_a at date
+ * n (n = 0..N).  Element (path, asset, date) draws from Philox counter
+ * (path, date, stream, asset).  With rho_assets > 0 the log-price shocks of
+ * the assets share one factor (equicorrelation rho_assets):
+ * Z_X,a <- sqrt(rho_assets) Z_c + sqrt(1 - rho_assets) Z_X,a, with Z_c the
+ * quantile of the words (2, 3) grid point of counter
+ * (path, date, stream, 0xFFFFFFFF).  rho_assets = 0: independent assets,
+ * two random numbers per element as in the paper.  Returns 0 or < 0. */
+int orc_multi_max(const orc_heston* models, uint32_t A, double T, int scheme, int grid,
+                  double rho_assets, uint32_t P, uint32_t N, uint64_t seed,
+                  uint32_t stream, double* M, int n_threads);
+/* The path of one asset of one multi-asset path (same arithmetic as
+ * orc_multi_max): S[n] for n = 0..N. */
+int orc_asset_path(const orc_heston* m, uint32_t asset, double T, int scheme, int grid,
+                   double rho_assets, uint32_t path, uint32_t N, uint64_t seed,
+                   uint32_t stream, double* S);
 
 /* Longstaff-Schwartz backward induction over given paths.
  * out = {price, price_se, european_price, continuation}.
