@@ -280,6 +280,48 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             "precision": precision, "graph": True, "autotuned_shape_sub_ppt": subs}
 
 
+# The paper's STAC-A2 runtimes (Table A1, Alveo U280 multi-kernel, total
+# runtime including transfers and host reordering; and the 2 x 24-core Xeon
+# CPU reference, Table 2), milliseconds: context for the path reduction, not
+# the same measurement.
+PAPER_STAC_MS = {"fpga_fp64": [75.97, 141.39, 592.79, 1971.64, 10644.86],
+                 "fpga_fp32": [46.11, 82.01, 341.82, 1178.14, 5838.23],
+                 "cpu_fp64": [369.07, 638.67, 1551.90, 4558.11, 15561.09]}
+
+
+def measure_stac(api, L, torch, reps=3):
+    """STAC-A2 path reduction (Heston QE paths of every asset, exp, max over
+    assets per path and date) at the paper's five problem sizes, 25,000
+    paths, in FP64, float pairs and FP32: device time per run (CUDA events),
+    elements (path x asset x date) per second."""
+    out = {}
+    stream = torch.cuda.Stream()
+    for i, (name, (A, N)) in enumerate(workloads.STAC_SIZES.items()):
+        P = workloads.STAC_PATHS
+        models = [L.lsmc_heston(**m) for m in workloads.stac_models(A)]
+        row = {"assets": A, "dates": N, "paths": P, "elements": A * N * P}
+        for prec, tag, dt, width in ((L.LSMC_FP64, "fp64", torch.float64, 1),
+                                     (L.LSMC_DF, "df", torch.float32, 2),
+                                     (L.LSMC_MIXED, "fp32", torch.float32, 1)):
+            M = torch.empty((N + 1) * P * width, dtype=dt, device="cuda")
+            with torch.cuda.stream(stream):
+                L.lsmc_multi_asset_max(models, N / 252.0, L.LSMC_SCHEME_QE, prec, 0.0, P, N,
+                                       2022, 0, M.data_ptr(), stream.cuda_stream)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    L.lsmc_multi_asset_max(models, N / 252.0, L.LSMC_SCHEME_QE, prec, 0.0, P, N,
+                                           2022, 0, M.data_ptr(), stream.cuda_stream)
+                e1.record(stream)
+            stream.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[tag] = {"ms": ms, "elements_per_s": A * N * P / (ms / 1e3)}
+            del M
+        row["paper_context_ms"] = {k: v[i] for k, v in PAPER_STAC_MS.items()}
+        out[name] = row
+    return out
+
+
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
                     precision="mixed", max_inflight=16):
     """Poisson stream of book-distributed requests with continuous batching
@@ -430,6 +472,7 @@ def main():
                 ("book", lambda *a: {"df": measure_book(*a, precision="df"),
                                      "mixed": measure_book(*a, precision="mixed"),
                                      "fp64": measure_book(*a, precision="fp64")}),
+                ("stac_a2_path_reduction", lambda *a: measure_stac(*a)),
                 ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
                                         "mixed": measure_serving(*a, precision="mixed",
                                                                  max_inflight=4)}))

@@ -260,6 +260,23 @@ int lsmc_paths(const lsmc_heston* model, double T, int32_t scheme,
                int32_t precision, uint32_t n_paths, uint32_t n_steps,
                uint64_t seed, uint32_t stream_id, void* d_S, void* d_V,
                void* cuda_stream);
+/* STAC-A2 path reduction (Sec. 2.2.1 and Sec. 4.1: Heston QE paths of every
+ * asset, their exponential, and the Longstaff-Schwartz path reduction that
+ * keeps, for every path and date, the largest value held by any asset).
+ * models: host, n_assets (1..64) Heston models, one per asset; element
+ * (path, asset, date) draws from Philox counter (path, date, stream_id,
+ * asset) under key seed.  rho_assets in [0, 1]: equicorrelation of the
+ * assets' log-price shocks through one common factor per (path, date)
+ * (counter (path, date, stream_id, 0xFFFFFFFF)); 0 = independent assets,
+ * two random numbers per element as in the paper.  d_M (device): (n_steps
+ * + 1) x n_paths values of the precision (double, float, or float pairs hi,
+ * lo), row n = date n, row 0 = the largest S0.  Asynchronous on cuda_stream;
+ * LSMC_EINVAL before any launch for invalid arguments. */
+int lsmc_multi_asset_max(const lsmc_heston* models, uint32_t n_assets, double T,
+                         int32_t scheme, int32_t precision, double rho_assets,
+                         uint32_t n_paths, uint32_t n_steps, uint64_t seed,
+                         uint32_t stream_id, void* d_M, void* cuda_stream);
+
 /* Longstaff-Schwartz backward pass over given paths (same layout as
  * lsmc_paths output).  d_out (device, 5 doubles): price, price_se,
  * european_price, continuation value, near-tie decisions (see lsmc_result).  d_beta (device, optional):

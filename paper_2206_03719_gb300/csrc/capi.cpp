@@ -987,6 +987,36 @@ static int stage_plan(const lsmc_heston* m, double T, int32_t scheme, int32_t pr
   return LSMC_OK;
 }
 
+int lsmc_multi_asset_max(const lsmc_heston* models, uint32_t n_assets, double T, int32_t scheme,
+                         int32_t precision, double rho_assets, uint32_t n_paths, uint32_t n_steps,
+                         uint64_t seed, uint32_t stream_id, void* d_M, void* s) {
+  if (!models || !d_M || n_assets == 0 || n_assets > (uint32_t)kMaxAssets) return LSMC_EINVAL;
+  if (n_paths == 0 || n_steps == 0 || n_paths > (1u << 30) || n_steps > (1u << 20))
+    return LSMC_EINVAL;
+  if (!(rho_assets >= 0.0 && rho_assets <= 1.0)) return LSMC_EINVAL;
+  if ((uint64_t)n_paths * (n_steps + 1) >= (1ull << 40)) return LSMC_EINVAL;
+  MultiArgs a{};
+  for (uint32_t i = 0; i < n_assets; ++i) {
+    // the per-asset checks of a pricing request
+    const lsmc_contract cc{LSMC_PUT, LSMC_EUROPEAN, 1.0, T};
+    const lsmc_request q = default_request(&models[i], &cc, 1, 1, LSMC_BASIS_S2, nullptr, 0);
+    const int rc = validate_request(q, precision, scheme);
+    if (rc) return rc;
+    const lsmc_heston& m = models[i];
+    a.assets[i] = MultiModel{m.S0, m.r, m.q, m.v0, m.kappa, m.theta, m.xi, m.rho};
+  }
+  a.n_assets = n_assets;
+  a.P = n_paths;
+  a.N = n_steps;
+  a.stream_id = stream_id;
+  a.seed = seed;
+  a.T = T;
+  a.sqrt_rho = std::sqrt(rho_assets);
+  a.sqrt_1m_rho = std::sqrt(1.0 - rho_assets);
+  a.M = d_M;
+  return cuda_status(launch_multi_max(a, precision, scheme, (cudaStream_t)s));
+}
+
 int lsmc_paths(const lsmc_heston* m, double T, int32_t scheme, int32_t precision, uint32_t P,
                uint32_t N, uint64_t seed, uint32_t stream_id, void* d_S, void* d_V, void* s) {
   if (!m || !d_S || !d_V) return LSMC_EINVAL;

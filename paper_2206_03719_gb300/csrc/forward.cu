@@ -280,6 +280,113 @@ forward_kernel(FwdArgs a) {
   }
 }
 
+// ---- STAC-A2 multi-asset path reduction (Sec. 2.2.1, Sec. 4.1) ---------------
+// M[n][p] = max over assets of S_a[n][p].  Like the paper's loop interchange,
+// the assets are the outer loop of a thread (KA of them at a time, their
+// state in registers and their steps interleaved), the dates the inner
+// loop, and the running maximum lives in M itself (read, compared, written
+// back by the one thread that owns the path).  Element (path, asset, date)
+// draws from Philox counter (path, date, stream, asset); the common
+// log-price shock of (path, date), used when the assets are correlated,
+// from counter (path, date, stream, 0xFFFFFFFF).
+
+template <typename Real>
+__device__ __forceinline__ Real common_shock(uint4 w, const DfTables* t);
+template <>
+__device__ __forceinline__ double common_shock<double>(uint4 w, const DfTables*) {
+  return normcdfinv(uniform52(w.z, w.w));
+}
+template <>
+__device__ __forceinline__ float common_shock<float>(uint4 w, const DfTables*) {
+  return normcdfinvf(uniform23(w.z));
+}
+template <>
+__device__ __forceinline__ df common_shock<df>(uint4 w, const DfTables* t) {
+  return Draw<df>::quantile(w.z, w.w, t);
+}
+
+template <typename Real, int SCHEME, int KA>
+__global__ void __launch_bounds__(kFwdBlock)
+multi_max_kernel(MultiArgs a) {
+  __shared__ GroupConst<Real> gc[kMaxAssets];
+  constexpr bool kPair = std::is_same<Real, df>::value;
+  __shared__ __align__(16) unsigned char tab_raw[kPair ? sizeof(DfTables) : 16];
+  DfTables* tabs = reinterpret_cast<DfTables*>(tab_raw);
+  if constexpr (kPair) load_df_tables(tabs);
+  const double dt = a.T / (double)a.N;
+  for (uint32_t i = threadIdx.x; i < a.n_assets; i += blockDim.x) {
+    const MultiModel& m = a.assets[i];
+    FwdGroup g{};
+    g.v0 = m.v0; g.kappa = m.kappa; g.theta = m.theta; g.xi = m.xi; g.rho = m.rho;
+    g.r = m.r; g.q = m.q; g.dt = dt; g.out_scale = m.S0;
+    make_group_const<Real>(g, gc[i]);
+  }
+  __syncthreads();
+  const uint32_t p = blockIdx.x * kFwdBlock + threadIdx.x;
+  if (p >= a.P) return;
+  const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+  const bool corr = a.sqrt_rho > 0.0;
+  const Real sr = (Real)a.sqrt_rho, s1r = (Real)a.sqrt_1m_rho;
+  Real* M = (Real*)a.M;
+  const size_t P = a.P;
+
+  for (uint32_t a0 = 0; a0 < a.n_assets; a0 += KA) {
+    Real x[KA], v[KA];
+    Real m0 = (Real)0;
+#pragma unroll
+    for (int k = 0; k < KA; ++k) {
+      const uint32_t ai = a0 + k < a.n_assets ? a0 + k : a0;
+      x[k] = (Real)0;
+      v[k] = gc[ai].v0;
+      if (k == 0 || gc[ai].out_scale > m0) m0 = gc[ai].out_scale;
+    }
+    M[p] = a0 == 0 ? m0 : fmax(M[p], m0);
+    for (uint32_t n = 0; n < a.N; ++n) {
+      Real zc = (Real)0;
+      if (corr)
+        zc = common_shock<Real>(philox4x32_10(make_uint4(p, n, a.stream_id, 0xFFFFFFFFu), key),
+                                tabs);
+      Real mx = (Real)0;
+#pragma unroll
+      for (int k = 0; k < KA; ++k) {
+        if (a0 + k < a.n_assets) {
+          const GroupConst<Real>& c = gc[a0 + k];
+          const uint4 w = philox4x32_10(make_uint4(p, n, a.stream_id, a0 + k), key);
+          Real u, omu, zV, zX;
+          Draw<Real>::make(w, u, omu, zV, zX, tabs);
+          if (corr) zX = sr * zc + s1r * zX;
+          if (SCHEME == kSchemeQE) {
+            qe_step<Real>(c, x[k], v[k], omu, zV, zX, tabs);
+          } else {
+            ft_step<Real>(c, x[k], v[k], zV, zX);
+          }
+          const Real S = c.out_scale * Fm<Real>::exp_(x[k], tabs);
+          mx = k == 0 ? S : fmax(mx, S);
+        }
+      }
+      const size_t off = (size_t)(n + 1) * P + p;
+      M[off] = a0 == 0 ? mx : fmax(M[off], mx);
+    }
+  }
+}
+
+template <typename Real>
+static void launch_multi_t(const MultiArgs& a, int scheme, cudaStream_t s) {
+  const unsigned blocks = (a.P + kFwdBlock - 1) / kFwdBlock;
+  if (scheme == kSchemeQE)
+    multi_max_kernel<Real, kSchemeQE, 4><<<blocks, kFwdBlock, 0, s>>>(a);
+  else
+    multi_max_kernel<Real, kSchemeFT, 4><<<blocks, kFwdBlock, 0, s>>>(a);
+}
+
+cudaError_t launch_multi_max(const MultiArgs& a, int precision, int scheme, cudaStream_t s) {
+  if (a.P == 0 || a.N == 0 || a.n_assets == 0) return cudaSuccess;
+  if (precision == kPrecFP64) launch_multi_t<double>(a, scheme, s);
+  else if (precision == kPrecDF) launch_multi_t<df>(a, scheme, s);
+  else launch_multi_t<float>(a, scheme, s);
+  return cudaGetLastError();
+}
+
 __global__ void philox_kernel(const uint4* __restrict__ ctr, uint2 key,
                               uint4* __restrict__ out, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -65,6 +65,20 @@ struct FwdArgs {
   uint32_t n_blocks;
 };
 
+// ---- STAC-A2 multi-asset path reduction --------------------------------------
+constexpr int kMaxAssets = 64;
+struct MultiModel {       // one asset's Heston model
+  double S0, r, q, v0, kappa, theta, xi, rho;
+};
+struct MultiArgs {        // passed by value (about 4 KB of kernel parameters)
+  MultiModel assets[kMaxAssets];
+  uint32_t n_assets, P, N, stream_id;
+  uint64_t seed;
+  double T;
+  double sqrt_rho, sqrt_1m_rho;  // loadings of the common shock (0, 1: independent)
+  void* M;                       // (N + 1) x P values of the working precision
+};
+
 // ---- backward -------------------------------------------------------------
 struct BwdInstance {
   const void* E;      // group rows 1..N (exp(x) scaled by the group's out_scale)

@@ -32,7 +32,8 @@ EXPORTS = [
     "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
     "lsmc_plan_set_timing", "lsmc_plan_kernel_times", "lsmc_autotune",
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
-    "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_backward", "lsmc_backward_noalloc",
+    "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
+    "lsmc_backward_noalloc",
 ]
 
 
@@ -143,6 +144,8 @@ def load(build_if_missing: bool = False):
             "lsmc_ticket_times": ([vp, u64, P(dbl), P(dbl), P(dbl)], ctypes.c_int),
             "lsmc_philox": ([vp, u32, u32, vp, sz, vp], ctypes.c_int),
             "lsmc_draws": ([u64, u32, vp, vp, sz, i32, vp, vp], ctypes.c_int),
+            "lsmc_multi_asset_max": ([P(lsmc_heston), u32, dbl, i32, i32, dbl, u32, u32, u64,
+                                      u32, vp, vp], ctypes.c_int),
             "lsmc_paths": ([P(lsmc_heston), dbl, i32, i32, u32, u32, u64, u32, vp, vp, vp],
                            ctypes.c_int),
             "lsmc_backward": ([vp, vp, u32, u32, i32, P(lsmc_heston), P(lsmc_contract), i32,
@@ -320,6 +323,15 @@ def lsmc_paths(model, T, scheme, precision, n_paths, n_steps, seed, stream_id, d
                stream=None):
     return check(load().lsmc_paths(ctypes.byref(model), T, scheme, precision, n_paths, n_steps,
                                    seed, stream_id, d_S, d_V, stream), "lsmc_paths")
+
+
+def lsmc_multi_asset_max(models, T, scheme, precision, rho_assets, n_paths, n_steps, seed,
+                         stream_id, d_M, stream=None):
+    """STAC-A2 path reduction into device memory d_M ((n_steps + 1) x n_paths)."""
+    arr = (lsmc_heston * len(models))(*models)
+    return check(load().lsmc_multi_asset_max(arr, len(models), T, scheme, precision, rho_assets,
+                                             n_paths, n_steps, seed, stream_id, d_M, stream),
+                 "lsmc_multi_asset_max")
 
 
 def lsmc_backward(d_S, d_V, n_paths, n_steps, precision, model, contract, basis, d_out,

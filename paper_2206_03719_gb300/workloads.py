@@ -141,3 +141,24 @@ def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int = 7,
             break
         out.append(t)
     return np.asarray(out)
+
+
+# ---- STAC-A2 path reduction: the paper's problem sizes (Table 1) ------------
+# (assets, daily dates) at 25,000 paths; one trading day per date, so the
+# horizon is dates / 252 years.
+STAC_SIZES = {"tiny": (5, 126), "small": (10, 126), "medium": (20, 252),
+              "large": (30, 504), "huge": (50, 1260)}
+STAC_PATHS = 25_000
+
+
+def stac_models(n_assets: int, seed: int = 2022):
+    """Heston models of the assets of a STAC-A2 path reduction (the paper's
+    per-asset configurations are not published): drawn with numpy PCG64 --
+    S0 ~ U[80, 120], q ~ U[0, 0.03], v0 ~ U[0.01, 0.09], kappa ~ U[0.5, 3],
+    theta ~ U[0.02, 0.09], xi ~ U[0.1, 0.8], rho ~ U[-0.9, -0.3], r = 0.02."""
+    rng = np.random.default_rng(seed)
+    return [dict(S0=float(rng.uniform(80, 120)), r=0.02, q=float(rng.uniform(0, 0.03)),
+                 v0=float(rng.uniform(0.01, 0.09)), kappa=float(rng.uniform(0.5, 3.0)),
+                 theta=float(rng.uniform(0.02, 0.09)), xi=float(rng.uniform(0.1, 0.8)),
+                 rho=float(rng.uniform(-0.9, -0.3)))
+            for _ in range(n_assets)]
