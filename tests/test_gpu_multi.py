@@ -106,3 +106,27 @@ def test_invalid_arguments(torch):
                                    L.LSMC_SCHEME_QE, L.LSMC_FP64, kw["rho_assets"], kw["P"],
                                    kw["N"], 1, 0, M.data_ptr())
         assert e.value.status == L.LSMC_EINVAL
+
+
+def test_longstaff_schwartz_on_the_reduced_path(torch):
+    # the curve fit of the reduced path (a best-of call) is the single-asset
+    # backward pass run on M, checked against the oracle's on the oracle's M
+    from gpu_common import parity_tol
+    models = _models(4, 11)
+    P, N, T, K = 4000, 24, 1.0, 105.0
+    Mo = oracle.multi_max([oracle.heston(**m) for m in models], T, oracle.QE, P, N, 5, 0)
+    S0 = float(Mo[0, 0])
+    model = dict(models[0], S0=S0, r=0.02)
+    dS = torch.from_numpy(Mo).cuda()
+    dV = torch.zeros_like(dS)
+    out = torch.zeros(5, dtype=torch.float64, device="cuda")
+    c = L.lsmc_contract(L.LSMC_CALL, L.LSMC_AMERICAN, K, T)
+    L.lsmc_backward(dS.data_ptr(), dV.data_ptr(), P, N, L.LSMC_FP64, L.lsmc_heston(**model), c,
+                    L.LSMC_BASIS_S2, out.data_ptr())
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    ref = oracle.lsmc(Mo, np.zeros_like(Mo), S0, K, T, 0.02, model["theta"], type_=oracle.CALL,
+                      style=oracle.AMERICAN, basis=oracle.BASIS_S2)
+    tol = parity_tol(got[4])
+    assert abs(got[0] - ref["price"]) <= tol * abs(ref["price"])
+    assert got[0] >= got[2] - 1e-12  # American >= European
