@@ -25,6 +25,7 @@
 //      normal equations by Cholesky in FP64 and publishes the coefficients.
 // Every wait is bounded in time; on expiry the kernel records an error code
 // and returns.
+#include <atomic>
 #include <cstdio>
 #include <type_traits>
 
@@ -345,6 +346,22 @@ __device__ __forceinline__ void accumulate_moments(Real* t, uint32_t& cnt, Real 
   }
 }
 
+// Per-warp buffers of the backward kernel (dynamic shared memory): S and v
+// of the in-the-money paths compacted for the exercise test; S, v and cash
+// flow of those compacted for the moment sums (room for a sub-tile plus the
+// fewer than 32 items carried from the previous one; the job-end reduction
+// reuses this space); the origins of the exercise items; the cash flows of
+// the sub-tile after the exercise test.
+template <typename Real, int PPT>
+struct BwdWarpBufs {
+  static constexpr int kCap = 32 * PPT;
+  Real xs[kCap];
+  Real xv[kCap];
+  Real m[3][kCap + 32];
+  Real zn[PPT][32];
+  unsigned short co[kCap];
+};
+
 // Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
 // current exercise time tau.  The regression target of date n, the cash flow
 // discounted to t_n, is Z exp(r n dt): the same factor for every path, so the
@@ -371,14 +388,13 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_chunk[NW][kNSum];
   __shared__ double s_sum[kNSum];
   __shared__ Real s_c[16];            // per-job constants, converted once
-  // per-warp compaction of in-the-money paths: the heavy arithmetic runs on
-  // dense lists instead of on lanes that are mostly out of the money
-  constexpr int CAP = 32 * PPT;
-  // per warp: S, v (basis SV2) and cash flow of the compacted paths; the
-  // job-end reduction reuses the same space
-  __shared__ Real s_cbuf[NW][3][CAP];
-  __shared__ unsigned short s_co[NW][CAP];  // origin k * 32 + lane (exercise)
-  __shared__ Real s_zn[NW][PPT][32];  // cash flows after the exercise test
+  // per-warp compaction of in-the-money paths (dynamic shared memory, one
+  // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
+  // of on lanes that are mostly out of the money
+  using Bufs = BwdWarpBufs<Real, PPT>;
+  constexpr int CAP = Bufs::kCap;
+  extern __shared__ __align__(16) unsigned char bwd_dyn[];
+  Bufs& wb = reinterpret_cast<Bufs*>(bwd_dyn)[threadIdx.x >> 5];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // single precision and float pairs reduce through float pairs; double
@@ -522,10 +538,13 @@ backward_kernel(BwdArgs a) {
     uint32_t ties = 0;
 
     const unsigned lane_lt = (1u << lane) - 1u;
-    Real* cs = s_cbuf[warp][0];
-    Real* cv = s_cbuf[warp][1];
-    Real* cy = s_cbuf[warp][2];
-    unsigned short* co = s_co[warp];
+    Real* cs = wb.xs;
+    Real* cv = wb.xv;
+    Real* ms = wb.m[0];
+    Real* mv = wb.m[1];
+    Real* my = wb.m[2];
+    int mcarry = 0;  // compacted moment items carried to the next sub-tile
+    unsigned short* co = wb.co;
     for (uint32_t sb = 0; sb < sub; ++sb) {
       const uint32_t sub_base = tile_base + sb * TILE0;
       if (sub_base >= P) break;  // uniform across the CTA
@@ -614,7 +633,7 @@ backward_kernel(BwdArgs a) {
               co[pos] = (unsigned short)(k * 32 + lane);
             }
             cnt += __popc(m);
-            s_zn[warp][k][lane] = z[k];
+            wb.zn[k][lane] = z[k];
           }
           __syncwarp();
           for (int j = lane; j < cnt; j += 32) {
@@ -638,13 +657,13 @@ backward_kernel(BwdArgs a) {
                 hz = fma(h, d1, h * d1lo);
               }
               const int o = co[j], kk = o >> 5, ll = o & 31;
-              s_zn[warp][kk][ll] = hz;
+              wb.zn[kk][ll] = hz;
               if (!final_job) Z[sub_base + warp * 32 + ll + kk * kBlock] = hz;
             }
           }
           __syncwarp();
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) z[k] = s_zn[warp][k][lane];
+          for (int k = 0; k < PPT; ++k) z[k] = wb.zn[k][lane];
           __syncwarp();
         }
       }
@@ -672,8 +691,10 @@ backward_kernel(BwdArgs a) {
         }
         acc.fold();
       } else {
-        // moment sums of date n over the in-the-money paths, compacted
-        int cnt = 0;
+        // moment sums of date n over the in-the-money paths, compacted; only
+        // whole warps of items are summed, the rest is carried to the next
+        // sub-tile (or summed at the end of the job), so the lanes stay busy
+        int cnt = mcarry;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
@@ -682,19 +703,40 @@ backward_kernel(BwdArgs a) {
           const unsigned m = __ballot_sync(0xffffffffu, itm);
           if (itm) {
             const int pos = cnt + __popc(m & lane_lt);
-            cs[pos] = S;
-            if (BASIS == kBasisSV2) cv[pos] = v0[k];
-            cy[pos] = z[k];
+            ms[pos] = S;
+            if (BASIS == kBasisSV2) mv[pos] = v0[k];
+            my[pos] = z[k];
           }
           cnt += __popc(m);
         }
         __syncwarp();
         Real* t = acc.target();
-        for (int j = lane; j < cnt; j += 32)
-          accumulate_moments<Real, BASIS, NM>(t, n_itm, cs[j], cv[j], cy[j], invK, invTh);
+        const int full = cnt & ~31;
+        for (int j = lane; j < full; j += 32)
+          accumulate_moments<Real, BASIS, NM>(t, n_itm, ms[j], mv[j], my[j], invK, invTh);
+        mcarry = cnt - full;
+        Real r0 = (Real)0, r1 = (Real)0, r2 = (Real)0;
+        if (lane < mcarry) {
+          r0 = ms[full + lane];
+          if (BASIS == kBasisSV2) r1 = mv[full + lane];
+          r2 = my[full + lane];
+        }
+        __syncwarp();
+        if (lane < mcarry) {
+          ms[lane] = r0;
+          if (BASIS == kBasisSV2) mv[lane] = r1;
+          my[lane] = r2;
+        }
         __syncwarp();
         acc.fold();
       }
+    }
+
+    if (kCompact && mcarry > 0) {  // the carried moment items of the last sub-tile
+      if (lane < mcarry)
+        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, ms[lane], mv[lane], my[lane],
+                                            invK, invTh);
+      __syncwarp();
     }
 
     // ---- block reduction into the tile partial --------------------------------
@@ -707,10 +749,10 @@ backward_kernel(BwdArgs a) {
       sy2 = warp_sum(sy2);
     } else {
       using RedT = typename std::conditional<kSingle, float2, double>::type;
-      // rows per pass: as many as the warp's compaction buffers hold
-      constexpr int RROWS = (int)((3 * CAP * sizeof(Real)) / (33 * sizeof(RedT)));
+      // rows per pass: as many as the warp's moment buffers hold
+      constexpr int RROWS = (int)(sizeof(wb.m) / (33 * sizeof(RedT)));
       static_assert(RROWS >= 1 && RROWS <= 32, "reduction rows per pass");
-      RedT(*red)[33] = reinterpret_cast<RedT(*)[33]>(cs);
+      RedT(*red)[33] = reinterpret_cast<RedT(*)[33]>(&wb.m[0][0]);
       __syncwarp();
 #pragma unroll
       for (int a0 = 0; a0 < NA; a0 += RROWS) {
@@ -896,9 +938,32 @@ cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <typename Real, int PPT>
+static size_t bwd_dyn_bytes() {
+  return (size_t)(kBlock / 32) * sizeof(BwdWarpBufs<Real, PPT>);
+}
+
+// dynamic shared memory above 48 KB needs the kernel's opt-in, once per device
+template <typename Real, int BASIS, int PPT>
+static cudaError_t bwd_prepare() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load() & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(backward_kernel<Real, BASIS, PPT>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)bwd_dyn_bytes<Real, PPT>());
+  if (e == cudaSuccess && bit) done.fetch_or(bit);
+  return e;
+}
+
 template <typename Real, int BASIS, int PPT>
 static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t s) {
-  backward_kernel<Real, BASIS, PPT><<<grid, kBlock, 0, s>>>(a);
+  const cudaError_t e = bwd_prepare<Real, BASIS, PPT>();
+  if (e != cudaSuccess) return e;
+  backward_kernel<Real, BASIS, PPT><<<grid, kBlock, bwd_dyn_bytes<Real, PPT>(), s>>>(a);
   return cudaGetLastError();
 }
 
@@ -932,8 +997,10 @@ cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt,
 template <typename Real, int BASIS, int PPT>
 static int occ_t() {
   int n = 0;
+  if (bwd_prepare<Real, BASIS, PPT>() != cudaSuccess) return 1;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<Real, BASIS, PPT>,
-                                                       kBlock, 0) == cudaSuccess ? n : 1;
+                                                       kBlock, bwd_dyn_bytes<Real, PPT>()) ==
+                 cudaSuccess ? n : 1;
 }
 
 template <typename Real, int PPT>
