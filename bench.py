@@ -68,6 +68,8 @@ def parse():
                     help="backward sub-tiles per job; 0 = pick by the autotuner")
     ap.add_argument("--ppt", type=int, default=0,
                     help="backward paths per lane with --sub (0 = the precision's default)")
+    ap.add_argument("--regenerate", action="store_true",
+                    help="no path store: regenerate segments from saved states")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -379,6 +381,8 @@ def main():
     wl = pick_workload(args.workload)
     if args.paths:
         wl = wl.replace(n_paths=args.paths, name=wl.name + "-paths%d" % args.paths)
+    if args.regenerate:
+        wl = wl.replace(regenerate=True, name=wl.name + "-regenerate")
     if args.impl == "reference":
         run_reference(args, wl)
         return

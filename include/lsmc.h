@@ -136,8 +136,18 @@ typedef struct lsmc_request {
   lsmc_bumps bumps;
   uint64_t seed;
   uint32_t stream_id;
-  uint32_t reserved;
+  uint32_t flags;          /* LSMC_FLAG_* (0: defaults) */
 } lsmc_request;
+
+/* lsmc_request.flags.  LSMC_FLAG_REGENERATE: keep no path store; the forward
+ * pass saves the state (x, v) of every path every ceil(sqrt(n_steps)) dates,
+ * and before each segment of the backward induction the segment's dates are
+ * simulated again from the saved state (the random inputs are counter-based,
+ * so the regenerated paths are the stored ones, bit for bit).  Device memory
+ * for the paths drops from n_steps rows to about 2 sqrt(n_steps); the
+ * forward work doubles.  All requests of a plan must agree on the flag and,
+ * with it, on n_steps. */
+enum { LSMC_FLAG_REGENERATE = 1 };
 
 typedef struct lsmc_ctx lsmc_ctx;
 typedef struct lsmc_plan lsmc_plan;

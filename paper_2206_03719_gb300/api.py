@@ -48,6 +48,7 @@ class Request:
                                mask, 0)
         r.seed = wl.seed
         r.stream_id = wl.stream
+        r.flags = L.LSMC_FLAG_REGENERATE if wl.regenerate else 0
         self.c = r
 
 

@@ -525,11 +525,14 @@ backward_kernel(BwdArgs a) {
     const Real s1 = s_c[6], d1 = s_c[7], sN = s_c[8], s0 = s_c[9];
     const Real K = s_c[10], invK = s_c[11], invTh = s_c[12];
     const Real d1lo = s_c[13], dNhi = s_c[14], dNlo = s_c[15];
-    const Real* EN = E + (size_t)(N - 1) * ld;
-    const Real* E1 = E + (size_t)n * ld;                        // date n + 1
-    const Real* V1 = BASIS == kBasisSV2 ? V + (size_t)n * ld : nullptr;
-    const Real* E0 = final_job ? nullptr : E + (size_t)(n - 1) * ld;  // date n
-    const Real* V0 = (BASIS == kBasisSV2 && !final_job) ? V + (size_t)(n - 1) * ld : nullptr;
+    // row of date d at index d - a.row0 (rows of dates 1..N, or one segment)
+    const ptrdiff_t r0 = (ptrdiff_t)a.row0;
+    const Real* EN = E + ((ptrdiff_t)N - r0) * (ptrdiff_t)ld;
+    const Real* E1 = E + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld;                    // date n + 1
+    const Real* V1 = BASIS == kBasisSV2 ? V + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld : nullptr;
+    const Real* E0 = final_job ? nullptr : E + ((ptrdiff_t)n - r0) * (ptrdiff_t)ld;  // date n
+    const Real* V0 = (BASIS == kBasisSV2 && !final_job)
+                         ? V + ((ptrdiff_t)n - r0) * (ptrdiff_t)ld : nullptr;
 
     Acc<Real, NA> acc;
     acc.zero();

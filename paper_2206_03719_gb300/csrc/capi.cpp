@@ -197,6 +197,8 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
       G.E = paths + L.group_E_off[g];
       G.V = L.group_V_off[g] == SIZE_MAX ? nullptr : paths + L.group_V_off[g];
       G.E_row0 = G.V_row0 = nullptr;
+      G.CX = L.group_CX_off[g] == SIZE_MAX ? nullptr : paths + L.group_CX_off[g];
+      G.CV = L.group_CV_off[g] == SIZE_MAX ? nullptr : paths + L.group_CV_off[g];
     }
   }
   for (size_t i = 0; i < L.inst.size(); ++i) {
@@ -231,6 +233,14 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->fa.groups = dG;
   p->fa.n_contracts = (uint32_t)L.contracts.size();
   p->fa.n_blocks = L.fwd_blocks;
+  p->fa.n0 = p->fa.n1 = 0;
+  p->fa.row0 = 1;
+  p->fa.ck_stride = L.opt.regen ? L.opt.ck_stride : 0;
+  p->fa.store_rows = 1;
+  p->fa.save_states = 0;
+  p->fa.next_job = nullptr;
+  p->fa.next_job_value = 0;
+  p->ba.row0 = 1;
   p->ba.inst = p->d_inst;
   p->ba.state = (BwdState*)p->d_state;
   p->ba.results = p->d_results;
@@ -296,6 +306,7 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
   o->precision = resolve(ctx, reqs[0].precision, dprec);
   o->scheme = resolve(ctx, reqs[0].scheme, dsch);
   o->basis = reqs[0].basis;
+  o->regen = (reqs[0].flags & LSMC_FLAG_REGENERATE) != 0;
   for (size_t i = 0; i < n; ++i) {
     const int prec = resolve(ctx, reqs[i].precision, dprec);
     const int sch = resolve(ctx, reqs[i].scheme, dsch);
@@ -303,6 +314,15 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
     if (rc) return rc;
     if (prec != o->precision || sch != o->scheme || reqs[i].basis != o->basis)
       return LSMC_ENOTIMPL;
+    // regenerate mode: one flag and one date grid for the whole plan
+    if (((reqs[i].flags & LSMC_FLAG_REGENERATE) != 0) != o->regen) return LSMC_ENOTIMPL;
+    if (o->regen && reqs[i].n_steps != reqs[0].n_steps) return LSMC_ENOTIMPL;
+  }
+  if (o->regen) {
+    const uint32_t N = reqs[0].n_steps;
+    uint32_t c = 1;
+    while ((uint64_t)c * c < N) ++c;
+    o->ck_stride = c;  // ceil(sqrt(N))
   }
   return LSMC_OK;
 }
@@ -385,12 +405,53 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
   LSMC_CUDA(mark(0));
   if (p->run_backward) LSMC_CUDA(launch_setup(p->d_inst, (uint32_t)p->L.inst.size(), p->stream));
   LSMC_CUDA(mark(1));
-  if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, prec, p->L.opt.scheme, p->stream));
-  LSMC_CUDA(mark(2));
-  if (p->run_backward)
-    LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, plan_ppt(p->L.opt), p->bwd_grid,
-                              p->stream));
-  LSMC_CUDA(mark(3));
+  if (p->L.opt.regen && p->run_forward && p->run_backward) {
+    // regenerate mode: one pass saving the states, then per segment of
+    // dates (last first) the segment's rows simulated again and the
+    // backward rounds whose dates lie in it; in the timing, the segments'
+    // simulation counts with the backward pass
+    FwdArgs f = p->fa;
+    f.store_rows = 0;
+    f.save_states = 1;
+    LSMC_CUDA(launch_forward(f, prec, p->L.opt.scheme, p->stream));
+    LSMC_CUDA(mark(2));
+    const uint32_t N = p->L.contracts.empty() ? 0 : p->L.contracts[0].N;
+    const uint32_t C = p->L.opt.ck_stride;
+    const int occ = occupancy(p->ctx, prec, p->L.opt.basis, plan_ppt(p->L.opt));
+    const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
+    for (int sgi = (int)p->L.n_segments - 1; sgi >= 0; --sgi) {
+      const uint32_t d0 = (uint32_t)sgi * C, d1 = std::min<uint32_t>(N, d0 + C);
+      // rounds r with regression date n = N - 1 - r in [d0, d1 - 1]
+      const uint32_t r_lo = N - d1, r_hi = N - 1 - d0;  // inclusive
+      const uint64_t nr = p->L.round_off.size() - 1;
+      const uint64_t j0 = p->L.round_off[std::min<uint64_t>(r_lo, nr)];
+      const uint64_t j1 = p->L.round_off[std::min<uint64_t>((uint64_t)r_hi + 1, nr)];
+      FwdArgs g = p->fa;
+      g.n0 = d0;
+      g.n1 = d1;
+      g.row0 = d0;
+      g.store_rows = 1;
+      g.save_states = 0;
+      g.next_job = &p->d_ctl->next_job;
+      g.next_job_value = j0;
+      LSMC_CUDA(launch_forward(g, prec, p->L.opt.scheme, p->stream));
+      if (j1 > j0) {
+        BwdArgs b = p->ba;
+        b.row0 = d0;
+        b.total_jobs = j1;
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, j1 - j0));
+        LSMC_CUDA(launch_backward(b, prec, p->L.opt.basis, plan_ppt(p->L.opt), grid, p->stream));
+      }
+    }
+    LSMC_CUDA(mark(3));
+  } else {
+    if (p->run_forward) LSMC_CUDA(launch_forward(p->fa, prec, p->L.opt.scheme, p->stream));
+    LSMC_CUDA(mark(2));
+    if (p->run_backward)
+      LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, plan_ppt(p->L.opt), p->bwd_grid,
+                                p->stream));
+    LSMC_CUDA(mark(3));
+  }
   if (p->run_greeks)
     LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out, p->stream));
   LSMC_CUDA(mark(4));

@@ -55,6 +55,8 @@ struct GroupConst {
   Real v0, out_scale;
   Real* E;
   Real* V;
+  Real* CX;
+  Real* CV;
   uint64_t ld;
 };
 
@@ -90,6 +92,8 @@ __device__ void make_group_const(const FwdGroup& g, GroupConst<Real>& c) {
   c.out_scale = (Real)g.out_scale;
   c.E = (Real*)g.E;
   c.V = (Real*)g.V;
+  c.CX = (Real*)g.CX;
+  c.CV = (Real*)g.CV;
   c.ld = g.ld;
 }
 
@@ -143,7 +147,10 @@ __device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
   v = v1;
 }
 
-template <typename Real, int SCHEME>
+// SEG: the launch covers dates (n0, n1] and may start from, or save, states
+// (regenerate mode); without it, the whole horizon from the initial state
+// into the full row store (the hot loop stays free of the segment logic).
+template <typename Real, int SCHEME, bool SEG>
 // register budgets: 128 per thread for double, 64 for float (eight CTAs of
 // 128 threads per SM), unconstrained for float pairs
 __global__ void __launch_bounds__(kFwdBlock, std::is_same<Real, double>::value ? 4 : (std::is_same<Real, float>::value ? 8 : 1))
@@ -169,10 +176,21 @@ forward_kernel(FwdArgs a) {
   if constexpr (kPair) load_df_tables(tabs);
   __syncthreads();
 
+  if (SEG && a.next_job && blockIdx.x == 0 && threadIdx.x == 0) *a.next_job = a.next_job_value;
   const uint32_t p = (blockIdx.x - sc.block0) * kFwdBlock + threadIdx.x;
   if (p >= sc.P) return;
   const int ng = (int)sc.n_groups;
   const uint2 key = make_uint2((uint32_t)sc.seed, (uint32_t)(sc.seed >> 32));
+  // dates (n0, n1] of this launch; the state at n0 is the initial one or a
+  // saved one; E/V row of date d at index d - row0
+  const uint32_t n0 = SEG ? a.n0 : 0u, n1 = SEG && a.n1 ? a.n1 : sc.N;
+  const uint32_t row0 = SEG ? a.row0 : 1u;
+  const bool store_rows = SEG ? a.store_rows != 0 : true;
+  const size_t ck_index = SEG && a.ck_stride && n0 ? (size_t)(n0 / a.ck_stride) : 0;
+  const bool first_row = SEG && store_rows && n0 >= row0;  // a segment: row of date n0 too
+  auto save_at = [&](uint32_t d) {  // save the state after date d?
+    return SEG && a.save_states && d % a.ck_stride == 0 && d < sc.N;
+  };
 
   for (int g = 0; g < ng; ++g) {
     const FwdGroup& gg = a.groups[sc.group0 + g];
@@ -201,8 +219,24 @@ forward_kernel(FwdArgs a) {
       rowV[g] = c.V ? c.V + p : nullptr;
     }
     const size_t ld = gc[0].ld;  // one row stride for the groups of a contract
-    size_t off = 0;
-    for (uint32_t n = 0; n < sc.N; ++n, off += ld) {
+    if (ck_index) {
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g)
+        if (g < ng) {
+          x[g] = gc[g].CX[ck_index * ld + p];
+          v[g] = gc[g].CV[ck_index * ld + p];
+        }
+    }
+    if (first_row) {
+#pragma unroll
+      for (int g = 0; g < kMaxGroups; ++g)
+        if (g < ng) {
+          rowE[g][0] = os[g] * __expf(x[g]);
+          if (rowV[g]) rowV[g][0] = v[g];
+        }
+    }
+    size_t off = (size_t)(n0 + 1 - row0) * ld;
+    for (uint32_t n = n0; n < n1; ++n, off += ld) {
       const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
       float u, omu, zV, zX;
       Draw<float>::make(w, u, omu, zV, zX, tabs);
@@ -214,8 +248,14 @@ forward_kernel(FwdArgs a) {
                          zV, zX, tabs);
           x[g] = xg;
           v[g] = vg;
-          rowE[g][off] = os[g] * __expf(xg);
-          if (rowV[g]) rowV[g][off] = vg;
+          if (store_rows) {
+            rowE[g][off] = os[g] * __expf(xg);
+            if (rowV[g]) rowV[g][off] = vg;
+          }
+          if (save_at(n + 1)) {
+            gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p] = xg;
+            gc[g].CV[(size_t)((n + 1) / a.ck_stride) * ld + p] = vg;
+          }
         }
       }
     }
@@ -227,8 +267,17 @@ forward_kernel(FwdArgs a) {
     for (int g = 0; g < kMaxGroups; ++g) {
       x[g] = (Real)0;
       v[g] = g < ng ? gc[g].v0 : (Real)0;
+      if (ck_index && g < ng) {
+        x[g] = gc[g].CX[ck_index * gc[g].ld + p];
+        v[g] = gc[g].CV[ck_index * gc[g].ld + p];
+      }
+      if (first_row && g < ng) {
+        const GroupConst<Real>& c = gc[g];
+        c.E[p] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
+        if (c.V) c.V[p] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+      }
     }
-    for (uint32_t n = 0; n < sc.N; ++n) {
+    for (uint32_t n = n0; n < n1; ++n) {
       const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
       Real u, omu, zV, zX;
       Draw<Real>::make(w, u, omu, zV, zX, tabs);
@@ -241,9 +290,15 @@ forward_kernel(FwdArgs a) {
           } else {
             ft_step<Real>(c, x[g], v[g], zV, zX);
           }
-          const size_t off = (size_t)n * c.ld + p;
-          c.E[off] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
-          if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+          if (store_rows) {
+            const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
+            c.E[off] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
+            if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+          }
+          if (save_at(n + 1)) {
+            c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = x[g];
+            c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = v[g];
+          }
         }
       }
     }
@@ -254,10 +309,15 @@ forward_kernel(FwdArgs a) {
     __shared__ Real xs[kMaxGroups][kFwdBlock], vs[kMaxGroups][kFwdBlock];
     const int t = threadIdx.x;
     for (int g = 0; g < ng; ++g) {
-      xs[g][t] = (Real)0;
-      vs[g][t] = gc[g].v0;
+      const GroupConst<Real>& c = gc[g];
+      xs[g][t] = ck_index ? c.CX[ck_index * c.ld + p] : (Real)0;
+      vs[g][t] = ck_index ? c.CV[ck_index * c.ld + p] : c.v0;
+      if (first_row) {
+        c.E[p] = c.out_scale * Fm<Real>::exp_(xs[g][t], tabs);
+        if (c.V) c.V[p] = (SCHEME == kSchemeFT && vs[g][t] < (Real)0) ? (Real)0 : vs[g][t];
+      }
     }
-    for (uint32_t n = 0; n < sc.N; ++n) {
+    for (uint32_t n = n0; n < n1; ++n) {
       const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
       Real u, omu, zV, zX;
       Draw<Real>::make(w, u, omu, zV, zX, tabs);
@@ -272,9 +332,15 @@ forward_kernel(FwdArgs a) {
         }
         xs[g][t] = xg;
         vs[g][t] = vg;
-        const size_t off = (size_t)n * c.ld + p;
-        c.E[off] = c.out_scale * Fm<Real>::exp_(xg, tabs);
-        if (c.V) c.V[off] = (SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg;
+        if (store_rows) {
+          const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
+          c.E[off] = c.out_scale * Fm<Real>::exp_(xg, tabs);
+          if (c.V) c.V[off] = (SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg;
+        }
+        if (save_at(n + 1)) {
+          c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = xg;
+          c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = vg;
+        }
       }
     }
   }
@@ -417,10 +483,15 @@ __global__ void draws_kernel(uint2 key, uint32_t stream_id,
 
 template <typename Real>
 static void launch_forward_t(const FwdArgs& a, int scheme, cudaStream_t s) {
-  if (scheme == kSchemeQE)
-    forward_kernel<Real, kSchemeQE><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
-  else
-    forward_kernel<Real, kSchemeFT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+  const bool seg = a.n0 != 0 || a.n1 != 0 || a.row0 != 1 || !a.store_rows || a.save_states ||
+                   a.next_job;
+  if (scheme == kSchemeQE) {
+    if (seg) forward_kernel<Real, kSchemeQE, true><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    else forward_kernel<Real, kSchemeQE, false><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+  } else {
+    if (seg) forward_kernel<Real, kSchemeFT, true><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    else forward_kernel<Real, kSchemeFT, false><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+  }
 }
 
 cudaError_t launch_forward(const FwdArgs& a, int precision, int scheme, cudaStream_t s) {

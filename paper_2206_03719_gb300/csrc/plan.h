@@ -43,10 +43,12 @@ enum : uint32_t { kDevErrTimeout = 1, kDevErrBadJob = 2 };
 struct FwdGroup {
   double v0, kappa, theta, xi, rho, r, q, dt;
   double out_scale;   // E row value = out_scale * exp(x)
-  void* E;            // rows 1..N at index n-1, ld elements apart
-  void* V;            // rows 1..N (nullptr: not stored)
+  void* E;            // rows of dates row0.., ld elements apart (FwdArgs::row0)
+  void* V;            // the same for v (nullptr: not stored)
   void* E_row0;       // optional row 0 (= out_scale)
   void* V_row0;       // optional row 0 (= v0)
+  void* CX;           // regenerate mode: saved x at dates k ck_stride (index k)
+  void* CV;           // regenerate mode: saved v (raw) at the same dates
   uint64_t ld;
 };
 
@@ -63,6 +65,15 @@ struct FwdArgs {
   const FwdGroup* groups;
   uint32_t n_contracts;
   uint32_t n_blocks;
+  // dates simulated: (n0, n1] from the state at n0 (n0 = 0: the initial
+  // state, else the saved state at n0); n1 = 0 means each contract's N
+  uint32_t n0, n1;
+  uint32_t row0;        // date of E/V row index 0 (1: rows of dates 1..N)
+  uint32_t ck_stride;   // regenerate mode: dates between saved states (else 0)
+  int32_t store_rows;   // write the E/V rows
+  int32_t save_states;  // save the state at every date k ck_stride < N
+  unsigned long long* next_job;  // if set, block 0 stores next_job_value there
+  unsigned long long next_job_value;
 };
 
 // ---- STAC-A2 multi-asset path reduction --------------------------------------
@@ -134,6 +145,7 @@ struct BwdArgs {
   unsigned long long total_jobs;
   unsigned long long timeout_ns;
   uint32_t n_rounds, n_inst;
+  uint32_t row0;             // date of E/V row index 0 of the instances' rows
 };
 
 // ---- Greeks ---------------------------------------------------------------

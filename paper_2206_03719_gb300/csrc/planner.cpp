@@ -97,6 +97,7 @@ int validate_request(const lsmc_request& q, int precision, int scheme) {
   if (q.type != LSMC_PUT && q.type != LSMC_CALL) return LSMC_EINVAL;
   if (q.style != LSMC_AMERICAN && q.style != LSMC_EUROPEAN) return LSMC_EINVAL;
   if (q.basis != LSMC_BASIS_S2 && q.basis != LSMC_BASIS_SV2) return LSMC_EINVAL;
+  if (q.flags & ~(uint32_t)LSMC_FLAG_REGENERATE) return LSMC_EINVAL;
   if (q.n_paths == 0 || q.n_steps == 0 || q.n_strikes == 0 || !q.strikes) return LSMC_EINVAL;
   if (q.n_paths > (1u << 30) || q.n_steps > (1u << 20) || q.n_strikes > 4096) return LSMC_EINVAL;
   for (uint32_t k = 0; k < q.n_strikes; ++k)
@@ -220,14 +221,28 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         G.dt = sc[s].T / (double)N;
         G.out_scale = opt.raw_paths ? m.S0 : 1.0;
         G.ld = ld;
-        G.E = G.V = G.E_row0 = G.V_row0 = nullptr;
+        G.E = G.V = G.E_row0 = G.V_row0 = G.CX = G.CV = nullptr;
+        // rows of the store: dates 1..N, or in regenerate mode one segment
+        // of dates c..c + ck_stride (ck_stride + 1 rows)
+        const size_t rows = opt.regen ? (size_t)opt.ck_stride + 1 : (size_t)N;
         L->group_E_off.push_back(off_paths);
-        off_paths += round_up((size_t)N * ld * real, 256);
+        off_paths += round_up(rows * ld * real, 256);
         if (store_v) {
           L->group_V_off.push_back(off_paths);
-          off_paths += round_up((size_t)N * ld * real, 256);
+          off_paths += round_up(rows * ld * real, 256);
         } else {
           L->group_V_off.push_back(SIZE_MAX);
+        }
+        if (opt.regen) {
+          // saved states x, v at dates k ck_stride, k = 0..n_segments-1
+          const size_t segs = (N + opt.ck_stride - 1) / opt.ck_stride;
+          L->group_CX_off.push_back(off_paths);
+          off_paths += round_up(segs * ld * real, 256);
+          L->group_CV_off.push_back(off_paths);
+          off_paths += round_up(segs * ld * real, 256);
+        } else {
+          L->group_CX_off.push_back(SIZE_MAX);
+          L->group_CV_off.push_back(SIZE_MAX);
         }
         found = (int)gT.size();
         gT.push_back(sc[s].T);
@@ -329,6 +344,8 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
   L->total_jobs = L->round_off[R];
 
   L->bytes_paths = off_paths;
+  if (opt.regen && n > 0)
+    L->n_segments = (reqs[0].n_steps + opt.ck_stride - 1) / opt.ck_stride;
   L->bytes_y = off_y;
   L->bytes_partial = off_partial;
   L->bytes_scale = off_scale;

@@ -56,6 +56,10 @@ struct PlanOptions {
   uint32_t sub = 1;             // sub-tiles per backward job
   std::vector<uint32_t> sub_req; // per request (if not empty: overrides sub)
   uint32_t ppt = 0;             // paths per thread of a sub-tile (0: the precision's default)
+  // regenerate mode: no path store; states saved every ck_stride dates and
+  // each segment of ck_stride dates simulated again before its backward rounds
+  bool regen = false;
+  uint32_t ck_stride = 0;
 };
 
 // Paths per lane of a plan's backward sub-tiles.
@@ -81,6 +85,9 @@ struct PlanLayout {
   // region offsets (bytes) of each group's E and V rows (V: SIZE_MAX if not
   // stored) and of each sorted instance's Y, partials and scale table
   std::vector<size_t> group_E_off, group_V_off;
+  // regenerate mode: each group's saved states (x and v at dates k ck_stride)
+  std::vector<size_t> group_CX_off, group_CV_off;
+  uint32_t n_segments = 0;                // regenerate mode: segments of dates
   struct InstOff { size_t y, partial, scale; uint32_t group; };
   std::vector<InstOff> inst_off;
   uint32_t n_results = 0;                 // BwdResult slots

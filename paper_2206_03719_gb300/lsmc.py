@@ -20,6 +20,7 @@ LSMC_PUT, LSMC_CALL = 0, 1
 LSMC_AMERICAN, LSMC_EUROPEAN = 0, 1
 LSMC_SCHEME_QE, LSMC_SCHEME_FT_EULER = 0, 1
 LSMC_BASIS_S2, LSMC_BASIS_SV2 = 0, 1
+LSMC_FLAG_REGENERATE = 1
 LSMC_FP64, LSMC_MIXED, LSMC_DF = 0, 1, 2
 LSMC_GREEK_DELTA, LSMC_GREEK_GAMMA, LSMC_GREEK_VEGA = 1, 2, 4
 LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31
@@ -80,7 +81,7 @@ class lsmc_request(ctypes.Structure):
                 ("n_steps", ctypes.c_uint32), ("basis", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("scheme", ctypes.c_int32),
                 ("bumps", lsmc_bumps), ("seed", ctypes.c_uint64),
-                ("stream_id", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("stream_id", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class lsmc_plan_info(ctypes.Structure):

@@ -48,6 +48,7 @@ class Workload:
     abs_dT: float = 1.0 / 252.0
     seed: int = 42
     stream: int = 0
+    regenerate: bool = False     # no path store: regenerate segments from checkpoints
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)
