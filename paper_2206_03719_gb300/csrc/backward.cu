@@ -60,11 +60,6 @@ template <typename R> __device__ __forceinline__ R qfma(R a, R b, R c) { return 
 template <> __device__ __forceinline__ df qfma<df>(df a, df b, df c) {
   return add_sloppy(mul_nr(a, b), c);
 }
-// in-the-money payoff: h > 0 (for pairs, the sign of the unevaluated sum)
-template <typename R> __device__ __forceinline__ bool positive(R h) { return h > (R)0; }
-template <> __device__ __forceinline__ bool positive<df>(df h) {
-  return h.hi > 0.0f || (h.hi == 0.0f && h.lo > 0.0f);
-}
 template <typename R> __device__ __forceinline__ R qsub(R a, R b) { return a - b; }
 template <> __device__ __forceinline__ df qsub<df>(df a, df b) { return add_sloppy(a, -b); }
 // payoff without the max: put K - S, call S - K
@@ -392,7 +387,6 @@ backward_kernel(BwdArgs a) {
   // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
   // of on lanes that are mostly out of the money
   using Bufs = BwdWarpBufs<Real, PPT>;
-  constexpr int CAP = Bufs::kCap;
   extern __shared__ __align__(16) unsigned char bwd_dyn[];
   Bufs& wb = reinterpret_cast<Bufs*>(bwd_dyn)[threadIdx.x >> 5];
 
