@@ -102,6 +102,13 @@ def lib():
                                      ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                      ctypes.c_uint32, dp]
+        L.orc_lsmc_oos.argtypes = [dp, dp, dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
+            [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + [dp, u32p]
+        L.orc_price_greeks_ex.argtypes = [
+            ctypes.POINTER(Heston), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+            dp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
+            ctypes.c_int, ctypes.c_int, ctypes.POINTER(Bumps), ctypes.c_uint64,
+            ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result), dp]
         L.orc_lsmc.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
             [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + \
             [dp, u32p, dp, ctypes.POINTER(ctypes.c_uint8)]
@@ -259,6 +266,21 @@ def lsmc(S, V, S0, K, T, r, theta, type_=PUT, style=AMERICAN, basis=BASIS_S2,
     return d
 
 
+def lsmc_oos(SA, VA, SB, VB, S0, K, T, r, theta, type_=PUT, style=AMERICAN, basis=BASIS_S2):
+    """Out-of-sample estimate: the policy of the regressions on (SA, VA)
+    applied to (SB, VB).  Returns a dict like lsmc."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (SA, VA, SB, VB)]
+    N, P = arrs[0].shape[0] - 1, arrs[0].shape[1]
+    out = (ctypes.c_double * 4)()
+    ns = ctypes.c_uint32(0)
+    rc = lib().orc_lsmc_oos(*[_ptr(a, ctypes.c_double) for a in arrs], P, N, S0, K, T, r,
+                            theta, type_, style, basis, out, ctypes.byref(ns))
+    if rc != 0:
+        raise ValueError("orc_lsmc_oos rejected its arguments (%d)" % rc)
+    return {"price": out[0], "price_se": out[1], "european_price": out[2],
+            "continuation": out[3], "n_singular": ns.value}
+
+
 def scenarios(model: Heston, T, b: Bumps):
     models = (Heston * 11)()
     Ts = (ctypes.c_double * 11)()
@@ -271,18 +293,21 @@ def scenarios(model: Heston, T, b: Bumps):
 
 def price_greeks(model: Heston, strikes, T, P, N, *, type_=PUT, style=AMERICAN,
                  scheme=QE, grid=GRID_F64, basis=BASIS_S2, b: Bumps | None = None,
-                 seed=42, stream=0, n_threads=None, want_scenarios=False):
-    """Price and Greeks for each strike (list of dicts)."""
+                 seed=42, stream=0, n_threads=None, want_scenarios=False,
+                 out_of_sample=False):
+    """Price and Greeks for each strike (list of dicts); out_of_sample: the
+    policy of the regressions on `stream` priced on stream ^ 0x80000000."""
     b = b or bumps()
     strikes = np.ascontiguousarray(strikes, dtype=np.float64).reshape(-1)
     nk = strikes.size
     res = (Result * nk)()
     scen = np.empty(11 * nk, dtype=np.float64)
-    rc = lib().orc_price_greeks(ctypes.byref(model), type_, style, T,
-                                _ptr(strikes, ctypes.c_double), nk, P, N, scheme,
-                                grid, basis, ctypes.byref(b), seed, stream,
-                                n_threads or default_threads(), res,
-                                _ptr(scen, ctypes.c_double))
+    rc = lib().orc_price_greeks_ex(ctypes.byref(model), type_, style, T,
+                                   _ptr(strikes, ctypes.c_double), nk, P, N, scheme,
+                                   grid, basis, ctypes.byref(b), seed, stream,
+                                   1 if out_of_sample else 0,
+                                   n_threads or default_threads(), res,
+                                   _ptr(scen, ctypes.c_double))
     if rc != 0:
         raise ValueError("orc_price_greeks rejected its arguments (%d)" % rc)
     out = [res[i].as_dict() for i in range(nk)]

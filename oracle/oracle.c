@@ -582,6 +582,68 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
   return 0;
 }
 
+/* ---- out-of-sample Longstaff-Schwartz ------------------------------------ */
+/* The exercise policy estimated by the regressions on one path set (A) is   */
+/* applied to an independent path set (B): a path of B stops at the first    */
+/* date n in 1..N-1 where it is in the money and its payoff beats the fitted */
+/* continuation value beta_n(A) . phi(S_n, v_n), else at N; the estimator is */
+/* the mean discounted cash flow (a low-biased price).  Discounting repeats  */
+/* the one-step factor as orc_lsmc does, so with B = A the result is the     */
+/* in-sample price exactly.                                                  */
+int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const double* VB,
+                 uint32_t P, uint32_t N, double S0, double K, double T, double r,
+                 double theta, int type, int style, int basis, double out[4],
+                 uint32_t* n_singular) {
+  if (!SA || !VA || !SB || !VB || !out || P == 0 || N == 0) return -1;
+  double* beta = (double*)malloc(sizeof(double) * (size_t)N * 6);
+  if (!beta) return -2;
+  double ins[4];
+  int rc = orc_lsmc(SA, VA, P, N, S0, K, T, r, theta, type, style, basis, ins, n_singular,
+                    beta, NULL);
+  if (rc) { free(beta); return rc; }
+  const double dt = T / (double)N;
+  const double D = exp(-r * dt);
+  const int B = basis == ORC_BASIS_SV2 ? 6 : 3;
+  double s = 0.0, s2 = 0.0, sum_h = 0.0;
+  for (uint32_t p = 0; p < P; ++p) {
+    const double hN = orc_payoff(type, K, SB[(size_t)N * P + p]);
+    sum_h += hN;
+    double y = hN;
+    uint32_t tau = N;
+    if (style == ORC_AMERICAN) {
+      for (uint32_t n = 1; n < N; ++n) {
+        if (isnan(beta[(size_t)n * 6])) continue;  /* no regression at n: no exercise */
+        const double sn = SB[(size_t)n * P + p];
+        const double h = orc_payoff(type, K, sn);
+        if (!(h > 0.0)) continue;
+        double phi[6];
+        orc_basis(basis, sn, VB[(size_t)n * P + p], K, theta, phi);
+        double cont = 0.0;
+        for (int i = 0; i < B; ++i) cont += beta[(size_t)n * 6 + i] * phi[i];
+        if (h > cont) { y = h; tau = n; break; }
+      }
+    }
+    /* discount from t_tau to t_0 one step at a time */
+    if (style == ORC_AMERICAN) {
+      for (uint32_t n = tau; n >= 2; --n) y *= D;
+      y *= D;
+    } else {
+      y *= exp(-r * T);
+    }
+    s += y;
+    s2 += y * y;
+  }
+  const double mean = s / (double)P;
+  const double var = P > 1 ? (s2 - (double)P * mean * mean) / (double)(P - 1) : 0.0;
+  const double h0 = orc_payoff(type, K, S0);
+  out[0] = style == ORC_AMERICAN && h0 > mean ? h0 : mean;
+  out[1] = var > 0.0 ? sqrt(var / (double)P) : 0.0;
+  out[2] = exp(-r * T) * (sum_h / (double)P);
+  out[3] = mean;
+  free(beta);
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Bump-and-revalue scenarios (the paper gives no Greek method; the Greeks  */
 /* are central finite differences under common random numbers: every       */
@@ -650,14 +712,17 @@ typedef struct {
   double* aux;       /* per strike: se, european */
   uint32_t* singular; /* per strike */
   int* rc;
+  const double *SB, *VB; /* out of sample: the pricing paths (else NULL) */
 } orc_bwd_ctx;
 
 static void orc_bwd_strike(void* vctx, uint32_t k) {
   orc_bwd_ctx* c = (orc_bwd_ctx*)vctx;
   double out[4];
   uint32_t ns = 0;
-  int rc = orc_lsmc(c->S, c->V, c->P, c->N, c->S0, c->strikes[k], c->T, c->r,
-                    c->theta, c->type, c->style, c->basis, out, &ns, NULL, NULL);
+  int rc = c->SB ? orc_lsmc_oos(c->S, c->V, c->SB, c->VB, c->P, c->N, c->S0, c->strikes[k],
+                                c->T, c->r, c->theta, c->type, c->style, c->basis, out, &ns)
+                 : orc_lsmc(c->S, c->V, c->P, c->N, c->S0, c->strikes[k], c->T, c->r,
+                            c->theta, c->type, c->style, c->basis, out, &ns, NULL, NULL);
   c->rc[k] = rc;
   c->vals[k] = out[0];
   c->aux[2 * k] = out[1];
@@ -670,6 +735,16 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      uint32_t N, int scheme, int grid, int basis,
                      const orc_bumps* b, uint64_t seed, uint32_t stream,
                      int n_threads, orc_result* out, double* scen_prices) {
+  return orc_price_greeks_ex(m, type, style, T, strikes, n_strikes, P, N, scheme, grid, basis,
+                             b, seed, stream, 0, n_threads, out, scen_prices);
+}
+
+int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
+                        const double* strikes, uint32_t n_strikes, uint32_t P,
+                        uint32_t N, int scheme, int grid, int basis,
+                        const orc_bumps* b, uint64_t seed, uint32_t stream,
+                        int out_of_sample, int n_threads, orc_result* out,
+                        double* scen_prices) {
   if (!m || !strikes || !b || !out || n_strikes == 0 || P == 0 || N == 0)
     return -1;
   orc_heston models[ORC_SC_COUNT];
@@ -685,22 +760,31 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
   size_t cells = (size_t)(N + 1) * P;
   double* S = (double*)malloc(sizeof(double) * cells);
   double* V = (double*)malloc(sizeof(double) * cells);
+  /* out of sample: pricing paths from stream ^ 0x80000000 */
+  double* SB = out_of_sample ? (double*)malloc(sizeof(double) * cells) : NULL;
+  double* VB = out_of_sample ? (double*)malloc(sizeof(double) * cells) : NULL;
   double* vals = (double*)malloc(sizeof(double) * n_sc * n_strikes);
   double* aux = (double*)malloc(sizeof(double) * 2 * n_strikes);
   uint32_t* sing = (uint32_t*)calloc((size_t)n_sc * n_strikes, sizeof(uint32_t));
   int* rcs = (int*)malloc(sizeof(int) * n_strikes);
   double* base_aux = (double*)malloc(sizeof(double) * 2 * n_strikes);
   int rc = 0;
-  if (!S || !V || !vals || !aux || !sing || !rcs || !base_aux) { rc = -2; goto done; }
+  if (!S || !V || !vals || !aux || !sing || !rcs || !base_aux ||
+      (out_of_sample && (!SB || !VB))) { rc = -2; goto done; }
 
   for (int s = 0; s < n_sc && rc == 0; ++s) {
     rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream, S, V,
                    n_threads);
     if (rc) break;
+    if (out_of_sample) {
+      rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream ^ 0x80000000u, SB, VB,
+                     n_threads);
+      if (rc) break;
+    }
     orc_bwd_ctx c = {S, V, strikes, P, N, models[s].S0, Ts[s], models[s].r,
                      models[s].theta, type, style, basis,
                      vals + (size_t)s * n_strikes, aux,
-                     sing + (size_t)s * n_strikes, rcs};
+                     sing + (size_t)s * n_strikes, rcs, SB, VB};
     orc_parallel_for(n_strikes, n_threads, orc_bwd_strike, &c);
     for (uint32_t k = 0; k < n_strikes; ++k)
       if (rcs[k]) rc = rcs[k];
@@ -748,6 +832,7 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
   if (scen_prices) memcpy(scen_prices, vals, sizeof(double) * n_sc * n_strikes);
 done:
   free(S); free(V); free(vals); free(aux); free(sing); free(rcs); free(base_aux);
+  free(SB); free(VB);
   return rc;
 }
 

@@ -135,6 +135,16 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
              int style, int basis, double out[4], uint32_t* n_singular,
              double* beta, uint8_t* exercise);
 
+/* Out-of-sample Longstaff-Schwartz: the exercise policy of the regressions on
+ * paths (SA, VA) applied to the independent paths (SB, VB) of the same model
+ * (first date in 1..N-1 where an in-the-money path's payoff beats the fitted
+ * continuation value, else N).  out = {price, price_se, european price on
+ * B, mean discounted cash flow}.  With SB = SA, VB = VA it is orc_lsmc. */
+int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const double* VB,
+                 uint32_t P, uint32_t N, double S0, double K, double T, double r,
+                 double theta, int type, int style, int basis, double out[4],
+                 uint32_t* n_singular);
+
 /* Scenario table of a bump specification: fills up to ORC_SC_COUNT models,
  * maturities and kinds; returns the number of scenarios or a negative error. */
 int orc_scenarios(const orc_heston* m, double T, const orc_bumps* b,
@@ -147,6 +157,16 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      uint32_t N, int scheme, int grid, int basis,
                      const orc_bumps* b, uint64_t seed, uint32_t stream,
                      int n_threads, orc_result* out, double* scen_prices);
+
+/* orc_price_greeks with out_of_sample != 0: every scenario's price is the
+ * out-of-sample estimate, regressions on stream `stream`, pricing paths on
+ * stream `stream ^ 0x80000000`. */
+int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
+                        const double* strikes, uint32_t n_strikes, uint32_t P,
+                        uint32_t N, int scheme, int grid, int basis,
+                        const orc_bumps* b, uint64_t seed, uint32_t stream,
+                        int out_of_sample, int n_threads, orc_result* out,
+                        double* scen_prices);
 
 /* Array forms of the scalar functions above (plain loops). */
 void orc_philox_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out,
