@@ -70,6 +70,8 @@ def parse():
                     help="backward paths per lane with --sub (0 = the precision's default)")
     ap.add_argument("--regenerate", action="store_true",
                     help="no path store: regenerate segments from saved states")
+    ap.add_argument("--out-of-sample", action="store_true",
+                    help="price the regression policy on independent paths")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -247,6 +249,35 @@ def measure_precision(api, L, torch, wl, reps=3):
     return out
 
 
+def measure_variants(api, L, torch, reps=3):
+    """The paper-size book in regenerate mode (no path store) and out of
+    sample (policy priced on independent paths), FP64 and float pairs:
+    device time per step, device bytes, and the change against the default."""
+    out = {}
+    for prec in ("fp64", "df"):
+        base = workloads.PAPER_FP64.replace(precision=prec)
+        for tag, wl in (("default", base), ("regenerate", base.replace(regenerate=True)),
+                        ("out_of_sample", base.replace(out_of_sample=True))):
+            need = L.lsmc_request_footprint(None, api.Request(wl).c)
+            with api.Context(workspace_bytes=need + (256 << 20)) as ctx:
+                plan = ctx.plan([wl])
+                for _ in range(2):
+                    plan.launch()
+                plan.fetch()
+                plan.set_timing(True)
+                for _ in range(reps):
+                    plan.launch()
+                res = plan.fetch()
+                kms, n = plan.kernel_times()
+                info = plan.info()
+                plan.close()
+            ms = sum(kms) / max(1, n)
+            out["%s_%s" % (prec, tag)] = {"ms_per_step": ms, "greeks_per_s": wl.n_greeks / (ms / 1e3),
+                                          "device_bytes": int(info.device_bytes),
+                                          "price_k100": res[2]["price"], "price_se_k100": res[2]["price_se"]}
+    return out
+
+
 def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     """Uneven book (512 contracts, all bump scenarios, in the given precision)
     in launches of `chunk` contracts, each captured once in a CUDA
@@ -383,6 +414,8 @@ def main():
         wl = wl.replace(n_paths=args.paths, name=wl.name + "-paths%d" % args.paths)
     if args.regenerate:
         wl = wl.replace(regenerate=True, name=wl.name + "-regenerate")
+    if args.out_of_sample:
+        wl = wl.replace(out_of_sample=True, name=wl.name + "-out-of-sample")
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -477,6 +510,7 @@ def main():
                                      "mixed": measure_book(*a, precision="mixed"),
                                      "fp64": measure_book(*a, precision="fp64")}),
                 ("stac_a2_path_reduction", lambda *a: measure_stac(*a)),
+                ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
                 ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
                                         "mixed": measure_serving(*a, precision="mixed",
                                                                  max_inflight=4)}))

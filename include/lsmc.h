@@ -148,6 +148,16 @@ typedef struct lsmc_request {
  * forward work doubles.  All requests of a plan must agree on the flag and,
  * with it, on n_steps. */
 enum { LSMC_FLAG_REGENERATE = 1 };
+/* lsmc_request.flags.  LSMC_FLAG_OUT_OF_SAMPLE: out-of-sample
+ * Longstaff-Schwartz.  The regressions run on the paths of stream_id; the
+ * exercise policy they define is then applied to independent paths, the
+ * same simulation on stream stream_id ^ 0x80000000, each stopping at the
+ * first date where it is in the money and its discounted payoff beats the
+ * fitted continuation value.  Prices, and the Greeks made from them, are the
+ * means of those cash flows: low-biased estimates of the American values,
+ * free of the in-sample estimator's look-ahead.  Not combined with
+ * LSMC_FLAG_REGENERATE. */
+enum { LSMC_FLAG_OUT_OF_SAMPLE = 2 };
 
 typedef struct lsmc_ctx lsmc_ctx;
 typedef struct lsmc_plan lsmc_plan;

@@ -48,7 +48,8 @@ class Request:
                                mask, 0)
         r.seed = wl.seed
         r.stream_id = wl.stream
-        r.flags = L.LSMC_FLAG_REGENERATE if wl.regenerate else 0
+        r.flags = (L.LSMC_FLAG_REGENERATE if wl.regenerate else 0) | \
+            (L.LSMC_FLAG_OUT_OF_SAMPLE if wl.out_of_sample else 0)
         self.c = r
 
 

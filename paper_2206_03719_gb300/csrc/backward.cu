@@ -873,12 +873,135 @@ backward_kernel(BwdArgs a) {
             I.beta_hist[(size_t)n * 6 + i] =
                 ok ? (i < NB ? beta[i] * to_n : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
         }
+        if (I.beta_z) {  // the date's coefficients, kept for an out-of-sample pass
+          for (int i = 0; i < 6; ++i) I.beta_z[(size_t)n * 8 + i] = ok ? beta[i] : 0.0;
+          I.beta_z[(size_t)n * 8 + 6] = ok ? 1.0 : 0.0;
+        }
         __threadfence();
         st_release_gpu(&st->ready, r + 1);
       }
     }
     __syncthreads();
   }
+}
+
+// Out-of-sample pricing pass: the policy of the regressions (beta_z, one row
+// per date, cash flows discounted to t_0) applied to the paths now in the
+// instance's rows (the pricing paths).  A path stops at the first date
+// n = 1..N-1 where it is in the money and its discounted payoff beats the
+// fitted continuation value (the test of the backward pass, the same
+// arithmetic), else at N.  Per CTA: sums over kOosTile paths.
+template <typename Real, int BASIS>
+__global__ void __launch_bounds__(kBlock)
+oos_kernel(const BwdInstance* __restrict__ inst) {
+  constexpr int PPT = kOosTile / kBlock;
+  const BwdInstance& I = inst[blockIdx.y];
+  const uint32_t P = I.P, N = I.N;
+  const uint32_t base = blockIdx.x * kOosTile;
+  if (base >= P) return;  // the whole block
+  const Real* E = (const Real*)I.E;
+  const Real* V = (const Real*)I.V;
+  const size_t ld = I.ld;
+  const double* stab = I.scale_tab;
+  const double* dtab = I.scale_tab + N + 1;
+  const int type = I.type;
+  const bool american = I.style == kAmerican;
+  const Real K = (Real)I.K, invK = (Real)I.invK, invTh = (Real)I.inv_theta;
+  const double dN = dtab[N];
+  const Real dNhi = (Real)dN, dNlo = (Real)(dN - (double)(Real)dN);
+  double sz = 0.0, sz2 = 0.0, euro = 0.0;
+  uint32_t ties = 0;
+  for (int k = 0; k < PPT; ++k) {
+    const uint32_t p = base + k * kBlock + threadIdx.x;
+    if (p >= P) break;
+    bool stopped = false;
+    double z = 0.0;
+    if (american) {
+      for (uint32_t n = 1; n < N; ++n) {
+        const double* bz = I.beta_z + (size_t)n * 8;
+        if (__ldg(bz + 6) == 0.0) continue;  // no regression at n: no exercise
+        const Real S = (Real)__ldg(stab + n) * E[(size_t)(n - 1) * ld + p];
+        if (!in_money<Real>(type, K, S)) continue;
+        Real b[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) b[i] = (Real)__ldg(bz + i);
+        const double dn = __ldg(dtab + n);
+        const Real d1 = (Real)dn, d1lo = (Real)(dn - (double)(Real)dn);
+        const Real h = intrinsic<Real>(type, K, S);
+        const Real x = qfma(S, invK, (Real)-1);
+        Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+        if (BASIS == kBasisSV2) {
+          const Real w = qfma(V[(size_t)(n - 1) * ld + p], invTh, (Real)-1);
+          c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+        }
+        const Real hd = qmul(h, d1);
+        bool exercise, tie;
+        decide<Real>(hd, c, exercise, tie);
+        if (tie) ++ties;
+        if (exercise) {
+          Real hz;
+          if constexpr (std::is_same<Real, df>::value) hz = quick_two_sum(hd.hi, hd.lo);
+          else hz = fma(h, d1, h * d1lo);
+          z = (double)hz;
+          stopped = true;
+          break;
+        }
+      }
+    }
+    const Real SN = (Real)stab[N] * E[(size_t)(N - 1) * ld + p];
+    const Real hN = payoff<Real>(type, K, SN);
+    const double zN = (double)fma(hN, dNhi, hN * dNlo);
+    if (!stopped) z = zN;
+    sz += z;
+    sz2 += z * z;
+    euro += zN;
+  }
+  // fixed-order block sums
+  __shared__ double s_part[kBlock / 32][4];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  sz = warp_sum(sz);
+  sz2 = warp_sum(sz2);
+  euro = warp_sum(euro);
+  ties = __reduce_add_sync(0xffffffffu, ties);
+  if (lane == 0) {
+    s_part[warp][0] = sz;
+    s_part[warp][1] = sz2;
+    s_part[warp][2] = euro;
+    s_part[warp][3] = (double)ties;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double v = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) v += s_part[w][threadIdx.x];
+    I.oos_sum[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
+  }
+}
+
+// The out-of-sample estimator of every instance (one warp each): the tile
+// sums added in tile order, the result written as the pricing result.
+__global__ void oos_finish_kernel(const BwdInstance* __restrict__ inst, uint32_t n_inst,
+                                  const BwdState* __restrict__ state,
+                                  BwdResult* __restrict__ results) {
+  const uint32_t i = blockIdx.x;
+  if (i >= n_inst || threadIdx.x != 0) return;
+  const BwdInstance& I = inst[i];
+  const uint32_t tiles = (I.P + kOosTile - 1) / kOosTile;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (uint32_t t = 0; t < tiles; ++t)
+    for (int k = 0; k < 4; ++k) s[k] += I.oos_sum[(size_t)t * 4 + k];
+  const double Pd = (double)I.P;
+  const double mean = s[0] / Pd;
+  const double var = I.P > 1 ? (s[1] - Pd * mean * mean) / (Pd - 1.0) : 0.0;
+  BwdResult res;
+  res.cont = mean;
+  res.se = var > 0.0 ? sqrt(var / Pd) : 0.0;
+  res.euro = s[2] / Pd;
+  res.price = I.style == kEuropean ? mean : fmax(I.h0, mean);
+  res.itm = state[i].itm;
+  res.ties = state[i].ties + s[3];
+  res.singular = state[i].singular;
+  res.done = 1;
+  results[I.out_index] = res;
 }
 
 // Greeks of each (request, strike) by central differences of the scenario
@@ -1009,6 +1132,26 @@ int backward_occupancy(int precision, int basis, int ppt) {
   if (precision == kPrecFP64) return ppt == 2 ? occ_basis<double, 2>(basis) : occ_basis<double, 4>(basis);
   if (precision == kPrecDF) return ppt == 2 ? occ_basis<df, 2>(basis) : occ_basis<df, 4>(basis);
   return ppt == 4 ? occ_basis<float, 4>(basis) : occ_basis<float, 8>(basis);
+}
+
+cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
+                       const BwdState* state, BwdResult* results, int precision, int basis,
+                       cudaStream_t s) {
+  if (n_inst == 0 || max_paths == 0) return cudaSuccess;
+  const dim3 grid((max_paths + kOosTile - 1) / kOosTile, n_inst);
+  const bool sv2 = basis == kBasisSV2;
+  if (precision == kPrecFP64) {
+    if (sv2) oos_kernel<double, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
+    else oos_kernel<double, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
+  } else if (precision == kPrecDF) {
+    if (sv2) oos_kernel<df, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
+    else oos_kernel<df, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
+  } else {
+    if (sv2) oos_kernel<float, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
+    else oos_kernel<float, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
+  }
+  oos_finish_kernel<<<n_inst, 32, 0, s>>>(inst, n_inst, state, results);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,

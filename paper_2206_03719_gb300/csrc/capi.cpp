@@ -212,6 +212,8 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
     I.partial = (double*)(preg + o.partial);
     I.scale_tab = (double*)(sreg + o.scale);
     I.beta_hist = beta_hist;
+    I.beta_z = o.beta == SIZE_MAX ? nullptr : (double*)(sreg + o.beta);
+    I.oos_sum = o.oos_partial == SIZE_MAX ? nullptr : (double*)(sreg + o.oos_partial);
   }
   const FwdContract* dC = (const FwdContract*)put(L.contracts.data(), sizeof(FwdContract) * L.contracts.size());
   const FwdGroup* dG = (const FwdGroup*)put(L.groups.data(), sizeof(FwdGroup) * L.groups.size());
@@ -240,6 +242,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->fa.save_states = 0;
   p->fa.next_job = nullptr;
   p->fa.next_job_value = 0;
+  p->fa.stream_xor = 0;
   p->ba.row0 = 1;
   p->ba.inst = p->d_inst;
   p->ba.state = (BwdState*)p->d_state;
@@ -307,6 +310,8 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
   o->scheme = resolve(ctx, reqs[0].scheme, dsch);
   o->basis = reqs[0].basis;
   o->regen = (reqs[0].flags & LSMC_FLAG_REGENERATE) != 0;
+  o->oos = (reqs[0].flags & LSMC_FLAG_OUT_OF_SAMPLE) != 0;
+  if (o->regen && o->oos) return LSMC_ENOTIMPL;
   for (size_t i = 0; i < n; ++i) {
     const int prec = resolve(ctx, reqs[i].precision, dprec);
     const int sch = resolve(ctx, reqs[i].scheme, dsch);
@@ -316,6 +321,7 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
       return LSMC_ENOTIMPL;
     // regenerate mode: one flag and one date grid for the whole plan
     if (((reqs[i].flags & LSMC_FLAG_REGENERATE) != 0) != o->regen) return LSMC_ENOTIMPL;
+    if (((reqs[i].flags & LSMC_FLAG_OUT_OF_SAMPLE) != 0) != o->oos) return LSMC_ENOTIMPL;
     if (o->regen && reqs[i].n_steps != reqs[0].n_steps) return LSMC_ENOTIMPL;
   }
   if (o->regen) {
@@ -450,6 +456,17 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
     if (p->run_backward)
       LSMC_CUDA(launch_backward(p->ba, prec, p->L.opt.basis, plan_ppt(p->L.opt), p->bwd_grid,
                                 p->stream));
+    if (p->L.opt.oos && p->run_forward && p->run_backward) {
+      // out of sample: the pricing paths (stream ^ 0x80000000) over the
+      // regression paths' store, the policy applied to them, the estimator
+      FwdArgs f = p->fa;
+      f.stream_xor = 0x80000000u;
+      LSMC_CUDA(launch_forward(f, prec, p->L.opt.scheme, p->stream));
+      uint32_t max_p = 0;
+      for (const auto& c : p->L.contracts) max_p = std::max(max_p, c.P);
+      LSMC_CUDA(launch_oos(p->d_inst, (uint32_t)p->L.inst.size(), max_p, p->ba.state,
+                           p->d_results, prec, p->L.opt.basis, p->stream));
+    }
     LSMC_CUDA(mark(3));
   }
   if (p->run_greeks)

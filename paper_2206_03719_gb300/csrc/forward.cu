@@ -237,7 +237,7 @@ forward_kernel(FwdArgs a) {
     }
     size_t off = (size_t)(n0 + 1 - row0) * ld;
     for (uint32_t n = n0; n < n1; ++n, off += ld) {
-      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
       float u, omu, zV, zX;
       Draw<float>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll
@@ -278,7 +278,7 @@ forward_kernel(FwdArgs a) {
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
-      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
       Real u, omu, zV, zX;
       Draw<Real>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll
@@ -318,7 +318,7 @@ forward_kernel(FwdArgs a) {
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
-      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id, 0u), key);
+      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
       Real u, omu, zV, zX;
       Draw<Real>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll 1

@@ -18,6 +18,10 @@ cudaError_t launch_multi_max(const MultiArgs& a, int precision, int scheme, cuda
 cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt, int grid,
                             cudaStream_t s);
+// out-of-sample pricing pass over the instances' rows and its estimator
+cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
+                       const BwdState* state, BwdResult* results, int precision, int basis,
+                       cudaStream_t s);
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
                           DevResult* out, cudaStream_t s);
 // Paths per thread of a backward sub-tile (a sub-tile is kBlock * ppt

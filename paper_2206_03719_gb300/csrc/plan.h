@@ -14,6 +14,7 @@
 namespace lsmc {
 
 constexpr int kBlock = 256;      // threads per CTA of the backward pass
+constexpr int kOosTile = 1024;   // paths per CTA of the out-of-sample pricing pass
 constexpr int kFwdBlock = 128;   // threads (paths) per CTA of the forward pass
 constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
 constexpr int kNSum = 25;        // doubles per tile partial
@@ -74,6 +75,8 @@ struct FwdArgs {
   int32_t save_states;  // save the state at every date k ck_stride < N
   unsigned long long* next_job;  // if set, block 0 stores next_job_value there
   unsigned long long next_job_value;
+  uint32_t stream_xor;  // xored into every contract's stream id (pricing paths)
+  uint32_t pad2_;
 };
 
 // ---- STAC-A2 multi-asset path reduction --------------------------------------
@@ -109,6 +112,10 @@ struct BwdInstance {
   int32_t type, style, basis;
   uint32_t out_index; // result slot
   uint32_t sub;       // sub-tiles of kBlock * PPT paths per job (a tile)
+  double* beta_z;     // out of sample: N x 8, date n: 6 coefficients (cash flows
+                      // discounted to t_0), then 1 if the regression was solved
+  double* oos_sum;    // out of sample: per pricing tile of kOosTile paths: sum Z,
+                      // sum Z^2, European sum, near ties
 };
 
 struct BwdState {

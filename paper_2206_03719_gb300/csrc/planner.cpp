@@ -97,7 +97,7 @@ int validate_request(const lsmc_request& q, int precision, int scheme) {
   if (q.type != LSMC_PUT && q.type != LSMC_CALL) return LSMC_EINVAL;
   if (q.style != LSMC_AMERICAN && q.style != LSMC_EUROPEAN) return LSMC_EINVAL;
   if (q.basis != LSMC_BASIS_S2 && q.basis != LSMC_BASIS_SV2) return LSMC_EINVAL;
-  if (q.flags & ~(uint32_t)LSMC_FLAG_REGENERATE) return LSMC_EINVAL;
+  if (q.flags & ~(uint32_t)(LSMC_FLAG_REGENERATE | LSMC_FLAG_OUT_OF_SAMPLE)) return LSMC_EINVAL;
   if (q.n_paths == 0 || q.n_steps == 0 || q.n_strikes == 0 || !q.strikes) return LSMC_EINVAL;
   if (q.n_paths > (1u << 30) || q.n_steps > (1u << 20) || q.n_strikes > 4096) return LSMC_EINVAL;
   for (uint32_t k = 0; k < q.n_strikes; ++k)
@@ -290,6 +290,13 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         off_partial += round_up((size_t)tiles * kNSum * 8, 256);
         o.scale = off_scale;
         off_scale += round_up((size_t)2 * (N + 1) * 8, 256);
+        o.beta = SIZE_MAX;
+        if (opt.oos) {  // coefficients of every date, and the pricing pass's tile sums
+          o.beta = off_scale;
+          off_scale += round_up((size_t)N * 8 * 8, 256);
+          o.oos_partial = off_scale;
+          off_scale += round_up((size_t)((P + kOosTile - 1) / kOosTile) * 4 * 8, 256);
+        }
         I.Y = nullptr;
         I.partial = nullptr;
         I.scale_tab = nullptr;

@@ -60,6 +60,7 @@ struct PlanOptions {
   // each segment of ck_stride dates simulated again before its backward rounds
   bool regen = false;
   uint32_t ck_stride = 0;
+  bool oos = false;             // out-of-sample pricing pass
 };
 
 // Paths per lane of a plan's backward sub-tiles.
@@ -88,7 +89,9 @@ struct PlanLayout {
   // regenerate mode: each group's saved states (x and v at dates k ck_stride)
   std::vector<size_t> group_CX_off, group_CV_off;
   uint32_t n_segments = 0;                // regenerate mode: segments of dates
-  struct InstOff { size_t y, partial, scale; uint32_t group; };
+  // scale: the date tables; beta / oos_partial (out-of-sample mode, inside
+  // the same region): coefficients of every date, the pricing pass's sums
+  struct InstOff { size_t y, partial, scale, beta = SIZE_MAX, oos_partial = SIZE_MAX; uint32_t group; };
   std::vector<InstOff> inst_off;
   uint32_t n_results = 0;                 // BwdResult slots
   uint32_t fwd_blocks = 0;

@@ -49,6 +49,7 @@ class Workload:
     seed: int = 42
     stream: int = 0
     regenerate: bool = False     # no path store: regenerate segments from checkpoints
+    out_of_sample: bool = False  # price the regression policy on independent paths
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)
