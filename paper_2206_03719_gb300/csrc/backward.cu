@@ -31,88 +31,13 @@
 
 #include "device_common.cuh"
 #include "dfloat.cuh"
+#include "exercise.cuh"
 #include "kernels.h"
 #include "plan.h"
 
 namespace lsmc {
 
 namespace {
-
-__device__ __forceinline__ double payoff_d(int type, double K, double S) {
-  const double h = type == kPut ? K - S : S - K;
-  return h > 0.0 ? h : 0.0;
-}
-
-template <typename Real>
-__device__ __forceinline__ Real payoff(int type, Real K, Real S) {
-  const Real h = type == kPut ? K - S : S - K;
-  return h > (Real)0 ? h : (Real)0;
-}
-
-// Inner-loop arithmetic: plain operators for float and double, the cheaper
-// unnormalised forms for float pairs.
-template <typename R> __device__ __forceinline__ R qmul(R a, R b) { return a * b; }
-template <> __device__ __forceinline__ df qmul<df>(df a, df b) { return mul_nr(a, b); }
-template <typename R> __device__ __forceinline__ void qacc(R& s, R t) { s += t; }
-template <> __device__ __forceinline__ void qacc<df>(df& s, df t) { acc_pair(s, t); }
-// a * b + c
-template <typename R> __device__ __forceinline__ R qfma(R a, R b, R c) { return fma(a, b, c); }
-template <> __device__ __forceinline__ df qfma<df>(df a, df b, df c) {
-  return add_sloppy(mul_nr(a, b), c);
-}
-template <typename R> __device__ __forceinline__ R qsub(R a, R b) { return a - b; }
-template <> __device__ __forceinline__ df qsub<df>(df a, df b) { return add_sloppy(a, -b); }
-// payoff without the max: put K - S, call S - K
-template <typename R>
-__device__ __forceinline__ R intrinsic(int type, R K, R S) {
-  return type == kPut ? qsub(K, S) : qsub(S, K);
-}
-
-// In the money (payoff strictly positive) without forming the payoff: for
-// positive doubles the bit patterns order like the values, so the test runs
-// on the integer pipe instead of the narrow FP64 one.
-template <typename R>
-__device__ __forceinline__ bool in_money(int type, R K, R S) {
-  return type == kPut ? S < K : K < S;
-}
-template <>
-__device__ __forceinline__ bool in_money<double>(int type, double K, double S) {
-  const long long s = __double_as_longlong(S), k = __double_as_longlong(K);
-  return type == kPut ? s < k : k < s;
-}
-
-// Exercise decision (discounted payoff hd against fitted value c) and the
-// near-tie flag (|hd - c| within about 1e-10 of max(|c|, hd)).
-template <typename R>
-__device__ __forceinline__ void decide(R hd, R c, bool& exercise, bool& tie) {
-  tie = fabs(hd - c) <= (R)kTieRel * fmax(fabs(c), hd);
-  exercise = hd > c;
-}
-template <>
-__device__ __forceinline__ void decide<double>(double hd, double c, bool& exercise, bool& tie) {
-  // one FP64 subtraction; sign and exponents compared as integers
-  // (2^-33 = 1.16e-10 relative)
-  const double d = hd - c;
-  const long long bd = __double_as_longlong(d);
-  exercise = bd > 0;
-  const int ed = (int)((bd >> 52) & 0x7ff);
-  const int ec = (int)((__double_as_longlong(c) >> 52) & 0x7ff);
-  const int eh = (int)((__double_as_longlong(hd) >> 52) & 0x7ff);
-  tie = ed + 33 <= max(ec, eh);
-}
-template <>
-__device__ __forceinline__ void decide<df>(df hd, df c, bool& exercise, bool& tie) {
-  const df d = add_sloppy(hd, -c);
-  tie = fabsf(d.hi) <= (float)kTieRel * fmaxf(fabsf(c.hi), hd.hi);
-  exercise = d.hi > 0.0f || (d.hi == 0.0f && d.lo > 0.0f);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
-}
 
 // monomial slot of x^a w^b
 __host__ __device__ constexpr int mono(int a, int b) {
@@ -383,6 +308,7 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_chunk[NW][kNSum];
   __shared__ double s_sum[kNSum];
   __shared__ Real s_c[16];            // per-job constants, converted once
+  __shared__ long long s_thr[2];      // double: in-the-money thresholds of dates n + 1, n
   // per-warp compaction of in-the-money paths (dynamic shared memory, one
   // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
   // of on lanes that are mostly out of the money
@@ -506,6 +432,9 @@ backward_kernel(BwdArgs a) {
           default: v = first ? 0.0 : s_beta[lane]; break;
         }
         s_c[lane] = (Real)v;
+      } else if (std::is_same<Real, double>::value && lane < 18) {
+        const double sv = lane == 16 ? stab[n + 1] : stab[n];
+        s_thr[lane - 16] = __double_as_longlong(itm_threshold(type, sv, I.K));
       }
     }
     __syncthreads();
@@ -519,6 +448,10 @@ backward_kernel(BwdArgs a) {
     const Real s1 = s_c[6], d1 = s_c[7], sN = s_c[8], s0 = s_c[9];
     const Real K = s_c[10], invK = s_c[11], invTh = s_c[12];
     const Real d1lo = s_c[13], dNhi = s_c[14], dNlo = s_c[15];
+    // double: S = RN(s e) is in the money exactly when e's bits pass the
+    // date's threshold, so only in-the-money paths pay for the product
+    const long long thr1 = std::is_same<Real, double>::value ? s_thr[0] : 0;
+    const long long thr0 = std::is_same<Real, double>::value ? s_thr[1] : 0;
     // row of date d at index d - a.row0 (rows of dates 1..N, or one segment)
     const ptrdiff_t r0 = (ptrdiff_t)a.row0;
     const Real* EN = E + ((ptrdiff_t)N - r0) * (ptrdiff_t)ld;
@@ -620,12 +553,11 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             const uint32_t p = p_base + k * kBlock;
-            const Real S = s1 * e1[k];  // normalised: the comparison reads hi first
-            const bool itm = p < P && in_money<Real>(type, K, S);
+            const bool itm = p < P && itm_test(type, K, s1, e1[k], thr1);
             const unsigned m = __ballot_sync(0xffffffffu, itm);
             if (itm) {
               const int pos = cnt + __popc(m & lane_lt);
-              cs[pos] = S;
+              cs[pos] = s1 * e1[k];
               if (BASIS == kBasisSV2) cv[pos] = v1[k];
               co[pos] = (unsigned short)(k * 32 + lane);
             }
@@ -695,12 +627,11 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
-          const Real S = s0 * e0[k];  // normalised: the comparison reads hi first
-          const bool itm = p < P && in_money<Real>(type, K, S);
+          const bool itm = p < P && itm_test(type, K, s0, e0[k], thr0);
           const unsigned m = __ballot_sync(0xffffffffu, itm);
           if (itm) {
             const int pos = cnt + __popc(m & lane_lt);
-            ms[pos] = S;
+            ms[pos] = s0 * e0[k];
             if (BASIS == kBasisSV2) mv[pos] = v0[k];
             my[pos] = z[k];
           }
@@ -885,125 +816,6 @@ backward_kernel(BwdArgs a) {
   }
 }
 
-// Out-of-sample pricing pass: the policy of the regressions (beta_z, one row
-// per date, cash flows discounted to t_0) applied to the paths now in the
-// instance's rows (the pricing paths).  A path stops at the first date
-// n = 1..N-1 where it is in the money and its discounted payoff beats the
-// fitted continuation value (the test of the backward pass, the same
-// arithmetic), else at N.  Per CTA: sums over kOosTile paths.
-template <typename Real, int BASIS>
-__global__ void __launch_bounds__(kBlock)
-oos_kernel(const BwdInstance* __restrict__ inst) {
-  constexpr int PPT = kOosTile / kBlock;
-  const BwdInstance& I = inst[blockIdx.y];
-  const uint32_t P = I.P, N = I.N;
-  const uint32_t base = blockIdx.x * kOosTile;
-  if (base >= P) return;  // the whole block
-  const Real* E = (const Real*)I.E;
-  const Real* V = (const Real*)I.V;
-  const size_t ld = I.ld;
-  const double* stab = I.scale_tab;
-  const double* dtab = I.scale_tab + N + 1;
-  const int type = I.type;
-  const bool american = I.style == kAmerican;
-  const Real K = (Real)I.K, invK = (Real)I.invK, invTh = (Real)I.inv_theta;
-  const double dN = dtab[N];
-  const Real dNhi = (Real)dN, dNlo = (Real)(dN - (double)(Real)dN);
-  double sz = 0.0, sz2 = 0.0, euro = 0.0;
-  uint32_t ties = 0;
-  for (int k = 0; k < PPT; ++k) {
-    const uint32_t p = base + k * kBlock + threadIdx.x;
-    if (p >= P) break;
-    bool stopped = false;
-    double z = 0.0;
-    if (american) {
-      for (uint32_t n = 1; n < N; ++n) {
-        const double* bz = I.beta_z + (size_t)n * 8;
-        if (__ldg(bz + 6) == 0.0) continue;  // no regression at n: no exercise
-        const Real S = (Real)__ldg(stab + n) * E[(size_t)(n - 1) * ld + p];
-        if (!in_money<Real>(type, K, S)) continue;
-        Real b[6];
-#pragma unroll
-        for (int i = 0; i < 6; ++i) b[i] = (Real)__ldg(bz + i);
-        const double dn = __ldg(dtab + n);
-        const Real d1 = (Real)dn, d1lo = (Real)(dn - (double)(Real)dn);
-        const Real h = intrinsic<Real>(type, K, S);
-        const Real x = qfma(S, invK, (Real)-1);
-        Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
-        if (BASIS == kBasisSV2) {
-          const Real w = qfma(V[(size_t)(n - 1) * ld + p], invTh, (Real)-1);
-          c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
-        }
-        const Real hd = qmul(h, d1);
-        bool exercise, tie;
-        decide<Real>(hd, c, exercise, tie);
-        if (tie) ++ties;
-        if (exercise) {
-          Real hz;
-          if constexpr (std::is_same<Real, df>::value) hz = quick_two_sum(hd.hi, hd.lo);
-          else hz = fma(h, d1, h * d1lo);
-          z = (double)hz;
-          stopped = true;
-          break;
-        }
-      }
-    }
-    const Real SN = (Real)stab[N] * E[(size_t)(N - 1) * ld + p];
-    const Real hN = payoff<Real>(type, K, SN);
-    const double zN = (double)fma(hN, dNhi, hN * dNlo);
-    if (!stopped) z = zN;
-    sz += z;
-    sz2 += z * z;
-    euro += zN;
-  }
-  // fixed-order block sums
-  __shared__ double s_part[kBlock / 32][4];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  sz = warp_sum(sz);
-  sz2 = warp_sum(sz2);
-  euro = warp_sum(euro);
-  ties = __reduce_add_sync(0xffffffffu, ties);
-  if (lane == 0) {
-    s_part[warp][0] = sz;
-    s_part[warp][1] = sz2;
-    s_part[warp][2] = euro;
-    s_part[warp][3] = (double)ties;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double v = 0.0;
-    for (int w = 0; w < kBlock / 32; ++w) v += s_part[w][threadIdx.x];
-    I.oos_sum[(size_t)blockIdx.x * 4 + threadIdx.x] = v;
-  }
-}
-
-// The out-of-sample estimator of every instance (one warp each): the tile
-// sums added in tile order, the result written as the pricing result.
-__global__ void oos_finish_kernel(const BwdInstance* __restrict__ inst, uint32_t n_inst,
-                                  const BwdState* __restrict__ state,
-                                  BwdResult* __restrict__ results) {
-  const uint32_t i = blockIdx.x;
-  if (i >= n_inst || threadIdx.x != 0) return;
-  const BwdInstance& I = inst[i];
-  const uint32_t tiles = (I.P + kOosTile - 1) / kOosTile;
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (uint32_t t = 0; t < tiles; ++t)
-    for (int k = 0; k < 4; ++k) s[k] += I.oos_sum[(size_t)t * 4 + k];
-  const double Pd = (double)I.P;
-  const double mean = s[0] / Pd;
-  const double var = I.P > 1 ? (s[1] - Pd * mean * mean) / (Pd - 1.0) : 0.0;
-  BwdResult res;
-  res.cont = mean;
-  res.se = var > 0.0 ? sqrt(var / Pd) : 0.0;
-  res.euro = s[2] / Pd;
-  res.price = I.style == kEuropean ? mean : fmax(I.h0, mean);
-  res.itm = state[i].itm;
-  res.ties = state[i].ties + s[3];
-  res.singular = state[i].singular;
-  res.done = 1;
-  results[I.out_index] = res;
-}
-
 // Greeks of each (request, strike) by central differences of the scenario
 // prices (the bump layout of the request's scenario table).
 __global__ void greeks_kernel(const GreekOut* __restrict__ g,
@@ -1132,26 +944,6 @@ int backward_occupancy(int precision, int basis, int ppt) {
   if (precision == kPrecFP64) return ppt == 2 ? occ_basis<double, 2>(basis) : occ_basis<double, 4>(basis);
   if (precision == kPrecDF) return ppt == 2 ? occ_basis<df, 2>(basis) : occ_basis<df, 4>(basis);
   return ppt == 4 ? occ_basis<float, 4>(basis) : occ_basis<float, 8>(basis);
-}
-
-cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
-                       const BwdState* state, BwdResult* results, int precision, int basis,
-                       cudaStream_t s) {
-  if (n_inst == 0 || max_paths == 0) return cudaSuccess;
-  const dim3 grid((max_paths + kOosTile - 1) / kOosTile, n_inst);
-  const bool sv2 = basis == kBasisSV2;
-  if (precision == kPrecFP64) {
-    if (sv2) oos_kernel<double, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
-    else oos_kernel<double, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
-  } else if (precision == kPrecDF) {
-    if (sv2) oos_kernel<df, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
-    else oos_kernel<df, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
-  } else {
-    if (sv2) oos_kernel<float, kBasisSV2><<<grid, kBlock, 0, s>>>(inst);
-    else oos_kernel<float, kBasisS2><<<grid, kBlock, 0, s>>>(inst);
-  }
-  oos_finish_kernel<<<n_inst, 32, 0, s>>>(inst, n_inst, state, results);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,

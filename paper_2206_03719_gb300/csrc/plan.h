@@ -15,6 +15,7 @@ namespace lsmc {
 
 constexpr int kBlock = 256;      // threads per CTA of the backward pass
 constexpr int kOosTile = 1024;   // paths per CTA of the out-of-sample pricing pass
+constexpr int kOosConsts = 12;   // per-date constants of the out-of-sample pricing pass
 constexpr int kFwdBlock = 128;   // threads (paths) per CTA of the forward pass
 constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
 constexpr int kNSum = 25;        // doubles per tile partial
@@ -116,6 +117,9 @@ struct BwdInstance {
                       // discounted to t_0), then 1 if the regression was solved
   double* oos_sum;    // out of sample: per pricing tile of kOosTile paths: sum Z,
                       // sum Z^2, European sum, near ties
+  void* oos_tab;      // out of sample: (N + 1) x kOosConsts values of the working
+                      // precision per date: 6 coefficients, solved flag, S multiplier,
+                      // discount factor as a pair (hi, lo), in-the-money threshold
 };
 
 struct BwdState {

@@ -91,7 +91,10 @@ struct PlanLayout {
   uint32_t n_segments = 0;                // regenerate mode: segments of dates
   // scale: the date tables; beta / oos_partial (out-of-sample mode, inside
   // the same region): coefficients of every date, the pricing pass's sums
-  struct InstOff { size_t y, partial, scale, beta = SIZE_MAX, oos_partial = SIZE_MAX; uint32_t group; };
+  struct InstOff {
+    size_t y, partial, scale, beta = SIZE_MAX, oos_partial = SIZE_MAX, oos_tab = SIZE_MAX;
+    uint32_t group;
+  };
   std::vector<InstOff> inst_off;
   uint32_t n_results = 0;                 // BwdResult slots
   uint32_t fwd_blocks = 0;
