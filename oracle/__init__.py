@@ -108,7 +108,12 @@ def lib():
             ctypes.POINTER(Heston), ctypes.c_int, ctypes.c_int, ctypes.c_double,
             dp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
             ctypes.c_int, ctypes.c_int, ctypes.POINTER(Bumps), ctypes.c_uint64,
-            ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result), dp]
+            ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result), dp]
+        L.orc_round_f16.argtypes = [ctypes.c_double]
+        L.orc_round_f16.restype = ctypes.c_double
+        L.orc_round_bf16.argtypes = [ctypes.c_double]
+        L.orc_round_bf16.restype = ctypes.c_double
+        L.orc_round_n.argtypes = [dp, dp, ctypes.c_size_t, ctypes.c_int]
         L.orc_lsmc.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
             [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + \
             [dp, u32p, dp, ctypes.POINTER(ctypes.c_uint8)]
@@ -291,12 +296,27 @@ def scenarios(model: Heston, T, b: Bumps):
     return [(SC_KINDS[kinds[i]], models[i], Ts[i]) for i in range(n)]
 
 
+STORE_NATIVE, STORE_F16, STORE_BF16 = 0, 1, 2
+
+
+def round_store(x, store):
+    """x (array of doubles) rounded to nearest, ties to even, to binary16
+    (store = STORE_F16) or bfloat16 (STORE_BF16), returned as doubles."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty_like(x)
+    lib().orc_round_n(_ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double), x.size, int(store))
+    return y
+
+
 def price_greeks(model: Heston, strikes, T, P, N, *, type_=PUT, style=AMERICAN,
                  scheme=QE, grid=GRID_F64, basis=BASIS_S2, b: Bumps | None = None,
                  seed=42, stream=0, n_threads=None, want_scenarios=False,
-                 out_of_sample=False):
+                 out_of_sample=False, store=STORE_NATIVE):
     """Price and Greeks for each strike (list of dicts); out_of_sample: the
-    policy of the regressions on `stream` priced on stream ^ 0x80000000."""
+    policy of the regressions on `stream` priced on stream ^ 0x80000000;
+    store: STORE_F16 / STORE_BF16 for a 16-bit path store (exp(x) and v
+    rounded to the format, a rate bump reading the base simulation's
+    values times exp(+-dr t_n))."""
     b = b or bumps()
     strikes = np.ascontiguousarray(strikes, dtype=np.float64).reshape(-1)
     nk = strikes.size
@@ -305,7 +325,7 @@ def price_greeks(model: Heston, strikes, T, P, N, *, type_=PUT, style=AMERICAN,
     rc = lib().orc_price_greeks_ex(ctypes.byref(model), type_, style, T,
                                    _ptr(strikes, ctypes.c_double), nk, P, N, scheme,
                                    grid, basis, ctypes.byref(b), seed, stream,
-                                   1 if out_of_sample else 0,
+                                   1 if out_of_sample else 0, int(store),
                                    n_threads or default_threads(), res,
                                    _ptr(scen, ctypes.c_double))
     if rc != 0:

@@ -56,6 +56,41 @@ double orc_uniform_f32(uint32_t w) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Rounding to a narrower binary floating-point format, to nearest with     */
+/* ties to even, from the format's definition: p significant bits, normal   */
+/* exponents emin..emax (a value below 2^emin is a multiple of the smallest */
+/* subnormal 2^(emin - p + 1)), anything that rounds above the largest      */
+/* finite value (2 - 2^(1 - p)) 2^emax becomes infinite.  IEEE binary16:    */
+/* p = 11, emin = -14, emax = 15; bfloat16: p = 8, emin = -126, emax = 127. */
+/* Used for the reduced-precision path store (the paper's study of data     */
+/* types, Sec. 4.3, applied to storage).                                    */
+/* ------------------------------------------------------------------------ */
+static double orc_round_format(double x, int p, int emin, int emax) {
+  if (x != x || x == 0.0 || isinf(x)) return x;
+  const double a = fabs(x);
+  int e;
+  frexp(a, &e);          /* a = f 2^e with f in [1/2, 1): leading bit 2^(e-1) */
+  int E = e - 1;
+  if (E < emin) E = emin; /* subnormal range: the quantum stays 2^(emin-p+1) */
+  const double q = ldexp(1.0, E - p + 1);  /* spacing of the format near a */
+  const double r = a / q;                   /* exact: q is a power of two */
+  const double fl = floor(r), frac = r - fl;
+  double n;
+  if (frac > 0.5) n = fl + 1.0;
+  else if (frac < 0.5) n = fl;
+  else n = fmod(fl, 2.0) == 0.0 ? fl : fl + 1.0;  /* tie: the even neighbour */
+  double res = n * q;
+  if (res > ldexp(2.0 - ldexp(1.0, 1 - p), emax)) res = INFINITY;
+  return copysign(res, x);
+}
+
+double orc_round_f16(double x) { return orc_round_format(x, 11, -14, 15); }
+double orc_round_bf16(double x) { return orc_round_format(x, 8, -126, 127); }
+void orc_round_n(const double* x, double* y, size_t n, int store) {
+  for (size_t i = 0; i < n; ++i) y[i] = store == 1 ? orc_round_f16(x[i]) : orc_round_bf16(x[i]);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Normal quantile from its definition: Phi(z) = erfc(-z / sqrt 2) / 2,     */
 /* and z(u) is the root of Phi(z) = u.  Newton's method inside a bracket   */
 /* that always holds the root (bisection when a step leaves it).            */
@@ -736,17 +771,48 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      const orc_bumps* b, uint64_t seed, uint32_t stream,
                      int n_threads, orc_result* out, double* scen_prices) {
   return orc_price_greeks_ex(m, type, style, T, strikes, n_strikes, P, N, scheme, grid, basis,
-                             b, seed, stream, 0, n_threads, out, scen_prices);
+                             b, seed, stream, 0, 0, n_threads, out, scen_prices);
+}
+
+/* Paths of scenario s as a 16-bit path store holds them (store = 1:
+ * binary16, 2: bfloat16).  A stored value is exp(x) of the simulation (x =
+ * log(S / S0), started at 0) or its variance, rounded to the format; a
+ * scenario reads S = S0 exp(x) as its S0 times the stored value.  A rate
+ * bump moves every log-price of the scheme by (+-dr) t_n and nothing else,
+ * so the rate scenarios read the base simulation's stored values times
+ * exp(+-dr t_n). */
+static int orc_paths_store16(const orc_heston* base, const orc_heston* ms, int kind,
+                             double T, int scheme, int grid, uint32_t P, uint32_t N,
+                             uint64_t seed, uint32_t stream, int store, double* S,
+                             double* V, int n_threads) {
+  const int rate = kind == ORC_SC_R_UP || kind == ORC_SC_R_DN;
+  orc_heston unit = rate ? *base : *ms;
+  unit.S0 = 1.0;  /* rows of exp(x) */
+  const int rc = orc_paths(&unit, T, scheme, grid, P, N, seed, stream, S, V, n_threads);
+  if (rc) return rc;
+  const double dr = rate ? ms->r - base->r : 0.0;
+  const double dt = T / (double)N;
+  for (uint32_t n = 0; n <= N; ++n) {
+    const double f = rate ? ms->S0 * exp((double)n * dr * dt) : ms->S0;
+    for (uint32_t p = 0; p < P; ++p) {
+      const size_t i = (size_t)n * P + p;
+      const double e = store == 1 ? orc_round_f16(S[i]) : orc_round_bf16(S[i]);
+      S[i] = f * e;
+      V[i] = store == 1 ? orc_round_f16(V[i]) : orc_round_bf16(V[i]);
+    }
+  }
+  return 0;
 }
 
 int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
                         const double* strikes, uint32_t n_strikes, uint32_t P,
                         uint32_t N, int scheme, int grid, int basis,
                         const orc_bumps* b, uint64_t seed, uint32_t stream,
-                        int out_of_sample, int n_threads, orc_result* out,
+                        int out_of_sample, int store, int n_threads, orc_result* out,
                         double* scen_prices) {
   if (!m || !strikes || !b || !out || n_strikes == 0 || P == 0 || N == 0)
     return -1;
+  if (store < 0 || store > 2) return -1;
   orc_heston models[ORC_SC_COUNT];
   double Ts[ORC_SC_COUNT];
   int kinds[ORC_SC_COUNT];
@@ -773,12 +839,20 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
       (out_of_sample && (!SB || !VB))) { rc = -2; goto done; }
 
   for (int s = 0; s < n_sc && rc == 0; ++s) {
-    rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream, S, V,
-                   n_threads);
+    if (store)
+      rc = orc_paths_store16(&models[0], &models[s], kinds[s], Ts[s], scheme, grid, P, N,
+                             seed, stream, store, S, V, n_threads);
+    else
+      rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream, S, V,
+                     n_threads);
     if (rc) break;
     if (out_of_sample) {
-      rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream ^ 0x80000000u, SB, VB,
-                     n_threads);
+      if (store)
+        rc = orc_paths_store16(&models[0], &models[s], kinds[s], Ts[s], scheme, grid, P, N,
+                               seed, stream ^ 0x80000000u, store, SB, VB, n_threads);
+      else
+        rc = orc_paths(&models[s], Ts[s], scheme, grid, P, N, seed, stream ^ 0x80000000u, SB,
+                       VB, n_threads);
       if (rc) break;
     }
     orc_bwd_ctx c = {S, V, strikes, P, N, models[s].S0, Ts[s], models[s].r,

@@ -165,8 +165,15 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
                         const double* strikes, uint32_t n_strikes, uint32_t P,
                         uint32_t N, int scheme, int grid, int basis,
                         const orc_bumps* b, uint64_t seed, uint32_t stream,
-                        int out_of_sample, int n_threads, orc_result* out,
+                        int out_of_sample, int store, int n_threads, orc_result* out,
                         double* scen_prices);
+
+/* Rounding to nearest, ties to even, from a double to IEEE binary16 and to
+ * bfloat16 (returned as doubles; overflow gives infinity). */
+double orc_round_f16(double x);
+double orc_round_bf16(double x);
+/* y[i] = x[i] rounded (store 1: binary16, 2: bfloat16). */
+void orc_round_n(const double* x, double* y, size_t n, int store);
 
 /* Array forms of the scalar functions above (plain loops). */
 void orc_philox_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out,
