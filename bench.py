@@ -72,6 +72,8 @@ def parse():
                     help="no path store: regenerate segments from saved states")
     ap.add_argument("--out-of-sample", action="store_true",
                     help="price the regression policy on independent paths")
+    ap.add_argument("--store", default="native", choices=["native", "fp16", "bf16"],
+                    help="element type of the path store")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -278,6 +280,64 @@ def measure_variants(api, L, torch, reps=3):
     return out
 
 
+# The paper's deviation of half-precision arithmetic from double on its
+# multi-asset path reduction, by number of time steps (its table of data
+# types; context only: here only the path store is 16-bit)
+PAPER_HALF_DEVIATION_PCT = {126: 0.06, 252: 0.38, 504: 1.01, 1260: 11.14, 2520: 14.65}
+
+
+def measure_store16(api, L, torch, reps=2, paths=65536):
+    """The 16-bit path store against the full-precision store on the same
+    random streams, for the paper's step counts: largest relative deviation
+    of the price and of each Greek over the five strikes, device time and
+    path-store bytes.  Float-pair arithmetic (within 1e-11 of FP64), so the
+    deviations are the store's; plus FP64 and MIXED timings at their
+    headline sizes."""
+    keys = ("price", "delta", "gamma", "vega", "rho", "theta")
+
+    def run(wl):
+        need = L.lsmc_request_footprint(None, api.Request(wl).c)
+        with api.Context(workspace_bytes=need + (256 << 20)) as ctx:
+            plan = ctx.plan([wl])
+            for _ in range(2):
+                plan.launch()
+            plan.fetch()
+            plan.set_timing(True)
+            for _ in range(reps):
+                plan.launch()
+            res = plan.fetch()
+            kms, n = plan.kernel_times()
+            bytes_ = int(plan.info().device_bytes)
+            plan.close()
+        return res, sum(kms) / max(1, n), bytes_
+
+    def dev(a, b):
+        return {k: max(abs(x[k] - y[k]) / max(abs(y[k]), 1e-12) for x, y in zip(a, b))
+                for k in keys}
+
+    out = {"paths": paths, "arithmetic": "df", "by_steps": {}}
+    for N in sorted(PAPER_HALF_DEVIATION_PCT):
+        base = workloads.PAPER_FP64.replace(precision="df", n_paths=paths, n_steps=N)
+        ref, ms0, b0 = run(base)
+        row = {"native": {"ms": ms0, "device_bytes": b0,
+                          "price_se_k100": ref[2]["price_se"]},
+               "paper_half_arith_deviation_pct": PAPER_HALF_DEVIATION_PCT[N]}
+        for fmt in ("fp16", "bf16"):
+            got, ms, b = run(base.replace(store=fmt))
+            d = dev(got, ref)
+            row[fmt] = {"ms": ms, "device_bytes": b, "max_rel_dev": d,
+                        "price_dev_pct": 100.0 * d["price"],
+                        "price_dev_in_se_k100": abs(got[2]["price"] - ref[2]["price"]) /
+                                                ref[2]["price_se"]}
+        out["by_steps"][str(N)] = row
+    for tag, wl in (("fp64_paper", workloads.PAPER_FP64),
+                    ("mixed_large", workloads.LARGE_MIXED)):
+        _, ms0, b0 = run(wl)
+        _, ms1, b1 = run(wl.replace(store="fp16"))
+        out[tag] = {"native_ms": ms0, "fp16_ms": ms1, "native_bytes": b0, "fp16_bytes": b1}
+    return out
+
+
 def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     """Uneven book (512 contracts, all bump scenarios, in the given precision)
     in launches of `chunk` contracts, each captured once in a CUDA
@@ -416,6 +476,8 @@ def main():
         wl = wl.replace(regenerate=True, name=wl.name + "-regenerate")
     if args.out_of_sample:
         wl = wl.replace(out_of_sample=True, name=wl.name + "-out-of-sample")
+    if args.store != "native":
+        wl = wl.replace(store=args.store, name=wl.name + "-store-" + args.store)
     if args.impl == "reference":
         run_reference(args, wl)
         return
@@ -511,6 +573,7 @@ def main():
                                      "fp64": measure_book(*a, precision="fp64")}),
                 ("stac_a2_path_reduction", lambda *a: measure_stac(*a)),
                 ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
+                ("store16_precision_study", lambda *a: measure_store16(*a)),
                 ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
                                         "mixed": measure_serving(*a, precision="mixed",
                                                                  max_inflight=4)}))

@@ -158,6 +158,23 @@ enum { LSMC_FLAG_REGENERATE = 1 };
  * free of the in-sample estimator's look-ahead.  Not combined with
  * LSMC_FLAG_REGENERATE. */
 enum { LSMC_FLAG_OUT_OF_SAMPLE = 2 };
+/* lsmc_request.flags.  LSMC_FLAG_STORE_FP16 / LSMC_FLAG_STORE_BF16: a 16-bit
+ * path store (the paper's study of reduced data types, Sec. 4.3, applied to
+ * the stored paths only).  The forward pass computes every step in the
+ * request's precision and writes exp(x) (x = log(S / S0), the path's log
+ * price relative to its start) and the variance as IEEE binary16 or
+ * bfloat16, rounded to nearest with ties to even; the backward induction
+ * widens them exactly and works in the request's precision.  A scenario
+ * reads S as its S0 times the stored value, a rate bump (which moves every
+ * log price by +-dr t_n and nothing else) as the base simulation's value
+ * times S0 exp(+-dr t_n).  The store takes 2 bytes per value instead of 8
+ * (FP64, float pairs) or 4 (MIXED).  binary16 keeps 11 significant bits
+ * (relative rounding error at most 2^-11) and overflows above 65504, i.e.
+ * for x > 11.09; bfloat16 keeps 8 bits and the float range.  The two flags
+ * exclude each other (LSMC_EINVAL); all requests of a plan agree on them.
+ * Combines with LSMC_FLAG_REGENERATE (the segment rows are 16-bit, the saved
+ * states are not) and with LSMC_FLAG_OUT_OF_SAMPLE. */
+enum { LSMC_FLAG_STORE_FP16 = 4, LSMC_FLAG_STORE_BF16 = 8 };
 
 typedef struct lsmc_ctx lsmc_ctx;
 typedef struct lsmc_plan lsmc_plan;

@@ -49,7 +49,8 @@ class Request:
         r.seed = wl.seed
         r.stream_id = wl.stream
         r.flags = (L.LSMC_FLAG_REGENERATE if wl.regenerate else 0) | \
-            (L.LSMC_FLAG_OUT_OF_SAMPLE if wl.out_of_sample else 0)
+            (L.LSMC_FLAG_OUT_OF_SAMPLE if wl.out_of_sample else 0) | \
+            {"native": 0, "fp16": L.LSMC_FLAG_STORE_FP16, "bf16": L.LSMC_FLAG_STORE_BF16}[wl.store]
         self.c = r
 
 

@@ -34,6 +34,7 @@
 #include "exercise.cuh"
 #include "kernels.h"
 #include "plan.h"
+#include "store16.cuh"
 
 namespace lsmc {
 
@@ -290,9 +291,11 @@ struct BwdWarpBufs {
 //
 // A job covers `I.sub` sub-tiles of kBlock * PPT paths: the wait for the
 // previous round, the block reduction and the arrival are paid once per job.
-template <typename Real, int BASIS, int PPT>
+template <typename Real, int BASIS, int PPT, int FMT>
 __global__ void __launch_bounds__(kBlock, 2)
 backward_kernel(BwdArgs a) {
+  using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
+  using St = typename RR::raw;
   constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
   constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
   constexpr int NA = NM + NB;                         // register sums
@@ -323,6 +326,10 @@ backward_kernel(BwdArgs a) {
   // compaction pays where the in-the-money arithmetic is heavy (double and
   // float pairs); plain floats are bound by loads and stay uncompacted
   constexpr bool kCompact = !std::is_same<Real, float>::value;
+  // double: the in-the-money test needs no product (threshold on the stored
+  // value), so the compaction buffers hold the stored value and S = s e is
+  // formed on the dense lists, where no lane idles
+  constexpr bool kProdLate = std::is_same<Real, double>::value;
   // Job decoding by thread 0: the job number `next` was taken from the
   // counter one job earlier, so the atomic's latency is hidden.
   unsigned long long next = 0;
@@ -367,8 +374,8 @@ backward_kernel(BwdArgs a) {
     BwdState* st = &a.state[ji.inst];
     const uint32_t N = I.N, P = I.P, r = ji.round;
     const size_t ld = I.ld;
-    const Real* E = (const Real*)I.E;
-    const Real* V = (const Real*)I.V;
+    const St* E = (const St*)I.E;
+    const St* V = (const St*)I.V;
     Real* Z = (Real*)I.Y;
     const double* stab = I.scale_tab;          // S multipliers, dates 0..N
     const double* dtab = I.scale_tab + N + 1;  // discount to t_0, dates 0..N
@@ -454,11 +461,11 @@ backward_kernel(BwdArgs a) {
     const long long thr0 = std::is_same<Real, double>::value ? s_thr[1] : 0;
     // row of date d at index d - a.row0 (rows of dates 1..N, or one segment)
     const ptrdiff_t r0 = (ptrdiff_t)a.row0;
-    const Real* EN = E + ((ptrdiff_t)N - r0) * (ptrdiff_t)ld;
-    const Real* E1 = E + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld;                    // date n + 1
-    const Real* V1 = BASIS == kBasisSV2 ? V + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld : nullptr;
-    const Real* E0 = final_job ? nullptr : E + ((ptrdiff_t)n - r0) * (ptrdiff_t)ld;  // date n
-    const Real* V0 = (BASIS == kBasisSV2 && !final_job)
+    const St* EN = E + ((ptrdiff_t)N - r0) * (ptrdiff_t)ld;
+    const St* E1 = E + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld;                    // date n + 1
+    const St* V1 = BASIS == kBasisSV2 ? V + ((ptrdiff_t)n + 1 - r0) * (ptrdiff_t)ld : nullptr;
+    const St* E0 = final_job ? nullptr : E + ((ptrdiff_t)n - r0) * (ptrdiff_t)ld;  // date n
+    const St* V0 = (BASIS == kBasisSV2 && !final_job)
                          ? V + ((ptrdiff_t)n - r0) * (ptrdiff_t)ld : nullptr;
 
     Acc<Real, NA> acc;
@@ -481,27 +488,37 @@ backward_kernel(BwdArgs a) {
       const uint32_t p_base = sub_base + tid;
       // every load of the sub-tile is issued before any arithmetic, so each
       // thread has up to 5 * PPT independent loads in flight
-      Real zr[PPT], e1[PPT], v1[PPT], e0[PPT], v0[PPT];
+      Real zr[PPT];
+      St e1r[PPT], v1r[PPT], e0r[PPT], v0r[PPT];
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const uint32_t p = p_base + k * kBlock;
         const bool valid = p < P;
-        zr[k] = e1[k] = v1[k] = e0[k] = v0[k] = (Real)0;
+        zr[k] = (Real)0;
+        e1r[k] = v1r[k] = e0r[k] = v0r[k] = (St)0;
         if (valid) {
           if (first) {
-            e1[k] = EN[p];
+            e1r[k] = EN[p];
           } else {
             zr[k] = ld_cg(Z + p);
             if (bok) {
-              e1[k] = E1[p];
-              if (BASIS == kBasisSV2) v1[k] = V1[p];
+              e1r[k] = E1[p];
+              if (BASIS == kBasisSV2) v1r[k] = V1[p];
             }
           }
           if (!final_job) {
-            e0[k] = E0[p];
-            if (BASIS == kBasisSV2) v0[k] = V0[p];
+            e0r[k] = E0[p];
+            if (BASIS == kBasisSV2) v0r[k] = V0[p];
           }
         }
+      }
+      Real e1[PPT], v1[PPT], e0[PPT], v0[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        e1[k] = RR::widen(e1r[k]);
+        v1[k] = RR::widen(v1r[k]);
+        e0[k] = RR::widen(e0r[k]);
+        v0[k] = RR::widen(v0r[k]);
       }
       Real z[PPT];
       if (first) {
@@ -557,7 +574,7 @@ backward_kernel(BwdArgs a) {
             const unsigned m = __ballot_sync(0xffffffffu, itm);
             if (itm) {
               const int pos = cnt + __popc(m & lane_lt);
-              cs[pos] = s1 * e1[k];
+              cs[pos] = kProdLate ? e1[k] : s1 * e1[k];
               if (BASIS == kBasisSV2) cv[pos] = v1[k];
               co[pos] = (unsigned short)(k * 32 + lane);
             }
@@ -566,7 +583,7 @@ backward_kernel(BwdArgs a) {
           }
           __syncwarp();
           for (int j = lane; j < cnt; j += 32) {
-            const Real S = cs[j];
+            const Real S = kProdLate ? s1 * cs[j] : cs[j];
             const Real h = intrinsic<Real>(type, K, S);
             const Real x = qfma(S, invK, (Real)-1);
             Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
@@ -631,7 +648,7 @@ backward_kernel(BwdArgs a) {
           const unsigned m = __ballot_sync(0xffffffffu, itm);
           if (itm) {
             const int pos = cnt + __popc(m & lane_lt);
-            ms[pos] = s0 * e0[k];
+            ms[pos] = kProdLate ? e0[k] : s0 * e0[k];
             if (BASIS == kBasisSV2) mv[pos] = v0[k];
             my[pos] = z[k];
           }
@@ -641,7 +658,8 @@ backward_kernel(BwdArgs a) {
         Real* t = acc.target();
         const int full = cnt & ~31;
         for (int j = lane; j < full; j += 32)
-          accumulate_moments<Real, BASIS, NM>(t, n_itm, ms[j], mv[j], my[j], invK, invTh);
+          accumulate_moments<Real, BASIS, NM>(t, n_itm, kProdLate ? s0 * ms[j] : ms[j], mv[j],
+                                              my[j], invK, invTh);
         mcarry = cnt - full;
         Real r0 = (Real)0, r1 = (Real)0, r2 = (Real)0;
         if (lane < mcarry) {
@@ -662,8 +680,9 @@ backward_kernel(BwdArgs a) {
 
     if (kCompact && mcarry > 0) {  // the carried moment items of the last sub-tile
       if (lane < mcarry)
-        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, ms[lane], mv[lane], my[lane],
-                                            invK, invTh);
+        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm,
+                                            kProdLate ? s0 * ms[lane] : ms[lane], mv[lane],
+                                            my[lane], invK, invTh);
       __syncwarp();
     }
 
@@ -876,7 +895,7 @@ static size_t bwd_dyn_bytes() {
 }
 
 // dynamic shared memory above 48 KB needs the kernel's opt-in, once per device
-template <typename Real, int BASIS, int PPT>
+template <typename Real, int BASIS, int PPT, int FMT>
 static cudaError_t bwd_prepare() {
   static std::atomic<unsigned long long> done{0};
   int dev = 0;
@@ -884,19 +903,58 @@ static cudaError_t bwd_prepare() {
   if (e != cudaSuccess) return e;
   const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
   if (bit && (done.load() & bit)) return cudaSuccess;
-  e = cudaFuncSetAttribute(backward_kernel<Real, BASIS, PPT>,
+  e = cudaFuncSetAttribute(backward_kernel<Real, BASIS, PPT, FMT>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)bwd_dyn_bytes<Real, PPT>());
   if (e == cudaSuccess && bit) done.fetch_or(bit);
   return e;
 }
 
-template <typename Real, int BASIS, int PPT>
-static cudaError_t launch_bwd_t(const BwdArgs& a, int grid, cudaStream_t s) {
-  const cudaError_t e = bwd_prepare<Real, BASIS, PPT>();
-  if (e != cudaSuccess) return e;
-  backward_kernel<Real, BASIS, PPT><<<grid, kBlock, bwd_dyn_bytes<Real, PPT>(), s>>>(a);
-  return cudaGetLastError();
+template <typename Real, int BASIS, int PPT, int FMT>
+struct BwdLaunch {
+  static cudaError_t run(const BwdArgs& a, int grid, cudaStream_t s) {
+    const cudaError_t e = bwd_prepare<Real, BASIS, PPT, FMT>();
+    if (e != cudaSuccess) return e;
+    backward_kernel<Real, BASIS, PPT, FMT><<<grid, kBlock, bwd_dyn_bytes<Real, PPT>(), s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+template <typename Real, int BASIS, int PPT, int FMT>
+struct BwdOccupancy {
+  static int run() {
+    int n = 0;
+    if (bwd_prepare<Real, BASIS, PPT, FMT>() != cudaSuccess) return 1;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &n, backward_kernel<Real, BASIS, PPT, FMT>, kBlock,
+               bwd_dyn_bytes<Real, PPT>()) == cudaSuccess ? n : 1;
+  }
+};
+
+// F<Real, BASIS, PPT, FMT>::run(args...) for a (basis, store format)
+template <template <typename, int, int, int> class F, typename Real, int PPT, typename... A>
+static auto by_basis_format(int basis, int fmt, A... args) {
+  if (basis == kBasisSV2) {
+    if (fmt == kStoreF16) return F<Real, kBasisSV2, PPT, kStoreF16>::run(args...);
+    if (fmt == kStoreBF16) return F<Real, kBasisSV2, PPT, kStoreBF16>::run(args...);
+    return F<Real, kBasisSV2, PPT, kStoreNative>::run(args...);
+  }
+  if (fmt == kStoreF16) return F<Real, kBasisS2, PPT, kStoreF16>::run(args...);
+  if (fmt == kStoreBF16) return F<Real, kBasisS2, PPT, kStoreBF16>::run(args...);
+  return F<Real, kBasisS2, PPT, kStoreNative>::run(args...);
+}
+
+// ... for a (precision, basis, paths per thread, store format)
+template <template <typename, int, int, int> class F, typename... A>
+static auto by_variant(int precision, int basis, int ppt, int fmt, A... args) {
+  if (precision == kPrecFP64)
+    return ppt == 2 ? by_basis_format<F, double, 2>(basis, fmt, args...)
+                    : by_basis_format<F, double, 4>(basis, fmt, args...);
+  if (precision == kPrecDF)
+    return ppt == 2 ? by_basis_format<F, df, 2>(basis, fmt, args...)
+                    : by_basis_format<F, df, 4>(basis, fmt, args...);
+  return ppt == 4 ? by_basis_format<F, float, 4>(basis, fmt, args...)
+                  : by_basis_format<F, float, 8>(basis, fmt, args...);
 }
 
 // Paths per thread in a sub-tile: 2 or 4 for double and float pairs, 4 or 8
@@ -906,44 +964,17 @@ bool backward_ppt_valid(int precision, int ppt) {
   return precision == kPrecMixed ? (ppt == 4 || ppt == 8) : (ppt == 2 || ppt == 4);
 }
 
-template <typename Real, int PPT>
-static cudaError_t launch_bwd_basis(const BwdArgs& a, int basis, int grid, cudaStream_t s) {
-  return basis == kBasisSV2 ? launch_bwd_t<Real, kBasisSV2, PPT>(a, grid, s)
-                            : launch_bwd_t<Real, kBasisS2, PPT>(a, grid, s);
-}
-
 cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt, int grid,
                             cudaStream_t s) {
   if (a.total_jobs == 0) return cudaSuccess;
   if (!backward_ppt_valid(precision, ppt)) return cudaErrorInvalidValue;
-  if (precision == kPrecFP64)
-    return ppt == 2 ? launch_bwd_basis<double, 2>(a, basis, grid, s)
-                    : launch_bwd_basis<double, 4>(a, basis, grid, s);
-  if (precision == kPrecDF)
-    return ppt == 2 ? launch_bwd_basis<df, 2>(a, basis, grid, s)
-                    : launch_bwd_basis<df, 4>(a, basis, grid, s);
-  return ppt == 4 ? launch_bwd_basis<float, 4>(a, basis, grid, s)
-                  : launch_bwd_basis<float, 8>(a, basis, grid, s);
+  if (a.store_fmt < kStoreNative || a.store_fmt > kStoreBF16) return cudaErrorInvalidValue;
+  return by_variant<BwdLaunch>(precision, basis, ppt, a.store_fmt, a, grid, s);
 }
 
-template <typename Real, int BASIS, int PPT>
-static int occ_t() {
-  int n = 0;
-  if (bwd_prepare<Real, BASIS, PPT>() != cudaSuccess) return 1;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, backward_kernel<Real, BASIS, PPT>,
-                                                       kBlock, bwd_dyn_bytes<Real, PPT>()) ==
-                 cudaSuccess ? n : 1;
-}
-
-template <typename Real, int PPT>
-static int occ_basis(int basis) {
-  return basis == kBasisSV2 ? occ_t<Real, kBasisSV2, PPT>() : occ_t<Real, kBasisS2, PPT>();
-}
-
-int backward_occupancy(int precision, int basis, int ppt) {
-  if (precision == kPrecFP64) return ppt == 2 ? occ_basis<double, 2>(basis) : occ_basis<double, 4>(basis);
-  if (precision == kPrecDF) return ppt == 2 ? occ_basis<df, 2>(basis) : occ_basis<df, 4>(basis);
-  return ppt == 4 ? occ_basis<float, 4>(basis) : occ_basis<float, 8>(basis);
+int backward_occupancy(int precision, int basis, int ppt, int fmt) {
+  if (!backward_ppt_valid(precision, ppt)) return 1;
+  return by_variant<BwdOccupancy>(precision, basis, ppt, fmt);
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,

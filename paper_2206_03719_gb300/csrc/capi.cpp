@@ -143,14 +143,14 @@ int cuda_status(cudaError_t e) {
 
 int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? dflt : dflt) : v; }
 
-int occupancy(lsmc_ctx* ctx, int precision, int basis, int ppt) {
+int occupancy(lsmc_ctx* ctx, int precision, int basis, int ppt, int fmt) {
   if (ctx) {
     std::lock_guard<std::mutex> g(ctx->occ_mu);
-    int& o = ctx->occ[(precision * 4 + basis) * 16 + ppt];
-    if (o == 0) o = std::max(1, backward_occupancy(precision, basis, ppt));
+    int& o = ctx->occ[((precision * 4 + basis) * 16 + ppt) * 4 + fmt];
+    if (o == 0) o = std::max(1, backward_occupancy(precision, basis, ppt, fmt));
     return o;
   }
-  return std::max(1, backward_occupancy(precision, basis, ppt));
+  return std::max(1, backward_occupancy(precision, basis, ppt, fmt));
 }
 
 int sm_count(lsmc_ctx* ctx) {
@@ -244,7 +244,9 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->fa.next_job = nullptr;
   p->fa.next_job_value = 0;
   p->fa.stream_xor = 0;
+  p->fa.store_fmt = L.opt.store;
   p->ba.row0 = 1;
+  p->ba.store_fmt = L.opt.store;
   p->ba.inst = p->d_inst;
   p->ba.state = (BwdState*)p->d_state;
   p->ba.results = p->d_results;
@@ -256,7 +258,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
-  const int occ = occupancy(p->ctx, prec, L.opt.basis, plan_ppt(L.opt));
+  const int occ = occupancy(p->ctx, prec, L.opt.basis, plan_ppt(L.opt), L.opt.store);
   const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
   p->h_out.resize(L.greeks.size());
@@ -312,6 +314,9 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
   o->basis = reqs[0].basis;
   o->regen = (reqs[0].flags & LSMC_FLAG_REGENERATE) != 0;
   o->oos = (reqs[0].flags & LSMC_FLAG_OUT_OF_SAMPLE) != 0;
+  const uint32_t store_flags = LSMC_FLAG_STORE_FP16 | LSMC_FLAG_STORE_BF16;
+  o->store = (reqs[0].flags & LSMC_FLAG_STORE_FP16) ? kStoreF16
+             : (reqs[0].flags & LSMC_FLAG_STORE_BF16) ? kStoreBF16 : kStoreNative;
   if (o->regen && o->oos) return LSMC_ENOTIMPL;
   for (size_t i = 0; i < n; ++i) {
     const int prec = resolve(ctx, reqs[i].precision, dprec);
@@ -323,6 +328,7 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
     // regenerate mode: one flag and one date grid for the whole plan
     if (((reqs[i].flags & LSMC_FLAG_REGENERATE) != 0) != o->regen) return LSMC_ENOTIMPL;
     if (((reqs[i].flags & LSMC_FLAG_OUT_OF_SAMPLE) != 0) != o->oos) return LSMC_ENOTIMPL;
+    if ((reqs[i].flags & store_flags) != (reqs[0].flags & store_flags)) return LSMC_ENOTIMPL;
     if (o->regen && reqs[i].n_steps != reqs[0].n_steps) return LSMC_ENOTIMPL;
   }
   if (o->regen) {
@@ -346,7 +352,7 @@ uint64_t tune_key(const lsmc_request* reqs, size_t n, const PlanOptions& o) {
   }
   uint64_t lg = 0;
   while ((2ull << lg) <= tiles) ++lg;
-  return ((uint64_t)o.precision << 40) | ((uint64_t)o.basis << 32) | lg;
+  return ((uint64_t)o.store << 48) | ((uint64_t)o.precision << 40) | ((uint64_t)o.basis << 32) | lg;
 }
 
 // Backward shape of a plan: autotuned if this kind of launch was tuned, else
@@ -361,7 +367,7 @@ void choose_shape(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions
   o->ppt = tuned >> 16;
   if (ctx && ctx->ppt_override) o->ppt = ctx->ppt_override;
   const int ppt = plan_ppt(*o);
-  const uint32_t ctas = (uint32_t)occupancy(ctx, o->precision, o->basis, ppt) *
+  const uint32_t ctas = (uint32_t)occupancy(ctx, o->precision, o->basis, ppt, o->store) *
                         (uint32_t)sm_count(ctx);
   o->sub = choose_sub(reqs, n, o->precision, ppt, ctas);
   if (tuned & 0xffffu) o->sub = tuned & 0xffffu;
@@ -424,7 +430,7 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
     LSMC_CUDA(mark(2));
     const uint32_t N = p->L.contracts.empty() ? 0 : p->L.contracts[0].N;
     const uint32_t C = p->L.opt.ck_stride;
-    const int occ = occupancy(p->ctx, prec, p->L.opt.basis, plan_ppt(p->L.opt));
+    const int occ = occupancy(p->ctx, prec, p->L.opt.basis, plan_ppt(p->L.opt), p->L.opt.store);
     const uint64_t cap = (uint64_t)occ * sm_count(p->ctx);
     for (int sgi = (int)p->L.n_segments - 1; sgi >= 0; --sgi) {
       const uint32_t d0 = (uint32_t)sgi * C, d1 = std::min<uint32_t>(N, d0 + C);
@@ -466,7 +472,7 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
       uint32_t max_p = 0;
       for (const auto& c : p->L.contracts) max_p = std::max(max_p, c.P);
       LSMC_CUDA(launch_oos(p->d_inst, (uint32_t)p->L.inst.size(), max_p, p->ba.state,
-                           p->d_results, prec, p->L.opt.basis, p->stream));
+                           p->d_results, prec, p->L.opt.basis, p->L.opt.store, p->stream));
     }
     LSMC_CUDA(mark(3));
   }
@@ -558,7 +564,7 @@ void scheduler_loop(lsmc_ctx* ctx) {
     }
     // admissions, first come first served: the oldest pending request and
     // the pending requests right behind it that can share its launch (same
-    // precision, scheme, basis and paths per thread) while the workspace
+    // precision, scheme, basis, paths per thread and flags) while the workspace
     // has room for all of them
     while (!ctx->pending.empty()) {
       int free_slot = -1;
@@ -573,7 +579,9 @@ void scheduler_loop(lsmc_ctx* ctx) {
       for (size_t i = 1; i < ctx->pending.size() && batch.size() < kMaxBatch; ++i) {
         Ticket* t = ctx->pending[i];
         if (t->precision != t0->precision || t->scheme != t0->scheme ||
-            t->basis != t0->basis || t->ppt != t0->ppt || need + t->footprint > room)
+            t->basis != t0->basis || t->ppt != t0->ppt || t->req.flags != t0->req.flags ||
+            ((t->req.flags & LSMC_FLAG_REGENERATE) && t->req.n_steps != t0->req.n_steps) ||
+            need + t->footprint > room)
           break;
         batch.push_back(t);
         need += t->footprint;

@@ -17,6 +17,7 @@
 #include "dfloat.cuh"
 #include "kernels.h"
 #include "plan.h"
+#include "store16.cuh"
 
 namespace lsmc {
 
@@ -53,8 +54,8 @@ struct GroupConst {
   // FT-Euler
   Real dt, kdt, theta, xi, rho, rhob, mudt;
   Real v0, out_scale;
-  Real* E;
-  Real* V;
+  void* E;            // rows of the path store (element type: the launch's store format)
+  void* V;
   Real* CX;
   Real* CV;
   uint64_t ld;
@@ -90,8 +91,8 @@ __device__ void make_group_const(const FwdGroup& g, GroupConst<Real>& c) {
   c.mudt = (Real)((g.r - g.q) * dt);
   c.v0 = (Real)g.v0;
   c.out_scale = (Real)g.out_scale;
-  c.E = (Real*)g.E;
-  c.V = (Real*)g.V;
+  c.E = g.E;
+  c.V = g.V;
   c.CX = (Real*)g.CX;
   c.CV = (Real*)g.CV;
   c.ld = g.ld;
@@ -150,11 +151,12 @@ __device__ __forceinline__ void ft_step(const GroupConst<Real>& c, Real& x,
 // SEG: the launch covers dates (n0, n1] and may start from, or save, states
 // (regenerate mode); without it, the whole horizon from the initial state
 // into the full row store (the hot loop stays free of the segment logic).
-template <typename Real, int SCHEME, bool SEG>
+template <typename Real, int SCHEME, bool SEG, int FMT>
 // register budgets: 128 per thread for double, 64 for float (eight CTAs of
 // 128 threads per SM), unconstrained for float pairs
 __global__ void __launch_bounds__(kFwdBlock, std::is_same<Real, double>::value ? 4 : (std::is_same<Real, float>::value ? 8 : 1))
 forward_kernel(FwdArgs a) {
+  using St = typename StoreElem<Real, FMT>::type;  // element of the E/V rows
   __shared__ GroupConst<Real> gc[kMaxGroups];
   __shared__ FwdContract sc;
   if (threadIdx.x == 0) {
@@ -194,8 +196,8 @@ forward_kernel(FwdArgs a) {
 
   for (int g = 0; g < ng; ++g) {
     const FwdGroup& gg = a.groups[sc.group0 + g];
-    if (gg.E_row0) ((Real*)gg.E_row0)[p] = gc[g].out_scale;
-    if (gg.V_row0) ((Real*)gg.V_row0)[p] = gc[g].v0;
+    if (gg.E_row0) ((St*)gg.E_row0)[p] = narrow<St>(gc[g].out_scale);
+    if (gg.V_row0) ((St*)gg.V_row0)[p] = narrow<St>(gc[g].v0);
   }
 
   if constexpr (std::is_same<Real, float>::value && SCHEME == kSchemeQE) {
@@ -205,8 +207,8 @@ forward_kernel(FwdArgs a) {
     float x[kMaxGroups], v[kMaxGroups], mA[kMaxGroups], mB[kMaxGroups], sA[kMaxGroups],
         sB[kMaxGroups], c0[kMaxGroups], K1[kMaxGroups], K2[kMaxGroups], K3[kMaxGroups],
         os[kMaxGroups];
-    float* rowE[kMaxGroups];
-    float* rowV[kMaxGroups];
+    St* rowE[kMaxGroups];
+    St* rowV[kMaxGroups];
 #pragma unroll
     for (int g = 0; g < kMaxGroups; ++g) {
       const GroupConst<float>& c = gc[g < ng ? g : 0];
@@ -215,8 +217,8 @@ forward_kernel(FwdArgs a) {
       mA[g] = c.mA; mB[g] = c.mB; sA[g] = c.sA; sB[g] = c.sB;
       c0[g] = c.c0; K1[g] = c.K1; K2[g] = c.K2; K3[g] = c.K3;
       os[g] = c.out_scale;
-      rowE[g] = c.E + p;
-      rowV[g] = c.V ? c.V + p : nullptr;
+      rowE[g] = (St*)c.E + p;
+      rowV[g] = c.V ? (St*)c.V + p : nullptr;
     }
     const size_t ld = gc[0].ld;  // one row stride for the groups of a contract
     if (ck_index) {
@@ -231,8 +233,8 @@ forward_kernel(FwdArgs a) {
 #pragma unroll
       for (int g = 0; g < kMaxGroups; ++g)
         if (g < ng) {
-          rowE[g][0] = os[g] * __expf(x[g]);
-          if (rowV[g]) rowV[g][0] = v[g];
+          rowE[g][0] = narrow<St>(os[g] * __expf(x[g]));
+          if (rowV[g]) rowV[g][0] = narrow<St>(v[g]);
         }
     }
     size_t off = (size_t)(n0 + 1 - row0) * ld;
@@ -249,8 +251,8 @@ forward_kernel(FwdArgs a) {
           x[g] = xg;
           v[g] = vg;
           if (store_rows) {
-            rowE[g][off] = os[g] * __expf(xg);
-            if (rowV[g]) rowV[g][off] = vg;
+            rowE[g][off] = narrow<St>(os[g] * __expf(xg));
+            if (rowV[g]) rowV[g][off] = narrow<St>(vg);
           }
           if (save_at(n + 1)) {
             gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p] = xg;
@@ -273,8 +275,8 @@ forward_kernel(FwdArgs a) {
       }
       if (first_row && g < ng) {
         const GroupConst<Real>& c = gc[g];
-        c.E[p] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
-        if (c.V) c.V[p] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+        ((St*)c.E)[p] = narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs));
+        if (c.V) ((St*)c.V)[p] = narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]);
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
@@ -292,8 +294,8 @@ forward_kernel(FwdArgs a) {
           }
           if (store_rows) {
             const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
-            c.E[off] = c.out_scale * Fm<Real>::exp_(x[g], tabs);
-            if (c.V) c.V[off] = (SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g];
+            ((St*)c.E)[off] = narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs));
+            if (c.V) ((St*)c.V)[off] = narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]);
           }
           if (save_at(n + 1)) {
             c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = x[g];
@@ -313,8 +315,8 @@ forward_kernel(FwdArgs a) {
       xs[g][t] = ck_index ? c.CX[ck_index * c.ld + p] : (Real)0;
       vs[g][t] = ck_index ? c.CV[ck_index * c.ld + p] : c.v0;
       if (first_row) {
-        c.E[p] = c.out_scale * Fm<Real>::exp_(xs[g][t], tabs);
-        if (c.V) c.V[p] = (SCHEME == kSchemeFT && vs[g][t] < (Real)0) ? (Real)0 : vs[g][t];
+        ((St*)c.E)[p] = narrow<St>(c.out_scale * Fm<Real>::exp_(xs[g][t], tabs));
+        if (c.V) ((St*)c.V)[p] = narrow<St>((SCHEME == kSchemeFT && vs[g][t] < (Real)0) ? (Real)0 : vs[g][t]);
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
@@ -334,8 +336,8 @@ forward_kernel(FwdArgs a) {
         vs[g][t] = vg;
         if (store_rows) {
           const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
-          c.E[off] = c.out_scale * Fm<Real>::exp_(xg, tabs);
-          if (c.V) c.V[off] = (SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg;
+          ((St*)c.E)[off] = narrow<St>(c.out_scale * Fm<Real>::exp_(xg, tabs));
+          if (c.V) ((St*)c.V)[off] = narrow<St>((SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg);
         }
         if (save_at(n + 1)) {
           c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = xg;
@@ -481,21 +483,29 @@ __global__ void draws_kernel(uint2 key, uint32_t stream_id,
   out[3 * i + 2] = zX;
 }
 
-template <typename Real>
-static void launch_forward_t(const FwdArgs& a, int scheme, cudaStream_t s) {
+template <typename Real, int FMT>
+static void launch_forward_f(const FwdArgs& a, int scheme, cudaStream_t s) {
   const bool seg = a.n0 != 0 || a.n1 != 0 || a.row0 != 1 || !a.store_rows || a.save_states ||
                    a.next_job;
   if (scheme == kSchemeQE) {
-    if (seg) forward_kernel<Real, kSchemeQE, true><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
-    else forward_kernel<Real, kSchemeQE, false><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    if (seg) forward_kernel<Real, kSchemeQE, true, FMT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    else forward_kernel<Real, kSchemeQE, false, FMT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
   } else {
-    if (seg) forward_kernel<Real, kSchemeFT, true><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
-    else forward_kernel<Real, kSchemeFT, false><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    if (seg) forward_kernel<Real, kSchemeFT, true, FMT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
+    else forward_kernel<Real, kSchemeFT, false, FMT><<<a.n_blocks, kFwdBlock, 0, s>>>(a);
   }
+}
+
+template <typename Real>
+static void launch_forward_t(const FwdArgs& a, int scheme, cudaStream_t s) {
+  if (a.store_fmt == kStoreF16) launch_forward_f<Real, kStoreF16>(a, scheme, s);
+  else if (a.store_fmt == kStoreBF16) launch_forward_f<Real, kStoreBF16>(a, scheme, s);
+  else launch_forward_f<Real, kStoreNative>(a, scheme, s);
 }
 
 cudaError_t launch_forward(const FwdArgs& a, int precision, int scheme, cudaStream_t s) {
   if (a.n_blocks == 0) return cudaSuccess;
+  if (a.store_fmt < kStoreNative || a.store_fmt > kStoreBF16) return cudaErrorInvalidValue;
   if (precision == kPrecFP64) launch_forward_t<double>(a, scheme, s);
   else if (precision == kPrecDF) launch_forward_t<df>(a, scheme, s);
   else launch_forward_t<float>(a, scheme, s);

@@ -21,7 +21,7 @@ cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt,
 // out-of-sample pricing pass over the instances' rows and its estimator
 cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
                        const BwdState* state, BwdResult* results, int precision, int basis,
-                       cudaStream_t s);
+                       int fmt, cudaStream_t s);
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
                           DevResult* out, cudaStream_t s);
 // Paths per thread of a backward sub-tile (a sub-tile is kBlock * ppt
@@ -30,10 +30,14 @@ int backward_ppt_default(int precision);
 bool backward_ppt_valid(int precision, int ppt);
 // paths per backward sub-tile
 inline int backward_tile(int ppt) { return kBlock * ppt; }
-// resident backward CTAs per SM
-int backward_occupancy(int precision, int basis, int ppt);
-// bytes of one stored path value (E, V, cash flow) in a precision
+// resident backward CTAs per SM of a kernel variant (fmt: store format)
+int backward_occupancy(int precision, int basis, int ppt, int fmt);
+// bytes of one working-precision value (cash flow, saved state) in a precision
 inline size_t value_bytes(int precision) { return precision == kPrecMixed ? 4 : 8; }
+// bytes of one element of the E/V rows in a precision and store format
+inline size_t row_bytes(int precision, int fmt) {
+  return fmt == kStoreNative ? value_bytes(precision) : 2;
+}
 
 }  // namespace lsmc
 

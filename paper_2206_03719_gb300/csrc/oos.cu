@@ -22,6 +22,7 @@
 #include "exercise.cuh"
 #include "kernels.h"
 #include "plan.h"
+#include "store16.cuh"
 
 namespace lsmc {
 
@@ -87,10 +88,15 @@ __global__ void oos_table_kernel(const BwdInstance* __restrict__ inst) {
   }
 }
 
-template <typename Real, int BASIS>
+template <typename Real, int BASIS, int FMT>
 __global__ void __launch_bounds__(kOosBlock)
 oos_kernel(const BwdInstance* __restrict__ inst) {
+  using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
+  using St = typename RR::raw;
   constexpr int PPT = kOosPpt;
+  // double: candidates are found without the product s1 e (threshold), which
+  // is then formed on the compacted list
+  constexpr bool kProdLate = std::is_same<Real, double>::value;
   // consecutive CTAs take the same path tile of consecutive instances, so
   // the instances of one path group read the tile's rows while they are in L2
   const BwdInstance& I = inst[blockIdx.x];
@@ -101,8 +107,8 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   OosWarpBufs<Real, BASIS>& wb = s_wb[warp];
   const unsigned lane_lt = (1u << lane) - 1u;
-  const Real* E = (const Real*)I.E;
-  const Real* V = (const Real*)I.V;
+  const St* E = (const St*)I.E;
+  const St* V = (const St*)I.V;
   const size_t ld = I.ld;
   const Real* tab = (const Real*)I.oos_tab;
   const int type = I.type;
@@ -123,17 +129,23 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
       const Real* t = tab + (size_t)n * kOosConsts;
       if (!flag_set(t[6])) continue;  // no regression at n: no exercise (uniform)
       const Real s1 = t[7];
-      const Real* En = E + (size_t)(n - 1) * ld + base + tid;
-      const Real* Vn = BASIS == kBasisSV2 ? V + (size_t)(n - 1) * ld + base + tid : nullptr;
+      const St* En = E + (size_t)(n - 1) * ld + base + tid;
+      const St* Vn = BASIS == kBasisSV2 ? V + (size_t)(n - 1) * ld + base + tid : nullptr;
       // all loads of the date first, then the in-the-money tests
+      St er[PPT], vr[PPT];
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        er[k] = vr[k] = (St)0;
+        if (((valid & ~stopped) >> k) & 1u) {
+          er[k] = En[k * kOosBlock];
+          if (BASIS == kBasisSV2) vr[k] = Vn[k * kOosBlock];
+        }
+      }
       Real e[PPT], v[PPT];
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        e[k] = v[k] = (Real)0;
-        if (((valid & ~stopped) >> k) & 1u) {
-          e[k] = En[k * kOosBlock];
-          if (BASIS == kBasisSV2) v[k] = Vn[k * kOosBlock];
-        }
+        e[k] = RR::widen(er[k]);
+        v[k] = RR::widen(vr[k]);
       }
       uint32_t cand = 0;
       int cnt = 0;
@@ -146,7 +158,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
         const unsigned m = __ballot_sync(0xffffffffu, itm);
         if (itm) {
           const int pos = cnt + __popc(m & lane_lt);
-          wb.s[pos] = s1 * e[k];
+          wb.s[pos] = kProdLate ? e[k] : s1 * e[k];
           if (BASIS == kBasisSV2) wb.v[pos] = v[k];
           wb.o[pos] = (unsigned short)(k * 32 + lane);
           cand |= 1u << k;
@@ -160,7 +172,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
         for (int i = 0; i < 6; ++i) b[i] = t[i];
         const Real d1 = t[8], d1lo = t[9];
         for (int j = lane; j < cnt; j += 32) {
-          const Real S = wb.s[j];
+          const Real S = kProdLate ? s1 * wb.s[j] : wb.s[j];
           const Real h = intrinsic<Real>(type, K, S);
           const Real x = qfma(S, invK, (Real)-1);
           Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
@@ -190,12 +202,12 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
   }
   const Real* tN = tab + (size_t)N * kOosConsts;
   const Real sN = tN[7], dNhi = tN[8], dNlo = tN[9];
-  const Real* EN = E + (size_t)(N - 1) * ld + base + tid;
+  const St* EN = E + (size_t)(N - 1) * ld + base + tid;
   double sz = 0.0, sz2 = 0.0, euro = 0.0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     if (!((valid >> k) & 1u)) break;
-    const Real SN = sN * EN[k * kOosBlock];
+    const Real SN = sN * RR::widen(EN[k * kOosBlock]);
     const Real hN = payoff<Real>(type, K, SN);
     const double zN = (double)fma(hN, dNhi, hN * dNlo);
     const double z = ((stopped >> k) & 1u) ? (double)wb.z[k][lane] : zN;
@@ -250,25 +262,33 @@ __global__ void oos_finish_kernel(const BwdInstance* __restrict__ inst, uint32_t
   results[I.out_index] = res;
 }
 
+template <typename Real, int FMT>
+static void launch_oos_f(const BwdInstance* inst, dim3 grid, bool sv2, cudaStream_t s) {
+  if (sv2) oos_kernel<Real, kBasisSV2, FMT><<<grid, kOosBlock, 0, s>>>(inst);
+  else oos_kernel<Real, kBasisS2, FMT><<<grid, kOosBlock, 0, s>>>(inst);
+}
+
 template <typename Real>
-static void launch_oos_t(const BwdInstance* inst, uint32_t n_inst, dim3 grid, bool sv2,
+static void launch_oos_t(const BwdInstance* inst, uint32_t n_inst, dim3 grid, bool sv2, int fmt,
                          cudaStream_t s) {
   oos_table_kernel<Real><<<n_inst, 128, 0, s>>>(inst);
-  if (sv2) oos_kernel<Real, kBasisSV2><<<grid, kOosBlock, 0, s>>>(inst);
-  else oos_kernel<Real, kBasisS2><<<grid, kOosBlock, 0, s>>>(inst);
+  if (fmt == kStoreF16) launch_oos_f<Real, kStoreF16>(inst, grid, sv2, s);
+  else if (fmt == kStoreBF16) launch_oos_f<Real, kStoreBF16>(inst, grid, sv2, s);
+  else launch_oos_f<Real, kStoreNative>(inst, grid, sv2, s);
 }
 
 cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
                        const BwdState* state, BwdResult* results, int precision, int basis,
-                       cudaStream_t s) {
+                       int fmt, cudaStream_t s) {
   if (n_inst == 0 || max_paths == 0) return cudaSuccess;
+  if (fmt < kStoreNative || fmt > kStoreBF16) return cudaErrorInvalidValue;
   const uint32_t tiles = (max_paths + kOosTile - 1) / kOosTile;
   if (tiles > 65535u || n_inst > 0x7fffffffu) return cudaErrorInvalidValue;
   const dim3 grid(n_inst, tiles);
   const bool sv2 = basis == kBasisSV2;
-  if (precision == kPrecFP64) launch_oos_t<double>(inst, n_inst, grid, sv2, s);
-  else if (precision == kPrecDF) launch_oos_t<df>(inst, n_inst, grid, sv2, s);
-  else launch_oos_t<float>(inst, n_inst, grid, sv2, s);
+  if (precision == kPrecFP64) launch_oos_t<double>(inst, n_inst, grid, sv2, fmt, s);
+  else if (precision == kPrecDF) launch_oos_t<df>(inst, n_inst, grid, sv2, fmt, s);
+  else launch_oos_t<float>(inst, n_inst, grid, sv2, fmt, s);
   oos_finish_kernel<<<n_inst, 32, 0, s>>>(inst, n_inst, state, results);
   return cudaGetLastError();
 }

@@ -37,6 +37,9 @@ enum : int32_t { kPrecFP64 = 0, kPrecMixed = 1, kPrecDF = 2 };
 enum : int32_t { kPut = 0, kCall = 1 };
 enum : int32_t { kAmerican = 0, kEuropean = 1 };
 enum : int32_t { kBasisS2 = 0, kBasisSV2 = 1 };
+// element type of the path store (E and V rows): the working precision,
+// IEEE binary16 or bfloat16
+enum : int32_t { kStoreNative = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 
 // error codes written by kernels into Control::error
 enum : uint32_t { kDevErrTimeout = 1, kDevErrBadJob = 2 };
@@ -77,7 +80,7 @@ struct FwdArgs {
   unsigned long long* next_job;  // if set, block 0 stores next_job_value there
   unsigned long long next_job_value;
   uint32_t stream_xor;  // xored into every contract's stream id (pricing paths)
-  uint32_t pad2_;
+  int32_t store_fmt;    // element type of the E/V rows (kStore*)
 };
 
 // ---- STAC-A2 multi-asset path reduction --------------------------------------
@@ -157,6 +160,7 @@ struct BwdArgs {
   unsigned long long timeout_ns;
   uint32_t n_rounds, n_inst;
   uint32_t row0;             // date of E/V row index 0 of the instances' rows
+  int32_t store_fmt;         // element type of the E/V rows (kStore*)
 };
 
 // ---- Greeks ---------------------------------------------------------------

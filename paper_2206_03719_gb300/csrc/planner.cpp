@@ -97,7 +97,10 @@ int validate_request(const lsmc_request& q, int precision, int scheme) {
   if (q.type != LSMC_PUT && q.type != LSMC_CALL) return LSMC_EINVAL;
   if (q.style != LSMC_AMERICAN && q.style != LSMC_EUROPEAN) return LSMC_EINVAL;
   if (q.basis != LSMC_BASIS_S2 && q.basis != LSMC_BASIS_SV2) return LSMC_EINVAL;
-  if (q.flags & ~(uint32_t)(LSMC_FLAG_REGENERATE | LSMC_FLAG_OUT_OF_SAMPLE)) return LSMC_EINVAL;
+  if (q.flags & ~(uint32_t)(LSMC_FLAG_REGENERATE | LSMC_FLAG_OUT_OF_SAMPLE |
+                            LSMC_FLAG_STORE_FP16 | LSMC_FLAG_STORE_BF16))
+    return LSMC_EINVAL;
+  if ((q.flags & LSMC_FLAG_STORE_FP16) && (q.flags & LSMC_FLAG_STORE_BF16)) return LSMC_EINVAL;
   if (q.n_paths == 0 || q.n_steps == 0 || q.n_strikes == 0 || !q.strikes) return LSMC_EINVAL;
   if (q.n_paths > (1u << 30) || q.n_steps > (1u << 20) || q.n_strikes > 4096) return LSMC_EINVAL;
   for (uint32_t k = 0; k < q.n_strikes; ++k)
@@ -189,6 +192,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
   *L = PlanLayout();
   L->opt = opt;
   const size_t real = value_bytes(opt.precision);
+  const size_t rowb = row_bytes(opt.precision, opt.store);  // an element of the E/V rows
   const uint32_t tile0 = (uint32_t)backward_tile(plan_ppt(opt));
   const bool store_v = opt.basis == LSMC_BASIS_SV2;
   // device offsets are relative to the region starts; the caller binds them
@@ -226,10 +230,10 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         // of dates c..c + ck_stride (ck_stride + 1 rows)
         const size_t rows = opt.regen ? (size_t)opt.ck_stride + 1 : (size_t)N;
         L->group_E_off.push_back(off_paths);
-        off_paths += round_up(rows * ld * real, 256);
+        off_paths += round_up(rows * ld * rowb, 256);
         if (store_v) {
           L->group_V_off.push_back(off_paths);
-          off_paths += round_up(rows * ld * real, 256);
+          off_paths += round_up(rows * ld * rowb, 256);
         } else {
           L->group_V_off.push_back(SIZE_MAX);
         }

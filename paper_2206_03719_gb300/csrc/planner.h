@@ -61,6 +61,7 @@ struct PlanOptions {
   bool regen = false;
   uint32_t ck_stride = 0;
   bool oos = false;             // out-of-sample pricing pass
+  int store = 0;                // element type of the E/V rows (kStore*)
 };
 
 // Paths per lane of a plan's backward sub-tiles.

@@ -22,6 +22,8 @@ LSMC_SCHEME_QE, LSMC_SCHEME_FT_EULER = 0, 1
 LSMC_BASIS_S2, LSMC_BASIS_SV2 = 0, 1
 LSMC_FLAG_REGENERATE = 1
 LSMC_FLAG_OUT_OF_SAMPLE = 2
+LSMC_FLAG_STORE_FP16 = 4
+LSMC_FLAG_STORE_BF16 = 8
 LSMC_FP64, LSMC_MIXED, LSMC_DF = 0, 1, 2
 LSMC_GREEK_DELTA, LSMC_GREEK_GAMMA, LSMC_GREEK_VEGA = 1, 2, 4
 LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31

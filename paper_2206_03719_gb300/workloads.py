@@ -50,6 +50,7 @@ class Workload:
     stream: int = 0
     regenerate: bool = False     # no path store: regenerate segments from checkpoints
     out_of_sample: bool = False  # price the regression policy on independent paths
+    store: str = "native"        # path store element: "native", "fp16" or "bf16"
 
     def replace(self, **kw) -> "Workload":
         return dataclasses.replace(self, **kw)

@@ -31,7 +31,9 @@ def oracle_for(wl, grid=oracle.GRID_F64, n_threads=None):
         style=oracle.AMERICAN if wl.style == "american" else oracle.EUROPEAN,
         scheme=oracle.QE if wl.scheme == "qe" else oracle.FT_EULER, grid=grid,
         basis=oracle.BASIS_S2 if wl.basis == "s2" else oracle.BASIS_SV2, b=b, seed=wl.seed,
-        stream=wl.stream, n_threads=n_threads)
+        stream=wl.stream, n_threads=n_threads, out_of_sample=wl.out_of_sample,
+        store={"native": oracle.STORE_NATIVE, "fp16": oracle.STORE_F16,
+               "bf16": oracle.STORE_BF16}[wl.store])
 
 
 FP64_TOL = 1e-10     # FP64 GPU vs FP64 oracle on identical streams

@@ -68,7 +68,7 @@ def test_regenerate_rejections(ctx):
         ctx.price_book([a, workloads.SMALL_FP64])
     assert e.value.status == L.LSMC_ENOTIMPL
     r = api.Request(workloads.SMALL_FP64)
-    r.c.flags = 6
+    r.c.flags = 16  # no such flag
     with pytest.raises(L.LsmcError) as e:
         L.lsmc_price_request(ctx.ctx, r.c)
     assert e.value.status == L.LSMC_EINVAL
