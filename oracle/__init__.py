@@ -109,6 +109,10 @@ def lib():
             dp, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int,
             ctypes.c_int, ctypes.c_int, ctypes.POINTER(Bumps), ctypes.c_uint64,
             ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(Result), dp]
+        L.orc_dual_bound.argtypes = [
+            ctypes.POINTER(Heston), ctypes.c_int, ctypes.c_double, dp, ctypes.c_uint32,
+            ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, dp]
         L.orc_round_f16.argtypes = [ctypes.c_double]
         L.orc_round_f16.restype = ctypes.c_double
         L.orc_round_bf16.argtypes = [ctypes.c_double]
@@ -306,6 +310,21 @@ def round_store(x, store):
     y = np.empty_like(x)
     lib().orc_round_n(_ptr(x, ctypes.c_double), _ptr(y, ctypes.c_double), x.size, int(store))
     return y
+
+
+def dual_bound(model: Heston, strikes, T, P, N, n_outer, n_inner, *, type_=PUT, scheme=QE,
+               grid=GRID_F64, basis=BASIS_S2, seed=42, stream=0, n_threads=None):
+    """Lower (out-of-sample) and dual upper bounds of the American price per
+    strike: list of dicts lower, lower_se, upper, upper_se, pi_N, pi_N_se."""
+    strikes = np.ascontiguousarray(strikes, dtype=np.float64).reshape(-1)
+    out = np.empty(6 * strikes.size, dtype=np.float64)
+    rc = lib().orc_dual_bound(ctypes.byref(model), type_, T, _ptr(strikes, ctypes.c_double),
+                              strikes.size, P, N, scheme, grid, basis, seed, stream, n_outer,
+                              n_inner, n_threads or default_threads(), _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("orc_dual_bound rejected its arguments (%d)" % rc)
+    names = ("lower", "lower_se", "upper", "upper_se", "pi_N", "pi_N_se")
+    return [dict(zip(names, out[6 * k: 6 * k + 6])) for k in range(strikes.size)]
 
 
 def price_greeks(model: Heston, strikes, T, P, N, *, type_=PUT, style=AMERICAN,

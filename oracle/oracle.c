@@ -680,6 +680,213 @@ int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const dou
 }
 
 /* ------------------------------------------------------------------------ */
+/* Dual (Andersen-Broadie primal-dual) upper bound of the American price.   */
+/* The exercise policy is the one fitted by the regressions on the paths of */
+/* `stream`.  Outer paths: the first n_outer paths of the pricing stream     */
+/* (stream ^ 0x80000000).  Along outer path p, at every date n = 0..N-1, the */
+/* value of continuing and following the policy from n + 1 on,              */
+/* Q_n = E_n[Z_tau], Z the payoff discounted to t_0, is estimated by the     */
+/* mean over n_inner inner paths started from the outer state (x_n, v_n);   */
+/* inner path j draws from counter (j, m, stream ^ 0x40000000, 1 + p N + n) */
+/* for its step from date m.  The policy's value process is L_n = Z_n where  */
+/* the policy exercises (L_N = Z_N) and Q_n elsewhere; the martingale        */
+/* pi_0 = 0, pi_{n+1} = pi_n + L_{n+1} - Q_n (the part of L's change that is */
+/* not predictable at n); the bound is the mean over outer paths of         */
+/* max_{n = 0..N} (Z_n - pi_n), which no stopping rule can beat in          */
+/* expectation.                                                              */
+/* ------------------------------------------------------------------------ */
+/* the payoff h discounted from date n to t_0 by n one-step factors D, as   */
+/* orc_lsmc_oos does it */
+static double orc_disc(double h, uint32_t n, double D) {
+  for (uint32_t i = 0; i < n; ++i) h *= D;
+  return h;
+}
+
+/* 1 where the policy with date-n coefficients beta_n (NaN: no regression)  */
+/* exercises at spot s, stored variance v; *h = the payoff                  */
+static int orc_policy_exercises(int type, int basis, double K, double theta,
+                                const double* beta_n, double s, double v, double* h) {
+  *h = orc_payoff(type, K, s);
+  if (isnan(beta_n[0]) || !(*h > 0.0)) return 0;
+  double phi[6];
+  const int B = orc_basis(basis, s, v, K, theta, phi);
+  double cont = 0.0;
+  for (int i = 0; i < B; ++i) cont += beta_n[i] * phi[i];
+  return *h > cont;
+}
+
+/* one step of the scheme from (x, v); *vs = the stored variance (max(v, 0)
+ * under full truncation) */
+static void orc_step(const orc_heston* m, double dt, int scheme, const double d[3], double* x,
+                     double* v, double* vs) {
+  if (scheme == ORC_QE) {
+    double o[2];
+    orc_qe_step(m, dt, *x, *v, d[0], d[1], d[2], o);
+    *x = o[0]; *v = o[1]; *vs = o[1];
+  } else {
+    double o[3];
+    orc_ft_step(m, dt, *x, *v, d[1], d[2], o);
+    *x = o[0]; *v = o[1]; *vs = o[2];
+  }
+}
+
+typedef struct {
+  const orc_heston* m;
+  double T, dt, D;
+  int type, scheme, grid, basis;
+  uint32_t N, n_strikes, n_inner, n_outer;
+  uint64_t seed;
+  uint32_t stream;
+  const double* strikes;
+  const double* beta;  /* n_strikes x N x 6 */
+  double* dmax;        /* n_strikes x n_outer: max_n (Z_n - pi_n) */
+  double* piN;         /* n_strikes x n_outer: pi_N */
+  int rc;
+} orc_dual_ctx;
+
+static void orc_dual_path(void* vctx, uint32_t p) {
+  orc_dual_ctx* c = (orc_dual_ctx*)vctx;
+  const uint32_t N = c->N, nk = c->n_strikes;
+  const double theta = c->m->theta, S0 = c->m->S0;
+  double* xs = (double*)malloc(sizeof(double) * (N + 1));
+  double* vs = (double*)malloc(sizeof(double) * (N + 1));   /* state */
+  double* vb = (double*)malloc(sizeof(double) * (N + 1));   /* stored */
+  double* Q = (double*)malloc(sizeof(double) * (size_t)nk * N);
+  double* z = (double*)malloc(sizeof(double) * nk);
+  int* done = (int*)malloc(sizeof(int) * nk);
+  if (!xs || !vs || !vb || !Q || !z || !done) {
+    c->rc = -2;
+    free(xs); free(vs); free(vb); free(Q); free(z); free(done);
+    return;
+  }
+  /* the outer path: pricing stream, path p */
+  xs[0] = 0.0; vs[0] = c->m->v0; vb[0] = c->m->v0;
+  for (uint32_t n = 0; n < N; ++n) {
+    double d[3], x = xs[n], v = vs[n], w;
+    orc_draws(c->seed, c->stream ^ 0x80000000u, p, n, c->grid, d);
+    orc_step(c->m, c->dt, c->scheme, d, &x, &v, &w);
+    xs[n + 1] = x; vs[n + 1] = v; vb[n + 1] = w;
+  }
+  /* inner estimates Q_n for every date and strike */
+  for (uint32_t n = 0; n < N; ++n) {
+    for (uint32_t k = 0; k < nk; ++k) Q[(size_t)k * N + n] = 0.0;
+    for (uint32_t j = 0; j < c->n_inner; ++j) {
+      double x = xs[n], v = vs[n];
+      uint32_t left = nk;
+      for (uint32_t k = 0; k < nk; ++k) done[k] = 0;
+      for (uint32_t m = n; m < N && left > 0; ++m) {
+        double d[3], w;
+        orc_draws_asset(c->seed, c->stream ^ 0x40000000u, j, m, 1u + p * N + n, c->grid, d);
+        orc_step(c->m, c->dt, c->scheme, d, &x, &v, &w);
+        const double s = S0 * exp(x);
+        const uint32_t date = m + 1;
+        for (uint32_t k = 0; k < nk; ++k) {
+          if (done[k]) continue;
+          double h;
+          if (date < N) {
+            if (!orc_policy_exercises(c->type, c->basis, c->strikes[k], theta,
+                                      c->beta + ((size_t)k * N + date) * 6, s, w, &h))
+              continue;
+          } else {
+            h = orc_payoff(c->type, c->strikes[k], s);
+          }
+          z[k] = orc_disc(h, date, c->D);
+          done[k] = 1;
+          --left;
+        }
+      }
+      for (uint32_t k = 0; k < nk; ++k) Q[(size_t)k * N + n] += z[k];
+    }
+    for (uint32_t k = 0; k < nk; ++k) Q[(size_t)k * N + n] /= (double)c->n_inner;
+  }
+  /* the martingale and the pathwise maximum, per strike */
+  for (uint32_t k = 0; k < nk; ++k) {
+    const double K = c->strikes[k];
+    double pi = 0.0;
+    double best = orc_payoff(c->type, K, S0);  /* n = 0: Z_0 - pi_0 */
+    for (uint32_t n = 0; n < N; ++n) {
+      const uint32_t date = n + 1;
+      const double s = S0 * exp(xs[date]);
+      double h, L;
+      if (date < N) {
+        const int ex = orc_policy_exercises(c->type, c->basis, K, theta,
+                                            c->beta + ((size_t)k * N + date) * 6, s, vb[date], &h);
+        L = ex ? orc_disc(h, date, c->D) : Q[(size_t)k * N + date];
+      } else {
+        h = orc_payoff(c->type, K, s);
+        L = orc_disc(h, N, c->D);
+      }
+      pi += L - Q[(size_t)k * N + n];
+      const double Z = orc_disc(h, date, c->D);
+      if (Z - pi > best) best = Z - pi;
+    }
+    c->dmax[(size_t)k * c->n_outer + p] = best;
+    c->piN[(size_t)k * c->n_outer + p] = pi;
+  }
+  free(xs); free(vs); free(vb); free(Q); free(z); free(done);
+}
+
+int orc_dual_bound(const orc_heston* m, int type, double T, const double* strikes,
+                   uint32_t n_strikes, uint32_t P, uint32_t N, int scheme, int grid, int basis,
+                   uint64_t seed, uint32_t stream, uint32_t n_outer, uint32_t n_inner,
+                   int n_threads, double* out) {
+  if (!m || !strikes || !out || n_strikes == 0 || P == 0 || N == 0 || n_outer == 0 ||
+      n_inner == 0 || n_outer > P)
+    return -1;
+  if (!orc_model_ok(m, T, scheme)) return -1;
+  if ((uint64_t)n_outer * N + 1 > 0xffffffffull) return -1;
+  const size_t cells = (size_t)(N + 1) * P;
+  double* SA = (double*)malloc(sizeof(double) * cells);
+  double* VA = (double*)malloc(sizeof(double) * cells);
+  double* SB = (double*)malloc(sizeof(double) * cells);
+  double* VB = (double*)malloc(sizeof(double) * cells);
+  double* beta = (double*)malloc(sizeof(double) * (size_t)n_strikes * N * 6);
+  double* dmax = (double*)malloc(sizeof(double) * (size_t)n_strikes * n_outer);
+  double* piN = (double*)malloc(sizeof(double) * (size_t)n_strikes * n_outer);
+  int rc = 0;
+  if (!SA || !VA || !SB || !VB || !beta || !dmax || !piN) { rc = -2; goto done; }
+  rc = orc_paths(m, T, scheme, grid, P, N, seed, stream, SA, VA, n_threads);
+  if (!rc) rc = orc_paths(m, T, scheme, grid, P, N, seed, stream ^ 0x80000000u, SB, VB, n_threads);
+  for (uint32_t k = 0; k < n_strikes && !rc; ++k) {
+    double ins[4], oos[4];
+    uint32_t ns = 0;
+    rc = orc_lsmc(SA, VA, P, N, m->S0, strikes[k], T, m->r, m->theta, type, ORC_AMERICAN,
+                  basis, ins, &ns, beta + (size_t)k * N * 6, NULL);
+    if (!rc)
+      rc = orc_lsmc_oos(SA, VA, SB, VB, P, N, m->S0, strikes[k], T, m->r, m->theta, type,
+                        ORC_AMERICAN, basis, oos, &ns);
+    out[(size_t)k * 6 + 0] = oos[0];
+    out[(size_t)k * 6 + 1] = oos[1];
+  }
+  if (rc) goto done;
+  {
+    orc_dual_ctx c = {m, T, T / (double)N, exp(-m->r * (T / (double)N)), type, scheme, grid,
+                      basis, N, n_strikes, n_inner, n_outer, seed, stream, strikes, beta,
+                      dmax, piN, 0};
+    orc_parallel_for(n_outer, n_threads, orc_dual_path, &c);
+    rc = c.rc;
+    for (uint32_t k = 0; k < n_strikes && !rc; ++k) {
+      double s = 0.0, s2 = 0.0, t = 0.0, t2 = 0.0;
+      for (uint32_t p = 0; p < n_outer; ++p) {
+        const double d = dmax[(size_t)k * n_outer + p], q = piN[(size_t)k * n_outer + p];
+        s += d; s2 += d * d; t += q; t2 += q * q;
+      }
+      const double n = (double)n_outer;
+      const double mean = s / n, mq = t / n;
+      const double var = n_outer > 1 ? (s2 - n * mean * mean) / (n - 1.0) : 0.0;
+      const double vq = n_outer > 1 ? (t2 - n * mq * mq) / (n - 1.0) : 0.0;
+      out[(size_t)k * 6 + 2] = mean;
+      out[(size_t)k * 6 + 3] = var > 0.0 ? sqrt(var / n) : 0.0;
+      out[(size_t)k * 6 + 4] = mq;
+      out[(size_t)k * 6 + 5] = vq > 0.0 ? sqrt(vq / n) : 0.0;
+    }
+  }
+done:
+  free(SA); free(VA); free(SB); free(VB); free(beta); free(dmax); free(piN);
+  return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Bump-and-revalue scenarios (the paper gives no Greek method; the Greeks  */
 /* are central finite differences under common random numbers: every       */
 /* scenario re-simulates with the same counters).                           */

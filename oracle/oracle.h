@@ -168,6 +168,20 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
                         int out_of_sample, int store, int n_threads, orc_result* out,
                         double* scen_prices);
 
+/* Dual (Andersen-Broadie) upper bound of the American price for each strike,
+ * with the exercise policy fitted on the P paths of `stream` (in-sample
+ * regressions).  out[k*6 + 0..5]: lower bound (out-of-sample estimator on the
+ * P pricing paths of stream ^ 0x80000000) and its standard error, upper
+ * bound (mean over the first n_outer pricing paths of max_n (Z_n - pi_n))
+ * and its standard error, the mean of the martingale at maturity pi_N and
+ * its standard error (zero in expectation).  Inner path j of outer path p
+ * started at date n draws from counter (j, m, stream ^ 0x40000000,
+ * 1 + p N + n) for its step from date m.  Returns 0 or < 0. */
+int orc_dual_bound(const orc_heston* m, int type, double T, const double* strikes,
+                   uint32_t n_strikes, uint32_t P, uint32_t N, int scheme, int grid, int basis,
+                   uint64_t seed, uint32_t stream, uint32_t n_outer, uint32_t n_inner,
+                   int n_threads, double* out);
+
 /* Rounding to nearest, ties to even, from a double to IEEE binary16 and to
  * bfloat16 (returned as doubles; overflow gives infinity). */
 double orc_round_f16(double x);
