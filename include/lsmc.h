@@ -109,6 +109,17 @@ typedef struct lsmc_result {
   uint32_t n_near_ties;
 } lsmc_result;
 
+/* Bounds of one strike's American price (lsmc_price_bounds). */
+typedef struct lsmc_bounds {
+  double lower, lower_se;   /* out-of-sample estimator: the policy on independent paths */
+  double upper, upper_se;   /* dual upper bound */
+  double martingale_end;    /* mean over outer paths of the martingale at maturity */
+  double martingale_end_se; /* (zero in expectation; a diagnostic) */
+  double dual_ms;           /* device time of the dual pass (all strikes) */
+  uint32_t n_near_ties;     /* exercise decisions within rounding reach of their threshold */
+  int32_t status;           /* as lsmc_result.status */
+} lsmc_bounds;
+
 typedef struct lsmc_config {
   int32_t device;        /* CUDA device ordinal */
   int32_t precision;     /* default LSMC_FP64 / LSMC_MIXED */
@@ -254,6 +265,24 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                   uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
 /* Destroy every plan before the context it was created on. */
 void lsmc_plan_destroy(lsmc_plan* plan);
+
+/* Lower and upper bounds of the American price of every strike of one
+ * request (the request's bumps are ignored: base scenario only).  The
+ * regressions on the request's paths (stream_id) fix an exercise policy
+ * (Sec. 2.2.1's Longstaff-Schwartz stage).  Lower bound: that policy applied
+ * to independent paths (stream_id ^ 0x80000000, as LSMC_FLAG_OUT_OF_SAMPLE).
+ * Upper bound: the dual bound of Andersen and Broadie over the first n_outer
+ * of those paths: along each, at every date, n_inner inner paths (Philox
+ * counter (j, m, stream_id ^ 0x40000000, 1 + p n_steps + n) for inner path j
+ * of outer path p started at date n, step from date m) estimate the value of
+ * continuing under the policy; the policy's value process gives a martingale
+ * pi, and the bound is the mean of max_n (Z_n - pi_n), Z the payoff
+ * discounted to t_0.  Work ~ n_outer n_inner n_steps^2 / 2 path steps.
+ * outs: host, n_strikes entries.  LSMC_EINVAL: European style, n_outer = 0
+ * or > n_paths, n_inner = 0, more than 16 strikes, n_outer n_steps >= 2^31;
+ * LSMC_ENOTIMPL with LSMC_FLAG_REGENERATE.  Synchronous. */
+int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
+                      uint32_t n_inner, lsmc_bounds* outs);
 
 /* ---- serving: continuous batching -------------------------------------- */
 /* Queues a copy of *req; returns a ticket.  Whenever a slot

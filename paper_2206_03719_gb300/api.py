@@ -105,6 +105,12 @@ class Context:
         req = Request(wl, **kw)
         return [r.as_dict() for r in L.lsmc_price_request(self.ctx, req.c)]
 
+    def price_bounds(self, wl: Workload, n_outer: int, n_inner: int, **kw) -> List[dict]:
+        """Lower (out-of-sample) and dual upper bounds of each strike's
+        American price (base scenario)."""
+        req = Request(wl, **kw)
+        return [b.as_dict() for b in L.lsmc_price_bounds(self.ctx, req.c, n_outer, n_inner)]
+
     def price_book(self, wls: Sequence[Workload], **kw) -> List[dict]:
         reqs = [Request(w, **kw) for w in wls]
         return [r.as_dict() for r in L.lsmc_price_book(self.ctx, [q.c for q in reqs])]

@@ -881,6 +881,102 @@ int lsmc_price_book(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, lsmc_resu
   return rc;
 }
 
+int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
+                      uint32_t n_inner, lsmc_bounds* outs) {
+  if (!ctx || !req || !outs) return LSMC_EINVAL;
+  if (req->style != LSMC_AMERICAN || n_outer == 0 || n_inner == 0 ||
+      n_outer > req->n_paths || req->n_strikes == 0 ||
+      req->n_strikes > (uint32_t)kMaxDualStrikes ||
+      (uint64_t)n_outer * req->n_steps + 1 > 0x7fffffffull)
+    return LSMC_EINVAL;
+  if (req->flags & LSMC_FLAG_REGENERATE) return LSMC_ENOTIMPL;
+  // the base scenario only, with the policy's coefficients kept and priced
+  // out of sample: the lower bound
+  lsmc_request q = *req;
+  q.bumps.greek_mask = 0;
+  q.flags |= LSMC_FLAG_OUT_OF_SAMPLE;
+  lsmc_plan* p = nullptr;
+  int rc = lsmc_plan_create(ctx, &q, 1, &p);
+  if (rc) return rc;
+  const uint32_t nk = q.n_strikes, N = q.n_steps;
+  std::vector<lsmc_result> res(nk);
+  rc = plan_launch(p, false);
+  if (rc == LSMC_OK) rc = plan_collect(p, res.data());
+  if (rc) { plan_free(p); return rc; }
+  const PlanLayout& L = p->L;
+  const int prec = L.opt.precision;
+  DualArgs a{};
+  a.inst = p->d_inst;
+  for (uint32_t k = 0; k < nk; ++k) {
+    const int32_t slot = L.greeks[k].res[kScBase];
+    for (size_t i = 0; i < L.inst.size(); ++i)
+      if ((int32_t)L.inst[i].out_index == slot) a.inst_of_strike[k] = (uint32_t)i;
+  }
+  a.group = L.groups[L.contracts[0].group0];
+  a.seed = q.seed;
+  a.stream = q.stream_id;
+  a.type = q.type;
+  a.N = N;
+  a.n_outer = n_outer;
+  a.n_inner = n_inner;
+  a.n_strikes = nk;
+  const size_t real = value_bytes(prec);
+  const size_t bx = align256((size_t)(N + 1) * n_outer * real);
+  const size_t bq = align256((size_t)nk * n_outer * N * 8);
+  const size_t bd = align256((size_t)nk * n_outer * 8);
+  const size_t bti = align256((size_t)n_outer * N * 4);
+  const size_t btm = align256((size_t)nk * n_outer * 4);
+  const size_t bo = align256((size_t)nk * kDualOut * 8);
+  const size_t total = 2 * bx + bq + 2 * bd + bti + btm + bo;
+  char* mem = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<double> o((size_t)nk * kDualOut, 0.0);
+  float ms = 0.0f;
+  cudaError_t ce = cudaMallocAsync((void**)&mem, total, p->stream);
+  if (ce == cudaSuccess) {
+    char* c = mem;
+    a.X = c; c += bx;
+    a.V = c; c += bx;
+    a.Q = (double*)c; c += bq;
+    a.dmax = (double*)c; c += bd;
+    a.piN = (double*)c; c += bd;
+    a.inner_ties = (uint32_t*)c; c += bti;
+    a.max_ties = (uint32_t*)c; c += btm;
+    a.out = (double*)c;
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e0, p->stream);
+    if (ce == cudaSuccess) ce = launch_dual(a, prec, L.opt.scheme, L.opt.basis, p->stream);
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, p->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(o.data(), a.out, o.size() * 8, cudaMemcpyDeviceToHost, p->stream);
+    cudaFreeAsync(mem, p->stream);
+    const cudaError_t se = cudaStreamSynchronize(p->stream);
+    if (ce == cudaSuccess) ce = se;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  plan_free(p);
+  if (ce != cudaSuccess) return cuda_status(ce);
+  double ties = 0.0;
+  for (uint32_t k = 0; k < nk; ++k) ties += o[(size_t)k * kDualOut + 4];
+  for (uint32_t k = 0; k < nk; ++k) {
+    lsmc_bounds& b = outs[k];
+    const double* ok = o.data() + (size_t)k * kDualOut;
+    b.lower = res[k].price;
+    b.lower_se = res[k].price_se;
+    b.upper = ok[0];
+    b.upper_se = ok[1];
+    b.martingale_end = ok[2];
+    b.martingale_end_se = ok[3];
+    b.dual_ms = ms;
+    b.n_near_ties = res[k].n_near_ties + (uint32_t)ties;
+    b.status = res[k].status;
+  }
+  return LSMC_OK;
+}
+
 // ---- serving -------------------------------------------------------------------
 int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket) {
   if (!ctx || !req || !ticket) return LSMC_EINVAL;

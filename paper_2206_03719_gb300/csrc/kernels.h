@@ -22,6 +22,9 @@ cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt,
 cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
                        const BwdState* state, BwdResult* results, int precision, int basis,
                        int fmt, cudaStream_t s);
+// dual upper bound of the strikes of one request (the plan's policy tables
+// must be filled: after launch_oos)
+cudaError_t launch_dual(const DualArgs& a, int precision, int scheme, int basis, cudaStream_t s);
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
                           DevResult* out, cudaStream_t s);
 // Paths per thread of a backward sub-tile (a sub-tile is kBlock * ppt

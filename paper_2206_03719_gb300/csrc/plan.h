@@ -163,6 +163,28 @@ struct BwdArgs {
   int32_t store_fmt;         // element type of the E/V rows (kStore*)
 };
 
+// ---- dual upper bound ------------------------------------------------------
+constexpr int kMaxDualStrikes = 16;  // strikes of one request in the dual pass
+constexpr int kDualOut = 8;          // doubles of output per strike
+struct DualArgs {
+  const BwdInstance* inst;           // the plan's instances (policy tables oos_tab)
+  uint32_t inst_of_strike[kMaxDualStrikes];
+  FwdGroup group;                    // the base simulation's model
+  uint64_t seed;
+  uint32_t stream;                   // the request's stream id
+  int32_t type;
+  uint32_t N, n_outer, n_inner, n_strikes;
+  void* X;                           // (N + 1) x n_outer outer log prices (working precision)
+  void* V;                           // the same for the variance (state)
+  double* Q;                         // n_strikes x n_outer x N inner estimates
+  double* dmax;                      // n_strikes x n_outer pathwise maxima
+  double* piN;                       // n_strikes x n_outer martingale at maturity
+  uint32_t* inner_ties;              // n_outer x N near ties of the inner rules
+  uint32_t* max_ties;                // n_strikes x n_outer near ties along the outer paths
+  double* out;                       // n_strikes x kDualOut: bound, its standard error,
+                                     // mean pi_N, its standard error, near ties
+};
+
 // ---- Greeks ---------------------------------------------------------------
 // device mirror of lsmc_result (same layout; checked in capi.cpp)
 struct DevResult {

@@ -31,7 +31,7 @@ LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31
 EXPORTS = [
     "lsmc_strerror", "lsmc_abi_version", "lsmc_create", "lsmc_destroy",
     "lsmc_set_stream", "lsmc_set_workspace", "lsmc_request_footprint",
-    "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book",
+    "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book", "lsmc_price_bounds",
     "lsmc_plan_create", "lsmc_plan_launch", "lsmc_plan_fetch",
     "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
     "lsmc_plan_set_timing", "lsmc_plan_kernel_times", "lsmc_autotune",
@@ -64,6 +64,16 @@ class lsmc_result(ctypes.Structure):
                  "european_price")] + [
         ("n_singular_solves", ctypes.c_uint32), ("n_revaluations", ctypes.c_uint32),
         ("status", ctypes.c_int32), ("n_near_ties", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class lsmc_bounds(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("lower", "lower_se", "upper", "upper_se", "martingale_end",
+                 "martingale_end_se", "dual_ms")] + [
+        ("n_near_ties", ctypes.c_uint32), ("status", ctypes.c_int32)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -133,6 +143,8 @@ def load(build_if_missing: bool = False):
                                    P(lsmc_bumps), u64, P(lsmc_result)], ctypes.c_int),
             "lsmc_price_request": ([vp, P(lsmc_request), P(lsmc_result)], ctypes.c_int),
             "lsmc_price_book": ([vp, P(lsmc_request), sz, P(lsmc_result)], ctypes.c_int),
+            "lsmc_price_bounds": ([vp, P(lsmc_request), ctypes.c_uint32, ctypes.c_uint32,
+                                   P(lsmc_bounds)], ctypes.c_int),
             "lsmc_plan_create": ([vp, P(lsmc_request), sz, P(vp)], ctypes.c_int),
             "lsmc_plan_launch": ([vp, i32], ctypes.c_int),
             "lsmc_plan_fetch": ([vp, P(lsmc_result)], ctypes.c_int),
@@ -232,6 +244,13 @@ def lsmc_price_book(ctx, reqs):
     total = sum(r.n_strikes for r in reqs)
     outs = (lsmc_result * total)()
     check(load().lsmc_price_book(ctx, arr, len(reqs), outs), "lsmc_price_book")
+    return list(outs)
+
+
+def lsmc_price_bounds(ctx, req, n_outer, n_inner):
+    outs = (lsmc_bounds * req.n_strikes)()
+    check(load().lsmc_price_bounds(ctx, ctypes.byref(req), n_outer, n_inner, outs),
+          "lsmc_price_bounds")
     return list(outs)
 
 

@@ -51,9 +51,9 @@ def test_struct_layouts_match_header(lib, tmp_path):
 #include <stddef.h>
 #include "lsmc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsmc_heston), sizeof(lsmc_contract),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(lsmc_heston), sizeof(lsmc_contract),
          sizeof(lsmc_bumps), sizeof(lsmc_result), sizeof(lsmc_config), sizeof(lsmc_request),
-         sizeof(lsmc_plan_info));
+         sizeof(lsmc_plan_info), sizeof(lsmc_bounds));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(lsmc_request, strikes), offsetof(lsmc_request, bumps),
          offsetof(lsmc_request, seed), offsetof(lsmc_result, n_singular_solves),
          offsetof(lsmc_config, hbm_budget));
@@ -65,7 +65,7 @@ int main(void) {
     sizes, offs = [list(map(int, l.split())) for l in subprocess.check_output([str(exe)]).decode().split("\n")[:2]]
     assert sizes == [ctypes.sizeof(t) for t in (L.lsmc_heston, L.lsmc_contract, L.lsmc_bumps,
                                                    L.lsmc_result, L.lsmc_config, L.lsmc_request,
-                                                   L.lsmc_plan_info)]
+                                                   L.lsmc_plan_info, L.lsmc_bounds)]
     assert offs == [L.lsmc_request.strikes.offset, L.lsmc_request.bumps.offset,
                     L.lsmc_request.seed.offset, L.lsmc_result.n_singular_solves.offset,
                     L.lsmc_config.hbm_budget.offset]
