@@ -74,6 +74,8 @@ def parse():
                     help="price the regression policy on independent paths")
     ap.add_argument("--store", default="native", choices=["native", "fp16", "bf16"],
                     help="element type of the path store")
+    ap.add_argument("--extra", default="",
+                    help="run only this side measurement and print it (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -338,6 +340,34 @@ def measure_store16(api, L, torch, reps=2, paths=65536):
     return out
 
 
+def measure_dual(api, L, torch):
+    """Lower (out-of-sample) and dual upper bounds of the paper-size book's
+    five strikes (base scenario), with the dual pass's device time; inner
+    path-steps counted as the most the inner paths can take,
+    n_outer n_inner N (N + 1) / 2 (they stop early when every strike's rule
+    has exercised)."""
+    out = {}
+    for prec, n_outer, n_inner in (("df", 1024, 128), ("fp64", 256, 128), ("mixed", 1024, 128),
+                                   ("df", 8192, 64)):
+        wl = workloads.PAPER_FP64.replace(precision=prec)
+        need = L.lsmc_request_footprint(None, api.Request(wl).c)
+        with api.Context(workspace_bytes=need + (512 << 20)) as ctx:
+            ctx.price_bounds(wl, 64, 8)  # warm-up (module load, allocator)
+            b = ctx.price_bounds(wl, n_outer, n_inner)
+        N = wl.n_steps
+        steps = n_outer * n_inner * N * (N + 1) / 2
+        out["%s_%dx%d" % (prec, n_outer, n_inner)] = {
+            "dual_ms": b[0]["dual_ms"],
+            "inner_path_steps_per_s_at_most": steps / (b[0]["dual_ms"] / 1e3),
+            "strikes": [{"K": K, "lower": x["lower"], "lower_se": x["lower_se"],
+                         "upper": x["upper"], "upper_se": x["upper_se"],
+                         "gap": x["upper"] - x["lower"],
+                         "martingale_end": x["martingale_end"],
+                         "martingale_end_se": x["martingale_end_se"],
+                         "n_near_ties": x["n_near_ties"]} for K, x in zip(wl.strikes, b)]}
+    return out
+
+
 def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     """Uneven book (512 contracts, all bump scenarios, in the given precision)
     in launches of `chunk` contracts, each captured once in a CUDA
@@ -467,6 +497,29 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     return served
 
 
+def extra_jobs():
+    """The measurements reported beside the headline (name, function)."""
+    df_paper = workloads.PAPER_FP64.replace(
+        precision="df", name="american-put-heston-131072x252-5strikes-df")
+    df_large = workloads.LARGE_MIXED.replace(
+        precision="df", name="american-put-heston-1048576x252-5strikes-df")
+    jobs = (("precision_split", lambda *a: {
+                "df_paper": measure_precision(*a, df_paper),
+                "df_large": measure_precision(*a, df_large),
+                "mixed_large": measure_precision(*a, workloads.LARGE_MIXED)}),
+            ("book", lambda *a: {"df": measure_book(*a, precision="df"),
+                                 "mixed": measure_book(*a, precision="mixed"),
+                                 "fp64": measure_book(*a, precision="fp64")}),
+            ("stac_a2_path_reduction", lambda *a: measure_stac(*a)),
+            ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
+            ("store16_precision_study", lambda *a: measure_store16(*a)),
+            ("dual_upper_bound", lambda *a: measure_dual(*a)),
+            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
+                                    "mixed": measure_serving(*a, precision="mixed",
+                                                             max_inflight=4)}))
+    return jobs
+
+
 def main():
     args = parse()
     wl = pick_workload(args.workload)
@@ -494,6 +547,10 @@ def main():
     from paper_2206_03719_gb300 import api, build
     from paper_2206_03719_gb300 import lsmc as L
     build.build()
+    if args.extra:
+        # one of the side measurements alone (profiling runs)
+        print(json.dumps({"extra": args.extra, "result": dict(extra_jobs())[args.extra](api, L, torch)}))
+        return
     req = api.Request(wl)
     need = L.lsmc_request_footprint(None, req.c)
     if args.sub:
@@ -560,23 +617,7 @@ def main():
     ctx.close()
     extras = {}
     if not args.no_extras and not args.paths and args.workload == "paper_fp64" and world == 1:
-        df_paper = workloads.PAPER_FP64.replace(
-            precision="df", name="american-put-heston-131072x252-5strikes-df")
-        df_large = workloads.LARGE_MIXED.replace(
-            precision="df", name="american-put-heston-1048576x252-5strikes-df")
-        jobs = (("precision_split", lambda *a: {
-                    "df_paper": measure_precision(*a, df_paper),
-                    "df_large": measure_precision(*a, df_large),
-                    "mixed_large": measure_precision(*a, workloads.LARGE_MIXED)}),
-                ("book", lambda *a: {"df": measure_book(*a, precision="df"),
-                                     "mixed": measure_book(*a, precision="mixed"),
-                                     "fp64": measure_book(*a, precision="fp64")}),
-                ("stac_a2_path_reduction", lambda *a: measure_stac(*a)),
-                ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
-                ("store16_precision_study", lambda *a: measure_store16(*a)),
-                ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
-                                        "mixed": measure_serving(*a, precision="mixed",
-                                                                 max_inflight=4)}))
+        jobs = extra_jobs()
         for name, fn in jobs:
             torch.cuda.empty_cache()
             try:
