@@ -170,8 +170,8 @@ enum { LSMC_FLAG_REGENERATE = 1 };
  * LSMC_FLAG_REGENERATE. */
 enum { LSMC_FLAG_OUT_OF_SAMPLE = 2 };
 /* lsmc_request.flags.  LSMC_FLAG_STORE_FP16 / LSMC_FLAG_STORE_BF16: a 16-bit
- * path store (the paper's study of reduced data types, Sec. 4.3, applied to
- * the stored paths only).  The forward pass computes every step in the
+ * path store (the paper's study of reduced data types, Sec. 4.2 and Table 4,
+ * applied to the stored paths only).  The forward pass computes every step in the
  * request's precision and writes exp(x) (x = log(S / S0), the path's log
  * price relative to its start) and the variance as IEEE binary16 or
  * bfloat16, rounded to nearest with ties to even; the backward induction

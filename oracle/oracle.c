@@ -63,7 +63,7 @@ double orc_uniform_f32(uint32_t w) {
 /* finite value (2 - 2^(1 - p)) 2^emax becomes infinite.  IEEE binary16:    */
 /* p = 11, emin = -14, emax = 15; bfloat16: p = 8, emin = -126, emax = 127. */
 /* Used for the reduced-precision path store (the paper's study of data     */
-/* types, Sec. 4.3, applied to storage).                                    */
+/* types, Sec. 4.2 and Table 4, applied to storage).                      */
 /* ------------------------------------------------------------------------ */
 static double orc_round_format(double x, int p, int emin, int emax) {
   if (x != x || x == 0.0 || isinf(x)) return x;

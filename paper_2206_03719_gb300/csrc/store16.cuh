@@ -3,10 +3,10 @@
 //
 // The path store holds, per path group and date, exp(x) (x = log(S / S0))
 // and the variance.  Besides the working precision it can be IEEE binary16
-// or bfloat16 (the paper's study of reduced data types, Sec. 4.3, applied
-// to the stored paths only: every step is still computed in the working
-// precision, and a stored value is rounded once, to nearest with ties to
-// even, when it is written and widened exactly when it is read).
+// or bfloat16 (the paper's study of reduced data types, Sec. 4.2 and
+// Table 4, applied to the stored paths only: every step is still computed in
+// the working precision, and a stored value is rounded once, to nearest with
+// ties to even, when it is written and widened exactly when it is read).
 #pragma once
 
 #include <cuda_bf16.h>

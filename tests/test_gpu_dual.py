@@ -80,3 +80,18 @@ def test_dual_bound_rejections(ctx):
     with pytest.raises(L.LsmcError) as e:
         ctx.price_bounds(wl.replace(regenerate=True), 16, 8)
     assert e.value.status == L.LSMC_ENOTIMPL
+
+
+@pytest.mark.parametrize("n_steps,n_outer,n_inner", [(1, 5, 3), (2, 1, 1), (7, 33, 129)])
+def test_dual_bound_edge_sizes(ctx, n_steps, n_outer, n_inner):
+    # one date (no regression: the policy never exercises early), one outer or
+    # inner path, ragged outer and inner counts
+    wl = workloads.SMALL_FP64.replace(n_paths=777, n_steps=n_steps, basis="sv2", greeks=(),
+                                      strikes=[95.0, 104.0])
+    got = ctx.price_bounds(wl, n_outer, n_inner)
+    ref = _oracle(wl, n_outer, n_inner)
+    for g, r in zip(got, ref):
+        tol = 1e-10 if g["n_near_ties"] == 0 else 1e-4
+        scale = max(abs(r["lower"]), 1e-2)
+        for gk, rk in (("lower", "lower"), ("upper", "upper"), ("martingale_end", "pi_N")):
+            assert abs(g[gk] - r[rk]) <= tol * max(abs(r[rk]), scale), (gk, g[gk], r[rk])

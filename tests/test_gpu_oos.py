@@ -67,3 +67,16 @@ def test_out_of_sample_flag_rules(ctx):
     with pytest.raises(L.LsmcError) as e:
         ctx.price_book([workloads.SMALL_FP64.replace(out_of_sample=True), workloads.SMALL_FP64])
     assert e.value.status == L.LSMC_ENOTIMPL
+
+
+@pytest.mark.parametrize("n_paths,n_steps", [(31, 6), (1025, 1), (2049, 3)])
+def test_out_of_sample_edge_sizes(ctx, n_paths, n_steps):
+    # fewer paths than a warp, a single date (no exercise before maturity),
+    # a pricing tile of one path
+    wl = workloads.SMALL_FP64.replace(n_paths=n_paths, n_steps=n_steps, basis="sv2",
+                                      greeks=("delta",), strikes=[96.0, 103.0],
+                                      out_of_sample=True)
+    got = ctx.price(wl)
+    ref = _oracle_oos(wl)
+    for g, r in zip(got, ref):
+        assert_close(g, r, parity_tol(g["n_near_ties"]))

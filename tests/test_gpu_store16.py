@@ -98,3 +98,14 @@ def test_store16_flag_rules(ctx):
     with pytest.raises(L.LsmcError) as e:
         ctx.price_book([workloads.SMALL_FP64.replace(store="fp16"), workloads.SMALL_FP64])
     assert e.value.status == L.LSMC_ENOTIMPL
+
+
+@pytest.mark.parametrize("store", ["fp16", "bf16"])
+@pytest.mark.parametrize("n_paths,n_steps,style", [(33, 5, "american"), (1000, 1, "american"),
+                                                   (4097, 9, "european")])
+def test_store16_edge_sizes(ctx, store, n_paths, n_steps, style):
+    wl = _wl(store=store, n_paths=n_paths, n_steps=n_steps, style=style, strikes=[97.0])
+    got = ctx.price(wl)
+    ref = oracle_for(wl)
+    for g, r in zip(got, ref):
+        assert_close(g, r, parity_tol(g["n_near_ties"]))

@@ -1,5 +1,5 @@
 """Pins of the oracle's 16-bit path store (the paper's study of reduced
-data types, Sec. 4.3, applied to the stored paths only).
+data types, Sec. 4.2 and Table 4, applied to the stored paths only).
 
 * Rounding to binary16 agrees with numpy's float16 conversion on random
   doubles, on every midpoint between adjacent binary16 values (ties to even)
