@@ -24,7 +24,14 @@
  * and Black-Scholes; the backward induction against a least-squares solve by
  * QR on tiny path sets and against a stopping-time reconstruction; American
  * prices against a CRR tree restricted to the same exercise dates; Greeks
- * against Black-Scholes Greeks.  No function here is unpinned.
+ * against Black-Scholes Greeks; the multi-asset reduction against the
+ * single-asset paths and the distribution of the maximum of (correlated)
+ * lognormals in the Black-Scholes limit; the
+ * out-of-sample estimator against the in-sample one on the same paths and
+ * the binomial Bermudan price; the 16-bit rounding against numpy's float16
+ * and torch's bfloat16 conversions and the European Lipschitz bound; the
+ * dual upper bound against the immediate-exercise floor, the martingale's
+ * zero mean and the binomial bracket.  No function here is unpinned.
  */
 #ifndef LSMC_ORACLE_H
 #define LSMC_ORACLE_H
