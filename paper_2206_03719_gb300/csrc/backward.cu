@@ -312,6 +312,7 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_sum[kNSum];
   __shared__ Real s_c[16];            // per-job constants, converted once
   __shared__ long long s_thr[2];      // double: in-the-money thresholds of dates n + 1, n
+  __shared__ ScreenConsts s_q;        // the exercise test of date n + 1 in float
   // per-warp compaction of in-the-money paths (dynamic shared memory, one
   // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
   // of on lanes that are mostly out of the money
@@ -443,6 +444,11 @@ backward_kernel(BwdArgs a) {
         const double sv = lane == 16 ? stab[n + 1] : stab[n];
         s_thr[lane - 16] = __double_as_longlong(itm_threshold(type, sv, I.K));
       }
+      __syncwarp();
+      // the compaction buffers hold the row value e (double) or S itself
+      if (kCompact && lane == 0)
+        make_screen<BASIS, Real>(s_q, s_c, kProdLate ? s_c[6] : (Real)1, s_c[10], s_c[11],
+                                 s_c[12], s_c[7]);
     }
     __syncthreads();
     if (s_last < 0) return;
@@ -583,18 +589,25 @@ backward_kernel(BwdArgs a) {
           }
           __syncwarp();
           for (int j = lane; j < cnt; j += 32) {
+            // the float screen first; the test itself only where it cannot decide
+            const int pre = exercise_screen<BASIS>(s_q, type, approx_float(cs[j]),
+                                                   BASIS == kBasisSV2 ? approx_float(cv[j]) : 0.0f);
+            if (pre == 0) continue;  // continues, certainly
             const Real S = kProdLate ? s1 * cs[j] : cs[j];
             const Real h = intrinsic<Real>(type, K, S);
-            const Real x = qfma(S, invK, (Real)-1);
-            Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
-            if (BASIS == kBasisSV2) {
-              const Real w = qfma(cv[j], invTh, (Real)-1);
-              c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
-            }
             const Real hd = qmul(h, d1);
-            bool exercise, tie;
-            decide<Real>(hd, c, exercise, tie);
-            if (tie) ++ties;
+            bool exercise = pre == 1;
+            if (pre == 2) {
+              const Real x = qfma(S, invK, (Real)-1);
+              Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+              if (BASIS == kBasisSV2) {
+                const Real w = qfma(cv[j], invTh, (Real)-1);
+                c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+              }
+              bool tie;
+              decide<Real>(hd, c, exercise, tie);
+              if (tie) ++ties;
+            }
             if (exercise) {
               Real hz;
               if constexpr (std::is_same<Real, df>::value) {

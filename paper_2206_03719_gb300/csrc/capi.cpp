@@ -215,6 +215,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
     I.beta_z = o.beta == SIZE_MAX ? nullptr : (double*)(sreg + o.beta);
     I.oos_sum = o.oos_partial == SIZE_MAX ? nullptr : (double*)(sreg + o.oos_partial);
     I.oos_tab = o.oos_tab == SIZE_MAX ? nullptr : (void*)(sreg + o.oos_tab);
+    I.oos_screen = o.oos_screen == SIZE_MAX ? nullptr : (void*)(sreg + o.oos_screen);
   }
   const FwdContract* dC = (const FwdContract*)put(L.contracts.data(), sizeof(FwdContract) * L.contracts.size());
   const FwdGroup* dG = (const FwdGroup*)put(L.groups.data(), sizeof(FwdGroup) * L.groups.size());

@@ -46,29 +46,42 @@ template <> __device__ __forceinline__ bool flag_on<double>(double f) {
 template <> __device__ __forceinline__ bool flag_on<float>(float f) { return __float_as_int(f) != 0; }
 template <> __device__ __forceinline__ bool flag_on<df>(df f) { return __float_as_int(f.hi) != 0; }
 
-// The rule of one strike at date n (1..N-1) for a path at S (= s_n E) with
-// stored variance v: exercise where the regression was solved, the path is
-// in the money and its discounted payoff beats the fitted continuation value
-// (the backward pass's test, the same operations).  *z: the discounted cash
-// flow of exercising.
+__device__ __forceinline__ long long threshold_bits(double t) { return __double_as_longlong(t); }
+__device__ __forceinline__ long long threshold_bits(float) { return 0; }
+__device__ __forceinline__ long long threshold_bits(df) { return 0; }
+
+// The rule of one strike at date n (1..N-1) for a path with row value E
+// (S = s_n E) and stored variance v: exercise where the regression was
+// solved, the path is in the money and its discounted payoff beats the
+// fitted continuation value -- the backward pass's test with the same
+// operations, after the same float screen (q).  *z: the discounted cash flow
+// of exercising.
 template <typename Real, int BASIS>
-__device__ __forceinline__ bool rule_exercises(const Real* t, int type, Real K, Real invK,
-                                               Real invTh, Real S, Real v, double* z,
-                                               uint32_t* ties) {
-  if (!flag_on(t[6]) || !in_money<Real>(type, K, S)) return false;
+__device__ __forceinline__ bool rule_exercises(const Real* t, const ScreenConsts& q, int type,
+                                               Real K, Real invK, Real invTh, Real E, Real v,
+                                               double* z, uint32_t* ties) {
+  if (!flag_on(t[6]) || !itm_test(type, K, t[7], E, threshold_bits(t[10]))) return false;
+  int pre = 2;
+  if constexpr (!std::is_same<Real, float>::value)
+    pre = exercise_screen<BASIS>(q, type, approx_float(E),
+                                 BASIS == kBasisSV2 ? approx_float(v) : 0.0f);
+  if (pre == 0) return false;
+  const Real S = t[7] * E;
   const Real h = intrinsic<Real>(type, K, S);
-  const Real x = qfma(S, invK, (Real)-1);
-  Real c = qfma(qfma(t[2], x, t[1]), x, t[0]);
-  if (BASIS == kBasisSV2) {
-    const Real w = qfma(v, invTh, (Real)-1);
-    c = qfma(qfma(t[5], w, qfma(t[4], x, t[3])), w, c);
-  }
   const Real d1 = t[8], d1lo = t[9];
   const Real hd = qmul(h, d1);
-  bool exercise, tie;
-  decide<Real>(hd, c, exercise, tie);
-  if (tie) ++*ties;
-  if (!exercise) return false;
+  if (pre == 2) {
+    const Real x = qfma(S, invK, (Real)-1);
+    Real c = qfma(qfma(t[2], x, t[1]), x, t[0]);
+    if (BASIS == kBasisSV2) {
+      const Real w = qfma(v, invTh, (Real)-1);
+      c = qfma(qfma(t[5], w, qfma(t[4], x, t[3])), w, c);
+    }
+    bool exercise, tie;
+    decide<Real>(hd, c, exercise, tie);
+    if (tie) ++*ties;
+    if (!exercise) return false;
+  }
   Real hz;
   if constexpr (std::is_same<Real, df>::value) hz = quick_two_sum(hd.hi, hd.lo);
   else hz = fma(h, d1, h * d1lo);
@@ -144,6 +157,7 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
   __shared__ double s_acc[kMaxDualStrikes][kDualBlock];
   __shared__ uint32_t s_ties[kDualBlock];
   __shared__ const Real* s_tab[kMaxDualStrikes];
+  __shared__ const ScreenConsts* s_scr[kMaxDualStrikes];
   __shared__ Real s_K[kMaxDualStrikes], s_invK[kMaxDualStrikes], s_invTh[kMaxDualStrikes];
   const int tid = threadIdx.x;
   const uint32_t N = a.N, nk = a.n_strikes;
@@ -152,6 +166,7 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
   if (tid < (int)nk) {
     const BwdInstance& I = a.inst[a.inst_of_strike[tid]];
     s_tab[tid] = (const Real*)I.oos_tab;
+    s_scr[tid] = (const ScreenConsts*)I.oos_screen;
     s_K[tid] = (Real)I.K;
     s_invK[tid] = (Real)I.invK;
     s_invTh[tid] = (Real)I.inv_theta;
@@ -181,16 +196,15 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
       for (uint32_t k = 0; k < nk; ++k) {
         if ((done >> k) & 1u) continue;
         const Real* t = s_tab[k] + (size_t)date * kOosConsts;
-        const Real S = t[7] * E;
         if (date < N) {
           double z;
-          if (rule_exercises<Real, BASIS>(t, type, s_K[k], s_invK[k], s_invTh[k], S, vs, &z,
-                                          &ties)) {
+          if (rule_exercises<Real, BASIS>(t, s_scr[k][date], type, s_K[k], s_invK[k],
+                                          s_invTh[k], E, vs, &z, &ties)) {
             s_acc[k][tid] += z;
             done |= 1u << k;
           }
         } else {
-          s_acc[k][tid] += maturity_cash<Real>(t, type, s_K[k], S);
+          s_acc[k][tid] += maturity_cash<Real>(t, type, s_K[k], t[7] * E);
           done |= 1u << k;
         }
       }
@@ -224,6 +238,7 @@ __global__ void __launch_bounds__(kDualBlock) dual_max_kernel(DualArgs a) {
   if (p >= a.n_outer) return;
   const BwdInstance& I = a.inst[a.inst_of_strike[k]];
   const Real* tab = (const Real*)I.oos_tab;
+  const ScreenConsts* scr = (const ScreenConsts*)I.oos_screen;
   const Real K = (Real)I.K, invK = (Real)I.invK, invTh = (Real)I.inv_theta;
   const int type = a.type;
   const uint32_t N = a.N;
@@ -242,8 +257,8 @@ __global__ void __launch_bounds__(kDualBlock) dual_max_kernel(DualArgs a) {
       Z = date_cash<Real>(t, type, K, S);
       double zx;
       const Real vs = stored_variance<Real>(SCHEME, V[(size_t)date * a.n_outer + p]);
-      L = rule_exercises<Real, BASIS>(t, type, K, invK, invTh, S, vs, &zx, &ties) ? zx
-                                                                               : Q[date];
+      L = rule_exercises<Real, BASIS>(t, scr[date], type, K, invK, invTh, E, vs, &zx, &ties)
+              ? zx : Q[date];
     } else {
       Z = maturity_cash<Real>(t, type, K, S);
       L = Z;

@@ -115,6 +115,87 @@ __device__ __forceinline__ bool itm_test<double>(int type, double, double, doubl
   return type == kPut ? eb < thr : eb > thr;
 }
 
+// ---- float screen of the exercise test ---------------------------------------
+// The exercise test hd > c (hd the discounted payoff, c the fitted
+// continuation value) costs about a dozen operations of the working
+// precision per in-the-money path: FP64 ones, on GB300's narrow FP64 pipe,
+// or float-pair ones of ten FP32 instructions each.  Almost every decision
+// is far from its threshold, so it is first taken in float, with a bound on
+// the float result's error; only when |hd - c| is within that bound (and
+// always when the decision could be a near tie) does the caller run the test
+// in the working precision.  Decisions, near-tie counts and cash flows are
+// therefore exactly those of the test itself.
+//
+// Error bound.  The float inputs carry relative errors of at most 2^-23 (S,
+// v) and 2^-24 (constants), so x = S/K - 1 and w = v/theta - 1 are off by at
+// most 3.6e-7 (1 + |x|) and 2.4e-7 (1 + |w|); every monomial of the basis is
+// at most M^2 with M = 1 + |x| + |w|, and moves by at most 7.2e-7 M^2; the
+// coefficients' rounding and the six rounded operations add 4.2e-7 B M^2
+// (B = sum |beta_i|): |c_float - c| <= 1.2e-6 B M^2.  The payoff
+// h = K - S is off by at most 2.5e-7 (2K + |h|), so |hd_float - hd| <=
+// 5e-7 (K d + |hd|).  The screen decides only when |hd - c| exceeds
+// 3.2e-5 (B M^2 + K d + |hd|), 25 times the bound, which also exceeds the
+// near-tie distance 1e-10 max(|c|, hd) by far.
+struct ScreenConsts {
+  float b[6];      // coefficients (zero where the basis has fewer)
+  float s, K, invK, invTh, d;  // S multiplier of the row value, strike, 1/K, 1/theta, discount
+  float B;         // sum of |b_i|
+};
+static_assert(sizeof(ScreenConsts) == kScreenBytes, "table layout");
+
+// float value of a double within 2^-23 relative (the mantissa truncated,
+// integer operations only): 0 below float's normal range, infinity above
+__device__ __forceinline__ float approx_float(double x) {
+  const unsigned long long bits = __double_as_longlong(x);
+  const unsigned hi = (unsigned)(bits >> 32);
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  if (e < 1023 - 126) return 0.0f;
+  const unsigned sign = hi & 0x80000000u;
+  if (e > 1023 + 127) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned mag = (unsigned)((bits & 0x7fffffffffffffffull) >> 29) - ((1023u - 127u) << 23);
+  return __uint_as_float(sign | mag);
+}
+__device__ __forceinline__ float approx_float(df x) { return x.hi; }
+__device__ __forceinline__ float approx_float(float x) { return x; }
+
+// 1: exercise, 0: continue, 2: undecided.  e: the row value (S = s e) and v
+// the variance of an in-the-money path.
+template <int BASIS>
+__device__ __forceinline__ int exercise_screen(const ScreenConsts& q, int type, float e, float v) {
+  const float S = __fmul_rn(q.s, e);
+  const float x = __fmaf_rn(S, q.invK, -1.0f);
+  float c = __fmaf_rn(__fmaf_rn(q.b[2], x, q.b[1]), x, q.b[0]);
+  float M = 1.0f + fabsf(x);
+  if (BASIS == kBasisSV2) {
+    const float w = __fmaf_rn(v, q.invTh, -1.0f);
+    c = __fmaf_rn(__fmaf_rn(q.b[5], w, __fmaf_rn(q.b[4], x, q.b[3])), w, c);
+    M += fabsf(w);
+  }
+  const float h = type == kPut ? __fsub_rn(q.K, S) : __fsub_rn(S, q.K);
+  const float hd = __fmul_rn(h, q.d);
+  const float bound = 3.2e-5f * (q.B * M * M + q.K * q.d + fabsf(hd));
+  const float diff = __fsub_rn(hd, c);
+  return diff > bound ? 1 : (diff < -bound ? 0 : 2);
+}
+
+// ScreenConsts from the working-precision values (b: the basis's
+// coefficients, 3 or 6)
+template <int BASIS, typename Real>
+__device__ __forceinline__ void make_screen(ScreenConsts& q, const Real* b, Real s, Real K,
+                                            Real invK, Real invTh, Real d) {
+  float B = 0.0f;
+  for (int i = 0; i < 6; ++i) {
+    q.b[i] = (i < 3 || BASIS == kBasisSV2) ? (float)(double)b[i] : 0.0f;
+    B += fabsf(q.b[i]);
+  }
+  q.B = B;
+  q.s = (float)(double)s;
+  q.K = (float)(double)K;
+  q.invK = (float)(double)invK;
+  q.invTh = (float)(double)invTh;
+  q.d = (float)(double)d;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -85,6 +85,19 @@ __global__ void oos_table_kernel(const BwdInstance* __restrict__ inst) {
     t[9] = (Real)(d - (double)(Real)d);
     t[10] = (Real)(std::is_same<Real, double>::value ? itm_threshold(I.type, stab[n], I.K) : 0.0);
     t[11] = (Real)0;
+    // the float screen of the test (row value e, S = s e)
+    ScreenConsts& q = ((ScreenConsts*)I.oos_screen)[n];
+    float B = 0.0f;
+    for (int i = 0; i < 6; ++i) {
+      q.b[i] = (float)(double)t[i];
+      B += fabsf(q.b[i]);
+    }
+    q.B = B;
+    q.s = (float)(double)t[7];
+    q.K = (float)I.K;
+    q.invK = (float)I.invK;
+    q.invTh = (float)I.inv_theta;
+    q.d = (float)(double)t[8];
   }
 }
 
@@ -94,9 +107,10 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
   using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
   using St = typename RR::raw;
   constexpr int PPT = kOosPpt;
-  // double: candidates are found without the product s1 e (threshold), which
-  // is then formed on the compacted list
-  constexpr bool kProdLate = std::is_same<Real, double>::value;
+  // the compacted list holds the row values e: double finds its candidates
+  // without the product s1 e (threshold), and the float screen of the test
+  // reads e; S = s1 e is formed on the list where the test needs it
+  constexpr bool kScreen = !std::is_same<Real, float>::value;
   // consecutive CTAs take the same path tile of consecutive instances, so
   // the instances of one path group read the tile's rows while they are in L2
   const BwdInstance& I = inst[blockIdx.x];
@@ -158,7 +172,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
         const unsigned m = __ballot_sync(0xffffffffu, itm);
         if (itm) {
           const int pos = cnt + __popc(m & lane_lt);
-          wb.s[pos] = kProdLate ? e[k] : s1 * e[k];
+          wb.s[pos] = e[k];
           if (BASIS == kBasisSV2) wb.v[pos] = v[k];
           wb.o[pos] = (unsigned short)(k * 32 + lane);
           cand |= 1u << k;
@@ -171,19 +185,28 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) b[i] = t[i];
         const Real d1 = t[8], d1lo = t[9];
+        const ScreenConsts& q = ((const ScreenConsts*)I.oos_screen)[n];
         for (int j = lane; j < cnt; j += 32) {
-          const Real S = kProdLate ? s1 * wb.s[j] : wb.s[j];
+          int pre = 2;
+          if constexpr (kScreen)
+            pre = exercise_screen<BASIS>(q, type, approx_float(wb.s[j]),
+                                         BASIS == kBasisSV2 ? approx_float(wb.v[j]) : 0.0f);
+          if (pre == 0) continue;  // continues, certainly
+          const Real S = s1 * wb.s[j];
           const Real h = intrinsic<Real>(type, K, S);
-          const Real x = qfma(S, invK, (Real)-1);
-          Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
-          if (BASIS == kBasisSV2) {
-            const Real w = qfma(wb.v[j], invTh, (Real)-1);
-            c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
-          }
           const Real hd = qmul(h, d1);
-          bool exercise, tie;
-          decide<Real>(hd, c, exercise, tie);
-          if (tie) ++ties;
+          bool exercise = pre == 1;
+          if (pre == 2) {
+            const Real x = qfma(S, invK, (Real)-1);
+            Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+            if (BASIS == kBasisSV2) {
+              const Real w = qfma(wb.v[j], invTh, (Real)-1);
+              c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+            }
+            bool tie;
+            decide<Real>(hd, c, exercise, tie);
+            if (tie) ++ties;
+          }
           if (exercise) {
             Real hz;
             if constexpr (std::is_same<Real, df>::value) hz = quick_two_sum(hd.hi, hd.lo);

@@ -16,6 +16,7 @@ namespace lsmc {
 constexpr int kBlock = 256;      // threads per CTA of the backward pass
 constexpr int kOosTile = 1024;   // paths per CTA of the out-of-sample pricing pass
 constexpr int kOosConsts = 12;   // per-date constants of the out-of-sample pricing pass
+constexpr int kScreenBytes = 48; // one float screen of an exercise test (12 floats)
 constexpr int kFwdBlock = 128;   // threads (paths) per CTA of the forward pass
 constexpr int kMaxGroups = 5;    // path groups per contract (base, v0+, v0-, T-, T+)
 constexpr int kNSum = 25;        // doubles per tile partial
@@ -123,6 +124,8 @@ struct BwdInstance {
   void* oos_tab;      // out of sample: (N + 1) x kOosConsts values of the working
                       // precision per date: 6 coefficients, solved flag, S multiplier,
                       // discount factor as a pair (hi, lo), in-the-money threshold
+  void* oos_screen;   // out of sample: (N + 1) float screens of the exercise test
+                      // (ScreenConsts, kScreenBytes each)
 };
 
 struct BwdState {

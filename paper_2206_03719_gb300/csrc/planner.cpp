@@ -302,6 +302,8 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
           off_scale += round_up((size_t)((P + kOosTile - 1) / kOosTile) * 4 * 8, 256);
           o.oos_tab = off_scale;  // the per-date constants in the working precision
           off_scale += round_up((size_t)(N + 1) * kOosConsts * real, 256);
+          o.oos_screen = off_scale;  // and the per-date float screens of the test
+          off_scale += round_up((size_t)(N + 1) * kScreenBytes, 256);
         }
         I.Y = nullptr;
         I.partial = nullptr;

@@ -93,7 +93,8 @@ struct PlanLayout {
   // scale: the date tables; beta / oos_partial (out-of-sample mode, inside
   // the same region): coefficients of every date, the pricing pass's sums
   struct InstOff {
-    size_t y, partial, scale, beta = SIZE_MAX, oos_partial = SIZE_MAX, oos_tab = SIZE_MAX;
+    size_t y, partial, scale, beta = SIZE_MAX, oos_partial = SIZE_MAX, oos_tab = SIZE_MAX,
+           oos_screen = SIZE_MAX;
     uint32_t group;
   };
   std::vector<InstOff> inst_off;
