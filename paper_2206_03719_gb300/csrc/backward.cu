@@ -281,6 +281,7 @@ struct BwdWarpBufs {
   Real m[3][kCap + 32];
   Real zn[PPT][32];
   unsigned short co[kCap];
+  unsigned short ex[kCap];  // exercise items the float screen did not settle
 };
 
 // Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
@@ -588,11 +589,23 @@ backward_kernel(BwdArgs a) {
             wb.zn[k][lane] = z[k];
           }
           __syncwarp();
-          for (int j = lane; j < cnt; j += 32) {
-            // the float screen first; the test itself only where it cannot decide
-            const int pre = exercise_screen<BASIS>(s_q, type, approx_float(cs[j]),
-                                                   BASIS == kBasisSV2 ? approx_float(cv[j]) : 0.0f);
-            if (pre == 0) continue;  // continues, certainly
+          // the float screen of every item; the items it does not settle as
+          // continuing (exercise, or undecided) are compacted a second time,
+          // so the working-precision work runs on dense lists as well
+          int cnt2 = 0;
+          for (int j0 = 0; j0 < cnt; j0 += 32) {
+            const int j = j0 + lane;
+            int pre = 0;
+            if (j < cnt)
+              pre = exercise_screen<BASIS>(s_q, type, approx_float(cs[j]),
+                                           BASIS == kBasisSV2 ? approx_float(cv[j]) : 0.0f);
+            const unsigned m = __ballot_sync(0xffffffffu, pre != 0);
+            if (pre != 0) wb.ex[cnt2 + __popc(m & lane_lt)] = (unsigned short)(j | (pre << 12));
+            cnt2 += __popc(m);
+          }
+          __syncwarp();
+          for (int jj = lane; jj < cnt2; jj += 32) {
+            const int code = wb.ex[jj], j = code & 0xfff, pre = code >> 12;
             const Real S = kProdLate ? s1 * cs[j] : cs[j];
             const Real h = intrinsic<Real>(type, K, S);
             const Real hd = qmul(h, d1);
