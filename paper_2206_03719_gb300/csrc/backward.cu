@@ -466,6 +466,8 @@ backward_kernel(BwdArgs a) {
     // date's threshold, so only in-the-money paths pay for the product
     const long long thr1 = std::is_same<Real, double>::value ? s_thr[0] : 0;
     const long long thr0 = std::is_same<Real, double>::value ? s_thr[1] : 0;
+    // the moment items hold e (double) or S: x = e (s0 / K) - 1 or S / K - 1
+    const Real xK0 = kProdLate ? s0 * invK : invK;
     // row of date d at index d - a.row0 (rows of dates 1..N, or one segment)
     const ptrdiff_t r0 = (ptrdiff_t)a.row0;
     const St* EN = E + ((ptrdiff_t)N - r0) * (ptrdiff_t)ld;
@@ -684,8 +686,7 @@ backward_kernel(BwdArgs a) {
         Real* t = acc.target();
         const int full = cnt & ~31;
         for (int j = lane; j < full; j += 32)
-          accumulate_moments<Real, BASIS, NM>(t, n_itm, kProdLate ? s0 * ms[j] : ms[j], mv[j],
-                                              my[j], invK, invTh);
+          accumulate_moments<Real, BASIS, NM>(t, n_itm, ms[j], mv[j], my[j], xK0, invTh);
         mcarry = cnt - full;
         Real r0 = (Real)0, r1 = (Real)0, r2 = (Real)0;
         if (lane < mcarry) {
@@ -706,9 +707,8 @@ backward_kernel(BwdArgs a) {
 
     if (kCompact && mcarry > 0) {  // the carried moment items of the last sub-tile
       if (lane < mcarry)
-        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm,
-                                            kProdLate ? s0 * ms[lane] : ms[lane], mv[lane],
-                                            my[lane], invK, invTh);
+        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, ms[lane], mv[lane], my[lane],
+                                            xK0, invTh);
       __syncwarp();
     }
 

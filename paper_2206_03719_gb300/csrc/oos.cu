@@ -58,6 +58,7 @@ struct OosWarpBufs {
   Real v[BASIS == kBasisSV2 ? kOosPpt * 32 : 1];
   Real z[kOosPpt][32];
   unsigned short o[kOosPpt * 32];
+  unsigned short ex[kOosPpt * 32];  // items the float screen did not settle
 };
 
 }  // namespace
@@ -185,13 +186,26 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
 #pragma unroll
         for (int i = 0; i < 6; ++i) b[i] = t[i];
         const Real d1 = t[8], d1lo = t[9];
+        // the float screen of every item; those it does not settle as
+        // continuing are compacted again for the working-precision work
         const ScreenConsts& q = ((const ScreenConsts*)I.oos_screen)[n];
-        for (int j = lane; j < cnt; j += 32) {
-          int pre = 2;
-          if constexpr (kScreen)
-            pre = exercise_screen<BASIS>(q, type, approx_float(wb.s[j]),
-                                         BASIS == kBasisSV2 ? approx_float(wb.v[j]) : 0.0f);
-          if (pre == 0) continue;  // continues, certainly
+        int cnt2 = 0;
+        for (int j0 = 0; j0 < cnt; j0 += 32) {
+          const int j = j0 + lane;
+          int pre = 0;
+          if (j < cnt) {
+            pre = 2;
+            if constexpr (kScreen)
+              pre = exercise_screen<BASIS>(q, type, approx_float(wb.s[j]),
+                                           BASIS == kBasisSV2 ? approx_float(wb.v[j]) : 0.0f);
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pre != 0);
+          if (pre != 0) wb.ex[cnt2 + __popc(m & lane_lt)] = (unsigned short)(j | (pre << 12));
+          cnt2 += __popc(m);
+        }
+        __syncwarp();
+        for (int jj = lane; jj < cnt2; jj += 32) {
+          const int code = wb.ex[jj], j = code & 0xfff, pre = code >> 12;
           const Real S = s1 * wb.s[j];
           const Real h = intrinsic<Real>(type, K, S);
           const Real hd = qmul(h, d1);
