@@ -45,12 +45,12 @@ BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
 # DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel at 98,304 paths (2.625503e9 + 0.293540e9 bytes) scaled by the path
+# kernel at 98,304 paths (2.624766e9 + 0.294595e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
 # the kernel source it was taken from: reported as null once backward.cu
 # changes.
-BWD_TRAFFIC = {"bytes": (2.625503e9 + 0.293540352e9) * 131072 / 98304,
-               "source_sha256_16": "e0801e02197def62",
+BWD_TRAFFIC = {"bytes": (2.624766e9 + 0.294595328e9) * 131072 / 98304,
+               "source_sha256_16": "9194677c4c78bd44",
                "capture": "profiles/backward_kernel_fp64_98304x252.md, scaled by 131072/98304"}
 
 
