@@ -59,6 +59,30 @@ __device__ __forceinline__ df exp_df(df a, const float2* tab) {
   return df(__fmul_rn(res.hi, s), __fmul_rn(res.lo, s));
 }
 
+// exp(x) in double, table-driven (Tang's method): k = rint(x 128 / ln 2)
+// (adding 1.5 2^52 leaves k in the low mantissa bits), r = x - k ln2/128 by
+// two fused multiply-adds (|r| <= ln2/256), exp(r) - 1 = r + r^2 (1/2 + r/6 +
+// r^2/24 + r^3/120) (the truncated terms stay below 6e-19), and
+// exp(x) = 2^(k >> 7) * 2^((k & 127)/128) (1 + (exp(r) - 1)): about 10 FP64
+// operations against CUDA's exp at about 16 (measured on GB300), within one
+// unit in the last place.  Outside |x| < 512 (where the final scaling by
+// the exponent field could overflow or underflow) CUDA's exp.
+__device__ __forceinline__ double exp_f64(double x) {
+  const unsigned long long bits = __double_as_longlong(x);
+  if (((bits >> 52) & 0x7ffull) >= 1023ull + 9ull) return exp(x);
+  const double magic = 6755399441055744.0;  // 1.5 * 2^52
+  const double t = fma(x, kExpF64InvL, magic);
+  const int k = __double2loint(t);
+  const double kf = t - magic;
+  double r = fma(-kf, kExpF64C1, x);
+  r = fma(-kf, kExpF64C2, r);
+  const double q = fma(fma(fma(r, 1.0 / 120.0, 1.0 / 24.0), r, 1.0 / 6.0), r, 0.5);
+  const double p = fma(r * r, q, r);
+  const double T = __ldg(&kExp2F64[k & (kExpTab - 1)]);
+  const double y = fma(T, p, T);
+  return __longlong_as_double(__double_as_longlong(y) + ((long long)(k >> 7) << 52));
+}
+
 // log(a), a > 0: y0 = logf(a.hi), then one Newton step on exp(y) = a,
 // y1 = y0 + a exp(-y0) - 1 (quadratic: the float error squared)
 __device__ __forceinline__ df log_df(df a, const float2* tab) {

@@ -7,6 +7,9 @@ Tables:
 * 2^(j/128), j = 0..127, as float pairs, for exp(a) = 2^n 2^(j/128) exp(r);
 * ln2 / 128 split into three floats (Cody and Waite's reduction): the first
   with few enough bits that k times it is exact for every |k| < 2^14;
+* for the double-precision exp: 2^(j/128) rounded to double and ln2 / 128 in
+  two doubles (the reduction runs in fused multiply-adds, so the first part
+  needs no trailing zeros);
 * G(z) = Phi(z) exp(z^2 / 2) on z <= 0 (Phi the standard normal
   distribution function) as one polynomial in x = z - c per interval,
   fitted by interpolation at Chebyshev nodes.  Intervals: [-0.25, 0]
@@ -106,6 +109,19 @@ def main():
         hi, lo = split(mp.mpf(2) ** (mp.mpf(j) / N_EXP))
         w("    {%.9ef, %.9ef}," % (hi, lo))
     w("};")
+    w("")
+    # double-precision exp: 2^(j / 128) rounded to double, ln 2 / 128 in two parts
+    w("// double exp: 2^(j / %d), j = 0..%d, rounded to double" % (N_EXP, N_EXP - 1))
+    w("static __device__ const double kExp2F64[%d] = {" % N_EXP)
+    for j0 in range(0, N_EXP, 4):
+        w("    " + ", ".join("%.17e" % float(mp.mpf(2) ** (mp.mpf(j) / N_EXP))
+                             for j in range(j0, j0 + 4)) + ",")
+    w("};")
+    d1 = float(L)
+    d2 = float(L - mp.mpf(d1))
+    w("constexpr double kExpF64InvL = %.17e;  // %d / ln 2" % (float(1 / L), N_EXP))
+    w("constexpr double kExpF64C1 = %.17e;    // ln 2 / %d in two parts" % (d1, N_EXP))
+    w("constexpr double kExpF64C2 = %.17e;" % d2)
     w("")
     w("constexpr int kQDegree = %d;       // G polynomials: degree" % DEGREE)
     w("constexpr int kQPair = %d;         // coefficients 0..kQPair-1 are pairs" % N_PAIR)
