@@ -663,9 +663,14 @@ def main():
     cpu = None
     if not args.no_cpu_baseline:
         dt, rate, cores = oracle_sample_rate(wl, 2048)
+        dt1, rate1, _ = oracle_sample_rate(wl, 256, threads=1)
         cpu = {"value": rate, "unit": "Greeks/s", "cores": cores, "kind": "oracle",
                "sample": "FP64 oracle on 2048 of %d paths (all strikes and revaluations, "
-                         "%.1f s), scaled linearly to the full path count" % (wl.n_paths, dt)}
+                         "%.1f s), scaled linearly to the full path count; its forward pass "
+                         "splits paths over the threads, its backward pass strikes (%d)"
+                         % (wl.n_paths, dt, len(wl.strikes)),
+               "single_thread": {"value": rate1, "unit": "Greeks/s", "cores": 1,
+                                 "sample": "256 paths (%.1f s), scaled linearly" % dt1}}
     line = {
         "metric": "Greeks/s", "value": value, "unit": "Greeks/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
