@@ -284,6 +284,27 @@ struct BwdWarpBufs {
   unsigned short ex[kCap];  // exercise items the float screen did not settle
 };
 
+// Compaction buffer items.  With a 16-bit store in double precision the row
+// values stay floats (exact: every 16-bit value is a float) until the dense
+// loops, so the float -> double conversions, which run on the FP64 pipe,
+// happen once per in-the-money item rather than once per path; such an item
+// sits in the low half of its double slot.
+template <typename Real, typename LoadT>
+__device__ __forceinline__ void put_item(Real* buf, int i, LoadT x) {
+  if constexpr (std::is_same<Real, LoadT>::value) buf[i] = x;
+  else reinterpret_cast<float*>(buf + i)[0] = x;
+}
+template <typename Real, typename LoadT>
+__device__ __forceinline__ Real get_item(const Real* buf, int i) {
+  if constexpr (std::is_same<Real, LoadT>::value) return buf[i];
+  else return (Real)reinterpret_cast<const float*>(buf + i)[0];
+}
+template <typename Real, typename LoadT>
+__device__ __forceinline__ float item_float(const Real* buf, int i) {
+  if constexpr (std::is_same<Real, LoadT>::value) return approx_float(buf[i]);
+  else return reinterpret_cast<const float*>(buf + i)[0];
+}
+
 // Cash flows are kept discounted to t_0: Z = h(S_tau) exp(-r tau dt) for the
 // current exercise time tau.  The regression target of date n, the cash flow
 // discounted to t_n, is Z exp(r n dt): the same factor for every path, so the
@@ -297,6 +318,10 @@ __global__ void __launch_bounds__(kBlock, 2)
 backward_kernel(BwdArgs a) {
   using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
   using St = typename RR::raw;
+  // double with a 16-bit store: row values kept as floats until the dense loops
+  constexpr bool kNarrow64 = std::is_same<Real, double>::value && FMT != kStoreNative;
+  using LoadT = typename std::conditional<kNarrow64, float, Real>::type;
+  using RF = RowRead<LoadT, FMT>;
   constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
   constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
   constexpr int NA = NM + NB;                         // register sums
@@ -313,6 +338,7 @@ backward_kernel(BwdArgs a) {
   __shared__ double s_sum[kNSum];
   __shared__ Real s_c[16];            // per-job constants, converted once
   __shared__ long long s_thr[2];      // double: in-the-money thresholds of dates n + 1, n
+  __shared__ int s_thrf[2];           // the same for float row values (16-bit store)
   __shared__ ScreenConsts s_q;        // the exercise test of date n + 1 in float
   // per-warp compaction of in-the-money paths (dynamic shared memory, one
   // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
@@ -443,7 +469,12 @@ backward_kernel(BwdArgs a) {
         s_c[lane] = (Real)v;
       } else if (std::is_same<Real, double>::value && lane < 18) {
         const double sv = lane == 16 ? stab[n + 1] : stab[n];
-        s_thr[lane - 16] = __double_as_longlong(itm_threshold(type, sv, I.K));
+        const double T = itm_threshold(type, sv, I.K);
+        s_thr[lane - 16] = __double_as_longlong(T);
+        // float e: e < T iff e < (T rounded up to a float); e > T iff e > (T rounded down)
+        if constexpr (kNarrow64)
+          s_thrf[lane - 16] =
+              __float_as_int(type == kPut ? __double2float_ru(T) : __double2float_rd(T));
       }
       __syncwarp();
       // the compaction buffers hold the row value e (double) or S itself
@@ -521,13 +552,13 @@ backward_kernel(BwdArgs a) {
           }
         }
       }
-      Real e1[PPT], v1[PPT], e0[PPT], v0[PPT];
+      LoadT e1[PPT], v1[PPT], e0[PPT], v0[PPT];
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
-        e1[k] = RR::widen(e1r[k]);
-        v1[k] = RR::widen(v1r[k]);
-        e0[k] = RR::widen(e0r[k]);
-        v0[k] = RR::widen(v0r[k]);
+        e1[k] = RF::widen(e1r[k]);
+        v1[k] = RF::widen(v1r[k]);
+        e0[k] = RF::widen(e0r[k]);
+        v0[k] = RF::widen(v0r[k]);
       }
       Real z[PPT];
       if (first) {
@@ -536,7 +567,7 @@ backward_kernel(BwdArgs a) {
           const uint32_t p = p_base + k * kBlock;
           z[k] = (Real)0;
           if (p < P) {
-            const Real h = payoff<Real>(type, K, sN * e1[k]);
+            const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
             z[k] = fma(h, dNhi, h * dNlo);
             euro += (double)z[k];
             if (!final_job) Z[p] = z[k];
@@ -557,7 +588,7 @@ backward_kernel(BwdArgs a) {
               const Real x = qfma(S, invK, (Real)-1);
               Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
               if (BASIS == kBasisSV2) {
-                const Real w = qfma(v1[k], invTh, (Real)-1);
+                const Real w = qfma((Real)v1[k], invTh, (Real)-1);
                 c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
               }
               const Real hd = qmul(h, d1);
@@ -579,12 +610,19 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             const uint32_t p = p_base + k * kBlock;
-            const bool itm = p < P && itm_test(type, K, s1, e1[k], thr1);
+            bool itm;
+            if constexpr (kNarrow64) {
+              const int eb = __float_as_int(e1[k]);
+              itm = p < P && (type == kPut ? eb < s_thrf[0] : eb > s_thrf[0]);
+            } else {
+              itm = p < P && itm_test(type, K, s1, e1[k], thr1);
+            }
             const unsigned m = __ballot_sync(0xffffffffu, itm);
             if (itm) {
               const int pos = cnt + __popc(m & lane_lt);
-              cs[pos] = kProdLate ? e1[k] : s1 * e1[k];
-              if (BASIS == kBasisSV2) cv[pos] = v1[k];
+              if constexpr (kProdLate) put_item<Real, LoadT>(cs, pos, e1[k]);
+              else cs[pos] = s1 * e1[k];
+              if (BASIS == kBasisSV2) put_item<Real, LoadT>(cv, pos, v1[k]);
               co[pos] = (unsigned short)(k * 32 + lane);
             }
             cnt += __popc(m);
@@ -599,8 +637,9 @@ backward_kernel(BwdArgs a) {
             const int j = j0 + lane;
             int pre = 0;
             if (j < cnt)
-              pre = exercise_screen<BASIS>(s_q, type, approx_float(cs[j]),
-                                           BASIS == kBasisSV2 ? approx_float(cv[j]) : 0.0f);
+              pre = exercise_screen<BASIS>(s_q, type, item_float<Real, LoadT>(cs, j),
+                                           BASIS == kBasisSV2 ? item_float<Real, LoadT>(cv, j)
+                                                              : 0.0f);
             const unsigned m = __ballot_sync(0xffffffffu, pre != 0);
             if (pre != 0) wb.ex[cnt2 + __popc(m & lane_lt)] = (unsigned short)(j | (pre << 12));
             cnt2 += __popc(m);
@@ -608,7 +647,7 @@ backward_kernel(BwdArgs a) {
           __syncwarp();
           for (int jj = lane; jj < cnt2; jj += 32) {
             const int code = wb.ex[jj], j = code & 0xfff, pre = code >> 12;
-            const Real S = kProdLate ? s1 * cs[j] : cs[j];
+            const Real S = kProdLate ? s1 * get_item<Real, LoadT>(cs, j) : cs[j];
             const Real h = intrinsic<Real>(type, K, S);
             const Real hd = qmul(h, d1);
             bool exercise = pre == 1;
@@ -616,7 +655,7 @@ backward_kernel(BwdArgs a) {
               const Real x = qfma(S, invK, (Real)-1);
               Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
               if (BASIS == kBasisSV2) {
-                const Real w = qfma(cv[j], invTh, (Real)-1);
+                const Real w = qfma(get_item<Real, LoadT>(cv, j), invTh, (Real)-1);
                 c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
               }
               bool tie;
@@ -672,12 +711,19 @@ backward_kernel(BwdArgs a) {
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
-          const bool itm = p < P && itm_test(type, K, s0, e0[k], thr0);
+          bool itm;
+          if constexpr (kNarrow64) {
+            const int eb = __float_as_int(e0[k]);
+            itm = p < P && (type == kPut ? eb < s_thrf[1] : eb > s_thrf[1]);
+          } else {
+            itm = p < P && itm_test(type, K, s0, e0[k], thr0);
+          }
           const unsigned m = __ballot_sync(0xffffffffu, itm);
           if (itm) {
             const int pos = cnt + __popc(m & lane_lt);
-            ms[pos] = kProdLate ? e0[k] : s0 * e0[k];
-            if (BASIS == kBasisSV2) mv[pos] = v0[k];
+            if constexpr (kProdLate) put_item<Real, LoadT>(ms, pos, e0[k]);
+            else ms[pos] = s0 * e0[k];
+            if (BASIS == kBasisSV2) put_item<Real, LoadT>(mv, pos, v0[k]);
             my[pos] = z[k];
           }
           cnt += __popc(m);
@@ -686,7 +732,8 @@ backward_kernel(BwdArgs a) {
         Real* t = acc.target();
         const int full = cnt & ~31;
         for (int j = lane; j < full; j += 32)
-          accumulate_moments<Real, BASIS, NM>(t, n_itm, ms[j], mv[j], my[j], xK0, invTh);
+          accumulate_moments<Real, BASIS, NM>(t, n_itm, get_item<Real, LoadT>(ms, j),
+                                              get_item<Real, LoadT>(mv, j), my[j], xK0, invTh);
         mcarry = cnt - full;
         Real r0 = (Real)0, r1 = (Real)0, r2 = (Real)0;
         if (lane < mcarry) {
@@ -707,8 +754,9 @@ backward_kernel(BwdArgs a) {
 
     if (kCompact && mcarry > 0) {  // the carried moment items of the last sub-tile
       if (lane < mcarry)
-        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, ms[lane], mv[lane], my[lane],
-                                            xK0, invTh);
+        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, get_item<Real, LoadT>(ms, lane),
+                                            get_item<Real, LoadT>(mv, lane), my[lane], xK0,
+                                            invTh);
       __syncwarp();
     }
 
