@@ -45,12 +45,12 @@ BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
 # DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel at 98,304 paths (2.624766e9 + 0.294595e9 bytes) scaled by the path
+# kernel at 98,304 paths (2.619791e9 + 0.290274e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
 # the kernel source it was taken from: reported as null once backward.cu
 # changes.
-BWD_TRAFFIC = {"bytes": (2.624766e9 + 0.294595328e9) * 131072 / 98304,
-               "source_sha256_16": "9194677c4c78bd44",
+BWD_TRAFFIC = {"bytes": (2.619791e9 + 0.290273536e9) * 131072 / 98304,
+               "source_sha256_16": "b289097e1463d092",
                "capture": "profiles/backward_kernel_fp64_98304x252.md, scaled by 131072/98304"}
 
 
