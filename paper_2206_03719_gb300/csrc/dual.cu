@@ -46,9 +46,6 @@ template <> __device__ __forceinline__ bool flag_on<double>(double f) {
 template <> __device__ __forceinline__ bool flag_on<float>(float f) { return __float_as_int(f) != 0; }
 template <> __device__ __forceinline__ bool flag_on<df>(df f) { return __float_as_int(f.hi) != 0; }
 
-__device__ __forceinline__ long long threshold_bits(double t) { return __double_as_longlong(t); }
-__device__ __forceinline__ long long threshold_bits(float) { return 0; }
-__device__ __forceinline__ long long threshold_bits(df) { return 0; }
 
 // The rule of one strike at date n (1..N-1) for a path with row value E
 // (S = s_n E) and stored variance v: exercise where the regression was

@@ -103,6 +103,12 @@ __device__ double itm_threshold(int type, double s1, double K) {
   return e;
 }
 
+// the bits of a stored in-the-money threshold (double only; the other
+// precisions test the product itself)
+__device__ __forceinline__ long long threshold_bits(double t) { return __double_as_longlong(t); }
+__device__ __forceinline__ long long threshold_bits(float) { return 0; }
+__device__ __forceinline__ long long threshold_bits(df) { return 0; }
+
 // in_money(type, K, RN(s e)); for double through the threshold's bits
 template <typename R>
 __device__ __forceinline__ bool itm_test(int type, R K, R s, R e, long long) {

@@ -44,9 +44,6 @@ __device__ __forceinline__ bool stopped_value(double z) { return __double_as_lon
 __device__ __forceinline__ bool stopped_value(float z) { return __float_as_int(z) >= 0; }
 __device__ __forceinline__ bool stopped_value(df z) { return __float_as_int(z.hi) >= 0; }
 
-__device__ __forceinline__ long long as_bits(double v) { return __double_as_longlong(v); }
-__device__ __forceinline__ long long as_bits(float) { return 0; }
-__device__ __forceinline__ long long as_bits(df) { return 0; }
 
 // Shared memory of one warp: the compacted candidates of the current date
 // (S, v and origin = slot * 32 + lane) and, by origin, the discounted cash
@@ -166,7 +163,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
       int cnt = 0;
       // double: the in-the-money test on the stored value's bits against the
       // date's threshold, so only candidates pay for the product s1 e
-      const long long thr = as_bits(t[10]);
+      const long long thr = threshold_bits(t[10]);
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const bool itm = (((valid & ~stopped) >> k) & 1u) && itm_test(type, K, s1, e[k], thr);
