@@ -95,3 +95,15 @@ def test_dual_bound_edge_sizes(ctx, n_steps, n_outer, n_inner):
         scale = max(abs(r["lower"]), 1e-2)
         for gk, rk in (("lower", "lower"), ("upper", "upper"), ("martingale_end", "pi_N")):
             assert abs(g[gk] - r[rk]) <= tol * max(abs(r[rk]), scale), (gk, g[gk], r[rk])
+
+
+def test_dual_bound_with_a_16_bit_store(ctx):
+    # the lower bound prices on the 16-bit rows (the out-of-sample price of
+    # the same request), the dual pass re-simulates its outer paths in full
+    wl = workloads.SMALL_FP64.replace(n_paths=3000, n_steps=12, basis="sv2", greeks=(),
+                                      strikes=[100.0], store="fp16")
+    b = ctx.price_bounds(wl, 64, 32)[0]
+    oos = ctx.price(wl.replace(out_of_sample=True))[0]
+    assert b["lower"] == oos["price"]
+    ref = _oracle(wl.replace(store="native"), 64, 32)[0]
+    assert abs(b["upper"] - ref["upper"]) < 0.05 * ref["upper"]
