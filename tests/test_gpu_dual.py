@@ -107,3 +107,12 @@ def test_dual_bound_with_a_16_bit_store(ctx):
     assert b["lower"] == oos["price"]
     ref = _oracle(wl.replace(store="native"), 64, 32)[0]
     assert abs(b["upper"] - ref["upper"]) < 0.05 * ref["upper"]
+
+
+def test_dual_bound_sixteen_strikes(ctx):
+    # the largest strike count of one call: every strike's rule on the same
+    # inner paths, shared-memory sums of 16 strikes per thread
+    wl = workloads.SMALL_FP64.replace(n_paths=2000, n_steps=6, basis="s2", greeks=(),
+                                      strikes=[84.0 + 2.0 * i for i in range(16)])
+    got = ctx.price_bounds(wl, 40, 20)
+    _check(got, _oracle(wl, 40, 20))
