@@ -15,11 +15,15 @@
 // A job (date n, tile t) of instance i:
 //   1. applies the exercise rule of date n+1 (coefficients published by the
 //      previous round) to the tile's cash flows, or initialises them with the
-//      payoff at maturity;
-//   2. accumulates, over in-the-money paths, the 15
+//      payoff at maturity: in-the-money paths compacted per warp, each
+//      decision first taken by a float screen with an error bound and, where
+//      the screen cannot decide, by the test in the working precision on a
+//      second compacted list (exercise.cuh);
+//   2. accumulates, over in-the-money paths (compacted again), the 15
 //      distinct monomials x^a w^b (a + b <= 4) that make up X^T X and the six
-//      entries of X^T Y (register sums, warp shuffles, a fixed-order sum over
-//      warps: no atomics, so results do not depend on scheduling);
+//      entries of X^T Y (register sums, a transposed fixed-order sum over the
+//      lanes and then over the warps: no atomics, so results do not depend on
+//      scheduling);
 //   3. writes the tile partial and arrives on the instance's counter.  The CTA
 //      that arrives last sums the tile partials in tile order, solves the
 //      normal equations by Cholesky in FP64 and publishes the coefficients.
