@@ -204,6 +204,17 @@ void lsmc_destroy(lsmc_ctx* ctx);
 /* Work of the synchronous calls runs on this CUDA stream (a cudaStream_t; NULL
  * = the context's own stream).  The caller keeps the stream alive. */
 int lsmc_set_stream(lsmc_ctx* ctx, void* cuda_stream);
+/* Device memory callbacks used instead of cudaMalloc / cudaFree for every
+ * allocation the context makes outside a workspace (plans, the serving
+ * arena, the dual bound's scratch): alloc(bytes, user) returns device memory
+ * of the context's device, 256-byte aligned, or NULL (LSMC_ENOMEM);
+ * release(ptr, user) gives it back, called only after the library's work on
+ * it has completed.  This is how a framework's caching allocator (e.g.
+ * PyTorch's) plugs in.  Both NULL: back to cudaMalloc.  LSMC_EBUSY once the
+ * serving loop has started; LSMC_EINVAL if exactly one callback is NULL.
+ * The callbacks may run on the context's scheduler thread. */
+int lsmc_set_allocator(lsmc_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
+                       void (*release)(void* ptr, void* user), void* user);
 /* Device memory the context sub-allocates from instead of cudaMalloc
  * (e.g. a PyTorch tensor).  Must be set before any plan exists and stay
  * valid until lsmc_destroy; 256-byte aligned. */

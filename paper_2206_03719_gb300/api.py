@@ -59,7 +59,8 @@ class Context:
 
     def __init__(self, workspace_bytes: int = 0, precision: str = "fp64",
                  scheme: str = "qe", hbm_budget: int = 0, max_inflight: int = 8,
-                 use_torch_stream: bool = True, device: Optional[int] = None):
+                 use_torch_stream: bool = True, device: Optional[int] = None,
+                 torch_allocator: bool = False):
         import torch
         self.torch = torch
         dev = torch.cuda.current_device() if device is None else device
@@ -67,6 +68,14 @@ class Context:
                             max_inflight, 0)
         self.ctx = L.lsmc_create(cfg)
         self._plans = weakref.WeakSet()
+        self._alloc_cbs = None
+        if torch_allocator:
+            # every allocation outside a workspace from PyTorch's caching allocator
+            def alloc(nbytes):
+                return torch.cuda.caching_allocator_alloc(nbytes, device=dev)
+
+            self._alloc_cbs = L.lsmc_set_allocator(self.ctx, alloc,
+                                                   torch.cuda.caching_allocator_delete)
         self.workspace = None
         if workspace_bytes:
             self.workspace = torch.empty(workspace_bytes, dtype=torch.uint8, device="cuda:%d" % dev)

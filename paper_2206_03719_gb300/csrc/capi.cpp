@@ -65,6 +65,10 @@ struct lsmc_ctx {
   int num_sms = 0;
   std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
   std::mutex occ_mu;          // guards occ (plans are built on several threads)
+  // device memory callbacks (lsmc_set_allocator); null: cudaMalloc / cudaFree
+  void* (*dev_alloc)(size_t, void*) = nullptr;
+  void (*dev_free)(void*, void*) = nullptr;
+  void* alloc_user = nullptr;
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
   uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
   // autotuned backward shape (ppt << 16 | sub-tiles per job), keyed by
@@ -89,7 +93,7 @@ struct lsmc_plan {
   cudaStream_t stream = nullptr;
   PlanLayout L;
   char* dev = nullptr;
-  int alloc_kind = 0;  // 0 cudaMalloc, 1 arena, 2 cudaMallocAsync
+  int alloc_kind = 0;  // 0 cudaMalloc, 1 arena, 2 cudaMallocAsync, 3 the context's allocator
   bool run_forward = true, run_backward = true, run_greeks = true;
   FwdArgs fa{};
   BwdArgs ba{};
@@ -275,6 +279,17 @@ int plan_alloc(lsmc_plan* p, bool use_arena, bool stream_ordered) {
     p->alloc_kind = 1;
     return LSMC_OK;
   }
+  if (p->ctx && p->ctx->dev_alloc) {
+    p->dev = (char*)p->ctx->dev_alloc(bytes, p->ctx->alloc_user);
+    if (!p->dev) return LSMC_ENOMEM;
+    if ((uintptr_t)p->dev & 255) {  // the layout needs 256-byte alignment
+      p->ctx->dev_free(p->dev, p->ctx->alloc_user);
+      p->dev = nullptr;
+      return LSMC_EINVAL;
+    }
+    p->alloc_kind = 3;
+    return LSMC_OK;
+  }
   if (stream_ordered) {
     LSMC_CUDA(cudaMallocAsync((void**)&p->dev, bytes, p->stream));
     p->alloc_kind = 2;
@@ -297,6 +312,9 @@ void plan_free(lsmc_plan* p) {
       p->ctx->arena.free(p->dev);
     } else if (p->alloc_kind == 2) {
       cudaFreeAsync(p->dev, p->stream);
+    } else if (p->alloc_kind == 3) {
+      cudaStreamSynchronize(p->stream);  // the callback may hand the memory out at once
+      p->ctx->dev_free(p->dev, p->ctx->alloc_user);
     } else {
       cudaStreamSynchronize(p->stream);
       cudaFree(p->dev);
@@ -638,7 +656,17 @@ int start_scheduler(lsmc_ctx* ctx) {
       LSMC_CUDA(cudaMemGetInfo(&fr, &tot));
       budget = std::min<size_t>(fr / 4 * 3, (size_t)64 << 30);
     }
-    LSMC_CUDA(cudaMalloc(&ctx->own_arena_mem, budget));
+    if (ctx->dev_alloc) {
+      ctx->own_arena_mem = ctx->dev_alloc(budget, ctx->alloc_user);
+      if (!ctx->own_arena_mem) return LSMC_ENOMEM;
+      if ((uintptr_t)ctx->own_arena_mem & 255) {
+        ctx->dev_free(ctx->own_arena_mem, ctx->alloc_user);
+        ctx->own_arena_mem = nullptr;
+        return LSMC_EINVAL;
+      }
+    } else {
+      LSMC_CUDA(cudaMalloc(&ctx->own_arena_mem, budget));
+    }
     ctx->arena.reset(ctx->own_arena_mem, budget);
   }
   ctx->slots.resize(ctx->max_inflight);
@@ -756,13 +784,28 @@ void lsmc_destroy(lsmc_ctx* ctx) {
     cudaStreamSynchronize(ctx->own_stream);
     cudaStreamDestroy(ctx->own_stream);
   }
-  if (ctx->own_arena_mem) cudaFree(ctx->own_arena_mem);
+  if (ctx->own_arena_mem) {
+    cudaDeviceSynchronize();
+    if (ctx->dev_free) ctx->dev_free(ctx->own_arena_mem, ctx->alloc_user);
+    else cudaFree(ctx->own_arena_mem);
+  }
   delete ctx;
 }
 
 int lsmc_set_stream(lsmc_ctx* ctx, void* s) {
   if (!ctx) return LSMC_EINVAL;
   ctx->stream = s ? (cudaStream_t)s : ctx->own_stream;
+  return LSMC_OK;
+}
+
+int lsmc_set_allocator(lsmc_ctx* ctx, void* (*alloc)(size_t, void*),
+                       void (*release)(void*, void*), void* user) {
+  if (!ctx || (alloc == nullptr) != (release == nullptr)) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  if (ctx->own_arena_mem || ctx->sched_started) return LSMC_EBUSY;
+  ctx->dev_alloc = alloc;
+  ctx->dev_free = release;
+  ctx->alloc_user = user;
   return LSMC_OK;
 }
 
@@ -933,7 +976,13 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   std::vector<double> o((size_t)nk * kDualOut, 0.0);
   float ms = 0.0f;
-  cudaError_t ce = cudaMallocAsync((void**)&mem, total, p->stream);
+  cudaError_t ce = cudaSuccess;
+  if (ctx->dev_alloc) {
+    mem = (char*)ctx->dev_alloc(total, ctx->alloc_user);
+    if (!mem) { plan_free(p); return LSMC_ENOMEM; }
+  } else {
+    ce = cudaMallocAsync((void**)&mem, total, p->stream);
+  }
   if (ce == cudaSuccess) {
     char* c = mem;
     a.X = c; c += bx;
@@ -951,8 +1000,9 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
     if (ce == cudaSuccess) ce = cudaEventRecord(e1, p->stream);
     if (ce == cudaSuccess)
       ce = cudaMemcpyAsync(o.data(), a.out, o.size() * 8, cudaMemcpyDeviceToHost, p->stream);
-    cudaFreeAsync(mem, p->stream);
     const cudaError_t se = cudaStreamSynchronize(p->stream);
+    if (ctx->dev_free) ctx->dev_free(mem, ctx->alloc_user);
+    else cudaFreeAsync(mem, p->stream);
     if (ce == cudaSuccess) ce = se;
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
   }

@@ -30,7 +30,7 @@ LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31
 
 EXPORTS = [
     "lsmc_strerror", "lsmc_abi_version", "lsmc_create", "lsmc_destroy",
-    "lsmc_set_stream", "lsmc_set_workspace", "lsmc_request_footprint",
+    "lsmc_set_stream", "lsmc_set_workspace", "lsmc_set_allocator", "lsmc_request_footprint",
     "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book", "lsmc_price_bounds",
     "lsmc_plan_create", "lsmc_plan_launch", "lsmc_plan_fetch",
     "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
@@ -138,6 +138,7 @@ def load(build_if_missing: bool = False):
             "lsmc_destroy": ([vp], None),
             "lsmc_set_stream": ([vp, vp], ctypes.c_int),
             "lsmc_set_workspace": ([vp, vp, sz], ctypes.c_int),
+            "lsmc_set_allocator": ([vp, ALLOC_FN, FREE_FN, vp], ctypes.c_int),
             "lsmc_request_footprint": ([vp, P(lsmc_request), P(sz)], ctypes.c_int),
             "lsmc_price_greeks": ([vp, P(lsmc_heston), P(lsmc_contract), u32, u32, i32,
                                    P(lsmc_bumps), u64, P(lsmc_result)], ctypes.c_int),
@@ -212,6 +213,24 @@ def lsmc_destroy(ctx):
 
 def lsmc_set_stream(ctx, stream):
     return check(load().lsmc_set_stream(ctx, stream), "lsmc_set_stream")
+
+
+# device memory callbacks: alloc(bytes, user) -> pointer, release(pointer, user)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def lsmc_set_allocator(ctx, alloc, release):
+    """alloc(nbytes) -> int device pointer (0 on failure), release(ptr);
+    returns the ctypes callbacks, which the caller keeps alive while the
+    context exists.  alloc = release = None restores cudaMalloc."""
+    if alloc is None:
+        check(load().lsmc_set_allocator(ctx, ALLOC_FN(), FREE_FN(), None), "lsmc_set_allocator")
+        return None
+    a = ALLOC_FN(lambda n, user: alloc(n) or None)
+    f = FREE_FN(lambda ptr, user: release(ptr))
+    check(load().lsmc_set_allocator(ctx, a, f, None), "lsmc_set_allocator")
+    return (a, f)
 
 
 def lsmc_set_workspace(ctx, ptr, nbytes):

@@ -151,3 +151,36 @@ def test_autotuned_plans_still_match_oracle(ctx):
     ref = oracle_for(wl)
     for g, r in zip(got, ref):
         assert_close(g, r, parity_tol(g["n_near_ties"]), keys=("price", "delta", "gamma", "vega"))
+
+
+def test_external_allocator():
+    # every plan allocation through callbacks (here PyTorch's caching
+    # allocator, counted): the same results as cudaMalloc, every block
+    # handed back once the context is gone
+    import torch
+    from paper_2206_03719_gb300 import lsmc as L
+    torch_cuda()
+    wl = workloads.SMALL_FP64.replace(n_paths=3000, n_steps=12)
+    calls = {"alloc": 0, "free": 0}
+
+    def alloc(n):
+        calls["alloc"] += 1
+        return torch.cuda.caching_allocator_alloc(n)
+
+    def release(ptr):
+        calls["free"] += 1
+        torch.cuda.caching_allocator_delete(ptr)
+
+    with api.Context() as ref_ctx:
+        ref = ref_ctx.price(wl)
+    ctx = api.Context()
+    keep = L.lsmc_set_allocator(ctx.ctx, alloc, release)
+    got = ctx.price(wl)
+    got_b = ctx.price_bounds(wl.replace(greeks=()), 32, 8)
+    ctx.close()
+    del keep
+    assert got == ref
+    assert got_b[0]["upper"] > 0.0
+    assert calls["alloc"] >= 3 and calls["alloc"] == calls["free"]
+    with api.Context(torch_allocator=True) as c2:
+        assert c2.price(wl) == ref
