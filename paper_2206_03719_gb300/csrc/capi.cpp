@@ -980,6 +980,11 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
   if (ctx->dev_alloc) {
     mem = (char*)ctx->dev_alloc(total, ctx->alloc_user);
     if (!mem) { plan_free(p); return LSMC_ENOMEM; }
+    if ((uintptr_t)mem & 255) {  // the sub-buffers are laid out on 256-byte boundaries
+      ctx->dev_free(mem, ctx->alloc_user);
+      plan_free(p);
+      return LSMC_EINVAL;
+    }
   } else {
     ce = cudaMallocAsync((void**)&mem, total, p->stream);
   }
