@@ -179,8 +179,12 @@ def test_external_allocator():
     got_b = ctx.price_bounds(wl.replace(greeks=()), 32, 8)
     ctx.close()
     del keep
-    assert got == ref
+    def same(a, b):  # Greeks not asked for are NaN on both sides
+        return all(x.keys() == y.keys() and all(
+            x[k] == y[k] or (x[k] != x[k] and y[k] != y[k]) for k in x) for x, y in zip(a, b))
+
+    assert len(got) == len(ref) and same(got, ref)
     assert got_b[0]["upper"] > 0.0
     assert calls["alloc"] >= 3 and calls["alloc"] == calls["free"]
     with api.Context(torch_allocator=True) as c2:
-        assert c2.price(wl) == ref
+        assert same(c2.price(wl), ref)
