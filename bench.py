@@ -9,8 +9,9 @@ estimator and finite-difference Greeks) for the American-put book of
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank prices its own
-replica of the workload (replicas only: the path needs no exchange) and
-rank 0 reports the sum of throughputs over the slowest rank's time.
+replica of the workload on its own random stream (replicas only: the path
+needs no exchange) and rank 0 reports the units of all ranks over the
+slowest rank's time.
 """
 from __future__ import annotations
 
@@ -112,6 +113,30 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_workload(wl, rank):
+    """The workload rank `rank` prices: the same request on its own random
+    stream (stream id + rank), an independent Monte Carlo replica of the same
+    size.  Rank 0 keeps the stream the stored oracle values were taken on."""
+    if rank == 0:
+        return wl
+    return wl.replace(stream=wl.stream + rank)
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's step time (every rank gets it); ms itself alone."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, units_per_rank, ms_max):
+    """Units all ranks processed per second of the slowest rank's step."""
+    return world * units_per_rank / (ms_max / 1e3)
 
 
 class ClockSampler:
@@ -547,6 +572,7 @@ def main():
         run_reference(args, wl)
         return
     rank, world, local = dist_env()
+    wl = replica_workload(wl, rank)
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device")
@@ -603,11 +629,8 @@ def main():
     kms, launches = plan.kernel_times()
     res = plan.fetch()
     info = plan.info()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * wl.n_greeks / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = job_throughput(world, wl.n_greeks, ms_max)
 
     plan.close()
     # end to end through the public call with host buffers
@@ -619,8 +642,8 @@ def main():
             t0 = time.perf_counter()
             out = L.lsmc_price_request(ctx.ctx, req.c)
             times.append(time.perf_counter() - t0)
-        e2e_s = sorted(times[1:])[len(times[1:]) // 2]
-        e2e = {"value": world * wl.n_greeks / e2e_s, "unit": "Greeks/s",
+        e2e_s = max_over_ranks(sorted(times[1:])[len(times[1:]) // 2] * 1e3, dist, "cuda") / 1e3
+        e2e = {"value": job_throughput(world, wl.n_greeks, e2e_s * 1e3), "unit": "Greeks/s",
                "h2d_bytes_per_step": int(info.h2d_bytes),
                "d2h_bytes_per_step": int(info.d2h_bytes),
                "ms_per_step": e2e_s * 1e3,
@@ -694,8 +717,8 @@ def main():
                    "backward_subtiles_per_job": tuned_sub,
                    "backward_paths_per_lane": tuned_ppt,
                    "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
-        "path_steps_per_s": {"generated": world * wl.generated_path_steps / (ms_max / 1e3),
-                             "lsmc": world * wl.lsmc_path_steps / (ms_max / 1e3)},
+        "path_steps_per_s": {"generated": job_throughput(world, wl.generated_path_steps, ms_max),
+                             "lsmc": job_throughput(world, wl.lsmc_path_steps, ms_max)},
         "max_rel_err_vs_oracle": acc,
         "accuracy_ok": (acc is not None and acc <= 1e-4) if acc is not None else None,
         "roofline": roofline,
