@@ -21,8 +21,8 @@
 //      second compacted list (exercise.cuh);
 //   2. accumulates, over in-the-money paths (compacted again), the 15
 //      distinct monomials x^a w^b (a + b <= 4) that make up X^T X and the six
-//      entries of X^T Y (register sums, a transposed fixed-order sum over the
-//      lanes and then over the warps: no atomics, so results do not depend on
+//      entries of X^T Y (register sums, a fixed-order sum over the lanes and
+//      then over the warps: no atomics, so results do not depend on
 //      scheduling);
 //   3. writes the tile partial and arrives on the instance's counter.  The CTA
 //      that arrives last sums the tile partials in tile order, solves the
@@ -188,6 +188,37 @@ template <int NA> struct Acc<float, NA> {
     }
   }
 };
+
+// Reduce-scatter of C per-lane doubles over the warp by recursive halving
+// over the lane bits O, O / 2, ..., 1: at each level lane l and its partner
+// l ^ O split the sums they still hold, the lane with the bit clear keeps the
+// lower half and its partner the upper half (padded with zeros), and each
+// adds the partner's copy of the half it keeps.  After the last level a lane
+// holds one complete sum over the 32 lanes, summed in a fixed order; `idx` is
+// its index (base + position), or -1 for a lane left with padding only.
+template <int C, int O>
+__device__ __forceinline__ void halving_sum(const double (&v)[C], int lane, int base, int real,
+                                            double& out, int& idx) {
+  constexpr int H = (C + 1) / 2;
+  const bool upper = (lane & O) != 0;
+  double nxt[H];
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    const double lo = v[i];
+    const double hi = (H + i < C) ? v[(H + i < C) ? H + i : i] : 0.0;
+    const double got = __shfl_xor_sync(0xffffffffu, upper ? lo : hi, O);
+    nxt[i] = (upper ? hi : lo) + got;
+  }
+  const int nbase = upper ? base + H : base;
+  const int nreal = upper ? (real > H ? real - H : 0) : (real < H ? real : H);
+  if constexpr (O == 1) {
+    static_assert(H == 1, "at most 32 sums");
+    out = nxt[0];
+    idx = nreal >= 1 ? nbase : -1;
+  } else {
+    halving_sum<H, O / 2>(nxt, lane, nbase, nreal, out, idx);
+  }
+}
 
 }  // namespace
 
@@ -765,19 +796,29 @@ backward_kernel(BwdArgs a) {
     }
 
     // ---- block reduction into the tile partial --------------------------------
-    // per warp, the lanes' sums go through shared memory transposed (a row per
-    // sum, padded against bank conflicts, in the warp's compaction buffers)
-    // and lane i adds row i in lane order: a fixed order, and one add per lane
-    // and sum instead of a five-level butterfly over every sum
+    // per warp first, in a fixed order: double precision by a reduce-scatter
+    // over shuffles; the float-pair sums through shared memory transposed (a
+    // row per sum, padded against bank conflicts, in the warp's compaction
+    // buffers), lane i adding row i in lane order
     if (final_job) {
       sy = warp_sum(sy);
       sy2 = warp_sum(sy2);
+    } else if constexpr (!kSingle) {
+      // double: reduce-scatter by recursive halving, all lanes busy (an FP64
+      // warp instruction takes the same pipe time whatever its active
+      // lanes): about NA adds per lane in place of 31 per sum on NA lanes
+      double vs[NA];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) vs[i] = i == 0 ? (double)n_itm : acc.s[i];  // the count: an integer
+      double out;
+      int i;
+      halving_sum<NA, 16>(vs, lane, 0, NA, out, i);
+      if (i >= 0) s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = out;
     } else {
-      using RedT = typename std::conditional<kSingle, float2, double>::type;
       // rows per pass: as many as the warp's moment buffers hold
-      constexpr int RROWS = (int)(sizeof(wb.m) / (33 * sizeof(RedT)));
+      constexpr int RROWS = (int)(sizeof(wb.m) / (33 * sizeof(float2)));
       static_assert(RROWS >= 1 && RROWS <= 32, "reduction rows per pass");
-      RedT(*red)[33] = reinterpret_cast<RedT(*)[33]>(&wb.m[0][0]);
+      float2(*red)[33] = reinterpret_cast<float2(*)[33]>(&wb.m[0][0]);
       __syncwarp();
 #pragma unroll
       for (int a0 = 0; a0 < NA; a0 += RROWS) {
@@ -786,23 +827,15 @@ backward_kernel(BwdArgs a) {
           // the path count: an integer, except in single precision
           if constexpr (std::is_same<Real, float>::value)
             red[i - a0][lane] = acc.pair(i);
-          else if constexpr (kSingle)
-            red[i - a0][lane] = i == 0 ? make_float2((float)n_itm, 0.0f) : acc.pair(i);
           else
-            red[i - a0][lane] = i == 0 ? (double)n_itm : acc.s[i];
+            red[i - a0][lane] = i == 0 ? make_float2((float)n_itm, 0.0f) : acc.pair(i);
         }
         __syncwarp();
         const int i = a0 + lane;
         if (lane < RROWS && i < NA) {
-          if constexpr (kSingle) {
-            float2 pr = red[lane][0];
-            for (int l = 1; l < 32; ++l) pr = pair_add(pr, red[lane][l]);
-            s_redf[warp][i] = pr;
-          } else {
-            double v = red[lane][0];
-            for (int l = 1; l < 32; ++l) v += red[lane][l];
-            s_red[warp][i < NM ? i : kSlotRhs + (i - NM)] = v;
-          }
+          float2 pr = red[lane][0];
+          for (int l = 1; l < 32; ++l) pr = pair_add(pr, red[lane][l]);
+          s_redf[warp][i] = pr;
         }
         __syncwarp();
       }
