@@ -46,12 +46,12 @@ BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
 # DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel at 98,304 paths (2.645751e9 + 0.299446e9 bytes) scaled by the path
+# kernel at 98,304 paths (2.936395e9 + 0.429968e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
 # the kernel source it was taken from: reported as null once the code of
 # backward.cu changes (code_sha256_16).
-BWD_TRAFFIC = {"bytes": (2.645750784e9 + 0.299445760e9) * 131072 / 98304,
-               "source_sha256_16": "4e7f8e0d7cc37c20",
+BWD_TRAFFIC = {"bytes": (2.936395264e9 + 0.429968128e9) * 131072 / 98304,
+               "source_sha256_16": "f6e6b3145e50d522",
                "capture": "profiles/backward_kernel_fp64_98304x252.md (traffic capture), "
                           "scaled by 131072/98304"}
 

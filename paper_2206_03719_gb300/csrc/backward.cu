@@ -16,10 +16,12 @@
 //   1. applies the exercise rule of date n+1 (coefficients published by the
 //      previous round) to the tile's cash flows, or initialises them with the
 //      payoff at maturity: in-the-money paths compacted per warp, each
-//      decision first taken by a float screen with an error bound and, where
-//      the screen cannot decide, by the test in the working precision on a
-//      second compacted list (exercise.cuh);
-//   2. accumulates, over in-the-money paths (compacted again), the 15
+//      decision first taken by a float screen with an error bound
+//      (exercise.cuh); the items it leaves (exercise, or undecided) are
+//      collected over the job and settled in the working precision a warp's
+//      width at a time;
+//   2. in a second pass over the tile, accumulates, over in-the-money paths
+//      (compacted again), the 15
 //      distinct monomials x^a w^b (a + b <= 4) that make up X^T X and the six
 //      entries of X^T Y (register sums, a fixed-order sum over the lanes and
 //      then over the warps: no atomics, so results do not depend on
@@ -314,9 +316,12 @@ struct BwdWarpBufs {
   Real xs[kCap];
   Real xv[kCap];
   Real m[3][kCap + 32];
-  Real zn[PPT][32];
   unsigned short co[kCap];
-  unsigned short ex[kCap];  // exercise items the float screen did not settle
+  // exercise items the float screen did not settle, collected over a job:
+  // row values, path offset in the job tile | screen verdict << 30
+  Real xe[kCap + 32];
+  Real xw[kCap + 32];
+  uint32_t xo[kCap + 32];
 };
 
 // Compaction buffer items.  With a 16-bit store in double precision the row
@@ -550,97 +555,195 @@ backward_kernel(BwdArgs a) {
     uint32_t ties = 0;
 
     const unsigned lane_lt = (1u << lane) - 1u;
-    Real* cs = wb.xs;
-    Real* cv = wb.xv;
-    Real* ms = wb.m[0];
-    Real* mv = wb.m[1];
-    Real* my = wb.m[2];
-    int mcarry = 0;  // compacted moment items carried to the next sub-tile
-    unsigned short* co = wb.co;
-    for (uint32_t sb = 0; sb < sub; ++sb) {
-      const uint32_t sub_base = tile_base + sb * TILE0;
-      if (sub_base >= P) break;  // uniform across the CTA
-      const uint32_t p_base = sub_base + tid;
-      // every load of the sub-tile is issued before any arithmetic, so each
-      // thread has up to 5 * PPT independent loads in flight
-      Real zr[PPT];
-      St e1r[PPT], v1r[PPT], e0r[PPT], v0r[PPT];
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        const uint32_t p = p_base + k * kBlock;
-        const bool valid = p < P;
-        zr[k] = (Real)0;
-        e1r[k] = v1r[k] = e0r[k] = v0r[k] = (St)0;
-        if (valid) {
-          if (first) {
-            e1r[k] = EN[p];
-          } else {
-            zr[k] = ld_cg(Z + p);
-            if (bok) {
-              e1r[k] = E1[p];
-              if (BASIS == kBasisSV2) v1r[k] = V1[p];
-            }
-          }
-          if (!final_job) {
-            e0r[k] = E0[p];
-            if (BASIS == kBasisSV2) v0r[k] = V0[p];
-          }
-        }
-      }
-      LoadT e1[PPT], v1[PPT], e0[PPT], v0[PPT];
-#pragma unroll
-      for (int k = 0; k < PPT; ++k) {
-        e1[k] = RF::widen(e1r[k]);
-        v1[k] = RF::widen(v1r[k]);
-        e0[k] = RF::widen(e0r[k]);
-        v0[k] = RF::widen(v0r[k]);
-      }
-      Real z[PPT];
-      if (first) {
+    if constexpr (!kCompact) {
+      // single precision: one predicated pass per sub-tile (bound by loads)
+      for (uint32_t sb = 0; sb < sub; ++sb) {
+        const uint32_t sub_base = tile_base + sb * TILE0;
+        if (sub_base >= P) break;  // uniform across the CTA
+        const uint32_t p_base = sub_base + tid;
+        // every load of the sub-tile is issued before any arithmetic, so each
+        // thread has up to 5 * PPT independent loads in flight
+        Real zr[PPT];
+        St e1r[PPT], v1r[PPT], e0r[PPT], v0r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
-          z[k] = (Real)0;
+          zr[k] = (Real)0;
+          e1r[k] = v1r[k] = e0r[k] = v0r[k] = (St)0;
           if (p < P) {
-            const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
-            z[k] = fma(h, dNhi, h * dNlo);
-            euro += (double)z[k];
-            if (!final_job) Z[p] = z[k];
+            if (first) {
+              e1r[k] = EN[p];
+            } else {
+              zr[k] = ld_cg(Z + p);
+              if (bok) {
+                e1r[k] = E1[p];
+                if (BASIS == kBasisSV2) v1r[k] = V1[p];
+              }
+            }
+            if (!final_job) {
+              e0r[k] = E0[p];
+              if (BASIS == kBasisSV2) v0r[k] = V0[p];
+            }
           }
         }
-      } else {
+        LoadT e1[PPT], v1[PPT], e0[PPT], v0[PPT];
 #pragma unroll
-        for (int k = 0; k < PPT; ++k) z[k] = zr[k];
-        if (bok && !kCompact) {
-          // exercise at date n + 1 where the discounted payoff beats the
-          // fitted continuation value (basis centred at the strike and theta)
+        for (int k = 0; k < PPT; ++k) {
+          e1[k] = RF::widen(e1r[k]);
+          v1[k] = RF::widen(v1r[k]);
+          e0[k] = RF::widen(e0r[k]);
+          v0[k] = RF::widen(v0r[k]);
+        }
+        Real z[PPT];
+        if (first) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
             const uint32_t p = p_base + k * kBlock;
-            const Real S = s1 * e1[k];
-            if (p < P && in_money<Real>(type, K, S)) {
-              const Real h = intrinsic<Real>(type, K, S);
-              const Real x = qfma(S, invK, (Real)-1);
-              Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
-              if (BASIS == kBasisSV2) {
-                const Real w = qfma((Real)v1[k], invTh, (Real)-1);
-                c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
-              }
-              const Real hd = qmul(h, d1);
-              bool exercise, tie;
-              decide<Real>(hd, c, exercise, tie);
-              if (tie) ++ties;
-              if (exercise) {
-                const Real hz = fma(h, d1, h * d1lo);
-                z[k] = hz;
-                if (!final_job) Z[p] = hz;
+            z[k] = (Real)0;
+            if (p < P) {
+              const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
+              z[k] = fma(h, dNhi, h * dNlo);
+              euro += (double)z[k];
+              if (!final_job) Z[p] = z[k];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) z[k] = zr[k];
+          if (bok) {
+            // exercise at date n + 1 where the discounted payoff beats the
+            // fitted continuation value (basis centred at the strike and theta)
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+              const uint32_t p = p_base + k * kBlock;
+              const Real S = s1 * e1[k];
+              if (p < P && in_money<Real>(type, K, S)) {
+                const Real h = intrinsic<Real>(type, K, S);
+                const Real x = qfma(S, invK, (Real)-1);
+                Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+                if (BASIS == kBasisSV2) {
+                  const Real w = qfma((Real)v1[k], invTh, (Real)-1);
+                  c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+                }
+                const Real hd = qmul(h, d1);
+                bool exercise, tie;
+                decide<Real>(hd, c, exercise, tie);
+                if (tie) ++ties;
+                if (exercise) {
+                  const Real hz = fma(h, d1, h * d1lo);
+                  z[k] = hz;
+                  if (!final_job) Z[p] = hz;
+                }
               }
             }
           }
-        } else if (bok) {
-          // the same with the in-the-money paths compacted per warp, so the
-          // heavy arithmetic runs on dense lists instead of on lanes that are
-          // mostly out of the money
+        }
+        if (final_job) {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            if (p < P) {
+              const double zv = (double)z[k];
+              sy += zv;
+              sy2 += zv * zv;
+            }
+          }
+        } else {
+          // moment sums of date n over the in-the-money paths
+          Real* t = acc.target();
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            const Real S = s0 * e0[k];
+            if (p < P && in_money<Real>(type, K, S)) {
+              accumulate_moments<Real, BASIS, NM>(t, n_itm, S, v0[k], z[k], invK, invTh);
+            }
+          }
+          acc.fold();
+        }
+      }
+    } else {
+      // ---- pass 1: the exercise rule of date n + 1 (or the payoff at
+      // maturity) on every sub-tile.  In-the-money paths are compacted per
+      // warp and screened in float; the items the screen does not settle as
+      // continuing (exercise, or undecided) are collected over the whole job
+      // and settled in the working precision a warp's width at a time, the
+      // remainder carried to the next sub-tile, so those lanes stay busy as
+      // well (an FP64 warp instruction costs the same whatever its active
+      // lanes).  The cash flows after the rule are in Z for pass 2.
+      if (first || bok) {
+        Real* cs = wb.xs;
+        Real* cv = wb.xv;
+        unsigned short* co = wb.co;
+        // one collected item: its row values (as the compaction buffers hold
+        // them), its path's offset in the job tile and the screen's verdict
+        auto settle = [&](int j) {
+          const uint32_t code = wb.xo[j];
+          const int pre = (int)(code >> 30);
+          const uint32_t p = tile_base + (code & 0x3fffffffu);
+          const Real S = kProdLate ? s1 * get_item<Real, LoadT>(wb.xe, j) : wb.xe[j];
+          const Real h = intrinsic<Real>(type, K, S);
+          const Real hd = qmul(h, d1);
+          bool exercise = pre == 1;
+          if (pre == 2) {
+            const Real x = qfma(S, invK, (Real)-1);
+            Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
+            if (BASIS == kBasisSV2) {
+              const Real w = qfma(get_item<Real, LoadT>(wb.xw, j), invTh, (Real)-1);
+              c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
+            }
+            bool tie;
+            decide<Real>(hd, c, exercise, tie);
+            if (tie) ++ties;
+          }
+          if (exercise) {
+            Real hz;
+            if constexpr (std::is_same<Real, df>::value) {
+              hz = quick_two_sum(hd.hi, hd.lo);
+            } else {
+              hz = fma(h, d1, h * d1lo);
+            }
+            Z[p] = hz;
+          }
+        };
+        int xn = 0;  // collected items not yet settled (fewer than 32)
+        for (uint32_t sb = 0; sb < sub; ++sb) {
+          const uint32_t sub_base = tile_base + sb * TILE0;
+          if (sub_base >= P) break;  // uniform across the CTA
+          const uint32_t p_base = sub_base + tid;
+          St e1r[PPT], v1r[PPT];
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            e1r[k] = v1r[k] = (St)0;
+            if (p < P) {
+              if (first) {
+                e1r[k] = EN[p];
+              } else {
+                e1r[k] = E1[p];
+                if (BASIS == kBasisSV2) v1r[k] = V1[p];
+              }
+            }
+          }
+          LoadT e1[PPT], v1[PPT];
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            e1[k] = RF::widen(e1r[k]);
+            v1[k] = RF::widen(v1r[k]);
+          }
+          if (first) {
+#pragma unroll
+            for (int k = 0; k < PPT; ++k) {
+              const uint32_t p = p_base + k * kBlock;
+              if (p < P) {
+                const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
+                const Real z = fma(h, dNhi, h * dNlo);
+                euro += (double)z;
+                Z[p] = z;
+              }
+            }
+            continue;
+          }
           int cnt = 0;
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
@@ -661,13 +764,8 @@ backward_kernel(BwdArgs a) {
               co[pos] = (unsigned short)(k * 32 + lane);
             }
             cnt += __popc(m);
-            wb.zn[k][lane] = z[k];
           }
           __syncwarp();
-          // the float screen of every item; the items it does not settle as
-          // continuing (exercise, or undecided) are compacted a second time,
-          // so the working-precision work runs on dense lists as well
-          int cnt2 = 0;
           for (int j0 = 0; j0 < cnt; j0 += 32) {
             const int j = j0 + lane;
             int pre = 0;
@@ -676,72 +774,87 @@ backward_kernel(BwdArgs a) {
                                            BASIS == kBasisSV2 ? item_float<Real, LoadT>(cv, j)
                                                               : 0.0f);
             const unsigned m = __ballot_sync(0xffffffffu, pre != 0);
-            if (pre != 0) wb.ex[cnt2 + __popc(m & lane_lt)] = (unsigned short)(j | (pre << 12));
-            cnt2 += __popc(m);
+            if (pre != 0) {
+              const int q = xn + __popc(m & lane_lt);
+              const int o = co[j];
+              wb.xe[q] = cs[j];
+              if (BASIS == kBasisSV2) wb.xw[q] = cv[j];
+              wb.xo[q] = (sb * TILE0 + (uint32_t)(o >> 5) * kBlock + warp * 32 + (o & 31)) |
+                         ((uint32_t)pre << 30);
+            }
+            xn += __popc(m);
           }
           __syncwarp();
-          for (int jj = lane; jj < cnt2; jj += 32) {
-            const int code = wb.ex[jj], j = code & 0xfff, pre = code >> 12;
-            const Real S = kProdLate ? s1 * get_item<Real, LoadT>(cs, j) : cs[j];
-            const Real h = intrinsic<Real>(type, K, S);
-            const Real hd = qmul(h, d1);
-            bool exercise = pre == 1;
-            if (pre == 2) {
-              const Real x = qfma(S, invK, (Real)-1);
-              Real c = qfma(qfma(b[2], x, b[1]), x, b[0]);
-              if (BASIS == kBasisSV2) {
-                const Real w = qfma(get_item<Real, LoadT>(cv, j), invTh, (Real)-1);
-                c = qfma(qfma(b[5], w, qfma(b[4], x, b[3])), w, c);
-              }
-              bool tie;
-              decide<Real>(hd, c, exercise, tie);
-              if (tie) ++ties;
-            }
-            if (exercise) {
-              Real hz;
-              if constexpr (std::is_same<Real, df>::value) {
-                hz = quick_two_sum(hd.hi, hd.lo);
-              } else {
-                hz = fma(h, d1, h * d1lo);
-              }
-              const int o = co[j], kk = o >> 5, ll = o & 31;
-              wb.zn[kk][ll] = hz;
-              if (!final_job) Z[sub_base + warp * 32 + ll + kk * kBlock] = hz;
-            }
+          const int full = xn & ~31;
+          for (int j = lane; j < full; j += 32) settle(j);
+          const int rem = xn - full;
+          Real t0 = (Real)0, t1 = (Real)0;
+          uint32_t t2 = 0;
+          if (lane < rem) {
+            t0 = wb.xe[full + lane];
+            if (BASIS == kBasisSV2) t1 = wb.xw[full + lane];
+            t2 = wb.xo[full + lane];
           }
           __syncwarp();
-#pragma unroll
-          for (int k = 0; k < PPT; ++k) z[k] = wb.zn[k][lane];
+          if (lane < rem) {
+            wb.xe[lane] = t0;
+            if (BASIS == kBasisSV2) wb.xw[lane] = t1;
+            wb.xo[lane] = t2;
+          }
           __syncwarp();
+          xn = rem;
         }
+        if (lane < xn) settle(lane);  // the items left from the last sub-tile
+        // the cash flows stored above are read back by other lanes of the warp
+        __threadfence_block();
+        __syncwarp();
       }
 
-      if (final_job) {
+      // ---- pass 2: the moment sums of date n over the in-the-money paths
+      // (the estimator sums in the last round) with the cash flows after the
+      // rule; only whole warps of compacted items are summed, the rest is
+      // carried to the next sub-tile (or summed at the end of the job)
+      Real* ms = wb.m[0];
+      Real* mv = wb.m[1];
+      Real* my = wb.m[2];
+      int mcarry = 0;  // compacted moment items carried to the next sub-tile
+      for (uint32_t sb = 0; sb < sub; ++sb) {
+        const uint32_t sub_base = tile_base + sb * TILE0;
+        if (sub_base >= P) break;  // uniform across the CTA
+        const uint32_t p_base = sub_base + tid;
+        Real z[PPT];
+        St e0r[PPT], v0r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
           const uint32_t p = p_base + k * kBlock;
+          z[k] = (Real)0;
+          e0r[k] = v0r[k] = (St)0;
           if (p < P) {
-            const double zv = (double)z[k];
-            sy += zv;
-            sy2 += zv * zv;
+            z[k] = ld_cg(Z + p);
+            if (!final_job) {
+              e0r[k] = E0[p];
+              if (BASIS == kBasisSV2) v0r[k] = V0[p];
+            }
           }
         }
-      } else if (!kCompact) {
-        // moment sums of date n over the in-the-money paths
-        Real* t = acc.target();
+        if (final_job) {
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            const uint32_t p = p_base + k * kBlock;
+            if (p < P) {
+              const double zv = (double)z[k];
+              sy += zv;
+              sy2 += zv * zv;
+            }
+          }
+          continue;
+        }
+        LoadT e0[PPT], v0[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          const uint32_t p = p_base + k * kBlock;
-          const Real S = s0 * e0[k];
-          if (p < P && in_money<Real>(type, K, S)) {
-            accumulate_moments<Real, BASIS, NM>(t, n_itm, S, v0[k], z[k], invK, invTh);
-          }
+          e0[k] = RF::widen(e0r[k]);
+          v0[k] = RF::widen(v0r[k]);
         }
-        acc.fold();
-      } else {
-        // moment sums of date n over the in-the-money paths, compacted; only
-        // whole warps of items are summed, the rest is carried to the next
-        // sub-tile (or summed at the end of the job), so the lanes stay busy
         int cnt = mcarry;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
@@ -785,14 +898,13 @@ backward_kernel(BwdArgs a) {
         __syncwarp();
         acc.fold();
       }
-    }
-
-    if (kCompact && mcarry > 0) {  // the carried moment items of the last sub-tile
-      if (lane < mcarry)
-        accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, get_item<Real, LoadT>(ms, lane),
-                                            get_item<Real, LoadT>(mv, lane), my[lane], xK0,
-                                            invTh);
-      __syncwarp();
+      if (mcarry > 0) {  // the carried moment items of the last sub-tile
+        if (lane < mcarry)
+          accumulate_moments<Real, BASIS, NM>(acc.target(), n_itm, get_item<Real, LoadT>(ms, lane),
+                                              get_item<Real, LoadT>(mv, lane), my[lane], xK0,
+                                              invTh);
+        __syncwarp();
+      }
     }
 
     // ---- block reduction into the tile partial --------------------------------
