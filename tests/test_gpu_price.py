@@ -51,6 +51,9 @@ VARIANTS = [
     dict(scheme="ft_euler", model=dict(workloads.HESTON_BASE, xi=0.0), basis="s2"),
     dict(model=dict(workloads.HESTON_BASE, kappa=0.5, theta=0.09, xi=0.6, rho=-0.3, v0=0.01),
          greeks=workloads.ALL_GREEKS, stream=17, seed=2**63 + 5),
+    # deep in the money: most paths exercise at every date, so the exercise
+    # items collected over a job fill several warps (ragged, several sub-tiles)
+    dict(strikes=[112.0, 116.0], n_paths=9000, n_steps=10, basis="sv2"),
 ]
 
 
