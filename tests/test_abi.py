@@ -116,3 +116,13 @@ def test_stage_entry_points_reject_bad_arguments_before_launch(lib):
     m = L.lsmc_heston(100, 0.02, 0, 0.04, 1.5, 0.04, 0.3, -0.7)
     assert lib.lsmc_paths(ctypes.byref(m), 1.0, 0, 0, 16, 4, 1, 0, None, None, None) == L.LSMC_EINVAL
     assert lib.lsmc_create(None, None) == L.LSMC_EINVAL
+
+
+def test_allocator_and_bounds_entry_points_reject_bad_arguments(lib):
+    # no context, or only one of the two callbacks: refused before anything runs
+    alloc = L.ALLOC_FN(lambda n, user: None)
+    release = L.FREE_FN(lambda p, user: None)
+    assert lib.lsmc_set_allocator(None, alloc, release, None) == L.LSMC_EINVAL
+    assert lib.lsmc_set_allocator(None, L.ALLOC_FN(), L.FREE_FN(), None) == L.LSMC_EINVAL
+    out = L.lsmc_bounds()
+    assert lib.lsmc_price_bounds(None, None, 16, 16, ctypes.byref(out)) == L.LSMC_EINVAL
