@@ -304,12 +304,14 @@ __device__ __forceinline__ void accumulate_moments(Real* t, uint32_t& cnt, Real 
   }
 }
 
-// Per-warp buffers of the backward kernel (dynamic shared memory): S and v
-// of the in-the-money paths compacted for the exercise test; S, v and cash
-// flow of those compacted for the moment sums (room for a sub-tile plus the
-// fewer than 32 items carried from the previous one; the job-end reduction
-// reuses this space); the origins of the exercise items; the cash flows of
-// the sub-tile after the exercise test.
+// Per-warp buffers of the backward kernel (dynamic shared memory): the row
+// values (e or S, and v) of the in-the-money paths compacted for the
+// exercise test and their origins (k * 32 + lane); the row values and cash
+// flows of those compacted for the moment sums (room for a sub-tile plus the
+// fewer than 32 items carried from the previous one; the float-pair job-end
+// reduction reuses this space); the exercise items the float screen did not
+// settle, collected over a job (the same room): row values, and the path's
+// offset in the job tile | the screen's verdict << 30.
 template <typename Real, int PPT>
 struct BwdWarpBufs {
   static constexpr int kCap = 32 * PPT;
@@ -317,8 +319,6 @@ struct BwdWarpBufs {
   Real xv[kCap];
   Real m[3][kCap + 32];
   unsigned short co[kCap];
-  // exercise items the float screen did not settle, collected over a job:
-  // row values, path offset in the job tile | screen verdict << 30
   Real xe[kCap + 32];
   Real xw[kCap + 32];
   uint32_t xo[kCap + 32];
