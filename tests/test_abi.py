@@ -126,3 +126,24 @@ def test_allocator_and_bounds_entry_points_reject_bad_arguments(lib):
     assert lib.lsmc_set_allocator(None, L.ALLOC_FN(), L.FREE_FN(), None) == L.LSMC_EINVAL
     out = L.lsmc_bounds()
     assert lib.lsmc_price_bounds(None, None, 16, 16, ctypes.byref(out)) == L.LSMC_EINVAL
+
+
+def test_request_flags_on_host(lib):
+    # footprints follow the flags (16-bit rows, no path store), and the flag
+    # rules are checked before anything is allocated
+    fp = lambda wl: L.lsmc_request_footprint(None, api.Request(wl).c)
+    base = workloads.PAPER_FP64
+    rows = 5 * 2 * 252 * 131072  # path groups x (E, v) x dates x paths
+    native = fp(base)
+    half = fp(base.replace(store="fp16"))
+    assert fp(base.replace(store="bf16")) == half
+    assert native - half >= rows * (8 - 2)
+    assert fp(base.replace(regenerate=True)) < native - rows * 8 * 3 // 4
+    assert fp(base.replace(regenerate=True, store="fp16")) < half
+    assert fp(base.replace(out_of_sample=True)) >= native
+    for flags in (16, 1 << 31, L.LSMC_FLAG_STORE_FP16 | L.LSMC_FLAG_STORE_BF16):
+        r = api.Request(base)
+        r.c.flags = flags
+        with pytest.raises(L.LsmcError) as e:
+            L.lsmc_request_footprint(None, r.c)
+        assert e.value.status == L.LSMC_EINVAL, flags
