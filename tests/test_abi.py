@@ -147,3 +147,19 @@ def test_request_flags_on_host(lib):
         with pytest.raises(L.LsmcError) as e:
             L.lsmc_request_footprint(None, r.c)
         assert e.value.status == L.LSMC_EINVAL, flags
+
+
+def test_path_groups_follow_the_bumps_on_host(lib):
+    # spot and rate bumps reuse the base simulation's rows (S0 scales the
+    # stored exp(x); a rate bump shifts every log price by +-dr t), while the
+    # v0 and maturity bumps are simulations of their own: one path group for
+    # price, delta, gamma and rho, two more each for vega and theta
+    base = workloads.PAPER_FP64
+    rows = 2 * 252 * 131072 * 8  # E and v rows of one path group
+    groups = {}
+    for g in [(), ("delta", "gamma", "rho"), ("vega",), ("theta",), workloads.ALL_GREEKS]:
+        n = L.lsmc_request_footprint(None, api.Request(base.replace(greeks=g)).c)
+        groups[g] = n // rows
+    assert groups[()] == groups[("delta", "gamma", "rho")] == 1
+    assert groups[("vega",)] == groups[("theta",)] == 3
+    assert groups[workloads.ALL_GREEKS] == 5
