@@ -141,3 +141,23 @@ def test_heston_mean_log_price_within_error():
     se = lx.std(ddof=1) / math.sqrt(P)
     ref = refs.heston_mean_log(100.0, 0.02, 0.0, T, 0.09, 2.0, 0.03)
     assert abs(lx.mean() - ref) < 4 * se + 2e-3
+
+
+@pytest.mark.parametrize("scheme", [oracle.QE, oracle.FT_EULER])
+def test_spot_and_rate_move_paths_by_known_factors(scheme):
+    # In the Heston model the variance does not depend on S0, r or q, and the
+    # log price relative to its start moves by (r - q) t: on common random
+    # numbers a spot bump scales every path value by (1 + h) and a rate bump
+    # by exp(dr t_n), with the variance paths unchanged.  (These are the facts
+    # that let the spot and rate revaluations share the base simulation.)
+    T, P, N, h, dr = 1.0, 64, 24, 0.01, 1e-3
+    base = oracle.heston(**H)
+    S, V = oracle.paths(base, T, scheme, P, N, 42, n_threads=1)
+    Ss, Vs = oracle.paths(oracle.heston(**dict(H, S0=H["S0"] * (1 + h))), T, scheme, P, N, 42,
+                          n_threads=1)
+    Sr, Vr = oracle.paths(oracle.heston(**dict(H, r=H["r"] + dr)), T, scheme, P, N, 42,
+                          n_threads=1)
+    assert np.array_equal(V, Vs) and np.array_equal(V, Vr)
+    np.testing.assert_allclose(Ss / S, 1 + h, rtol=1e-14, atol=0)
+    t = (np.arange(N + 1) * (T / N))[:, None]
+    np.testing.assert_allclose(np.log(Sr / S), dr * t * np.ones_like(S), rtol=0, atol=1e-13)
