@@ -592,13 +592,10 @@ def main():
         return
     req = api.Request(wl)
     need = L.lsmc_request_footprint(None, req.c)
-    if args.sub:
-        # fixed shape (profiling runs): the context reads the override at creation
-        os.environ["LSMC_BACKWARD_SUB"] = str(args.sub)
-        if args.ppt:
-            os.environ["LSMC_BACKWARD_PPT"] = str(args.ppt)
     ctx = api.Context(workspace_bytes=need + (256 << 20))
     if args.sub:
+        # a fixed backward shape (profiling runs) instead of the autotuner's
+        ctx.set_backward_shape(args.sub, args.ppt)
         tuned_sub, tuned_ppt = args.sub, args.ppt or None
     else:
         tuned_sub, tuned_ppt, _ = ctx.autotune([wl])

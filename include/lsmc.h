@@ -193,6 +193,12 @@ typedef struct lsmc_plan lsmc_plan;
 /* ---- library ----------------------------------------------------------- */
 const char* lsmc_strerror(int status);
 int lsmc_abi_version(void);
+/* Device allocations the library has made in this process: cudaMalloc and
+ * cudaMallocAsync calls and successful lsmc_set_allocator callbacks (not the
+ * sub-allocations from a workspace).  A diagnostic with no counterpart in the
+ * paper: lets a caller check that a code path allocated nothing.
+ * LSMC_EINVAL if count is NULL. */
+int lsmc_device_allocations(uint64_t* count);
 
 /* ---- context ----------------------------------------------------------- */
 /* Creates a context on config->device (NULL: device 0, FP64, QE).  The
@@ -215,6 +221,20 @@ int lsmc_set_stream(lsmc_ctx* ctx, void* cuda_stream);
  * The callbacks may run on the context's scheduler thread. */
 int lsmc_set_allocator(lsmc_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
                        void (*release)(void* ptr, void* user), void* user);
+/* Upper bound, in seconds, of every device-side wait of the context's later
+ * plans and launches (a backward job waiting for the previous exercise
+ * date's coefficients): on expiry the kernels record an error and return, and
+ * the host call reports LSMC_ETIMEOUT; the context stays usable.  Default
+ * 20 s; 0 fails any wait that is not satisfied at once.  LSMC_EINVAL outside
+ * [0, 3600].  Bounded waits are a deployment safeguard (the paper has none). */
+int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds);
+/* Tile shape of the backward pass for the context's later plans: sub
+ * sub-tiles per job and ppt paths per thread of a sub-tile (2 or 4 for
+ * LSMC_FP64 and LSMC_DF, 4 or 8 for LSMC_MIXED; a value not compiled for a
+ * plan's precision falls back to its default).  0, 0: chosen per plan (the
+ * autotuner's result when lsmc_autotune has tuned that kind of plan).
+ * LSMC_EINVAL for sub > 64 or ppt not in {0, 2, 4, 8}. */
+int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt);
 /* Device memory the context sub-allocates from instead of cudaMalloc
  * (e.g. a PyTorch tensor).  Must be set before any plan exists and stay
  * valid until lsmc_destroy; 256-byte aligned. */
@@ -247,6 +267,20 @@ int lsmc_plan_create(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
 int lsmc_plan_launch(lsmc_plan* plan, int32_t use_graph);
 /* Waits for the last launch and copies its results to outs (host). */
 int lsmc_plan_fetch(lsmc_plan* plan, lsmc_result* outs);
+/* Scenario kinds of the bump-and-revalue table (LSMC_SC_*), the index of a
+ * revaluation within one result's row of lsmc_plan_fetch_scenarios. */
+enum { LSMC_SC_BASE = 0, LSMC_SC_S_UP, LSMC_SC_S_DN, LSMC_SC_SG_UP, LSMC_SC_SG_DN,
+       LSMC_SC_V0_UP, LSMC_SC_V0_DN, LSMC_SC_R_UP, LSMC_SC_R_DN, LSMC_SC_T_DN,
+       LSMC_SC_T_UP, LSMC_SC_COUNT };
+/* The revaluations behind the Greeks of the last launch (Sec. 2.2: the
+ * Greeks are differences of these prices): prices (host, n_results x
+ * LSMC_SC_COUNT doubles) gets, for result k and scenario kind s, the price of
+ * that revaluation at [k * LSMC_SC_COUNT + s], NaN where the request has no
+ * such scenario; near_ties (host, optional, same shape) its near-tie
+ * decisions (see lsmc_result).  n_results must equal the plan's result
+ * count.  Waits for the last launch. */
+int lsmc_plan_fetch_scenarios(lsmc_plan* plan, double* prices, uint32_t* near_ties,
+                              size_t n_results);
 /* Device address of the launch's results (lsmc_result array). */
 int lsmc_plan_device_results(lsmc_plan* plan, void** device_ptr, size_t* count);
 /* Counters of the plan: kernels per launch, generated and LSMC path-steps,
@@ -373,11 +407,13 @@ int lsmc_backward(const void* d_S, const void* d_V, uint32_t n_paths,
  * keeps in device memory on every device that loads it, until the process
  * exits; a request needing more (about n_paths x 8 bytes plus n_steps x 64
  * bytes in FP64) returns LSMC_ENOMEM before anything is launched.  The
- * first call on a device looks up the array's device address (do that call
- * before any stream capture).  All calls share the one array and leave their
- * contents in it: calls whose work overlaps on the GPU (other streams, other
- * host threads) race and must be serialised by the caller.  Returns after
- * the work has finished (the call waits on cuda_stream). */
+ * first call on a device, and the first after the device's context changes
+ * (cudaDeviceReset, or a caller's own driver context), looks up the array's
+ * device address (do that call before any stream capture).  All calls
+ * share the one array and leave their contents in it: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Returns after the work has finished, on success
+ * and on failure alike (the call waits on cuda_stream). */
 int lsmc_backward_noalloc(const void* d_S, const void* d_V, uint32_t n_paths,
                           uint32_t n_steps, int32_t precision,
                           const lsmc_heston* model, const lsmc_contract* contract,

@@ -109,6 +109,12 @@ class Context:
         except Exception:
             pass
 
+    def set_wait_limit(self, seconds: float):
+        L.lsmc_set_wait_limit(self.ctx, seconds)
+
+    def set_backward_shape(self, sub: int = 0, ppt: int = 0):
+        L.lsmc_set_backward_shape(self.ctx, sub, ppt)
+
     # ---- synchronous ------------------------------------------------------
     def price(self, wl: Workload, **kw) -> List[dict]:
         req = Request(wl, **kw)
@@ -160,6 +166,13 @@ class Plan:
 
     def fetch(self) -> List[dict]:
         return [r.as_dict() for r in L.lsmc_plan_fetch(self.handle, self.n_results)]
+
+    def fetch_scenarios(self):
+        """Per result, {scenario kind: (price, near ties)} of the last launch
+        (the revaluations the Greeks are differences of)."""
+        prices, ties = L.lsmc_plan_fetch_scenarios(self.handle, self.n_results)
+        return [{kind: (p[i], t[i]) for i, kind in enumerate(L.LSMC_SC_KINDS) if p[i] == p[i]}
+                for p, t in zip(prices, ties)]
 
     def info(self):
         return L.lsmc_plan_get_info(self.handle)

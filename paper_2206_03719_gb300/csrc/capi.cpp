@@ -30,6 +30,8 @@ static_assert(sizeof(DevResult) == sizeof(lsmc_result), "result layout");
 static_assert(offsetof(DevResult, status) == offsetof(lsmc_result, status), "result layout");
 static_assert(offsetof(DevResult, n_near_ties) == offsetof(lsmc_result, n_near_ties), "result layout");
 static_assert(offsetof(BwdResult, ties) == 4 * sizeof(double), "stage output layout");
+static_assert(kScCount == LSMC_SC_COUNT && kScBase == LSMC_SC_BASE && kScVUp == LSMC_SC_V0_UP &&
+                  kScTUp == LSMC_SC_T_UP, "scenario kinds");
 
 namespace {
 
@@ -39,6 +41,12 @@ double now_s() {
 }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// device allocations made by the library in this process (cudaMalloc,
+// cudaMallocAsync and the callbacks of lsmc_set_allocator; sub-allocations
+// from a workspace are not counted): lsmc_device_allocations
+std::atomic<uint64_t> g_device_allocs{0};
+void count_device_alloc() { g_device_allocs.fetch_add(1, std::memory_order_relaxed); }
 
 struct Ticket;
 
@@ -71,6 +79,7 @@ struct lsmc_ctx {
   void* alloc_user = nullptr;
   uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
   uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
+  double wait_limit_s = 20.0; // bound of every device-side wait (lsmc_set_wait_limit)
   // autotuned backward shape (ppt << 16 | sub-tiles per job), keyed by
   // (precision, basis, log2 of the first round's sub-tile count)
   std::map<uint64_t, uint32_t> tuned;
@@ -260,7 +269,9 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.active = dA;
   p->ba.ctl = p->d_ctl;
   p->ba.total_jobs = L.total_jobs;
-  p->ba.timeout_ns = 20ull * 1000 * 1000 * 1000;  // 20 s per wait
+  // bound of each device-side wait: the context's limit (20 s unless set)
+  const double limit_s = p->ctx ? p->ctx->wait_limit_s : 20.0;
+  p->ba.timeout_ns = (unsigned long long)(limit_s * 1e9);
   p->ba.n_rounds = (uint32_t)L.active.size();
   p->ba.n_inst = (uint32_t)L.inst.size();
   const int occ = occupancy(p->ctx, prec, L.opt.basis, plan_ppt(L.opt), L.opt.store);
@@ -282,6 +293,7 @@ int plan_alloc(lsmc_plan* p, bool use_arena, bool stream_ordered) {
   if (p->ctx && p->ctx->dev_alloc) {
     p->dev = (char*)p->ctx->dev_alloc(bytes, p->ctx->alloc_user);
     if (!p->dev) return LSMC_ENOMEM;
+    count_device_alloc();
     if ((uintptr_t)p->dev & 255) {  // the layout needs 256-byte alignment
       p->ctx->dev_free(p->dev, p->ctx->alloc_user);
       p->dev = nullptr;
@@ -292,10 +304,12 @@ int plan_alloc(lsmc_plan* p, bool use_arena, bool stream_ordered) {
   }
   if (stream_ordered) {
     LSMC_CUDA(cudaMallocAsync((void**)&p->dev, bytes, p->stream));
+    count_device_alloc();
     p->alloc_kind = 2;
     return LSMC_OK;
   }
   LSMC_CUDA(cudaMalloc((void**)&p->dev, bytes));
+  count_device_alloc();
   p->alloc_kind = 0;
   return LSMC_OK;
 }
@@ -659,6 +673,7 @@ int start_scheduler(lsmc_ctx* ctx) {
     if (ctx->dev_alloc) {
       ctx->own_arena_mem = ctx->dev_alloc(budget, ctx->alloc_user);
       if (!ctx->own_arena_mem) return LSMC_ENOMEM;
+      count_device_alloc();
       if ((uintptr_t)ctx->own_arena_mem & 255) {
         ctx->dev_free(ctx->own_arena_mem, ctx->alloc_user);
         ctx->own_arena_mem = nullptr;
@@ -666,6 +681,7 @@ int start_scheduler(lsmc_ctx* ctx) {
       }
     } else {
       LSMC_CUDA(cudaMalloc(&ctx->own_arena_mem, budget));
+      count_device_alloc();
     }
     ctx->arena.reset(ctx->own_arena_mem, budget);
   }
@@ -721,6 +737,12 @@ const char* lsmc_strerror(int s) {
 
 int lsmc_abi_version(void) { return LSMC_ABI_VERSION; }
 
+int lsmc_device_allocations(uint64_t* count) {
+  if (!count) return LSMC_EINVAL;
+  *count = g_device_allocs.load(std::memory_order_relaxed);
+  return LSMC_OK;
+}
+
 int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   if (!out) return LSMC_EINVAL;
   *out = nullptr;
@@ -742,14 +764,6 @@ int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   ctx->max_inflight = c.max_inflight ? c.max_inflight : 8;
   ctx->queue_capacity = c.queue_capacity ? c.queue_capacity : 4096;
   ctx->t0 = now_s();
-  if (const char* e = std::getenv("LSMC_BACKWARD_SUB")) {  // tuning sweeps
-    const long v = std::strtol(e, nullptr, 10);
-    if (v > 0 && v <= 1024) ctx->sub_override = (uint32_t)v;
-  }
-  if (const char* e = std::getenv("LSMC_BACKWARD_PPT")) {
-    const long v = std::strtol(e, nullptr, 10);
-    if (v == 2 || v == 4 || v == 8) ctx->ppt_override = (uint32_t)v;
-  }
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete ctx;
     return LSMC_ECUDA;
@@ -809,6 +823,22 @@ int lsmc_set_allocator(lsmc_ctx* ctx, void* (*alloc)(size_t, void*),
   return LSMC_OK;
 }
 
+int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds >= 0.0) || !(seconds <= 3600.0)) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->wait_limit_s = seconds;
+  return LSMC_OK;
+}
+
+int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt) {
+  if (!ctx || sub > kMaxSub || !(ppt == 0 || ppt == 2 || ppt == 4 || ppt == 8))
+    return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->sub_override = sub;
+  ctx->ppt_override = ppt;
+  return LSMC_OK;
+}
+
 int lsmc_set_workspace(lsmc_ctx* ctx, void* ptr, size_t bytes) {
   if (!ctx || !ptr || bytes < 4096 || ((uintptr_t)ptr & 255)) return LSMC_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -846,6 +876,24 @@ int lsmc_plan_launch(lsmc_plan* p, int32_t use_graph) {
 int lsmc_plan_fetch(lsmc_plan* p, lsmc_result* outs) {
   if (!p || !outs) return LSMC_EINVAL;
   return plan_collect(p, outs);
+}
+
+int lsmc_plan_fetch_scenarios(lsmc_plan* p, double* prices, uint32_t* near_ties,
+                              size_t n_results) {
+  if (!p || !prices || n_results != p->L.greeks.size()) return LSMC_EINVAL;
+  if (!p->h_res.empty())
+    LSMC_CUDA(cudaMemcpyAsync(p->h_res.data(), p->d_results, sizeof(BwdResult) * p->h_res.size(),
+                              cudaMemcpyDeviceToHost, p->stream));
+  LSMC_CUDA(cudaStreamSynchronize(p->stream));
+  const double nan = std::nan("");
+  for (size_t k = 0; k < n_results; ++k)
+    for (int s = 0; s < kScCount; ++s) {
+      const int32_t i = p->L.greeks[k].res[s];
+      const bool have = i >= 0 && (size_t)i < p->h_res.size();
+      prices[k * kScCount + s] = have ? p->h_res[i].price : nan;
+      if (near_ties) near_ties[k * kScCount + s] = have ? (uint32_t)p->h_res[i].ties : 0u;
+    }
+  return LSMC_OK;
 }
 
 int lsmc_plan_device_results(lsmc_plan* p, void** ptr, size_t* count) {
@@ -980,6 +1028,7 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
   if (ctx->dev_alloc) {
     mem = (char*)ctx->dev_alloc(total, ctx->alloc_user);
     if (!mem) { plan_free(p); return LSMC_ENOMEM; }
+    count_device_alloc();
     if ((uintptr_t)mem & 255) {  // the sub-buffers are laid out on 256-byte boundaries
       ctx->dev_free(mem, ctx->alloc_user);
       plan_free(p);
@@ -987,6 +1036,7 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
     }
   } else {
     ce = cudaMallocAsync((void**)&mem, total, p->stream);
+    if (ce == cudaSuccess) count_device_alloc();
   }
   if (ce == cudaSuccess) {
     char* c = mem;
@@ -1338,7 +1388,11 @@ int backward_in_scratch(void* scratch, size_t scratch_bytes, const void* d_S, co
   Control ctl{};
   if (rc == LSMC_OK)
     rc = cuda_status(cudaMemcpyAsync(&ctl, p->d_ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
-  if (rc == LSMC_OK) rc = cuda_status(cudaStreamSynchronize(s));
+  // whatever was enqueued above reads or writes the shared scratch: wait for
+  // it on every path, a failed one included, so the call never returns while
+  // its kernels still use the array (the first error is kept)
+  const int sync_rc = cuda_status(cudaStreamSynchronize(s));
+  if (rc == LSMC_OK) rc = sync_rc;
   if (rc == LSMC_OK && ctl.error) rc = ctl.error == kDevErrTimeout ? LSMC_ETIMEOUT : LSMC_ECUDA;
   p->dev = nullptr;
   return rc;

@@ -37,8 +37,12 @@ EXPORTS = [
     "lsmc_plan_set_timing", "lsmc_plan_kernel_times", "lsmc_autotune",
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
-    "lsmc_backward_noalloc",
+    "lsmc_backward_noalloc", "lsmc_device_allocations", "lsmc_set_wait_limit",
+    "lsmc_set_backward_shape", "lsmc_plan_fetch_scenarios",
 ]
+# scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
+LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
+LSMC_SC_COUNT = len(LSMC_SC_KINDS)
 
 
 class lsmc_heston(ctypes.Structure):
@@ -169,6 +173,10 @@ def load(build_if_missing: bool = False):
                                vp, vp, vp, vp], ctypes.c_int),
             "lsmc_backward_noalloc": ([vp, vp, u32, u32, i32, P(lsmc_heston), P(lsmc_contract),
                                        i32, vp, vp, vp, vp], ctypes.c_int),
+            "lsmc_device_allocations": ([P(u64)], ctypes.c_int),
+            "lsmc_set_wait_limit": ([vp, dbl], ctypes.c_int),
+            "lsmc_set_backward_shape": ([vp, u32, u32], ctypes.c_int),
+            "lsmc_plan_fetch_scenarios": ([vp, P(dbl), P(u32), sz], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -233,6 +241,20 @@ def lsmc_set_allocator(ctx, alloc, release):
     return (a, f)
 
 
+def lsmc_device_allocations():
+    n = ctypes.c_uint64()
+    check(load().lsmc_device_allocations(ctypes.byref(n)), "lsmc_device_allocations")
+    return n.value
+
+
+def lsmc_set_wait_limit(ctx, seconds):
+    return check(load().lsmc_set_wait_limit(ctx, seconds), "lsmc_set_wait_limit")
+
+
+def lsmc_set_backward_shape(ctx, sub, ppt):
+    return check(load().lsmc_set_backward_shape(ctx, sub, ppt), "lsmc_set_backward_shape")
+
+
 def lsmc_set_workspace(ctx, ptr, nbytes):
     return check(load().lsmc_set_workspace(ctx, ptr, nbytes), "lsmc_set_workspace")
 
@@ -288,6 +310,16 @@ def lsmc_plan_fetch(plan, n_results):
     outs = (lsmc_result * n_results)()
     check(load().lsmc_plan_fetch(plan, outs), "lsmc_plan_fetch")
     return list(outs)
+
+
+def lsmc_plan_fetch_scenarios(plan, n_results):
+    """(prices, near_ties): lists of n_results rows of LSMC_SC_COUNT values."""
+    prices = (ctypes.c_double * (n_results * LSMC_SC_COUNT))()
+    ties = (ctypes.c_uint32 * (n_results * LSMC_SC_COUNT))()
+    check(load().lsmc_plan_fetch_scenarios(plan, prices, ties, n_results),
+          "lsmc_plan_fetch_scenarios")
+    rows = lambda a: [list(a[k * LSMC_SC_COUNT:(k + 1) * LSMC_SC_COUNT]) for k in range(n_results)]
+    return rows(prices), rows(ties)
 
 
 def lsmc_plan_device_results(plan):

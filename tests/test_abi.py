@@ -128,6 +128,20 @@ def test_allocator_and_bounds_entry_points_reject_bad_arguments(lib):
     assert lib.lsmc_price_bounds(None, None, 16, 16, ctypes.byref(out)) == L.LSMC_EINVAL
 
 
+def test_option_and_diagnostic_entry_points_on_host(lib):
+    # context options and the per-scenario fetch refuse a missing context or
+    # plan; the allocation count needs no device and starts at zero here
+    assert lib.lsmc_set_wait_limit(None, 1.0) == L.LSMC_EINVAL
+    assert lib.lsmc_set_backward_shape(None, 4, 4) == L.LSMC_EINVAL
+    prices = (ctypes.c_double * L.LSMC_SC_COUNT)()
+    assert lib.lsmc_plan_fetch_scenarios(None, prices, None, 1) == L.LSMC_EINVAL
+    assert lib.lsmc_device_allocations(None) == L.LSMC_EINVAL
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert L.lsmc_device_allocations() == 0
+    assert L.LSMC_SC_KINDS[0] == "base" and L.LSMC_SC_COUNT == 11
+
+
 def test_request_flags_on_host(lib):
     # footprints follow the flags (16-bit rows, no path store), and the flag
     # rules are checked before anything is allocated

@@ -64,12 +64,19 @@ def test_noalloc_matches_allocating_backward_on_two_calls_in_a_row(torch):
     ]
     for model, P, N, prec, K, basis, seed in cases:
         S, V = _paths(torch, model, P, N, prec, seed)
+        n0 = L.lsmc_device_allocations()
         ref = _run(torch, L.lsmc_backward, S, V, P, N, prec, model, K, basis)
+        n1 = L.lsmc_device_allocations()
         first = _run(torch, L.lsmc_backward_noalloc, S, V, P, N, prec, model, K, basis)
         second = _run(torch, L.lsmc_backward_noalloc, S, V, P, N, prec, model, K, basis)
+        n2 = L.lsmc_device_allocations()
         _same(first, ref)
         _same(second, ref)
         assert ref[0][0] > 0
+        # the allocating pass is seen by the library's allocation count; the
+        # two calls without allocation leave it where it was
+        assert n1 > n0
+        assert n2 == n1
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch(torch):
@@ -81,8 +88,10 @@ def test_noalloc_rejects_requests_beyond_its_scratch(torch):
     V = torch.full((N + 1, P), 0.04, dtype=torch.float64, device="cuda")
     out = torch.zeros(5, dtype=torch.float64, device="cuda")
     c = L.lsmc_contract(L.LSMC_PUT, L.LSMC_AMERICAN, 100.0, 1.0)
+    n0 = L.lsmc_device_allocations()
     with pytest.raises(L.LsmcError) as e:
         L.lsmc_backward_noalloc(S.data_ptr(), V.data_ptr(), P, N, L.LSMC_FP64,
                                 L.lsmc_heston(**H), c, L.LSMC_BASIS_SV2, out.data_ptr())
     assert e.value.status == L.LSMC_ENOMEM
+    assert L.lsmc_device_allocations() == n0
     assert torch.count_nonzero(out).item() == 0
