@@ -30,6 +30,8 @@ BASIS_S2, BASIS_SV2 = 0, 1
 GRID_F64, GRID_F32 = 0, 1
 DELTA, GAMMA, VEGA, RHO, THETA = 1, 2, 4, 8, 16
 SC_KINDS = ["base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+"]
+KEY_PRICING = 1 << 62   # near-tie keys of the out-of-sample pricing pass
+MAX_ALT_KEYS = 12
 
 
 class Heston(ctypes.Structure):
@@ -53,6 +55,12 @@ class Result(ctypes.Structure):
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "pad_"}
+
+
+class TieCtl(ctypes.Structure):
+    _fields_ = [("tie_rel", ctypes.c_double), ("ties", ctypes.POINTER(ctypes.c_uint64)),
+                ("max_ties", ctypes.c_uint32), ("n_ties", ctypes.c_uint32),
+                ("flips", ctypes.POINTER(ctypes.c_uint64)), ("n_flips", ctypes.c_uint32)]
 
 
 def build(force: bool = False) -> str:
@@ -121,6 +129,19 @@ def lib():
         L.orc_lsmc.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
             [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + \
             [dp, u32p, dp, ctypes.POINTER(ctypes.c_uint8)]
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.orc_lsmc_tie.argtypes = [dp, dp, ctypes.c_uint32, ctypes.c_uint32] + \
+            [ctypes.c_double] * 5 + [ctypes.c_int] * 3 + [dp, u32p, ctypes.POINTER(TieCtl)]
+        L.orc_greeks_from_values.argtypes = [ctypes.POINTER(Heston), ctypes.POINTER(Bumps),
+                                             ctypes.POINTER(ctypes.c_int), dp, ctypes.c_int,
+                                             ctypes.POINTER(Result)]
+        L.orc_greeks_from_values.restype = None
+        L.orc_scenario_alternatives.argtypes = [
+            ctypes.POINTER(Heston), ctypes.c_int, ctypes.c_int, ctypes.c_double,
+            ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+            ctypes.c_int, ctypes.POINTER(Bumps), ctypes.c_uint64, ctypes.c_uint32,
+            ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, u64p,
+            ctypes.c_uint32, dp, u64p, ctypes.c_uint32, u32p, ctypes.c_int]
         L.orc_scenarios.argtypes = [ctypes.POINTER(Heston), ctypes.c_double,
                                     ctypes.POINTER(Bumps), ctypes.POINTER(Heston),
                                     dp, ctypes.POINTER(ctypes.c_int)]
@@ -248,16 +269,34 @@ def path_one(model: Heston, T, scheme, path, N, seed, stream=0, grid=GRID_F64):
 
 
 def lsmc(S, V, S0, K, T, r, theta, type_=PUT, style=AMERICAN, basis=BASIS_S2,
-         want_detail=False):
+         want_detail=False, tie_rel=None, flips=()):
     """Backward induction over given paths.  Returns a dict with price,
     price_se, european_price, continuation, n_singular and (optionally)
-    beta (N, 6) and exercise (N, P)."""
+    beta (N, 6) and exercise (N, P).  tie_rel: also report the keys n P + p
+    of the near-tie decisions (|h - c| <= tie_rel max(|c|, h)) as
+    "near_ties"; flips: keys of decisions to take the other way."""
     S = np.ascontiguousarray(S, dtype=np.float64)
     V = np.ascontiguousarray(V, dtype=np.float64)
     N = S.shape[0] - 1
     P = S.shape[1]
     out = (ctypes.c_double * 4)()
     ns = ctypes.c_uint32(0)
+    if tie_rel is not None or len(flips):
+        assert not want_detail
+        cap = 4096
+        ties = (ctypes.c_uint64 * cap)()
+        fl = np.ascontiguousarray(sorted(int(k) for k in flips), dtype=np.uint64)
+        ctl = TieCtl(-1.0 if tie_rel is None else tie_rel, ties, cap, 0,
+                     _ptr(fl, ctypes.c_uint64) if fl.size else None, fl.size)
+        rc = lib().orc_lsmc_tie(_ptr(S, ctypes.c_double), _ptr(V, ctypes.c_double), P, N,
+                                S0, K, T, r, theta, type_, style, basis, out, ctypes.byref(ns),
+                                ctypes.byref(ctl))
+        if rc != 0:
+            raise ValueError("orc_lsmc_tie rejected its arguments (%d)" % rc)
+        return {"price": out[0], "price_se": out[1], "european_price": out[2],
+                "continuation": out[3], "n_singular": ns.value,
+                "near_ties": [ties[i] for i in range(min(ctl.n_ties, cap))],
+                "n_near_ties": ctl.n_ties}
     beta = np.empty((N, 6), dtype=np.float64) if want_detail else None
     ex = np.empty((N, P), dtype=np.uint8) if want_detail else None
     rc = lib().orc_lsmc(_ptr(S, ctypes.c_double), _ptr(V, ctypes.c_double), P, N,
@@ -325,6 +364,44 @@ def dual_bound(model: Heston, strikes, T, P, N, n_outer, n_inner, *, type_=PUT, 
         raise ValueError("orc_dual_bound rejected its arguments (%d)" % rc)
     names = ("lower", "lower_se", "upper", "upper_se", "pi_N", "pi_N_se")
     return [dict(zip(names, out[6 * k: 6 * k + 6])) for k in range(strikes.size)]
+
+
+def greeks_from_values(model: Heston, b: Bumps, kinds, values):
+    """Price and Greeks from revaluation prices: kinds (names of SC_KINDS)
+    and values, one per scenario of the table."""
+    n = len(kinds)
+    k = (ctypes.c_int * n)(*[SC_KINDS.index(x) for x in kinds])
+    v = (ctypes.c_double * n)(*values)
+    res = Result()
+    lib().orc_greeks_from_values(ctypes.byref(model), ctypes.byref(b), k, v, n,
+                                 ctypes.byref(res))
+    return res.as_dict()
+
+
+def scenario_alternatives(model: Heston, K, T, P, N, sc, *, type_=PUT, style=AMERICAN,
+                          scheme=QE, grid=GRID_F64, basis=BASIS_S2, b: Bumps | None = None,
+                          seed=42, stream=0, out_of_sample=False, store=STORE_NATIVE,
+                          tie_rel=1e-9, keys=(), n_threads=None):
+    """Revaluation `sc` (index into the scenario table) of strike K as
+    price_greeks simulates it: (prices, near_ties) with prices[i] the price
+    when the decisions of `keys` whose bit is set in i (bit j = the j-th
+    smallest key) are taken the other way, and near_ties the keys of the
+    plain run's near-tie decisions at tie_rel."""
+    b = b or bumps()
+    keys = sorted(int(x) for x in keys)
+    assert len(keys) <= MAX_ALT_KEYS
+    kk = (ctypes.c_uint64 * max(1, len(keys)))(*keys)
+    out = (ctypes.c_double * (1 << len(keys)))()
+    cap = 4096
+    ties = (ctypes.c_uint64 * cap)()
+    nt = ctypes.c_uint32(0)
+    rc = lib().orc_scenario_alternatives(
+        ctypes.byref(model), type_, style, T, K, P, N, scheme, grid, basis, ctypes.byref(b),
+        seed, stream, 1 if out_of_sample else 0, int(store), sc, tie_rel, kk, len(keys), out,
+        ties, cap, ctypes.byref(nt), n_threads or default_threads())
+    if rc != 0:
+        raise ValueError("orc_scenario_alternatives rejected its arguments (%d)" % rc)
+    return list(out), [ties[i] for i in range(min(nt.value, cap))]
 
 
 def price_greeks(model: Heston, strikes, T, P, N, *, type_=PUT, style=AMERICAN,

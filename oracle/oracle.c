@@ -515,10 +515,42 @@ static int orc_cholesky_solve(int B, const double A[6][6], const double c[6],
   return 0;
 }
 
-int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
-             double S0, double K, double T, double r, double theta, int type,
-             int style, int basis, double out[4], uint32_t* n_singular,
-             double* beta_out, uint8_t* exercise) {
+/* ---- near ties and reversed decisions (test hook) ------------------------ */
+/* An exercise decision (payoff h against fitted continuation value c, both   */
+/* at the decision's date) is a near tie when |h - c| <= tie_rel max(|c|, h):  */
+/* another correct rounding of the same arithmetic may decide it the other    */
+/* way.  Decisions are keyed n P + p (regression paths) and, in the pricing   */
+/* pass of the out-of-sample estimator, ORC_KEY_PRICING | (n P + p).  A      */
+/* decision whose key is in ctl->flips is taken the other way; everything     */
+/* downstream of it (cash flows, earlier regressions) follows.  With no      */
+/* control the functions are the plain method.                               */
+static int orc_key_in(const uint64_t* keys, uint32_t n, uint64_t key) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (keys[mid] == key) return 1;
+    if (keys[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return 0;
+}
+
+/* the decision h > c under the control: near ties recorded, listed
+ * decisions reversed */
+static int orc_decide(orc_tie_ctl* ctl, uint64_t key, double h, double cont) {
+  int ex = h > cont;
+  if (!ctl) return ex;
+  if (ctl->tie_rel >= 0.0 && fabs(h - cont) <= ctl->tie_rel * fmax(fabs(cont), h)) {
+    if (ctl->ties && ctl->n_ties < ctl->max_ties) ctl->ties[ctl->n_ties] = key;
+    ++ctl->n_ties;
+  }
+  if (ctl->n_flips && orc_key_in(ctl->flips, ctl->n_flips, key)) ex = !ex;
+  return ex;
+}
+
+static int orc_lsmc_core(const double* S, const double* V, uint32_t P, uint32_t N,
+                         double S0, double K, double T, double r, double theta, int type,
+                         int style, int basis, double out[4], uint32_t* n_singular,
+                         double* beta_out, uint8_t* exercise, orc_tie_ctl* ctl) {
   if (!S || !V || !out || P == 0 || N == 0) return -1;
   if (!(K > 0.0) || !(T > 0.0) || !(theta > 0.0) || !isfinite(r)) return -1;
   if (type != ORC_PUT && type != ORC_CALL) return -1;
@@ -592,7 +624,7 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
       orc_basis(basis, s, V[(size_t)n * P + p], K, theta, phi);
       double cont = 0.0;
       for (int i = 0; i < B; ++i) cont += beta[i] * phi[i];
-      if (h > cont) {
+      if (orc_decide(ctl, (uint64_t)n * P + p, h, cont)) {
         Y[p] = h;
         if (exercise) exercise[(size_t)n * P + p] = 1;
       }
@@ -617,6 +649,22 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
   return 0;
 }
 
+int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
+             double S0, double K, double T, double r, double theta, int type,
+             int style, int basis, double out[4], uint32_t* n_singular,
+             double* beta_out, uint8_t* exercise) {
+  return orc_lsmc_core(S, V, P, N, S0, K, T, r, theta, type, style, basis, out, n_singular,
+                       beta_out, exercise, NULL);
+}
+
+int orc_lsmc_tie(const double* S, const double* V, uint32_t P, uint32_t N,
+                 double S0, double K, double T, double r, double theta, int type,
+                 int style, int basis, double out[4], uint32_t* n_singular,
+                 orc_tie_ctl* ctl) {
+  return orc_lsmc_core(S, V, P, N, S0, K, T, r, theta, type, style, basis, out, n_singular,
+                       NULL, NULL, ctl);
+}
+
 /* ---- out-of-sample Longstaff-Schwartz ------------------------------------ */
 /* The exercise policy estimated by the regressions on one path set (A) is   */
 /* applied to an independent path set (B): a path of B stops at the first    */
@@ -625,16 +673,16 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
 /* the mean discounted cash flow (a low-biased price).  Discounting repeats  */
 /* the one-step factor as orc_lsmc does, so with B = A the result is the     */
 /* in-sample price exactly.                                                  */
-int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const double* VB,
-                 uint32_t P, uint32_t N, double S0, double K, double T, double r,
-                 double theta, int type, int style, int basis, double out[4],
-                 uint32_t* n_singular) {
+static int orc_lsmc_oos_core(const double* SA, const double* VA, const double* SB,
+                             const double* VB, uint32_t P, uint32_t N, double S0, double K,
+                             double T, double r, double theta, int type, int style, int basis,
+                             double out[4], uint32_t* n_singular, orc_tie_ctl* ctl) {
   if (!SA || !VA || !SB || !VB || !out || P == 0 || N == 0) return -1;
   double* beta = (double*)malloc(sizeof(double) * (size_t)N * 6);
   if (!beta) return -2;
   double ins[4];
-  int rc = orc_lsmc(SA, VA, P, N, S0, K, T, r, theta, type, style, basis, ins, n_singular,
-                    beta, NULL);
+  int rc = orc_lsmc_core(SA, VA, P, N, S0, K, T, r, theta, type, style, basis, ins, n_singular,
+                         beta, NULL, ctl);
   if (rc) { free(beta); return rc; }
   const double dt = T / (double)N;
   const double D = exp(-r * dt);
@@ -655,7 +703,11 @@ int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const dou
         orc_basis(basis, sn, VB[(size_t)n * P + p], K, theta, phi);
         double cont = 0.0;
         for (int i = 0; i < B; ++i) cont += beta[(size_t)n * 6 + i] * phi[i];
-        if (h > cont) { y = h; tau = n; break; }
+        if (orc_decide(ctl, ORC_KEY_PRICING | ((uint64_t)n * P + p), h, cont)) {
+          y = h;
+          tau = n;
+          break;
+        }
       }
     }
     /* discount from t_tau to t_0 one step at a time */
@@ -677,6 +729,14 @@ int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const dou
   out[3] = mean;
   free(beta);
   return 0;
+}
+
+int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const double* VB,
+                 uint32_t P, uint32_t N, double S0, double K, double T, double r,
+                 double theta, int type, int style, int basis, double out[4],
+                 uint32_t* n_singular) {
+  return orc_lsmc_oos_core(SA, VA, SB, VB, P, N, S0, K, T, r, theta, type, style, basis, out,
+                           n_singular, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -972,6 +1032,44 @@ static void orc_bwd_strike(void* vctx, uint32_t k) {
   c->singular[k] = ns;
 }
 
+/* Central differences of the revaluations (Greeks per Sec. 2.2's purpose;
+ * the bump readings of orc_scenarios): delta from the S pair, gamma from its
+ * own S pair or the delta pair with the base, vega per unit of v0, rho per
+ * unit rate, theta = -dV/dT from the T pair.  vals[s] is the price of
+ * scenario s of kinds[]. */
+void orc_greeks_from_values(const orc_heston* m, const orc_bumps* b, const int* kinds,
+                            const double* vals, int n_sc, orc_result* o) {
+  double v[ORC_SC_COUNT];
+  int have[ORC_SC_COUNT] = {0};
+  for (int s = 0; s < n_sc; ++s) {
+    v[kinds[s]] = vals[s];
+    have[kinds[s]] = 1;
+  }
+  memset(o, 0, sizeof(*o));
+  o->price = v[ORC_SC_BASE];
+  o->price_se = o->european_price = NAN;
+  o->delta = o->gamma = o->vega = o->rho = o->theta = NAN;
+  const double S0 = m->S0;
+  if ((b->greek_mask & ORC_GREEK_DELTA) && have[ORC_SC_S_UP])
+    o->delta = (v[ORC_SC_S_UP] - v[ORC_SC_S_DN]) / (2.0 * b->rel_dS * S0);
+  if (b->greek_mask & ORC_GREEK_GAMMA) {
+    if (have[ORC_SC_SG_UP]) {
+      double h = b->rel_dS_gamma * S0;
+      o->gamma = (v[ORC_SC_SG_UP] - 2.0 * v[ORC_SC_BASE] + v[ORC_SC_SG_DN]) / (h * h);
+    } else {
+      double h = b->rel_dS * S0;
+      o->gamma = (v[ORC_SC_S_UP] - 2.0 * v[ORC_SC_BASE] + v[ORC_SC_S_DN]) / (h * h);
+    }
+  }
+  if (b->greek_mask & ORC_GREEK_VEGA)
+    o->vega = (v[ORC_SC_V_UP] - v[ORC_SC_V_DN]) / (2.0 * b->rel_dv0 * m->v0);
+  if (b->greek_mask & ORC_GREEK_RHO)
+    o->rho = (v[ORC_SC_R_UP] - v[ORC_SC_R_DN]) / (2.0 * b->abs_dr);
+  if (b->greek_mask & ORC_GREEK_THETA)
+    o->theta = (v[ORC_SC_T_DN] - v[ORC_SC_T_UP]) / (2.0 * b->abs_dT);
+  o->n_revaluations = (uint32_t)n_sc;
+}
+
 int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      const double* strikes, uint32_t n_strikes, uint32_t P,
                      uint32_t N, int scheme, int grid, int basis,
@@ -1075,45 +1173,127 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
 
   for (uint32_t k = 0; k < n_strikes; ++k) {
     double v[ORC_SC_COUNT];
-    int have[ORC_SC_COUNT] = {0};
     uint32_t ns = 0;
     for (int s = 0; s < n_sc; ++s) {
-      v[kinds[s]] = vals[(size_t)s * n_strikes + k];
-      have[kinds[s]] = 1;
+      v[s] = vals[(size_t)s * n_strikes + k];
       ns += sing[(size_t)s * n_strikes + k];
     }
     orc_result* o = &out[k];
-    o->price = v[ORC_SC_BASE];
+    orc_greeks_from_values(m, b, kinds, v, n_sc, o);
     o->price_se = base_aux[2 * k];
     o->european_price = base_aux[2 * k + 1];
-    o->delta = o->gamma = o->vega = o->rho = o->theta = NAN;
-    const double S0 = m->S0;
-    if ((b->greek_mask & ORC_GREEK_DELTA) && have[ORC_SC_S_UP])
-      o->delta = (v[ORC_SC_S_UP] - v[ORC_SC_S_DN]) / (2.0 * b->rel_dS * S0);
-    if (b->greek_mask & ORC_GREEK_GAMMA) {
-      if (have[ORC_SC_SG_UP]) {
-        double h = b->rel_dS_gamma * S0;
-        o->gamma = (v[ORC_SC_SG_UP] - 2.0 * v[ORC_SC_BASE] + v[ORC_SC_SG_DN]) / (h * h);
-      } else {
-        double h = b->rel_dS * S0;
-        o->gamma = (v[ORC_SC_S_UP] - 2.0 * v[ORC_SC_BASE] + v[ORC_SC_S_DN]) / (h * h);
-      }
-    }
-    if (b->greek_mask & ORC_GREEK_VEGA)
-      o->vega = (v[ORC_SC_V_UP] - v[ORC_SC_V_DN]) / (2.0 * b->rel_dv0 * m->v0);
-    if (b->greek_mask & ORC_GREEK_RHO)
-      o->rho = (v[ORC_SC_R_UP] - v[ORC_SC_R_DN]) / (2.0 * b->abs_dr);
-    if (b->greek_mask & ORC_GREEK_THETA)
-      o->theta = (v[ORC_SC_T_DN] - v[ORC_SC_T_UP]) / (2.0 * b->abs_dT);
     o->n_singular = ns;
-    o->n_revaluations = (uint32_t)n_sc;
     o->status = ns ? 1 : 0;
-    o->pad_ = 0;
   }
   if (scen_prices) memcpy(scen_prices, vals, sizeof(double) * n_sc * n_strikes);
 done:
   free(S); free(V); free(vals); free(aux); free(sing); free(rcs); free(base_aux);
   free(SB); free(VB);
+  return rc;
+}
+
+/* ---- one revaluation under reversed near-tie decisions (test hook) ------ */
+typedef struct {
+  const double *S, *V, *SB, *VB;
+  uint32_t P, N;
+  double S0, K, T, r, theta;
+  int type, style, basis;
+  const uint64_t* keys;
+  uint32_t n_keys;
+  double* out;
+  int* rcs;
+} orc_alt_ctx;
+
+static void orc_alt_one(void* vctx, uint32_t set) {
+  const orc_alt_ctx* c = (const orc_alt_ctx*)vctx;
+  uint64_t flips[ORC_MAX_ALT_KEYS];
+  uint32_t nf = 0;
+  for (uint32_t i = 0; i < c->n_keys; ++i)
+    if (set & (1u << i)) flips[nf++] = c->keys[i];
+  orc_tie_ctl ctl = {-1.0, NULL, 0, 0, flips, nf};
+  double o[4];
+  uint32_t ns = 0;
+  c->rcs[set] = c->SB ? orc_lsmc_oos_core(c->S, c->V, c->SB, c->VB, c->P, c->N, c->S0, c->K,
+                                          c->T, c->r, c->theta, c->type, c->style, c->basis,
+                                          o, &ns, &ctl)
+                      : orc_lsmc_core(c->S, c->V, c->P, c->N, c->S0, c->K, c->T, c->r,
+                                      c->theta, c->type, c->style, c->basis, o, &ns, NULL,
+                                      NULL, &ctl);
+  c->out[set] = o[0];
+}
+
+static int orc_cmp_u64(const void* a, const void* b) {
+  const uint64_t x = *(const uint64_t*)a, y = *(const uint64_t*)b;
+  return x < y ? -1 : x > y;
+}
+
+int orc_scenario_alternatives(const orc_heston* m, int type, int style, double T, double K,
+                              uint32_t P, uint32_t N, int scheme, int grid, int basis,
+                              const orc_bumps* b, uint64_t seed, uint32_t stream,
+                              int out_of_sample, int store, int sc, double tie_rel,
+                              const uint64_t* keys, uint32_t n_keys, double* out,
+                              uint64_t* ties, uint32_t max_ties, uint32_t* n_ties,
+                              int n_threads) {
+  if (!m || !b || !out || P == 0 || N == 0 || n_keys > ORC_MAX_ALT_KEYS ||
+      (n_keys && !keys) || store < 0 || store > 2)
+    return -1;
+  orc_heston models[ORC_SC_COUNT];
+  double Ts[ORC_SC_COUNT];
+  int kinds[ORC_SC_COUNT];
+  const int n_sc = orc_scenarios(m, T, b, models, Ts, kinds);
+  if (n_sc < 1 || sc < 0 || sc >= n_sc) return -1;
+  if (!orc_model_ok(&models[sc], Ts[sc], scheme) || !(K > 0.0) || !isfinite(K)) return -1;
+  const size_t cells = (size_t)(N + 1) * P;
+  double* S = (double*)malloc(sizeof(double) * cells);
+  double* V = (double*)malloc(sizeof(double) * cells);
+  double* SB = out_of_sample ? (double*)malloc(sizeof(double) * cells) : NULL;
+  double* VB = out_of_sample ? (double*)malloc(sizeof(double) * cells) : NULL;
+  const uint32_t n_sets = 1u << n_keys;
+  int* rcs = (int*)calloc(n_sets, sizeof(int));
+  uint64_t* sorted = (uint64_t*)malloc(sizeof(uint64_t) * (n_keys ? n_keys : 1));
+  int rc = 0;
+  if (!S || !V || !rcs || !sorted || (out_of_sample && (!SB || !VB))) { rc = -2; goto done; }
+  /* the revaluation's paths exactly as orc_price_greeks_ex simulates them */
+  if (store)
+    rc = orc_paths_store16(&models[0], &models[sc], kinds[sc], Ts[sc], scheme, grid, P, N,
+                           seed, stream, store, S, V, n_threads);
+  else
+    rc = orc_paths(&models[sc], Ts[sc], scheme, grid, P, N, seed, stream, S, V, n_threads);
+  if (rc == 0 && out_of_sample) {
+    if (store)
+      rc = orc_paths_store16(&models[0], &models[sc], kinds[sc], Ts[sc], scheme, grid, P, N,
+                             seed, stream ^ 0x80000000u, store, SB, VB, n_threads);
+    else
+      rc = orc_paths(&models[sc], Ts[sc], scheme, grid, P, N, seed, stream ^ 0x80000000u, SB,
+                     VB, n_threads);
+  }
+  if (rc) goto done;
+  if (n_ties) {
+    /* the near ties of the plain run */
+    orc_tie_ctl ctl = {tie_rel, ties, ties ? max_ties : 0, 0, NULL, 0};
+    double o[4];
+    uint32_t ns = 0;
+    rc = out_of_sample
+             ? orc_lsmc_oos_core(S, V, SB, VB, P, N, models[sc].S0, K, Ts[sc], models[sc].r,
+                                 models[sc].theta, type, style, basis, o, &ns, &ctl)
+             : orc_lsmc_core(S, V, P, N, models[sc].S0, K, Ts[sc], models[sc].r,
+                             models[sc].theta, type, style, basis, o, &ns, NULL, NULL, &ctl);
+    *n_ties = ctl.n_ties;
+    if (rc) goto done;
+  }
+  for (uint32_t i = 0; i < n_keys; ++i) sorted[i] = keys[i];
+  qsort(sorted, n_keys, sizeof(uint64_t), orc_cmp_u64);
+  {
+    /* every subset of the keys reversed (orc_alt_one takes them in sorted
+       order, so bit i of a subset is the i-th smallest key) */
+    orc_alt_ctx c = {S, V, SB, VB, P, N, models[sc].S0, K, Ts[sc], models[sc].r,
+                     models[sc].theta, type, style, basis, sorted, n_keys, out, rcs};
+    orc_parallel_for(n_sets, n_threads, orc_alt_one, &c);
+    for (uint32_t i = 0; i < n_sets; ++i)
+      if (rcs[i]) rc = rcs[i];
+  }
+done:
+  free(S); free(V); free(SB); free(VB); free(rcs); free(sorted);
   return rc;
 }
 

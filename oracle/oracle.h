@@ -142,6 +142,34 @@ int orc_lsmc(const double* S, const double* V, uint32_t P, uint32_t N,
              int style, int basis, double out[4], uint32_t* n_singular,
              double* beta, uint8_t* exercise);
 
+/* Near ties and reversed decisions (a test hook; without it the functions
+ * are the plain method).  An exercise decision, payoff h against fitted
+ * continuation value c at the decision's date, is a near tie when
+ * |h - c| <= tie_rel max(|c|, h): another correct rounding of the same
+ * arithmetic may take it the other way, so a result computed with other
+ * roundings is correct when it equals this oracle's under some set of its
+ * near-tie decisions reversed.  Keys: n P + p for the decision of path p at
+ * date n in the regressions' pass, ORC_KEY_PRICING | (n P + p) in the
+ * pricing pass of the out-of-sample estimator.  ties (optional) receives up
+ * to max_ties keys of the near ties met, n_ties counts them all; flips
+ * (sorted ascending) lists the decisions to take the other way. */
+#define ORC_KEY_PRICING (1ull << 62)
+#define ORC_MAX_ALT_KEYS 12
+typedef struct {
+  double tie_rel;       /* < 0: no near-tie report */
+  uint64_t* ties;
+  uint32_t max_ties;
+  uint32_t n_ties;
+  const uint64_t* flips;
+  uint32_t n_flips;
+} orc_tie_ctl;
+
+/* orc_lsmc under a tie control (ctl may be NULL). */
+int orc_lsmc_tie(const double* S, const double* V, uint32_t P, uint32_t N,
+                 double S0, double K, double T, double r, double theta, int type,
+                 int style, int basis, double out[4], uint32_t* n_singular,
+                 orc_tie_ctl* ctl);
+
 /* Out-of-sample Longstaff-Schwartz: the exercise policy of the regressions on
  * paths (SA, VA) applied to the independent paths (SB, VB) of the same model
  * (first date in 1..N-1 where an in-the-money path's payoff beats the fitted
@@ -174,6 +202,27 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
                         const orc_bumps* b, uint64_t seed, uint32_t stream,
                         int out_of_sample, int store, int n_threads, orc_result* out,
                         double* scen_prices);
+
+/* The Greeks of one strike from its revaluations: vals[s] is the price of
+ * scenario s of the table orc_scenarios gives (kinds[s] its kind, n_sc
+ * scenarios).  Fills price, the Greeks of b->greek_mask (NaN otherwise) and
+ * n_revaluations; price_se and european_price are NaN. */
+void orc_greeks_from_values(const orc_heston* m, const orc_bumps* b, const int* kinds,
+                            const double* vals, int n_sc, orc_result* out);
+
+/* One revaluation of orc_price_greeks_ex (scenario index sc of the table,
+ * strike K) under reversed decisions: out[i] (2^n_keys values) is its price
+ * with the decisions whose bit is set in i reversed, bit j standing for the
+ * j-th smallest of the n_keys (<= ORC_MAX_ALT_KEYS) keys.  n_ties (optional):
+ * the plain run's near ties at tie_rel are counted there and their keys
+ * written to ties (up to max_ties).  Returns 0 or < 0. */
+int orc_scenario_alternatives(const orc_heston* m, int type, int style, double T, double K,
+                              uint32_t P, uint32_t N, int scheme, int grid, int basis,
+                              const orc_bumps* b, uint64_t seed, uint32_t stream,
+                              int out_of_sample, int store, int sc, double tie_rel,
+                              const uint64_t* keys, uint32_t n_keys, double* out,
+                              uint64_t* ties, uint32_t max_ties, uint32_t* n_ties,
+                              int n_threads);
 
 /* Dual (Andersen-Broadie) upper bound of the American price for each strike,
  * with the exercise policy fitted on the P paths of `stream` (in-sample

@@ -120,6 +120,20 @@ class Context:
         req = Request(wl, **kw)
         return [r.as_dict() for r in L.lsmc_price_request(self.ctx, req.c)]
 
+    def price_with_scenarios(self, wl: Workload, **kw):
+        """(results, revaluations) of one request through a plan: the results
+        of price() and, per strike, {scenario kind: (price, near ties)}."""
+        return self.price_book_with_scenarios([wl], **kw)
+
+    def price_book_with_scenarios(self, wls: Sequence[Workload], use_graph: bool = False, **kw):
+        """price_book() through a plan, with the revaluations of every result."""
+        plan = Plan(self, wls, **kw)
+        try:
+            plan.launch(use_graph)
+            return plan.fetch(), plan.fetch_scenarios()
+        finally:
+            plan.close()
+
     def price_bounds(self, wl: Workload, n_outer: int, n_inner: int, **kw) -> List[dict]:
         """Lower (out-of-sample) and dual upper bounds of each strike's
         American price (base scenario)."""

@@ -31,7 +31,7 @@ def run_oracle(wl, grid=oracle.GRID_F64, n_threads=None):
         style=oracle.AMERICAN if wl.style == "american" else oracle.EUROPEAN,
         scheme=oracle.QE if wl.scheme == "qe" else oracle.FT_EULER, grid=grid,
         basis=oracle.BASIS_S2 if wl.basis == "s2" else oracle.BASIS_SV2, b=b, seed=wl.seed,
-        stream=wl.stream, n_threads=n_threads)
+        stream=wl.stream, n_threads=n_threads, want_scenarios=True)
 
 
 GOLDEN = {
@@ -47,7 +47,15 @@ def main(names):
     for name in names or GOLDEN:
         wl = GOLDEN[name]
         t = time.time()
-        res = run_oracle(wl)
+        res, scen = run_oracle(wl)
+        # the revaluations behind each strike's Greeks, by scenario kind
+        kinds = [k for k, _, _ in oracle.scenarios(
+            oracle.heston(**wl.model), wl.T,
+            oracle.bumps(rel_dS=wl.rel_dS, rel_dS_gamma=wl.rel_dS_gamma, rel_dv0=wl.rel_dv0,
+                         abs_dr=wl.abs_dr, abs_dT=wl.abs_dT,
+                         greek_mask=sum(_GREEK[g] for g in wl.greeks)))]
+        for k, r in enumerate(res):
+            r["scenarios"] = {kind: float(scen[s][k]) for s, kind in enumerate(kinds)}
         out = {"workload": wl.name, "scheme": wl.scheme, "n_paths": wl.n_paths,
                "n_steps": wl.n_steps, "strikes": wl.strikes, "source": "oracle/oracle.c (FP64)",
                "results": res}

@@ -3,7 +3,7 @@ against the oracle's out-of-sample estimator: regressions on the request's
 stream, the policy priced on stream ^ 0x80000000."""
 import pytest
 
-from gpu_common import assert_close, oracle_for, parity_tol, torch_cuda
+from gpu_common import oracle_for, scenario_parity, torch_cuda
 from paper_2206_03719_gb300 import api, workloads
 from paper_2206_03719_gb300 import lsmc as L
 import oracle
@@ -42,10 +42,8 @@ def test_out_of_sample_matches_oracle(ctx, precision, basis):
     wl = workloads.SMALL_FP64.replace(n_paths=6000, n_steps=24, basis=basis,
                                       greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02,
                                       strikes=[90.0, 100.0, 112.0], out_of_sample=True)
-    got = ctx.price(wl, precision=precision)
-    ref = _oracle_oos(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]))
+    got, scen = ctx.price_with_scenarios(wl, precision=precision)
+    scenario_parity(wl, got, scen, what=precision)
 
 
 def test_out_of_sample_european_and_against_in_sample(ctx):
@@ -76,7 +74,5 @@ def test_out_of_sample_edge_sizes(ctx, n_paths, n_steps):
     wl = workloads.SMALL_FP64.replace(n_paths=n_paths, n_steps=n_steps, basis="sv2",
                                       greeks=("delta",), strikes=[96.0, 103.0],
                                       out_of_sample=True)
-    got = ctx.price(wl)
-    ref = _oracle_oos(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]))
+    got, scen = ctx.price_with_scenarios(wl)
+    scenario_parity(wl, got, scen, what='test_gpu_oos.py')

@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import KEYS, assert_close, oracle_for, parity_tol, rel_err, torch_cuda
+from gpu_common import (KEYS, assert_close, oracle_args, oracle_for, rel_err, scenario_parity,
+                        torch_cuda)
 from paper_2206_03719_gb300 import api, workloads
 from paper_2206_03719_gb300 import lsmc as L
 
@@ -29,13 +30,35 @@ def ctx():
 
 def test_small_american_put_matches_oracle(ctx):
     wl = workloads.SMALL_FP64
-    got = ctx.price(wl)
-    ref = oracle_for(wl)
+    got, scen = ctx.price_with_scenarios(wl)
+    assert got == ctx.price(wl)  # the plan and the one-call path agree bit for bit
     assert got[0]["n_revaluations"] == 5
-    assert_close(got[0], ref[0], parity_tol(got[0]["n_near_ties"]),
-                 keys=("price", "delta", "gamma", "vega", "european_price"))
+    scenario_parity(wl, got, scen, keys=("price", "delta", "gamma", "vega", "european_price"),
+                    what="small")
     assert math.isnan(got[0]["rho"]) and math.isnan(got[0]["theta"])
+    ref = oracle_for(wl)
     assert abs(got[0]["price_se"] - ref[0]["price_se"]) <= 1e-9 * ref[0]["price_se"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_price_greeks_single_contract_call_matches_oracle(ctx, prec):
+    # lsmc_price_greeks: one contract, the call of the method's purpose
+    # (Sec. 2.2: the Greeks); the small workload's American put with delta,
+    # gamma and vega, through the context's default precision
+    wl = workloads.SMALL_FP64
+    with api.Context(workspace_bytes=256 << 20, precision=prec) as c2:
+        m = L.lsmc_heston(**wl.model)
+        con = L.lsmc_contract(L.LSMC_PUT, L.LSMC_AMERICAN, wl.strikes[0], wl.T)
+        bumps = L.lsmc_bumps(wl.rel_dS, wl.rel_dS_gamma, wl.rel_dv0, wl.abs_dr, wl.abs_dT,
+                             L.LSMC_GREEK_DELTA | L.LSMC_GREEK_GAMMA | L.LSMC_GREEK_VEGA, 0)
+        got = L.lsmc_price_greeks(c2.ctx, m, con, wl.n_paths, wl.n_steps, L.LSMC_BASIS_S2,
+                                  bumps, wl.seed).as_dict()
+        # the same request through a plan gives its revaluations
+        got_p, scen = c2.price_with_scenarios(wl.replace(precision=prec))
+    assert got == got_p[0]
+    assert got["n_revaluations"] == 5
+    scenario_parity(wl, [got], scen, keys=("price", "delta", "gamma", "vega", "european_price"),
+                    what="lsmc_price_greeks " + prec)
 
 
 VARIANTS = [
@@ -62,14 +85,8 @@ VARIANTS = [
 def test_variants_match_oracle(ctx, kw, prec):
     wl = workloads.SMALL_FP64.replace(n_paths=4096, n_steps=24, **kw) if "n_paths" not in kw \
         else workloads.SMALL_FP64.replace(**kw)
-    wl = wl.replace(precision=prec)
-    got = ctx.price(wl)
-    ref = oracle_for(wl.replace(precision="fp64"))
-    for g, r in zip(got, ref):
-        keys = ["price", "european_price"] + [k for k in wl.greeks]
-        assert_close(g, r, parity_tol(g["n_near_ties"]), keys=keys, what=str(kw))
-        assert g["n_singular_solves"] == r["n_singular"]
-        assert g["n_revaluations"] == r["n_revaluations"]
+    got, scen = ctx.price_with_scenarios(wl.replace(precision=prec))
+    scenario_parity(wl, got, scen, what="%s %s" % (prec, kw))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "df"])
@@ -79,20 +96,18 @@ def test_paper_size_matches_stored_oracle_values(ctx, name, prec):
     gold = json.load(open(path))
     wl = workloads.PAPER_FP64.replace(scheme=gold["scheme"], precision=prec)
     assert gold["n_paths"] == wl.n_paths and gold["n_steps"] == wl.n_steps
-    got = ctx.price(wl)
-    seen = []
-    for g, r in zip(got, gold["results"]):
+    got, scen = ctx.price_with_scenarios(wl)
+    for k, (g, r) in enumerate(zip(got, gold["results"])):
         assert g["n_revaluations"] == 11
         print("%s %s K=%g near ties %d price rel err %.3g" % (
-            name, prec, wl.strikes[len(seen)], g["n_near_ties"], rel_err(g["price"], r["price"])))
-        seen.append(g)
-        # Greeks are differences of revaluations: a flipped decision in one of
-        # them is divided by the bump, so only the price falls back to 1e-4
-        if g["n_near_ties"] == 0:
-            assert_close(g, r, FP64_TOL, what=name)
-        else:
-            assert_close(g, r, parity_tol(g["n_near_ties"]), keys=("price", "european_price"),
-                         what=name)
+            name, prec, wl.strikes[k], g["n_near_ties"], rel_err(g["price"], r["price"])))
+    # every price and Greek at 1e-10; a revaluation with a decision taken the
+    # other way at a near tie is matched by the oracle re-run with it reversed
+    model, b, _ = oracle_args(wl)
+    kinds = [k for k, _, _ in oracle.scenarios(model, wl.T, b)]
+    ref_scen = [[r["scenarios"][kind] for r in gold["results"]] for kind in kinds]
+    scenario_parity(wl, got, scen, ref=gold["results"], ref_scen=ref_scen,
+                    what="%s %s" % (name, prec))
 
 
 def test_graph_replay_is_bit_identical(ctx):
@@ -110,31 +125,43 @@ def test_graph_replay_is_bit_identical(ctx):
     assert a == ctx.price(wl)
 
 
-def test_book_equals_requests_priced_one_by_one(ctx):
-    book = workloads.book(n_contracts=6, paths_hi=20000, steps=(8, 16, 33), precision="fp64")
-    together = ctx.price_book(book)
+@pytest.mark.parametrize("prec", ["fp64", "df"])
+def test_book_equals_requests_priced_one_by_one(ctx, prec):
+    # an uneven book (puts and calls, drawn models, maturities, path and step
+    # counts) in one graph-replayed launch: each result equals the request
+    # priced alone, and every contract matches the oracle
+    book = workloads.book(n_contracts=6, paths_hi=20000, steps=(8, 16, 33), precision=prec)
+    together, scen = ctx.price_book_with_scenarios(book, use_graph=True)
+    assert together == ctx.price_book(book)
     alone = [ctx.price(w)[0] for w in book]
     assert together == alone
-    for w, g in zip(book[:2], together[:2]):
-        r = oracle_for(w)[0]
-        assert_close(g, r, parity_tol(g["n_near_ties"]),
-                     keys=("price", "delta", "gamma", "vega", "rho", "theta"))
+    for i, w in enumerate(book):
+        scenario_parity(w.replace(precision="fp64"), [together[i]], [scen[i]],
+                        what="book %s contract %d" % (prec, i))
 
 
-def test_mixed_precision_within_1e4_of_fp64_oracle(ctx):
+# MIXED (single-precision paths on the 23-bit uniform grid) is not a 1e-4
+# form: its paths differ from the FP64 ones by ~1e-6 relative, which moves
+# exercise decisions near the boundary, and each moved decision changes a
+# price at first order; central differences divide those moves by the bumps.
+# The bounds below are the errors this form is reported with (measured at
+# this size with margin); the European price, which has no decisions, stays
+# at the single-precision path error.
+MIXED_BOUNDS = {"price": 1e-3, "european_price": 1e-4, "delta": 2e-2, "gamma": 0.5,
+                "vega": 0.2, "rho": 0.2, "theta": 1.0}
+
+
+def test_mixed_precision_errors_against_fp64_oracle_are_within_stated_bounds(ctx):
     wl = workloads.PAPER_FP64.replace(n_paths=32768, n_steps=64, precision="mixed")
     got = ctx.price(wl)
     ref = oracle_for(wl.replace(precision="fp64"))
     worst = {}
     for g, r in zip(got, ref):
-        for k in ("price", "delta", "vega", "rho", "theta", "european_price"):
+        for k in MIXED_BOUNDS:
             worst[k] = max(worst.get(k, 0.0), rel_err(g[k], r[k]))
     print("mixed vs FP64 oracle, worst relative errors:", worst)
-    # single-precision paths move a few exercise decisions per date; each
-    # moves the price at first order (see the precision findings), so the
-    # price bound is loose while the European price, which has no decisions,
-    # stays tight
-    assert worst["price"] <= 5e-3 and worst["european_price"] <= 1e-4
+    for k, bound in MIXED_BOUNDS.items():
+        assert worst[k] <= bound, (k, worst[k], bound)
 
 
 def test_invalid_requests_are_rejected_before_launch(ctx):
@@ -150,10 +177,13 @@ def test_autotuned_plans_still_match_oracle(ctx):
                                       greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02)
     sub, ppt, ms = ctx.autotune([wl])
     assert sub >= 1 and ppt in (2, 4) and ms > 0
-    got = ctx.price(wl)
-    ref = oracle_for(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]), keys=("price", "delta", "gamma", "vega"))
+    got, scen = ctx.price_with_scenarios(wl)
+    scenario_parity(wl, got, scen, what="autotuned")
+    # a fixed shape through the context option (other sums' order) matches too
+    with api.Context(workspace_bytes=1 << 30) as c2:
+        c2.set_backward_shape(3, 2)
+        got2, scen2 = c2.price_with_scenarios(wl)
+    scenario_parity(wl, got2, scen2, what="fixed shape 3 x 2")
 
 
 def test_external_allocator():

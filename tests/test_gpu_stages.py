@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import parity_tol, torch_cuda
+from gpu_common import backward_parity, torch_cuda
 from paper_2206_03719_gb300 import lsmc as L
 
 pytestmark = pytest.mark.gpu
@@ -178,9 +178,11 @@ def test_backward_fp64_and_pairs_match_oracle_on_oracle_paths(torch, prec, basis
     got, beta, ns = _backward(torch, S, V, prec, model, K, T, type_, style, basis)
     ref = oracle.lsmc(S, V, 100.0, K, T, model["r"], model["theta"], type_=type_, style=style,
                       basis=basis, want_detail=True)
-    tol = parity_tol(got[4])
-    for i, k in enumerate(("price", "price_se", "european_price", "continuation")):
-        assert abs(got[i] - ref[k]) <= tol * max(abs(ref[k]), 1e-12), (k, got[i], ref[k])
+    # price, its standard error, European price and continuation value at
+    # 1e-10 (against the oracle with near-tie decisions reversed where the
+    # GPU took them the other way)
+    backward_parity(got, S, V, 100.0, K, T, model["r"], model["theta"], type_=type_,
+                    style=style, basis=basis, what="backward %d" % prec)
     if style == L.LSMC_AMERICAN:
         assert ns == ref["n_singular"]
         rb = ref["beta"]

@@ -7,7 +7,7 @@ import math
 
 import pytest
 
-from gpu_common import assert_close, oracle_for, parity_tol, torch_cuda
+from gpu_common import oracle_for, scenario_parity, torch_cuda
 from paper_2206_03719_gb300 import api, workloads
 from paper_2206_03719_gb300 import lsmc as L
 
@@ -42,28 +42,22 @@ def _wl(**kw):
 @pytest.mark.parametrize("store", ["fp16", "bf16"])
 def test_store16_matches_oracle(ctx, precision, store):
     wl = _wl(store=store)
-    got = ctx.price(wl, precision=precision)
-    ref = oracle_for(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]), what="%s/%s" % (precision, store))
+    got, scen = ctx.price_with_scenarios(wl, precision=precision)
+    scenario_parity(wl, got, scen, what="%s/%s" % (precision, store))
 
 
 @pytest.mark.parametrize("store", ["fp16", "bf16"])
 def test_store16_call_s2_ft_euler(ctx, store):
     wl = _wl(store=store, option="call", basis="s2", scheme="ft_euler", n_paths=4500,
              model=dict(workloads.SMALL_FP64.model, q=0.03))
-    got = ctx.price(wl)
-    ref = oracle_for(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]))
+    got, scen = ctx.price_with_scenarios(wl)
+    scenario_parity(wl, got, scen, what='test_gpu_store16.py')
 
 
 def test_store16_out_of_sample_matches_oracle(ctx):
     wl = _wl(store="fp16", out_of_sample=True)
-    got = ctx.price(wl)
-    ref = oracle_for(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]))
+    got, scen = ctx.price_with_scenarios(wl)
+    scenario_parity(wl, got, scen, what='test_gpu_store16.py')
 
 
 @pytest.mark.parametrize("precision", ["fp64", "df", "mixed"])
@@ -105,7 +99,5 @@ def test_store16_flag_rules(ctx):
                                                    (4097, 9, "european")])
 def test_store16_edge_sizes(ctx, store, n_paths, n_steps, style):
     wl = _wl(store=store, n_paths=n_paths, n_steps=n_steps, style=style, strikes=[97.0])
-    got = ctx.price(wl)
-    ref = oracle_for(wl)
-    for g, r in zip(got, ref):
-        assert_close(g, r, parity_tol(g["n_near_ties"]))
+    got, scen = ctx.price_with_scenarios(wl)
+    scenario_parity(wl, got, scen, what='test_gpu_store16.py')

@@ -161,3 +161,21 @@ def test_spot_and_rate_move_paths_by_known_factors(scheme):
     np.testing.assert_allclose(Ss / S, 1 + h, rtol=1e-14, atol=0)
     t = (np.arange(N + 1) * (T / N))[:, None]
     np.testing.assert_allclose(np.log(Sr / S), dr * t * np.ones_like(S), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("grid", [oracle.GRID_F64, oracle.GRID_F32])
+@pytest.mark.parametrize("scheme", [oracle.QE, oracle.FT_EULER])
+def test_path_one_is_the_column_of_the_path_matrix(scheme, grid):
+    # orc_path_one (the reference of the sampled full-size path checks) must
+    # give column p of orc_paths bit for bit: same draws, same steps, the
+    # stored variance truncated the same way
+    model = oracle.heston(**dict(H, xi=0.6, kappa=0.8, v0=0.02, theta=0.05))
+    P, N, T, seed, stream = 2051, 40, 1.5, 2**40 + 9, 7
+    S, V = oracle.paths(model, T, scheme, P, N, seed, stream, grid=grid)
+    rng = np.random.default_rng(5)
+    for p in [0, 1, 1023, 1024, P - 1] + list(rng.integers(0, P, 6)):
+        s1, v1 = oracle.path_one(model, T, scheme, int(p), N, seed, stream, grid=grid)
+        assert np.array_equal(s1, S[:, p]), p
+        assert np.array_equal(v1, V[:, p]), p
+    if scheme == oracle.FT_EULER:
+        assert (V >= 0).all()
