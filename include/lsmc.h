@@ -352,6 +352,25 @@ int lsmc_wait(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs,
 int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
                       double* admit_s, double* done_s);
 
+/* ---- measurement ---------------------------------------------------------- */
+/* Measured throughput of the arithmetic pipes that bound this library's
+ * kernels, the denominators of their roofline fractions (a measurement aid;
+ * the paper has no counterpart).  fp64_tflops and fp32_tflops: fused
+ * multiply-adds in double and in float (2 flops each); xu_tops: the
+ * special-function unit (base-2 exponentials, one operation each).  Each
+ * probe runs 8 independent dependency chains per thread on 8 CTAs of 256
+ * threads per SM for about 20 ms, timed with CUDA events after a warm-up
+ * launch; *_ms are those times.  Synchronous on an internal stream of the
+ * device; changes no device setting and allocates nothing.  LSMC_EINVAL for a
+ * bad device ordinal or NULL out, LSMC_ENODEV without a device. */
+typedef struct lsmc_peaks {
+  double fp64_tflops, fp32_tflops, xu_tops;
+  double fp64_ms, fp32_ms, xu_ms;
+  int32_t sms;
+  int32_t reserved;
+} lsmc_peaks;
+int lsmc_measure_peaks(int32_t device, lsmc_peaks* out);
+
 /* ---- stage entry points (device pointers; for parity tests) ------------- */
 /* Philox4x32-10 of n counters: d_ctr n x 4 uint32 (device), key = (key_lo,
  * key_hi); d_out n x 4 uint32 (device).  (Random inputs of Sec. 2.2.1.) */

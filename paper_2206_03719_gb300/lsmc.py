@@ -38,7 +38,7 @@ EXPORTS = [
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
     "lsmc_backward_noalloc", "lsmc_device_allocations", "lsmc_set_wait_limit",
-    "lsmc_set_backward_shape", "lsmc_plan_fetch_scenarios",
+    "lsmc_set_backward_shape", "lsmc_plan_fetch_scenarios", "lsmc_measure_peaks",
 ]
 # scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
 LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
@@ -81,6 +81,15 @@ class lsmc_bounds(ctypes.Structure):
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+class lsmc_peaks(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("fp64_tflops", "fp32_tflops", "xu_tops", "fp64_ms", "fp32_ms", "xu_ms")] + [
+        ("sms", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "reserved"}
 
 
 class lsmc_config(ctypes.Structure):
@@ -177,6 +186,7 @@ def load(build_if_missing: bool = False):
             "lsmc_set_wait_limit": ([vp, dbl], ctypes.c_int),
             "lsmc_set_backward_shape": ([vp, u32, u32], ctypes.c_int),
             "lsmc_plan_fetch_scenarios": ([vp, P(dbl), P(u32), sz], ctypes.c_int),
+            "lsmc_measure_peaks": ([i32, P(lsmc_peaks)], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -245,6 +255,12 @@ def lsmc_device_allocations():
     n = ctypes.c_uint64()
     check(load().lsmc_device_allocations(ctypes.byref(n)), "lsmc_device_allocations")
     return n.value
+
+
+def lsmc_measure_peaks(device=0):
+    out = lsmc_peaks()
+    check(load().lsmc_measure_peaks(device, ctypes.byref(out)), "lsmc_measure_peaks")
+    return out.as_dict()
 
 
 def lsmc_set_wait_limit(ctx, seconds):

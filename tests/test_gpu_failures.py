@@ -88,7 +88,9 @@ def test_allocator_refusals_report_enomem_and_hand_every_block_back(torch):
         assert not state["live"]
         # memory again: the same context prices, serves and bounds as before
         state["limit"] = 10**9
-        assert ctx.price(wl) == ref
+        again = ctx.price(wl)
+        assert len(again) == len(ref) and all(
+            x[k] == y[k] or (x[k] != x[k] and y[k] != y[k]) for x, y in zip(again, ref) for k in x)
         t = ctx.submit(wl)
         st, out = ctx.wait(t, len(wl.strikes), 60.0)
         assert st == L.LSMC_OK
