@@ -32,9 +32,27 @@ sys.path.insert(0, _ROOT)
 from paper_2206_03719_gb300 import workloads  # noqa: E402
 
 GOLDEN = os.path.join(_ROOT, "tests", "golden", "paper_fp64.json")
+GOLDEN_BOOK = os.path.join(_ROOT, "tests", "golden", "book_subset.json")
+GOLDEN_SERVING = os.path.join(_ROOT, "tests", "golden", "serving_subset.json")
 PEAKS = os.path.join(_ROOT, "MEASURED_PEAKS.json")
-# nominal FP64 rate of a GB300 (used as the ALU roofline of the FP64 path)
-FP64_NOMINAL_TFLOPS = 1.25
+# algorithmic work of the stepper (forward pass), counted from the formulas
+# of the scheme (a fused multiply-add counts 2 flops; elementary functions --
+# division, square root, exponential, logarithm -- counted apart, each one
+# evaluation on the special-function unit in single precision):
+#   per simulated path-step, shared by the contract's path groups: the two
+#   uniforms (2 flops each), 1 - U (1), two normal quantiles (a degree-8
+#   polynomial, 18 flops, and one logarithm each)                -> 41 flops, 2 functions
+#   per path group, QE: m and s^2 (4), m^2, the branch test and its
+#   quadratic-branch arithmetic (11 with the two divisions' products), the
+#   log-price step (9), S0 exp(x) (2); two divisions, three square roots and
+#   one exponential                                              -> 26 flops, 6 functions
+#   per path group, full-truncation Euler: 11 flops, one square root, plus
+#   S0 exp(x) (2 flops, one exponential)                         -> 13 flops, 2 functions
+#   stored per path group: exp(x) and, with the SV2 basis, v.
+# measured peaks of this run (set by main before the side measurements)
+RUN = {"peaks": {}, "hbm_gbs": None}
+STEP_SHARED = {"flops": 41, "functions": 2}
+STEP_GROUP = {"qe": {"flops": 26, "functions": 6}, "ft_euler": {"flops": 13, "functions": 2}}
 # algorithmic FP64 operations of the backward pass (a fused multiply-add
 # counts as two):
 #   every (instance, path, date): S = scale*E, payoff, discount      -> 3
@@ -92,6 +110,10 @@ def parse():
                     help="run only this side measurement and print it (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--peaks", action="store_true",
+                    help="print the measured pipe throughputs (lsmc_measure_peaks) and exit")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="time the FP64 oracle once on the whole workload (all paths) and exit")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the precision-split, book and serving measurements")
     return ap.parse_args()
@@ -207,6 +229,71 @@ def oracle_sample_rate(wl, sample_paths, threads=None):
     return dt, wl.n_greeks / (dt * scale), n_threads
 
 
+def groups_of(wl):
+    """Simulations after folding the bumps onto path groups: the base one,
+    v0 +/- and T -/+ (S and r bumps share the base simulation)."""
+    return 1 + 2 * ("vega" in wl.greeks) + 2 * ("theta" in wl.greeks)
+
+
+def stepper_roofline(wl, fwd_ms, peaks, hbm_gbs):
+    """Roofline fractions of one forward launch: the FMA pipe (basic
+    flops of the formulas), the special-function unit (elementary functions;
+    single precision only -- in double they run on the FMA pipe) and DRAM (the
+    rows stored), each achieved over its measured peak, and their maximum."""
+    groups = groups_of(wl)
+    path_steps = wl.n_paths * wl.n_steps
+    g = STEP_GROUP[wl.scheme]
+    flops = path_steps * (STEP_SHARED["flops"] + groups * g["flops"])
+    funcs = path_steps * (STEP_SHARED["functions"] + groups * g["functions"])
+    value = 4 if wl.precision == "mixed" else 8
+    stored = path_steps * groups * value * (2 if wl.basis == "sv2" else 1)
+    t = fwd_ms / 1e3
+    single = wl.precision == "mixed"
+    fma_peak = peaks.get("fp32_tflops" if single else "fp64_tflops")
+    out = {"kernel": "forward_kernel", "workload": wl.name, "precision": wl.precision,
+           "kernel_ms": fwd_ms, "simulated_path_steps": path_steps * groups,
+           "fma": {"achieved": flops / t / 1e12, "peak": fma_peak, "unit": "TFLOP/s",
+                   "pipe": "FP32" if single else "FP64", "flops_per_path_step":
+                   STEP_SHARED["flops"] + groups * g["flops"]},
+           "dram": {"achieved": stored / t / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "bytes_per_path_step": stored / path_steps}}
+    if single:
+        out["xu"] = {"achieved": funcs / t / 1e12, "peak": peaks.get("xu_tops"), "unit": "Tops/s",
+                     "functions_per_path_step": STEP_SHARED["functions"] + groups * g["functions"]}
+    else:
+        out["elementary_functions_per_path_step"] = (STEP_SHARED["functions"] +
+                                                     groups * g["functions"])
+    fr = {}
+    for k in ("fma", "xu", "dram"):
+        if k in out and out[k]["peak"]:
+            out[k]["frac"] = out[k]["achieved"] / out[k]["peak"]
+            fr[k] = out[k]["frac"]
+    out["frac"] = max(fr.values()) if fr else None
+    out["bound"] = max(fr, key=fr.get) if fr else None
+    return out
+
+
+def subset_errors(results_by_index, gold_path):
+    """Largest relative error, per price and Greek, of results (contract
+    index -> result dict) against the oracle values stored for a subset."""
+    if not os.path.exists(gold_path):
+        return None
+    gold = json.load(open(gold_path))
+    worst, n = {}, 0
+    for i, c in zip(gold["indices"], gold["contracts"]):
+        g = results_by_index.get(i)
+        if g is None:
+            continue
+        n += 1
+        for k in ("price", "delta", "gamma", "vega", "rho", "theta"):
+            worst[k] = max(worst.get(k, 0.0), abs(g[k] - c["results"][k]) /
+                           max(abs(c["results"][k]), 1e-12))
+    if not n:
+        return None
+    return {"contracts_compared": n, "max_rel_err_vs_oracle": worst,
+            "within_1e-4": all(v <= 1e-4 for v in worst.values())}
+
+
 def max_rel_err(got, gold):
     worst = 0.0
     for g, r in zip(got, gold):
@@ -277,9 +364,7 @@ def measure_precision(api, L, torch, wl, reps=3):
             errs[k] = max(errs.get(k, 0.0), e)
     ms = sum(kms) / max(1, launches)
     fwd_ms = kms[1] / max(1, launches)
-    # simulations after folding the bumps onto path groups: base, v0 +/- and
-    # T -/+ (S and r bumps share the base simulation)
-    groups = 1 + 2 * ("vega" in wl.greeks) + 2 * ("theta" in wl.greeks)
+    groups = groups_of(wl)
     out.update({"greeks_per_s": wl.n_greeks / (ms / 1e3), "ms_per_step": ms,
                 "forward_simulated_path_steps_per_s": wl.n_paths * wl.n_steps * groups / (fwd_ms / 1e3),
                 "generated_path_steps_per_s": wl.generated_path_steps / (ms / 1e3),
@@ -287,7 +372,8 @@ def measure_precision(api, L, torch, wl, reps=3):
                 "kernel_ms": {"forward": kms[1] / max(1, launches),
                               "backward": kms[2] / max(1, launches)},
                 "max_rel_err_vs_fp64_gpu": errs,
-                "all_within_1e-4": all(v <= 1e-4 for v in errs.values())})
+                "all_within_1e-4": all(v <= 1e-4 for v in errs.values()),
+                "stepper_roofline": stepper_roofline(wl, fwd_ms, RUN["peaks"], RUN["hbm_gbs"])})
     return out
 
 
@@ -419,9 +505,10 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
     gen = sum(w.generated_path_steps for w in book)
     lsmc = sum(w.lsmc_path_steps for w in book)
     total_ms = 0.0
+    results = {}
     with api.Context(workspace_bytes=need + (512 << 20)) as ctx:
         subs = []
-        for c in chunks:
+        for ci, c in enumerate(chunks):
             sub, ppt, _ = ctx.autotune(c)
             subs.append([sub, ppt])
             p = ctx.plan(c)
@@ -431,10 +518,12 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             ev0.record(ctx.stream)
             p.launch(use_graph=True)
             ev1.record(ctx.stream)
-            p.fetch()
+            for j, r in enumerate(p.fetch()):
+                results[ci * chunk + j] = r
             total_ms += ev0.elapsed_time(ev1)
             p.close()
     return {"contracts": n_contracts, "launch_chunks": len(chunks), "device_ms": total_ms,
+            "error": subset_errors(results, GOLDEN_BOOK),
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
@@ -502,9 +591,12 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
                 time.sleep(t_arr - now)
             tickets.append((t_arr, w, srv.submit(w)))
         ok = 0
-        for _, w, t in tickets:
-            st, _ = srv.wait(t, len(w.strikes), 300.0)
+        served_results = {}
+        for i, (_, w, t) in enumerate(tickets):
+            st, res = srv.wait(t, len(w.strikes), 300.0)
             ok += st == L.LSMC_OK
+            if st == L.LSMC_OK:
+                served_results[i] = res[0].as_dict()
         wall = time.perf_counter() - t0
         times = [L.lsmc_ticket_times(srv.ctx, t) for _, _, t in tickets]
     lat = [d - s for (t_arr, _, _), (s, a, d) in zip(tickets, times) if t_arr >= warm_s]
@@ -516,7 +608,8 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     served = {"rate_per_s": rate, "window_s": window_s, "requests": len(tickets), "ok": ok,
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
-              "precision": precision, "max_inflight": max_inflight}
+              "precision": precision, "max_inflight": max_inflight,
+              "error": subset_errors(served_results, GOLDEN_SERVING)}
     # the same requests, one at a time, plain FP64
     serial = reqs[:serial_n]
     need = max(L.lsmc_request_footprint(None, api.Request(w, precision="fp64").c) for w in serial)
@@ -558,6 +651,51 @@ def extra_jobs():
     return jobs
 
 
+def within_1e4_summary(line, acc, value):
+    """Greeks/s of every form measured in this run whose prices and Greeks
+    are within 1e-4 relative of the FP64 oracle (the forms outside the bound
+    are listed apart, with their error)."""
+    ok, out = {}, {}
+    if acc is not None:
+        (ok if acc <= 1e-4 else out)["fp64_headline"] = value
+    ps = line.get("precision_split") or {}
+    for k, v in ps.items() if isinstance(ps, dict) else []:
+        if isinstance(v, dict) and "greeks_per_s" in v:
+            # error against the FP64 GPU path, which matches the oracle at 1e-10
+            (ok if v.get("all_within_1e-4") else out)["precision_split." + k] = v["greeks_per_s"]
+    for sect in ("book", "serving"):
+        d = line.get(sect) or {}
+        for k, v in d.items() if isinstance(d, dict) else []:
+            if isinstance(v, dict) and "greeks_per_s" in v:
+                e = v.get("error")
+                if e is None:
+                    continue
+                (ok if e["within_1e-4"] else out)["%s.%s" % (sect, k)] = v["greeks_per_s"]
+    best = max(ok, key=ok.get) if ok else None
+    return {"forms": ok, "best": best, "best_greeks_per_s": ok.get(best),
+            "outside_1e-4": out}
+
+
+def run_cpu_full(wl):
+    """The FP64 oracle once on the whole workload (every path, strike and
+    revaluation) on all host cores: a full-size CPU baseline."""
+    import oracle
+    sys.path.insert(0, os.path.join(_ROOT, "tests"))
+    from golden.make_golden import run_oracle  # noqa: E402
+    oracle.build()
+    n = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    res, _ = run_oracle(wl.replace(precision="fp64"), n_threads=n)
+    dt = time.perf_counter() - t0
+    acc = None
+    if os.path.exists(GOLDEN) and wl.n_paths == workloads.PAPER_FP64.n_paths and wl.scheme == "qe":
+        acc = max_rel_err(res, json.load(open(GOLDEN))["results"])
+    print(json.dumps({"cpu_full": {"workload": wl.name, "seconds": dt, "cores": n,
+                                   "greeks_per_s": wl.n_greeks / dt,
+                                   "lsmc_path_steps_per_s": wl.lsmc_path_steps / dt,
+                                   "max_rel_err_vs_stored_oracle": acc}}), flush=True)
+
+
 def main():
     args = parse()
     wl = pick_workload(args.workload)
@@ -571,6 +709,9 @@ def main():
         wl = wl.replace(store=args.store, name=wl.name + "-store-" + args.store)
     if args.impl == "reference":
         run_reference(args, wl)
+        return
+    if args.cpu_full:
+        run_cpu_full(wl)
         return
     rank, world, local = dist_env()
     wl = replica_workload(wl, rank)
@@ -586,6 +727,15 @@ def main():
     from paper_2206_03719_gb300 import api, build
     from paper_2206_03719_gb300 import lsmc as L
     build.build()
+    # the roofline denominators: HBM copy bandwidth from the pool's measured
+    # peaks, the arithmetic pipes measured here (timed probes, before any
+    # timed region)
+    mp = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    RUN["hbm_gbs"] = mp.get("hbm_gbs")
+    RUN["peaks"] = L.lsmc_measure_peaks(local)
+    if args.peaks:
+        print(json.dumps({"peaks": RUN["peaks"], "hbm_gbs": RUN["hbm_gbs"]}))
+        return
     if args.extra:
         # one of the side measurements alone (profiling runs)
         print(json.dumps({"extra": args.extra, "result": dict(extra_jobs())[args.extra](api, L, torch)}))
@@ -666,7 +816,7 @@ def main():
         gold = json.load(open(GOLDEN))["results"]
         acc = max_rel_err(res, gold)
 
-    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    fp64_peak = RUN["peaks"].get("fp64_tflops")
     bwd_ms = kms[2] / max(1, launches)
     fwd_ms = kms[1] / max(1, launches)
     itm = info.itm_path_steps
@@ -681,9 +831,10 @@ def main():
     roofline = {
         "kernel": "backward_kernel (Longstaff-Schwartz moments, solve, exercise)",
         "bound": "alu", "achieved": achieved,
-        "peak": FP64_NOMINAL_TFLOPS if fp64 else None, "unit": "TFLOP/s",
-        "frac": achieved / FP64_NOMINAL_TFLOPS if fp64 else None,
-        "peak_source": "nominal FP64 1.25 TFLOP/s of the profiling recipe (no measured FP64 peak)",
+        "peak": fp64_peak if fp64 else None, "unit": "TFLOP/s",
+        "frac": achieved / fp64_peak if fp64 and fp64_peak else None,
+        "peak_source": "measured: FP64 fused multiply-add probe (lsmc_measure_peaks, "
+                       "%.1f ms on every SM) in this run" % RUN["peaks"].get("fp64_ms", 0.0),
         "traffic": traffic,
         "traffic_source": BWD_TRAFFIC["capture"] if traffic else None,
         # the path store read once (E and v rows of every path group and date)
@@ -691,6 +842,10 @@ def main():
                             (1 + 2 * ("vega" in wl.greeks) + 2 * ("theta" in wl.greeks)),
         "kernel_ms": {"setup": kms[0] / max(1, launches), "forward": fwd_ms,
                       "backward": bwd_ms, "greeks": kms[3] / max(1, launches)},
+        "measured_peaks": dict(RUN["peaks"], hbm_gbs=RUN["hbm_gbs"]),
+        # the stepper of this workload; the single-precision stepper at
+        # 1,048,576 paths joins it from the precision split below
+        "stepper": {"headline": stepper_roofline(wl, fwd_ms, RUN["peaks"], RUN["hbm_gbs"])},
     }
     cpu = None
     if not args.no_cpu_baseline:
@@ -727,6 +882,10 @@ def main():
         "device_bytes": int(info.device_bytes),
     }
     line.update(extras)
+    ps = extras.get("precision_split") or {}
+    if isinstance(ps, dict) and "mixed_large" in ps and "stepper_roofline" in ps["mixed_large"]:
+        roofline["stepper"]["mixed_1048576"] = ps["mixed_large"]["stepper_roofline"]
+    line["greeks_per_s_within_1e-4"] = within_1e4_summary(line, acc, value)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -34,6 +34,29 @@ def run_oracle(wl, grid=oracle.GRID_F64, n_threads=None):
         stream=wl.stream, n_threads=n_threads, want_scenarios=True)
 
 
+# the book and serving subsets: seeded contract indices of the uneven book
+# (512 contracts) and the first requests of the served stream, whose oracle
+# values state the error of the batched and served forms
+BOOK_SUBSET = sorted(int(i) for i in
+                     __import__("numpy").random.default_rng(32).choice(512, 32, replace=False))
+SERVING_SUBSET = list(range(32))
+
+
+def _contract_results(wls):
+    out = []
+    for wl in wls:
+        t = time.time()
+        res = run_oracle(wl)[0][0]
+        out.append({"name": wl.name, "results": res, "seconds": time.time() - t})
+    return out
+
+
+SUBSETS = {
+    "book_subset": lambda: [workloads.book(n_contracts=512)[i] for i in BOOK_SUBSET],
+    "serving_subset": lambda: workloads.book(n_contracts=max(SERVING_SUBSET) + 1,
+                                             seed=99)[:len(SERVING_SUBSET)],
+}
+
 GOLDEN = {
     # American puts K = 80..120, 131072 paths x 252 steps, SV2 basis, QE, all Greeks
     "paper_fp64": workloads.PAPER_FP64,
@@ -44,7 +67,17 @@ GOLDEN = {
 
 def main(names):
     here = os.path.dirname(os.path.abspath(__file__))
-    for name in names or GOLDEN:
+    for name in names or list(GOLDEN) + list(SUBSETS):
+        if name in SUBSETS:
+            t = time.time()
+            wls = SUBSETS[name]()
+            out = {"indices": BOOK_SUBSET if name == "book_subset" else SERVING_SUBSET,
+                   "source": "oracle/oracle.c (FP64)",
+                   "contracts": _contract_results(wls)}
+            with open(os.path.join(here, name + ".json"), "w") as f:
+                json.dump(out, f, indent=1)
+            print(name, "%.1f s" % (time.time() - t))
+            continue
         wl = GOLDEN[name]
         t = time.time()
         res, scen = run_oracle(wl)

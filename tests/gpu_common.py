@@ -141,6 +141,15 @@ def backward_parity(got, S, V, S0, K, T, r, theta, type_=oracle.PUT, style=oracl
                          % (what, K, list(got[:4])))
 
 
+def same_results(a, b):
+    """Result dicts (or lists of them) equal bit for bit, NaN (a Greek not
+    asked for) equal to NaN."""
+    if isinstance(a, list):
+        return len(a) == len(b) and all(same_results(x, y) for x, y in zip(a, b))
+    return a.keys() == b.keys() and all(
+        a[k] == b[k] or (isinstance(a[k], float) and a[k] != a[k] and b[k] != b[k]) for k in a)
+
+
 def rel_err(a, b):
     """|a - b| / max(|b|, 1e-12); NaN on both sides counts as equal."""
     if math.isnan(b) and math.isnan(a):
