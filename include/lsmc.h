@@ -359,8 +359,8 @@ int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
  * multiply-adds in double and in float (2 flops each); xu_tops: the
  * special-function unit (base-2 exponentials, one operation each).  Each
  * probe runs 8 independent dependency chains per thread on 8 CTAs of 256
- * threads per SM for about 20 ms, timed with CUDA events after a warm-up
- * launch; *_ms are those times.  Synchronous on an internal stream of the
+ * threads per SM, 10 to 20 ms per launch; the fastest of five launches
+ * after two warm-up launches counts (CUDA events); *_ms are those times.  Synchronous on an internal stream of the
  * device; changes no device setting and allocates nothing.  LSMC_EINVAL for a
  * bad device ordinal or NULL out, LSMC_ENODEV without a device. */
 typedef struct lsmc_peaks {
