@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include "dfloat.cuh"
+#include "quantile_f32.h"
 
 namespace lsmc {
 
@@ -37,6 +38,44 @@ __device__ __forceinline__ float uniform23(uint32_t w) {
   return __fmaf_rn(__uint2float_rn(w >> 9), 0x1p-23f, 0x1p-24f);
 }
 
+// Standard normal quantile of a point u of the 23-bit grid (omu = 1 - u,
+// exact): with x = 2u - 1 and w = -log(4 u (1 - u)), Phi^-1(u) is x times a
+// smooth function of w (Giles' transformation of erfinv): a degree-8
+// polynomial in w - 2.5 for w < 5, in sqrt(w) - 3 beyond (the tails, about
+// 0.3% of the draws).  Coefficients: quantile_f32.h (gen_quantile_f32.py).
+// Within 1e-6 of the exact quantile, max(1, |z|) relative, on every grid
+// point; about 15 instructions against the library quantile's longer,
+// branchier sequence.
+__device__ __forceinline__ float norm_quantile_f32(float u, float omu) {
+  const float lg = __log2f(__fmul_rn(u, omu));        // log2(u (1 - u))
+  const float t = __fmaf_rn(lg, kQfNegLn2, kQfShift);  // w - 2.5
+  const float x = __fsub_rn(u, omu);                   // 2u - 1
+  float r;
+  if (t < kQfSplit) {
+    r = __fmaf_rn(kQfP8, t, kQfP7);
+    r = __fmaf_rn(r, t, kQfP6);
+    r = __fmaf_rn(r, t, kQfP5);
+    r = __fmaf_rn(r, t, kQfP4);
+    r = __fmaf_rn(r, t, kQfP3);
+    r = __fmaf_rn(r, t, kQfP2);
+    r = __fmaf_rn(r, t, kQfP1);
+    r = __fmaf_rn(r, t, kQfP0);
+  } else {
+    float q;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(q) : "f"(__fadd_rn(t, 2.5f)));
+    const float sv = __fsub_rn(q, 3.0f);
+    r = __fmaf_rn(kQfQ8, sv, kQfQ7);
+    r = __fmaf_rn(r, sv, kQfQ6);
+    r = __fmaf_rn(r, sv, kQfQ5);
+    r = __fmaf_rn(r, sv, kQfQ4);
+    r = __fmaf_rn(r, sv, kQfQ3);
+    r = __fmaf_rn(r, sv, kQfQ2);
+    r = __fmaf_rn(r, sv, kQfQ1);
+    r = __fmaf_rn(r, sv, kQfQ0);
+  }
+  return __fmul_rn(x, r);
+}
+
 // Random inputs of one path step from one Philox block: the uniform U_V,
 // 1 - U_V (exact in both grids), Z_V = Phi^-1(U_V) and Z_X.  The float-pair
 // specialisation is in df_math.cuh and uses the tables t stages in shared
@@ -60,8 +99,9 @@ template <> struct Draw<float> {
                                               float& zX, const DfTables*) {
     u = uniform23(w.x);
     omu = 1.0f - u;
-    zV = normcdfinvf(u);
-    zX = normcdfinvf(uniform23(w.z));
+    zV = norm_quantile_f32(u, omu);
+    const float uX = uniform23(w.z);
+    zX = norm_quantile_f32(uX, 1.0f - uX);
   }
 };
 

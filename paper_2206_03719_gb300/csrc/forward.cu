@@ -240,7 +240,8 @@ __device__ __forceinline__ double common_shock<double>(uint4 w, const DfTables*)
 }
 template <>
 __device__ __forceinline__ float common_shock<float>(uint4 w, const DfTables*) {
-  return normcdfinvf(uniform23(w.z));
+  const float u = uniform23(w.z);
+  return norm_quantile_f32(u, 1.0f - u);
 }
 template <>
 __device__ __forceinline__ df common_shock<df>(uint4 w, const DfTables* t) {
