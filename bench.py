@@ -575,7 +575,7 @@ def measure_stac(api, L, torch, reps=3):
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
-                    precision="mixed", max_inflight=16):
+                    precision="mixed", max_inflight=16, saturation=0):
     """Poisson stream of book-distributed requests with continuous batching
     (up to `max_inflight` launches on the device at once, each pricing the
     requests admitted together, admitted by workspace bytes), and the first
@@ -607,11 +607,27 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     greeks = sum(w.n_greeks for t_arr, w, _ in tickets if t_arr >= warm_s)
     first_done = min(s for s, a, d in times)
     last_done = max(d for s, a, d in times)
-    served = {"rate_per_s": rate, "window_s": window_s, "requests": len(tickets), "ok": ok,
+    served = {"rate_per_s": rate, "window_s": window_s, "warm_s": warm_s,
+              "requests": len(tickets), "ok": ok,
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
               "precision": precision, "max_inflight": max_inflight,
               "error": subset_errors(served_results, GOLDEN_SERVING)}
+    if saturation:
+        # capacity: a burst far above what the device can serve, all submitted
+        # at once; sustained Greeks/s from the first submission to the last
+        # completion
+        burst = workloads.book(n_contracts=saturation, seed=1234, precision=precision)
+        with api.Context(workspace_bytes=48 << 30, max_inflight=max_inflight,
+                         precision=precision) as srv:
+            srv.price(burst[0])  # module load
+            t0 = time.perf_counter()
+            ts = [srv.submit(w) for w in burst]
+            done = sum(srv.wait(t, 1, 600.0)[0] == L.LSMC_OK for t in ts)
+            dt = time.perf_counter() - t0
+        served["saturation"] = {"requests": saturation, "ok": done, "seconds": dt,
+                                "greeks_per_s": sum(w.n_greeks for w in burst) / dt,
+                                "requests_per_s": saturation / dt}
     # the same requests, one at a time, plain FP64
     serial = reqs[:serial_n]
     need = max(L.lsmc_request_footprint(None, api.Request(w, precision="fp64").c) for w in serial)
@@ -647,9 +663,15 @@ def extra_jobs():
             ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
             ("store16_precision_study", lambda *a: measure_store16(*a)),
             ("dual_upper_bound", lambda *a: measure_dual(*a)),
-            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2),
+            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=4,
+                                                          saturation=400),
                                     "mixed": measure_serving(*a, precision="mixed",
-                                                             max_inflight=4)}))
+                                                             max_inflight=4, saturation=800)}),
+            # not in the default run: the long window (10 s warm-up, 60 s
+            # measured) and the slot counts side by side
+            ("serving_long", lambda *a: {
+                "df_%d" % k: measure_serving(*a, precision="df", max_inflight=k, warm_s=10.0,
+                                             window_s=60.0) for k in (2, 4, 8)}))
     return jobs
 
 
@@ -802,7 +824,7 @@ def main():
     ctx.close()
     extras = {}
     if not args.no_extras and not args.paths and args.workload == "paper_fp64" and world == 1:
-        jobs = extra_jobs()
+        jobs = [j for j in extra_jobs() if j[0] != "serving_long"]
         for name, fn in jobs:
             torch.cuda.empty_cache()
             try:

@@ -619,29 +619,50 @@ void scheduler_loop(lsmc_ctx* ctx) {
         batch.push_back(t);
         need += t->footprint;
       }
+      // The batch leaves the queue and reserves the slot; its plan is built
+      // and launched without the context lock, so submit, poll and wait
+      // callers are not held up by validation, layout and the table upload
+      // (only this thread admits or completes batches).
       Slot& sl = ctx->slots[free_slot];
-      lsmc_plan* p = nullptr;
-      int rc = LSMC_ENOMEM;
-      while (!batch.empty()) {
-        std::vector<lsmc_request> reqs;
-        std::vector<uint32_t> subs;
-        for (Ticket* t : batch) {
-          reqs.push_back(t->req);
-          subs.push_back(t->sub);
-        }
-        rc = plan_create_on(ctx, reqs.data(), reqs.size(), sl.stream, true, &p, &subs, t0->ppt);
-        if (rc != LSMC_ENOMEM || batch.size() == 1) break;
-        batch.resize(batch.size() / 2);  // fragmentation: a smaller batch
-      }
-      if (rc == LSMC_ENOMEM) break;  // retry once others finish
       ctx->pending.erase(ctx->pending.begin(), ctx->pending.begin() + batch.size());
       const double t_admit = now_s() - ctx->t0;
       for (Ticket* t : batch) {
         t->t_admit = t_admit;
         t->slot = free_slot;
       }
+      sl.batch = batch;
+      sl.plan = nullptr;
+      const uint32_t ppt = t0->ppt;
+      lk.unlock();
+      lsmc_plan* p = nullptr;
+      int rc = LSMC_ENOMEM;
+      size_t take = batch.size();
+      while (take > 0) {
+        std::vector<lsmc_request> reqs;
+        std::vector<uint32_t> subs;
+        for (size_t i = 0; i < take; ++i) {
+          reqs.push_back(batch[i]->req);
+          subs.push_back(batch[i]->sub);
+        }
+        rc = plan_create_on(ctx, reqs.data(), reqs.size(), sl.stream, true, &p, &subs, ppt);
+        if (rc != LSMC_ENOMEM || take == 1) break;
+        take /= 2;  // fragmentation: a smaller batch
+      }
       if (rc == LSMC_OK) rc = plan_launch(p, false);
       if (rc == LSMC_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = LSMC_ECUDA;
+      lk.lock();
+      // requests that did not fit go back to the front of the queue, in order
+      const size_t back = rc == LSMC_ENOMEM ? 0 : take;
+      if (back < batch.size()) {
+        ctx->pending.insert(ctx->pending.begin(), batch.begin() + back, batch.end());
+        for (size_t i = back; i < batch.size(); ++i) {
+          batch[i]->t_admit = 0;
+          batch[i]->slot = -1;
+        }
+        batch.resize(back);
+      }
+      sl.batch.clear();
+      if (rc == LSMC_ENOMEM) break;  // retry once others finish
       if (rc != LSMC_OK) {
         if (p) plan_free(p);
         for (Ticket* t : batch) finish_ticket(ctx, t, rc);

@@ -164,15 +164,20 @@ def rel_err(a, b):
 _DENOM = {"delta": 2.0, "gamma": 1.0, "vega": 8e-4, "rho": 2e-3, "theta": 2.0 / 252}
 
 
+def floored_rel_err(got, ref, k):
+    """Relative error of result key k; a Greek relative to itself or, when it
+    is much smaller than the price differences it is made of, to price /
+    its bump denominator.  NaN on both sides counts as equal."""
+    if math.isnan(got[k]) and math.isnan(ref[k]):
+        return 0.0
+    floor = max(abs(ref.get("price", 1.0)), 1e-2) / _DENOM.get(k, 1.0)
+    return abs(got[k] - ref[k]) / max(abs(ref[k]), floor)
+
+
 def assert_close(got, ref, tol, keys=KEYS, what=""):
     errs = {}
-    scale = max(abs(ref.get("price", 1.0)), 1e-2)
     for k in keys:
-        # a Greek is compared relative to itself or, when it is much smaller
-        # than the price differences it is made of, to price / denominator
-        floor = scale / _DENOM.get(k, 1.0)
-        e = abs(got[k] - ref[k]) / max(abs(ref[k]), floor) if not (
-            math.isnan(got[k]) and math.isnan(ref[k])) else 0.0
+        e = floored_rel_err(got, ref, k)
         errs[k] = e
         assert e <= tol, "%s %s: got %.15g ref %.15g rel %.3g" % (what, k, got[k], ref[k], e)
     return errs

@@ -8,8 +8,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_common import (KEYS, assert_close, oracle_args, oracle_for, rel_err, same_results,
-                        scenario_parity, torch_cuda)
+from gpu_common import (KEYS, assert_close, floored_rel_err, oracle_args, oracle_for, rel_err,
+                        same_results, scenario_parity, torch_cuda)
 from paper_2206_03719_gb300 import api, workloads
 from paper_2206_03719_gb300 import lsmc as L
 
@@ -145,12 +145,14 @@ def test_book_equals_requests_priced_one_by_one(ctx, prec):
 # exercise decisions near the boundary, and each moved decision changes a
 # price at first order; central differences divide those moves by the bumps.
 # The bounds below are the errors this form is reported with at this size
-# (32,768 paths: measured price 1.1e-3, delta 1.3e-2, gamma 0.15, vega 0.81,
-# rho 0.13, theta 0.27 relative, with margin); the price moves by a fraction
-# of its Monte Carlo standard error, and the European price, which has no
-# decisions, stays at the single-precision path error.
-MIXED_BOUNDS = {"price": 3e-3, "european_price": 1e-5, "delta": 5e-2, "gamma": 0.5,
-                "vega": 2.0, "rho": 0.5, "theta": 1.0}
+# (32,768 paths x 64 dates), with margin: the price moves by a fraction of
+# its Monte Carlo standard error, and the European price, which has no
+# decisions, stays at the single-precision path error.  A Greek's error is
+# relative to itself or, where it is much smaller than the price differences
+# it is made of, to price / bump denominator (as in assert_close; measured:
+# at most 2e-2).
+MIXED_BOUNDS = {"price": 3e-3, "european_price": 1e-5, "delta": 0.05, "gamma": 0.05,
+                "vega": 0.05, "rho": 0.05, "theta": 0.05}
 
 
 def test_mixed_precision_errors_against_fp64_oracle_are_within_stated_bounds(ctx):
@@ -160,7 +162,7 @@ def test_mixed_precision_errors_against_fp64_oracle_are_within_stated_bounds(ctx
     worst = {}
     for g, r in zip(got, ref):
         for k in MIXED_BOUNDS:
-            worst[k] = max(worst.get(k, 0.0), rel_err(g[k], r[k]))
+            worst[k] = max(worst.get(k, 0.0), floored_rel_err(g, r, k))
     print("mixed vs FP64 oracle, worst relative errors:", worst)
     for k, bound in MIXED_BOUNDS.items():
         assert worst[k] <= bound, (k, worst[k], bound)
