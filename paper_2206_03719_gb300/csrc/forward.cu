@@ -111,30 +111,41 @@ forward_kernel(FwdArgs a) {
           if (rowV[g]) rowV[g][0] = narrow<St>(v[g]);
         }
     }
-    size_t off = (size_t)(n0 + 1 - row0) * ld;
-    for (uint32_t n = n0; n < n1; ++n, off += ld) {
-      const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
-      float u, omu, zV, zX;
-      Draw<float>::make(w, u, omu, zV, zX, tabs);
+    // the time loop, once with every group present and storing v (the full
+    // bump set with the SV2 basis: no per-group or per-store tests in the
+    // loop), once for the general case
+    auto time_loop = [&](auto all_groups) {
+      constexpr bool kAll = decltype(all_groups)::value;
+      size_t off = (size_t)(n0 + 1 - row0) * ld;
+      for (uint32_t n = n0; n < n1; ++n, off += ld) {
+        const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
+        float u, omu, zV, zX;
+        Draw<float>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll
-      for (int g = 0; g < kMaxGroups; ++g) {
-        if (g < ng) {
-          float xg = x[g], vg = v[g];
-          qe_core<float>(mA[g], mB[g], sA[g], sB[g], c0[g], K1[g], K2[g], K3[g], xg, vg, omu,
-                         zV, zX, tabs);
-          x[g] = xg;
-          v[g] = vg;
-          if (store_rows) {
-            rowE[g][off] = narrow<St>(os[g] * __expf(xg));
-            if (rowV[g]) rowV[g][off] = narrow<St>(vg);
-          }
-          if (save_at(n + 1)) {
-            gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p] = xg;
-            gc[g].CV[(size_t)((n + 1) / a.ck_stride) * ld + p] = vg;
+        for (int g = 0; g < kMaxGroups; ++g) {
+          if (kAll || g < ng) {
+            float xg = x[g], vg = v[g];
+            qe_core<float>(mA[g], mB[g], sA[g], sB[g], c0[g], K1[g], K2[g], K3[g], xg, vg, omu,
+                           zV, zX, tabs);
+            x[g] = xg;
+            v[g] = vg;
+            if (store_rows) {
+              rowE[g][off] = narrow<St>(os[g] * __expf(xg));
+              if (kAll || rowV[g]) rowV[g][off] = narrow<St>(vg);
+            }
+            if (save_at(n + 1)) {
+              gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p] = xg;
+              gc[g].CV[(size_t)((n + 1) / a.ck_stride) * ld + p] = vg;
+            }
           }
         }
       }
-    }
+    };
+    bool all = ng == kMaxGroups;
+#pragma unroll
+    for (int g = 0; g < kMaxGroups; ++g) all = all && rowV[g] != nullptr;
+    if (all) time_loop(std::true_type{});
+    else time_loop(std::false_type{});
   } else if constexpr (!kPair) {
     // double (and the float Euler scheme): every group's state in registers,
     // the group loop unrolled so the groups' independent chains interleave
