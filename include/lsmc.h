@@ -371,6 +371,16 @@ typedef struct lsmc_peaks {
 } lsmc_peaks;
 int lsmc_measure_peaks(int32_t device, lsmc_peaks* out);
 
+/* The checked build's bounds report (a diagnostic; the paper has none).  A
+ * build of this library compiled with LSMC_CHECKED tests every global-memory
+ * access of its kernels against the byte ranges the launch owns (the plan's
+ * allocation, the caller's arrays of a stage call); an access outside them
+ * is skipped and the first one is recorded.  *code: 0, or 3 once an access
+ * fell outside; *line: the kernel source line of that access.  reset != 0
+ * clears the record.  Synchronises the current device.  The ordinary build
+ * returns LSMC_ENOTIMPL; LSMC_EINVAL for NULL pointers. */
+int lsmc_check_report(uint32_t* code, uint32_t* line, int32_t reset);
+
 /* ---- stage entry points (device pointers; for parity tests) ------------- */
 /* Philox4x32-10 of n counters: d_ctr n x 4 uint32 (device), key = (key_lo,
  * key_hi); d_out n x 4 uint32 (device).  (Random inputs of Sec. 2.2.1.) */

@@ -35,6 +35,7 @@
 #include <cstdio>
 #include <type_traits>
 
+#include "checked.cuh"
 #include "device_common.cuh"
 #include "dfloat.cuh"
 #include "exercise.cuh"
@@ -103,9 +104,9 @@ struct JobInfo {
 // Derived per-instance constants: reciprocals of the basis scales, the
 // exercise value at t_0, the S multiplier of every date (scale0 exp(n dr dt))
 // and the discount factor of every date back to t_0 (exp(-r n dt)).
-__global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst) {
+__global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst CHK_PARAM) {
   const uint32_t i = blockIdx.x;
-  if (i >= n_inst) return;
+  if (i >= n_inst || !CHK_OK(chk, &inst[i], sizeof(BwdInstance))) return;
   BwdInstance& I = inst[i];
   if (threadIdx.x == 0) {
     I.disc = exp(-I.r * I.dt);
@@ -115,8 +116,8 @@ __global__ void setup_kernel(BwdInstance* inst, uint32_t n_inst) {
     I.h0 = payoff_d(I.type, I.K, I.spot);
   }
   for (uint32_t n = threadIdx.x; n <= I.N; n += blockDim.x) {
-    I.scale_tab[n] = I.dr_dt == 0.0 ? I.scale0 : I.scale0 * exp((double)n * I.dr_dt);
-    I.scale_tab[I.N + 1 + n] = exp(-I.r * ((double)n * I.dt));
+    CHK_ST(chk, &I.scale_tab[n], I.dr_dt == 0.0 ? I.scale0 : I.scale0 * exp((double)n * I.dr_dt));
+    CHK_ST(chk, &I.scale_tab[I.N + 1 + n], exp(-I.r * ((double)n * I.dt)));
   }
 }
 
@@ -414,20 +415,26 @@ backward_kernel(BwdArgs a) {
       uint32_t lo = 0, hi = a.n_rounds;
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) / 2;
-        if (a.round_off[mid] <= ji.job) lo = mid; else hi = mid;
+        if (CHK_LD(a.chk, &a.round_off[mid]) <= ji.job) lo = mid; else hi = mid;
       }
-      const uint32_t local = (uint32_t)(ji.job - a.round_off[lo]);
-      uint32_t klo = 0, khi = a.active[lo];
+      const uint32_t local = (uint32_t)(ji.job - CHK_LD(a.chk, &a.round_off[lo]));
+      uint32_t klo = 0, khi = CHK_LD(a.chk, &a.active[lo]);
       while (khi - klo > 1) {
         const uint32_t mid = (klo + khi) / 2;
-        if (a.cum_tiles[mid] <= local) klo = mid; else khi = mid;
+        if (CHK_LD(a.chk, &a.cum_tiles[mid]) <= local) klo = mid; else khi = mid;
       }
       ji.round = lo;
       ji.inst = klo;
-      ji.tile = local - a.cum_tiles[klo];
+      ji.tile = local - CHK_LD(a.chk, &a.cum_tiles[klo]);
+      // the job's instance and state must lie in the tables
+      if (!CHK_OK(a.chk, &a.inst[klo], sizeof(BwdInstance)) ||
+          !CHK_OK(a.chk, &a.state[klo], sizeof(BwdState)))
+        ji.abort = 1;
     }
     s_job = ji;
   };
+  // the control word (job counter, error word) must lie in the plan
+  if (!CHK_OK(a.chk, a.ctl, sizeof(Control))) return;
   if (tid == 0) {
     next = atomicAdd(&a.ctl->next_job, 1ull);
     decode();
@@ -491,24 +498,32 @@ backward_kernel(BwdArgs a) {
       if (lane < 16) {
         double v;
         switch (lane) {
-          case 6: v = stab[n + 1]; break;
-          case 7: v = dtab[n + 1]; break;
-          case 8: v = stab[N]; break;
-          case 9: v = stab[n]; break;
+          case 6: v = CHK_LD(a.chk, &stab[n + 1]); break;
+          case 7: v = CHK_LD(a.chk, &dtab[n + 1]); break;
+          case 8: v = CHK_LD(a.chk, &stab[N]); break;
+          case 9: v = CHK_LD(a.chk, &stab[n]); break;
           case 10: v = I.K; break;
           case 11: v = I.invK; break;
           case 12: v = I.inv_theta; break;
           // discount factors as unevaluated pairs (hi + lo): a cash flow is
           // h * hi + h * lo, one rounding, with no bias shared by the paths
           // that exercise on the same date
-          case 13: v = dtab[n + 1] - (double)(Real)dtab[n + 1]; break;
-          case 14: v = dtab[N]; break;
-          case 15: v = dtab[N] - (double)(Real)dtab[N]; break;
+          case 13: {
+            const double d = CHK_LD(a.chk, &dtab[n + 1]);
+            v = d - (double)(Real)d;
+            break;
+          }
+          case 14: v = CHK_LD(a.chk, &dtab[N]); break;
+          case 15: {
+            const double d = CHK_LD(a.chk, &dtab[N]);
+            v = d - (double)(Real)d;
+            break;
+          }
           default: v = first ? 0.0 : s_beta[lane]; break;
         }
         s_c[lane] = (Real)v;
       } else if (std::is_same<Real, double>::value && lane < 18) {
-        const double sv = lane == 16 ? stab[n + 1] : stab[n];
+        const double sv = CHK_LD(a.chk, lane == 16 ? &stab[n + 1] : &stab[n]);
         const double T = itm_threshold(type, sv, I.K);
         s_thr[lane - 16] = __double_as_longlong(T);
         // float e: e < T iff e < (T rounded up to a float); e > T iff e > (T rounded down)
@@ -572,17 +587,17 @@ backward_kernel(BwdArgs a) {
           e1r[k] = v1r[k] = e0r[k] = v0r[k] = (St)0;
           if (p < P) {
             if (first) {
-              e1r[k] = EN[p];
+              e1r[k] = CHK_LD(a.chk, &EN[p]);
             } else {
-              zr[k] = ld_cg(Z + p);
+              zr[k] = CHK_OK(a.chk, Z + p, sizeof(Real)) ? ld_cg(Z + p) : (Real)0;
               if (bok) {
-                e1r[k] = E1[p];
-                if (BASIS == kBasisSV2) v1r[k] = V1[p];
+                e1r[k] = CHK_LD(a.chk, &E1[p]);
+                if (BASIS == kBasisSV2) v1r[k] = CHK_LD(a.chk, &V1[p]);
               }
             }
             if (!final_job) {
-              e0r[k] = E0[p];
-              if (BASIS == kBasisSV2) v0r[k] = V0[p];
+              e0r[k] = CHK_LD(a.chk, &E0[p]);
+              if (BASIS == kBasisSV2) v0r[k] = CHK_LD(a.chk, &V0[p]);
             }
           }
         }
@@ -604,7 +619,7 @@ backward_kernel(BwdArgs a) {
               const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
               z[k] = fma(h, dNhi, h * dNlo);
               euro += (double)z[k];
-              if (!final_job) Z[p] = z[k];
+              if (!final_job) CHK_ST(a.chk, &Z[p], z[k]);
             }
           }
         } else {
@@ -632,7 +647,7 @@ backward_kernel(BwdArgs a) {
                 if (exercise) {
                   const Real hz = fma(h, d1, h * d1lo);
                   z[k] = hz;
-                  if (!final_job) Z[p] = hz;
+                  if (!final_job) CHK_ST(a.chk, &Z[p], hz);
                 }
               }
             }
@@ -703,7 +718,7 @@ backward_kernel(BwdArgs a) {
             } else {
               hz = fma(h, d1, h * d1lo);
             }
-            Z[p] = hz;
+            CHK_ST(a.chk, &Z[p], hz);
           }
         };
         int xn = 0;  // collected items not yet settled (fewer than 32)
@@ -718,10 +733,10 @@ backward_kernel(BwdArgs a) {
             e1r[k] = v1r[k] = (St)0;
             if (p < P) {
               if (first) {
-                e1r[k] = EN[p];
+                e1r[k] = CHK_LD(a.chk, &EN[p]);
               } else {
-                e1r[k] = E1[p];
-                if (BASIS == kBasisSV2) v1r[k] = V1[p];
+                e1r[k] = CHK_LD(a.chk, &E1[p]);
+                if (BASIS == kBasisSV2) v1r[k] = CHK_LD(a.chk, &V1[p]);
               }
             }
           }
@@ -739,7 +754,7 @@ backward_kernel(BwdArgs a) {
                 const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
                 const Real z = fma(h, dNhi, h * dNlo);
                 euro += (double)z;
-                Z[p] = z;
+                CHK_ST(a.chk, &Z[p], z);
               }
             }
             continue;
@@ -830,10 +845,10 @@ backward_kernel(BwdArgs a) {
           z[k] = (Real)0;
           e0r[k] = v0r[k] = (St)0;
           if (p < P) {
-            z[k] = ld_cg(Z + p);
+            z[k] = CHK_OK(a.chk, Z + p, sizeof(Real)) ? ld_cg(Z + p) : (Real)0;
             if (!final_job) {
-              e0r[k] = E0[p];
-              if (BASIS == kBasisSV2) v0r[k] = V0[p];
+              e0r[k] = CHK_LD(a.chk, &E0[p]);
+              if (BASIS == kBasisSV2) v0r[k] = CHK_LD(a.chk, &V0[p]);
             }
           }
         }
@@ -976,7 +991,7 @@ backward_kernel(BwdArgs a) {
           for (int w = 0; w < NW; ++w) v += s_red[w][tid];
         }
       }
-      I.partial[(size_t)ji.tile * kNSum + tid] = v;
+      CHK_ST(a.chk, &I.partial[(size_t)ji.tile * kNSum + tid], v);
     }
 
     // ---- arrive; the last tile of this round reduces and solves ---------------
@@ -1003,7 +1018,9 @@ backward_kernel(BwdArgs a) {
       if (lane < kNSum) {
         double v = 0.0;
         const uint32_t t0 = warp * per, t1 = min(tiles, t0 + per);
-        for (uint32_t t = t0; t < t1; ++t) v += __ldcg(&I.partial[(size_t)t * kNSum + lane]);
+        for (uint32_t t = t0; t < t1; ++t)
+          if (CHK_OK(a.chk, &I.partial[(size_t)t * kNSum + lane], sizeof(double)))
+            v += __ldcg(&I.partial[(size_t)t * kNSum + lane]);
         s_chunk[warp][lane] = v;
       }
       __syncthreads();
@@ -1029,7 +1046,7 @@ backward_kernel(BwdArgs a) {
         res.ties = __ldcg(&st->ties) + s_sum[kSlotTies];
         res.singular = __ldcg(&st->singular);
         res.done = 1;
-        a.results[I.out_index] = res;
+        CHK_ST(a.chk, &a.results[I.out_index], res);
       } else {
         double beta[6];
         const bool ok = solve_normal_equations(NB, s_sum, s_sum + kSlotRhs, beta);
@@ -1041,14 +1058,14 @@ backward_kernel(BwdArgs a) {
         for (int i = 0; i < 6; ++i) st->beta[i] = ok ? beta[i] : 0.0;
         if (I.beta_hist) {
           // coefficients in the units of the cash flow discounted to t_n
-          const double to_n = 1.0 / dtab[n];
+          const double to_n = 1.0 / CHK_LD(a.chk, &dtab[n]);
           for (int i = 0; i < 6; ++i)
-            I.beta_hist[(size_t)n * 6 + i] =
-                ok ? (i < NB ? beta[i] * to_n : 0.0) : __longlong_as_double(0x7ff8000000000000ll);
+            CHK_ST(a.chk, &I.beta_hist[(size_t)n * 6 + i],
+                   ok ? (i < NB ? beta[i] * to_n : 0.0) : __longlong_as_double(0x7ff8000000000000ll));
         }
         if (I.beta_z) {  // the date's coefficients, kept for an out-of-sample pass
-          for (int i = 0; i < 6; ++i) I.beta_z[(size_t)n * 8 + i] = ok ? beta[i] : 0.0;
-          I.beta_z[(size_t)n * 8 + 6] = ok ? 1.0 : 0.0;
+          for (int i = 0; i < 6; ++i) CHK_ST(a.chk, &I.beta_z[(size_t)n * 8 + i], ok ? beta[i] : 0.0);
+          CHK_ST(a.chk, &I.beta_z[(size_t)n * 8 + 6], ok ? 1.0 : 0.0);
         }
         __threadfence();
         st_release_gpu(&st->ready, r + 1);
@@ -1062,10 +1079,12 @@ backward_kernel(BwdArgs a) {
 // prices (the bump layout of the request's scenario table).
 __global__ void greeks_kernel(const GreekOut* __restrict__ g,
                               const BwdResult* __restrict__ res, uint32_t n_out,
-                              DevResult* __restrict__ out) {
+                              DevResult* __restrict__ out CHK_PARAM) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_out) return;
-  const GreekOut G = g[i];
+  const GreekOut G = CHK_LD(chk, &g[i]);
+  for (int k = 0; k < kScCount; ++k)
+    if (G.res[k] >= 0 && !CHK_OK(chk, &res[G.res[k]], sizeof(BwdResult))) return;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   auto V = [&](int kind) { return res[G.res[kind]].price; };
   DevResult o;
@@ -1103,12 +1122,12 @@ __global__ void greeks_kernel(const GreekOut* __restrict__ g,
   o.n_revaluations = nrev;
   o.status = sing ? 1 : 0;
   o.n_near_ties = (uint32_t)ties;
-  out[i] = o;
+  CHK_ST(chk, &out[i], o);
 }
 
-cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s) {
+cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s CHK_PARAM) {
   if (n_inst == 0) return cudaSuccess;
-  setup_kernel<<<n_inst, 128, 0, s>>>(inst, n_inst);
+  setup_kernel<<<n_inst, 128, 0, s>>>(inst, n_inst CHK_ARG(chk));
   return cudaGetLastError();
 }
 
@@ -1201,9 +1220,9 @@ int backward_occupancy(int precision, int basis, int ppt, int fmt) {
 }
 
 cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_out,
-                          DevResult* out, cudaStream_t s) {
+                          DevResult* out, cudaStream_t s CHK_PARAM) {
   if (n_out == 0) return cudaSuccess;
-  greeks_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(g, res, n_out, out);
+  greeks_kernel<<<(n_out + 127) / 128, 128, 0, s>>>(g, res, n_out, out CHK_ARG(chk));
   return cudaGetLastError();
 }
 

@@ -123,6 +123,9 @@ struct lsmc_plan {
   bool timing = false;
   std::vector<std::array<cudaEvent_t, 5>> ev;
   size_t ev_used = 0;
+#ifdef LSMC_CHECKED
+  CheckRanges chk{};  // the byte ranges the plan's launches may touch
+#endif
 };
 
 namespace {
@@ -141,6 +144,16 @@ struct Ticket {
   uint32_t ppt = 0, sub = 1;
   int precision = 0, scheme = 0, basis = 0;
 };
+
+#ifdef LSMC_CHECKED
+// one more byte range a checked launch may touch
+void add_range(CheckRanges& c, const void* q, size_t bytes) {
+  if (!q || !bytes || c.n >= (uint32_t)kMaxRanges) return;
+  c.lo[c.n] = (unsigned long long)q;
+  c.hi[c.n] = c.lo[c.n] + bytes;
+  ++c.n;
+}
+#endif
 
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return LSMC_OK;
@@ -279,6 +292,23 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->bwd_grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(cap, L.total_jobs));
   p->h_out.resize(L.greeks.size());
   p->h_res.resize(L.n_results);
+#ifdef LSMC_CHECKED
+  {
+    // the plan's allocation, and the caller's arrays of a stage call: paths
+    // (rows 0..N, P apart) and the coefficient history (N x 6 doubles)
+    CheckRanges c{};
+    add_range(c, p->dev, L.total_bytes);
+    const size_t N = L.contracts.empty() ? 0 : L.contracts[0].N;
+    const size_t P = L.contracts.empty() ? 0 : L.contracts[0].P;
+    add_range(c, ext_S, (N + 1) * P * real);
+    add_range(c, ext_V, (N + 1) * P * real);
+    add_range(c, beta_hist, N * 6 * sizeof(double));
+    if (check_word(&c.err, &c.info) != LSMC_OK) return LSMC_ECUDA;
+    p->chk = c;
+    p->fa.chk = c;
+    p->ba.chk = c;
+  }
+#endif
   return LSMC_OK;
 }
 
@@ -449,7 +479,8 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
   auto mark = [&](int i) { return ev ? cudaEventRecord(ev[i], p->stream) : cudaSuccess; };
   LSMC_CUDA(cudaMemsetAsync(p->d_state, 0, p->state_bytes, p->stream));
   LSMC_CUDA(mark(0));
-  if (p->run_backward) LSMC_CUDA(launch_setup(p->d_inst, (uint32_t)p->L.inst.size(), p->stream));
+  if (p->run_backward)
+    LSMC_CUDA(launch_setup(p->d_inst, (uint32_t)p->L.inst.size(), p->stream CHK_ARG(p->chk)));
   LSMC_CUDA(mark(1));
   if (p->L.opt.regen && p->run_forward && p->run_backward) {
     // regenerate mode: one pass saving the states, then per segment of
@@ -505,12 +536,14 @@ int plan_enqueue(lsmc_plan* p, bool timed = false) {
       uint32_t max_p = 0;
       for (const auto& c : p->L.contracts) max_p = std::max(max_p, c.P);
       LSMC_CUDA(launch_oos(p->d_inst, (uint32_t)p->L.inst.size(), max_p, p->ba.state,
-                           p->d_results, prec, p->L.opt.basis, p->L.opt.store, p->stream));
+                           p->d_results, prec, p->L.opt.basis, p->L.opt.store,
+                           p->stream CHK_ARG(p->chk)));
     }
     LSMC_CUDA(mark(3));
   }
   if (p->run_greeks)
-    LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out, p->stream));
+    LSMC_CUDA(launch_greeks(p->d_greeks, p->d_results, (uint32_t)p->L.greeks.size(), p->d_out,
+                            p->stream CHK_ARG(p->chk)));
   LSMC_CUDA(mark(4));
   return LSMC_OK;
 }
@@ -1069,6 +1102,10 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
     a.inner_ties = (uint32_t*)c; c += bti;
     a.max_ties = (uint32_t*)c; c += btm;
     a.out = (double*)c;
+#ifdef LSMC_CHECKED
+    a.chk = p->chk;
+    add_range(a.chk, mem, total);
+#endif
     if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
     if (ce == cudaSuccess) ce = cudaEventRecord(e0, p->stream);
@@ -1324,6 +1361,10 @@ int lsmc_multi_asset_max(const lsmc_heston* models, uint32_t n_assets, double T,
   a.sqrt_rho = std::sqrt(rho_assets);
   a.sqrt_1m_rho = std::sqrt(1.0 - rho_assets);
   a.M = d_M;
+#ifdef LSMC_CHECKED
+  add_range(a.chk, d_M, (size_t)(n_steps + 1) * n_paths * value_bytes(precision));
+  if (check_word(&a.chk.err, &a.chk.info) != LSMC_OK) return LSMC_ECUDA;
+#endif
   return cuda_status(launch_multi_max(a, precision, scheme, (cudaStream_t)s));
 }
 

@@ -22,6 +22,7 @@
 // Kernels: outer states (a thread per outer path); inner estimates (a CTA
 // per outer path and date, a thread per inner path); the pathwise maximum
 // (a thread per outer path and strike); fixed-order sums per strike.
+#include "checked.cuh"
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -129,16 +130,16 @@ __global__ void __launch_bounds__(kDualBlock) dual_outer_kernel(DualArgs a) {
   Real* X = (Real*)a.X;
   Real* V = (Real*)a.V;
   Real x = (Real)0, v = gc.v0;
-  X[p] = x;
-  V[p] = v;
+  CHK_ST(a.chk, &X[p], x);
+  CHK_ST(a.chk, &V[p], v);
   for (uint32_t n = 0; n < a.N; ++n) {
     const uint4 w = philox4x32_10(make_uint4(p, n, a.stream ^ 0x80000000u, 0u), key);
     Real u, omu, zV, zX;
     Draw<Real>::make(w, u, omu, zV, zX, tabs);
     if (SCHEME == kSchemeQE) qe_step<Real>(gc, x, v, omu, zV, zX, tabs);
     else ft_step<Real>(gc, x, v, zV, zX);
-    X[(size_t)(n + 1) * a.n_outer + p] = x;
-    V[(size_t)(n + 1) * a.n_outer + p] = v;
+    CHK_ST(a.chk, &X[(size_t)(n + 1) * a.n_outer + p], x);
+    CHK_ST(a.chk, &V[(size_t)(n + 1) * a.n_outer + p], v);
   }
 }
 
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
   const uint32_t p = blockIdx.x / N, n = blockIdx.x % N;
   if (tid == 0) make_group_const<Real>(a.group, gc);
   if (tid < (int)nk) {
-    const BwdInstance& I = a.inst[a.inst_of_strike[tid]];
+    const BwdInstance I = CHK_LD(a.chk, &a.inst[a.inst_of_strike[tid]]);
     s_tab[tid] = (const Real*)I.oos_tab;
     s_scr[tid] = (const ScreenConsts*)I.oos_screen;
     s_K[tid] = (Real)I.K;
@@ -173,8 +174,8 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
   __syncthreads();
   const int type = a.type;
   const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-  const Real x0 = ((const Real*)a.X)[(size_t)n * a.n_outer + p];
-  const Real v0 = ((const Real*)a.V)[(size_t)n * a.n_outer + p];
+  const Real x0 = CHK_LD(a.chk, &((const Real*)a.X)[(size_t)n * a.n_outer + p]);
+  const Real v0 = CHK_LD(a.chk, &((const Real*)a.V)[(size_t)n * a.n_outer + p]);
   const uint32_t all = nk >= 32 ? 0xffffffffu : (1u << nk) - 1u;
   const uint32_t w3 = 1u + p * N + n;
   uint32_t ties = 0;
@@ -193,6 +194,11 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
       for (uint32_t k = 0; k < nk; ++k) {
         if ((done >> k) & 1u) continue;
         const Real* t = s_tab[k] + (size_t)date * kOosConsts;
+        if (!CHK_OK(a.chk, t, sizeof(Real) * kOosConsts) ||
+            !CHK_OK(a.chk, &s_scr[k][date], sizeof(ScreenConsts))) {
+          done |= 1u << k;
+          continue;
+        }
         if (date < N) {
           double z;
           if (rule_exercises<Real, BASIS>(t, s_scr[k][date], type, s_K[k], s_invK[k],
@@ -213,12 +219,12 @@ __global__ void __launch_bounds__(kDualBlock) dual_inner_kernel(DualArgs a) {
   if (tid < (int)nk) {
     double s = 0.0;
     for (int i = 0; i < kDualBlock; ++i) s += s_acc[tid][i];
-    a.Q[((size_t)tid * a.n_outer + p) * N + n] = s / (double)a.n_inner;
+    CHK_ST(a.chk, &a.Q[((size_t)tid * a.n_outer + p) * N + n], s / (double)a.n_inner);
   }
   if (tid == 0) {
     uint32_t t = 0;
     for (int i = 0; i < kDualBlock; ++i) t += s_ties[i];
-    a.inner_ties[blockIdx.x] = t;
+    CHK_ST(a.chk, &a.inner_ties[blockIdx.x], t);
   }
 }
 
@@ -233,6 +239,7 @@ __global__ void __launch_bounds__(kDualBlock) dual_max_kernel(DualArgs a) {
   const uint32_t k = blockIdx.y;
   const uint32_t p = blockIdx.x * kDualBlock + threadIdx.x;
   if (p >= a.n_outer) return;
+  if (!CHK_OK(a.chk, &a.inst[a.inst_of_strike[k]], sizeof(BwdInstance))) return;
   const BwdInstance& I = a.inst[a.inst_of_strike[k]];
   const Real* tab = (const Real*)I.oos_tab;
   const ScreenConsts* scr = (const ScreenConsts*)I.oos_screen;
@@ -247,13 +254,17 @@ __global__ void __launch_bounds__(kDualBlock) dual_max_kernel(DualArgs a) {
   for (uint32_t n = 0; n < N; ++n) {
     const uint32_t date = n + 1;
     const Real* t = tab + (size_t)date * kOosConsts;
-    const Real E = Fm<Real>::exp_(X[(size_t)date * a.n_outer + p], tabs);
+    if (!CHK_OK(a.chk, t, sizeof(Real) * kOosConsts) ||
+        !CHK_OK(a.chk, &scr[date], sizeof(ScreenConsts)) ||
+        !CHK_OK(a.chk, &Q[n], sizeof(double) * (date < N ? 2 : 1)))
+      break;
+    const Real E = Fm<Real>::exp_(CHK_LD(a.chk, &X[(size_t)date * a.n_outer + p]), tabs);
     const Real S = t[7] * E;
     double Z, L;
     if (date < N) {
       Z = date_cash<Real>(t, type, K, S);
       double zx;
-      const Real vs = stored_variance<Real>(SCHEME, V[(size_t)date * a.n_outer + p]);
+      const Real vs = stored_variance<Real>(SCHEME, CHK_LD(a.chk, &V[(size_t)date * a.n_outer + p]));
       L = rule_exercises<Real, BASIS>(t, scr[date], type, K, invK, invTh, E, vs, &zx, &ties)
               ? zx : Q[date];
     } else {
@@ -263,9 +274,9 @@ __global__ void __launch_bounds__(kDualBlock) dual_max_kernel(DualArgs a) {
     pi += L - Q[n];
     best = fmax(best, Z - pi);
   }
-  a.dmax[(size_t)k * a.n_outer + p] = best;
-  a.piN[(size_t)k * a.n_outer + p] = pi;
-  a.max_ties[(size_t)k * a.n_outer + p] = ties;
+  CHK_ST(a.chk, &a.dmax[(size_t)k * a.n_outer + p], best);
+  CHK_ST(a.chk, &a.piN[(size_t)k * a.n_outer + p], pi);
+  CHK_ST(a.chk, &a.max_ties[(size_t)k * a.n_outer + p], ties);
 }
 
 // Per strike (a CTA each): sums over outer paths in a fixed order, the
@@ -275,13 +286,15 @@ __global__ void dual_sum_kernel(DualArgs a) {
   __shared__ double s[5][kDualBlock];
   double d = 0.0, d2 = 0.0, q = 0.0, q2 = 0.0, tt = 0.0;
   for (uint32_t p = threadIdx.x; p < a.n_outer; p += kDualBlock) {
-    const double x = a.dmax[(size_t)k * a.n_outer + p], y = a.piN[(size_t)k * a.n_outer + p];
+    const double x = CHK_LD(a.chk, &a.dmax[(size_t)k * a.n_outer + p]);
+    const double y = CHK_LD(a.chk, &a.piN[(size_t)k * a.n_outer + p]);
     d += x; d2 += x * x; q += y; q2 += y * y;
-    tt += (double)a.max_ties[(size_t)k * a.n_outer + p];
+    tt += (double)CHK_LD(a.chk, &a.max_ties[(size_t)k * a.n_outer + p]);
   }
   if (k == 0) {  // the inner rules' near ties, counted once
     const uint32_t cells = a.n_outer * a.N;
-    for (uint32_t c = threadIdx.x; c < cells; c += kDualBlock) tt += (double)a.inner_ties[c];
+    for (uint32_t c = threadIdx.x; c < cells; c += kDualBlock)
+      tt += (double)CHK_LD(a.chk, &a.inner_ties[c]);
   }
   s[0][threadIdx.x] = d; s[1][threadIdx.x] = d2; s[2][threadIdx.x] = q;
   s[3][threadIdx.x] = q2; s[4][threadIdx.x] = tt;
@@ -298,6 +311,7 @@ __global__ void dual_sum_kernel(DualArgs a) {
     const double var = a.n_outer > 1 ? (s[1][0] - n * mean * mean) / (n - 1.0) : 0.0;
     const double vq = a.n_outer > 1 ? (s[3][0] - n * mq * mq) / (n - 1.0) : 0.0;
     double* o = a.out + (size_t)k * kDualOut;
+    if (!CHK_OK(a.chk, o, sizeof(double) * 5)) return;
     o[0] = mean;
     o[1] = var > 0.0 ? sqrt(var / n) : 0.0;
     o[2] = mq;

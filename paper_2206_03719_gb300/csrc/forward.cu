@@ -17,6 +17,7 @@
 #include "dfloat.cuh"
 #include "kernels.h"
 #include "plan.h"
+#include "checked.cuh"
 #include "heston_step.cuh"
 #include "store16.cuh"
 
@@ -38,12 +39,14 @@ forward_kernel(FwdArgs a) {
     uint32_t lo = 0, hi = a.n_contracts;
     while (hi - lo > 1) {
       const uint32_t mid = (lo + hi) / 2;
-      if (a.contracts[mid].block0 <= blockIdx.x) lo = mid; else hi = mid;
+      if (CHK_LD(a.chk, &a.contracts[mid].block0) <= blockIdx.x) lo = mid; else hi = mid;
     }
-    sc = a.contracts[lo];
+    if (CHK_OK(a.chk, &a.contracts[lo], sizeof(FwdContract))) sc = a.contracts[lo];
+    else sc = FwdContract{};
   }
   __syncthreads();
-  if (threadIdx.x < sc.n_groups)
+  if (threadIdx.x < sc.n_groups && threadIdx.x < kMaxGroups &&
+      CHK_OK(a.chk, &a.groups[sc.group0 + threadIdx.x], sizeof(FwdGroup)))
     make_group_const<Real>(a.groups[sc.group0 + threadIdx.x], gc[threadIdx.x]);
   // float pairs: exp and quantile tables in shared memory
   constexpr bool kPair = std::is_same<Real, df>::value;
@@ -52,7 +55,8 @@ forward_kernel(FwdArgs a) {
   if constexpr (kPair) load_df_tables(tabs);
   __syncthreads();
 
-  if (SEG && a.next_job && blockIdx.x == 0 && threadIdx.x == 0) *a.next_job = a.next_job_value;
+  if (SEG && a.next_job && blockIdx.x == 0 && threadIdx.x == 0)
+    CHK_ST(a.chk, a.next_job, a.next_job_value);
   const uint32_t p = (blockIdx.x - sc.block0) * kFwdBlock + threadIdx.x;
   if (p >= sc.P) return;
   const int ng = (int)sc.n_groups;
@@ -70,8 +74,8 @@ forward_kernel(FwdArgs a) {
 
   for (int g = 0; g < ng; ++g) {
     const FwdGroup& gg = a.groups[sc.group0 + g];
-    if (gg.E_row0) ((St*)gg.E_row0)[p] = narrow<St>(gc[g].out_scale);
-    if (gg.V_row0) ((St*)gg.V_row0)[p] = narrow<St>(gc[g].v0);
+    if (gg.E_row0) CHK_ST(a.chk, &((St*)gg.E_row0)[p], narrow<St>(gc[g].out_scale));
+    if (gg.V_row0) CHK_ST(a.chk, &((St*)gg.V_row0)[p], narrow<St>(gc[g].v0));
   }
 
   if constexpr (std::is_same<Real, float>::value && SCHEME == kSchemeQE) {
@@ -99,16 +103,16 @@ forward_kernel(FwdArgs a) {
 #pragma unroll
       for (int g = 0; g < kMaxGroups; ++g)
         if (g < ng) {
-          x[g] = gc[g].CX[ck_index * ld + p];
-          v[g] = gc[g].CV[ck_index * ld + p];
+          x[g] = CHK_LD(a.chk, &gc[g].CX[ck_index * ld + p]);
+          v[g] = CHK_LD(a.chk, &gc[g].CV[ck_index * ld + p]);
         }
     }
     if (first_row) {
 #pragma unroll
       for (int g = 0; g < kMaxGroups; ++g)
         if (g < ng) {
-          rowE[g][0] = narrow<St>(os[g] * __expf(x[g]));
-          if (rowV[g]) rowV[g][0] = narrow<St>(v[g]);
+          CHK_ST(a.chk, &rowE[g][0], narrow<St>(os[g] * __expf(x[g])));
+          if (rowV[g]) CHK_ST(a.chk, &rowV[g][0], narrow<St>(v[g]));
         }
     }
     // the time loop, once with every group present and storing v (the full
@@ -130,12 +134,12 @@ forward_kernel(FwdArgs a) {
             x[g] = xg;
             v[g] = vg;
             if (store_rows) {
-              rowE[g][off] = narrow<St>(os[g] * __expf(xg));
-              if (kAll || rowV[g]) rowV[g][off] = narrow<St>(vg);
+              CHK_ST(a.chk, &rowE[g][off], narrow<St>(os[g] * __expf(xg)));
+              if (kAll || rowV[g]) CHK_ST(a.chk, &rowV[g][off], narrow<St>(vg));
             }
             if (save_at(n + 1)) {
-              gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p] = xg;
-              gc[g].CV[(size_t)((n + 1) / a.ck_stride) * ld + p] = vg;
+              CHK_ST(a.chk, &gc[g].CX[(size_t)((n + 1) / a.ck_stride) * ld + p], xg);
+              CHK_ST(a.chk, &gc[g].CV[(size_t)((n + 1) / a.ck_stride) * ld + p], vg);
             }
           }
         }
@@ -155,13 +159,15 @@ forward_kernel(FwdArgs a) {
       x[g] = (Real)0;
       v[g] = g < ng ? gc[g].v0 : (Real)0;
       if (ck_index && g < ng) {
-        x[g] = gc[g].CX[ck_index * gc[g].ld + p];
-        v[g] = gc[g].CV[ck_index * gc[g].ld + p];
+        x[g] = CHK_LD(a.chk, &gc[g].CX[ck_index * gc[g].ld + p]);
+        v[g] = CHK_LD(a.chk, &gc[g].CV[ck_index * gc[g].ld + p]);
       }
       if (first_row && g < ng) {
         const GroupConst<Real>& c = gc[g];
-        ((St*)c.E)[p] = narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs));
-        if (c.V) ((St*)c.V)[p] = narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]);
+        CHK_ST(a.chk, &((St*)c.E)[p], narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs)));
+        if (c.V)
+          CHK_ST(a.chk, &((St*)c.V)[p],
+                 narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]));
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
@@ -179,12 +185,14 @@ forward_kernel(FwdArgs a) {
           }
           if (store_rows) {
             const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
-            ((St*)c.E)[off] = narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs));
-            if (c.V) ((St*)c.V)[off] = narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]);
+            CHK_ST(a.chk, &((St*)c.E)[off], narrow<St>(c.out_scale * Fm<Real>::exp_(x[g], tabs)));
+            if (c.V)
+              CHK_ST(a.chk, &((St*)c.V)[off],
+                     narrow<St>((SCHEME == kSchemeFT && v[g] < (Real)0) ? (Real)0 : v[g]));
           }
           if (save_at(n + 1)) {
-            c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = x[g];
-            c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = v[g];
+            CHK_ST(a.chk, &c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p], x[g]);
+            CHK_ST(a.chk, &c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p], v[g]);
           }
         }
       }
@@ -197,11 +205,13 @@ forward_kernel(FwdArgs a) {
     const int t = threadIdx.x;
     for (int g = 0; g < ng; ++g) {
       const GroupConst<Real>& c = gc[g];
-      xs[g][t] = ck_index ? c.CX[ck_index * c.ld + p] : (Real)0;
-      vs[g][t] = ck_index ? c.CV[ck_index * c.ld + p] : c.v0;
+      xs[g][t] = ck_index ? CHK_LD(a.chk, &c.CX[ck_index * c.ld + p]) : (Real)0;
+      vs[g][t] = ck_index ? CHK_LD(a.chk, &c.CV[ck_index * c.ld + p]) : c.v0;
       if (first_row) {
-        ((St*)c.E)[p] = narrow<St>(c.out_scale * Fm<Real>::exp_(xs[g][t], tabs));
-        if (c.V) ((St*)c.V)[p] = narrow<St>((SCHEME == kSchemeFT && vs[g][t] < (Real)0) ? (Real)0 : vs[g][t]);
+        CHK_ST(a.chk, &((St*)c.E)[p], narrow<St>(c.out_scale * Fm<Real>::exp_(xs[g][t], tabs)));
+        if (c.V)
+          CHK_ST(a.chk, &((St*)c.V)[p],
+                 narrow<St>((SCHEME == kSchemeFT && vs[g][t] < (Real)0) ? (Real)0 : vs[g][t]));
       }
     }
     for (uint32_t n = n0; n < n1; ++n) {
@@ -221,12 +231,14 @@ forward_kernel(FwdArgs a) {
         vs[g][t] = vg;
         if (store_rows) {
           const size_t off = (size_t)(n + 1 - row0) * c.ld + p;
-          ((St*)c.E)[off] = narrow<St>(c.out_scale * Fm<Real>::exp_(xg, tabs));
-          if (c.V) ((St*)c.V)[off] = narrow<St>((SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg);
+          CHK_ST(a.chk, &((St*)c.E)[off], narrow<St>(c.out_scale * Fm<Real>::exp_(xg, tabs)));
+          if (c.V)
+            CHK_ST(a.chk, &((St*)c.V)[off],
+                   narrow<St>((SCHEME == kSchemeFT && vg < (Real)0) ? (Real)0 : vg));
         }
         if (save_at(n + 1)) {
-          c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = xg;
-          c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p] = vg;
+          CHK_ST(a.chk, &c.CX[(size_t)((n + 1) / a.ck_stride) * c.ld + p], xg);
+          CHK_ST(a.chk, &c.CV[(size_t)((n + 1) / a.ck_stride) * c.ld + p], vg);
         }
       }
     }
@@ -294,7 +306,7 @@ multi_max_kernel(MultiArgs a) {
       v[k] = gc[ai].v0;
       if (k == 0 || gc[ai].out_scale > m0) m0 = gc[ai].out_scale;
     }
-    M[p] = a0 == 0 ? m0 : fmax(M[p], m0);
+    CHK_ST(a.chk, &M[p], a0 == 0 ? m0 : fmax(CHK_LD(a.chk, &M[p]), m0));
     for (uint32_t n = 0; n < a.N; ++n) {
       Real zc = (Real)0;
       if (corr)
@@ -319,7 +331,7 @@ multi_max_kernel(MultiArgs a) {
         }
       }
       const size_t off = (size_t)(n + 1) * P + p;
-      M[off] = a0 == 0 ? mx : fmax(M[off], mx);
+      CHK_ST(a.chk, &M[off], a0 == 0 ? mx : fmax(CHK_LD(a.chk, &M[off]), mx));
     }
   }
 }

@@ -18,6 +18,7 @@
 // are out of the money or already stopped.
 #include <type_traits>
 
+#include "checked.cuh"
 #include "dfloat.cuh"
 #include "exercise.cuh"
 #include "kernels.h"
@@ -66,7 +67,8 @@ struct OosWarpBufs {
 // exp(-r t_n) as a pair (hi, lo).  Dates without a regression (t_0, t_N, a
 // European contract, a singular solve) get the flag 0.
 template <typename Real>
-__global__ void oos_table_kernel(const BwdInstance* __restrict__ inst) {
+__global__ void oos_table_kernel(const BwdInstance* __restrict__ inst CHK_PARAM) {
+  if (!CHK_OK(chk, &inst[blockIdx.x], sizeof(BwdInstance))) return;
   const BwdInstance& I = inst[blockIdx.x];
   Real* tab = (Real*)I.oos_tab;
   const double* stab = I.scale_tab;
@@ -75,6 +77,11 @@ __global__ void oos_table_kernel(const BwdInstance* __restrict__ inst) {
     Real* t = tab + (size_t)n * kOosConsts;
     const bool regress = n >= 1 && n < I.N && I.style == kAmerican;
     const double* bz = I.beta_z + (size_t)n * 8;
+    if (!CHK_OK(chk, t, sizeof(Real) * kOosConsts) ||
+        (regress && !CHK_OK(chk, bz, sizeof(double) * 7)) ||
+        !CHK_OK(chk, &stab[n], sizeof(double)) || !CHK_OK(chk, &dtab[n], sizeof(double)) ||
+        !CHK_OK(chk, &((ScreenConsts*)I.oos_screen)[n], sizeof(ScreenConsts)))
+      continue;
     for (int i = 0; i < 6; ++i) t[i] = (Real)(regress ? bz[i] : 0.0);
     t[6] = (Real)(regress && bz[6] != 0.0 ? 1.0 : 0.0);
     t[7] = (Real)stab[n];
@@ -101,7 +108,7 @@ __global__ void oos_table_kernel(const BwdInstance* __restrict__ inst) {
 
 template <typename Real, int BASIS, int FMT>
 __global__ void __launch_bounds__(kOosBlock)
-oos_kernel(const BwdInstance* __restrict__ inst) {
+oos_kernel(const BwdInstance* __restrict__ inst CHK_PARAM) {
   using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
   using St = typename RR::raw;
   constexpr int PPT = kOosPpt;
@@ -111,6 +118,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
   constexpr bool kScreen = !std::is_same<Real, float>::value;
   // consecutive CTAs take the same path tile of consecutive instances, so
   // the instances of one path group read the tile's rows while they are in L2
+  if (!CHK_OK(chk, &inst[blockIdx.x], sizeof(BwdInstance))) return;  // the whole block
   const BwdInstance& I = inst[blockIdx.x];
   const uint32_t P = I.P, N = I.N;
   const uint32_t base = blockIdx.y * kOosTile;
@@ -139,6 +147,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
       // the warp leaves the date loop once none of its paths is live
       if (__all_sync(0xffffffffu, (valid & ~stopped) == 0u)) break;
       const Real* t = tab + (size_t)n * kOosConsts;
+      if (!CHK_OK(chk, t, sizeof(Real) * kOosConsts)) continue;  // (uniform)
       if (!flag_set(t[6])) continue;  // no regression at n: no exercise (uniform)
       const Real s1 = t[7];
       const St* En = E + (size_t)(n - 1) * ld + base + tid;
@@ -149,8 +158,8 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
       for (int k = 0; k < PPT; ++k) {
         er[k] = vr[k] = (St)0;
         if (((valid & ~stopped) >> k) & 1u) {
-          er[k] = En[k * kOosBlock];
-          if (BASIS == kBasisSV2) vr[k] = Vn[k * kOosBlock];
+          er[k] = CHK_LD(chk, &En[k * kOosBlock]);
+          if (BASIS == kBasisSV2) vr[k] = CHK_LD(chk, &Vn[k * kOosBlock]);
         }
       }
       Real e[PPT], v[PPT];
@@ -185,7 +194,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
         const Real d1 = t[8], d1lo = t[9];
         // the float screen of every item; those it does not settle as
         // continuing are compacted again for the working-precision work
-        const ScreenConsts& q = ((const ScreenConsts*)I.oos_screen)[n];
+        const ScreenConsts q = CHK_LD(chk, &((const ScreenConsts*)I.oos_screen)[n]);
         int cnt2 = 0;
         for (int j0 = 0; j0 < cnt; j0 += 32) {
           const int j = j0 + lane;
@@ -235,13 +244,13 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
     }
   }
   const Real* tN = tab + (size_t)N * kOosConsts;
-  const Real sN = tN[7], dNhi = tN[8], dNlo = tN[9];
+  const Real sN = CHK_LD(chk, &tN[7]), dNhi = CHK_LD(chk, &tN[8]), dNlo = CHK_LD(chk, &tN[9]);
   const St* EN = E + (size_t)(N - 1) * ld + base + tid;
   double sz = 0.0, sz2 = 0.0, euro = 0.0;
 #pragma unroll
   for (int k = 0; k < PPT; ++k) {
     if (!((valid >> k) & 1u)) break;
-    const Real SN = sN * RR::widen(EN[k * kOosBlock]);
+    const Real SN = sN * RR::widen(CHK_LD(chk, &EN[k * kOosBlock]));
     const Real hN = payoff<Real>(type, K, SN);
     const double zN = (double)fma(hN, dNhi, hN * dNlo);
     const double z = ((stopped >> k) & 1u) ? (double)wb.z[k][lane] : zN;
@@ -265,7 +274,7 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
   if (tid < 4) {
     double acc = 0.0;
     for (int w = 0; w < kOosBlock / 32; ++w) acc += s_part[w][tid];
-    I.oos_sum[(size_t)blockIdx.y * 4 + tid] = acc;
+    CHK_ST(chk, &I.oos_sum[(size_t)blockIdx.y * 4 + tid], acc);
   }
 }
 
@@ -273,14 +282,16 @@ oos_kernel(const BwdInstance* __restrict__ inst) {
 // order, the result written as the pricing result.
 __global__ void oos_finish_kernel(const BwdInstance* __restrict__ inst, uint32_t n_inst,
                                   const BwdState* __restrict__ state,
-                                  BwdResult* __restrict__ results) {
+                                  BwdResult* __restrict__ results CHK_PARAM) {
   const uint32_t i = blockIdx.x;
   if (i >= n_inst || threadIdx.x != 0) return;
+  if (!CHK_OK(chk, &inst[i], sizeof(BwdInstance)) || !CHK_OK(chk, &state[i], sizeof(BwdState)))
+    return;
   const BwdInstance& I = inst[i];
   const uint32_t tiles = (I.P + kOosTile - 1) / kOosTile;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
   for (uint32_t t = 0; t < tiles; ++t)
-    for (int k = 0; k < 4; ++k) s[k] += I.oos_sum[(size_t)t * 4 + k];
+    for (int k = 0; k < 4; ++k) s[k] += CHK_LD(chk, &I.oos_sum[(size_t)t * 4 + k]);
   const double Pd = (double)I.P;
   const double mean = s[0] / Pd;
   const double var = I.P > 1 ? (s[1] - Pd * mean * mean) / (Pd - 1.0) : 0.0;
@@ -293,37 +304,37 @@ __global__ void oos_finish_kernel(const BwdInstance* __restrict__ inst, uint32_t
   res.ties = state[i].ties + s[3];
   res.singular = state[i].singular;
   res.done = 1;
-  results[I.out_index] = res;
+  CHK_ST(chk, &results[I.out_index], res);
 }
 
 template <typename Real, int FMT>
-static void launch_oos_f(const BwdInstance* inst, dim3 grid, bool sv2, cudaStream_t s) {
-  if (sv2) oos_kernel<Real, kBasisSV2, FMT><<<grid, kOosBlock, 0, s>>>(inst);
-  else oos_kernel<Real, kBasisS2, FMT><<<grid, kOosBlock, 0, s>>>(inst);
+static void launch_oos_f(const BwdInstance* inst, dim3 grid, bool sv2, cudaStream_t s CHK_PARAM) {
+  if (sv2) oos_kernel<Real, kBasisSV2, FMT><<<grid, kOosBlock, 0, s>>>(inst CHK_ARG(chk));
+  else oos_kernel<Real, kBasisS2, FMT><<<grid, kOosBlock, 0, s>>>(inst CHK_ARG(chk));
 }
 
 template <typename Real>
 static void launch_oos_t(const BwdInstance* inst, uint32_t n_inst, dim3 grid, bool sv2, int fmt,
-                         cudaStream_t s) {
-  oos_table_kernel<Real><<<n_inst, 128, 0, s>>>(inst);
-  if (fmt == kStoreF16) launch_oos_f<Real, kStoreF16>(inst, grid, sv2, s);
-  else if (fmt == kStoreBF16) launch_oos_f<Real, kStoreBF16>(inst, grid, sv2, s);
-  else launch_oos_f<Real, kStoreNative>(inst, grid, sv2, s);
+                         cudaStream_t s CHK_PARAM) {
+  oos_table_kernel<Real><<<n_inst, 128, 0, s>>>(inst CHK_ARG(chk));
+  if (fmt == kStoreF16) launch_oos_f<Real, kStoreF16>(inst, grid, sv2, s CHK_ARG(chk));
+  else if (fmt == kStoreBF16) launch_oos_f<Real, kStoreBF16>(inst, grid, sv2, s CHK_ARG(chk));
+  else launch_oos_f<Real, kStoreNative>(inst, grid, sv2, s CHK_ARG(chk));
 }
 
 cudaError_t launch_oos(const BwdInstance* inst, uint32_t n_inst, uint32_t max_paths,
                        const BwdState* state, BwdResult* results, int precision, int basis,
-                       int fmt, cudaStream_t s) {
+                       int fmt, cudaStream_t s CHK_PARAM) {
   if (n_inst == 0 || max_paths == 0) return cudaSuccess;
   if (fmt < kStoreNative || fmt > kStoreBF16) return cudaErrorInvalidValue;
   const uint32_t tiles = (max_paths + kOosTile - 1) / kOosTile;
   if (tiles > 65535u || n_inst > 0x7fffffffu) return cudaErrorInvalidValue;
   const dim3 grid(n_inst, tiles);
   const bool sv2 = basis == kBasisSV2;
-  if (precision == kPrecFP64) launch_oos_t<double>(inst, n_inst, grid, sv2, fmt, s);
-  else if (precision == kPrecDF) launch_oos_t<df>(inst, n_inst, grid, sv2, fmt, s);
-  else launch_oos_t<float>(inst, n_inst, grid, sv2, fmt, s);
-  oos_finish_kernel<<<n_inst, 32, 0, s>>>(inst, n_inst, state, results);
+  if (precision == kPrecFP64) launch_oos_t<double>(inst, n_inst, grid, sv2, fmt, s CHK_ARG(chk));
+  else if (precision == kPrecDF) launch_oos_t<df>(inst, n_inst, grid, sv2, fmt, s CHK_ARG(chk));
+  else launch_oos_t<float>(inst, n_inst, grid, sv2, fmt, s CHK_ARG(chk));
+  oos_finish_kernel<<<n_inst, 32, 0, s>>>(inst, n_inst, state, results CHK_ARG(chk));
   return cudaGetLastError();
 }
 

@@ -43,7 +43,29 @@ enum : int32_t { kBasisS2 = 0, kBasisSV2 = 1 };
 enum : int32_t { kStoreNative = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 
 // error codes written by kernels into Control::error
-enum : uint32_t { kDevErrTimeout = 1, kDevErrBadJob = 2 };
+enum : uint32_t { kDevErrTimeout = 1, kDevErrBadJob = 2, kDevErrBadIndex = 3 };
+
+// Checked build (compiled with LSMC_CHECKED): the byte ranges a launch may
+// touch.  Every global-memory access of the kernels is tested against them
+// (checked.cuh); one that falls outside every range is skipped (a load gives
+// zero), and the first such access records kDevErrBadIndex in *err and its
+// source line in *info.  The ordinary build carries none of this.
+constexpr int kMaxRanges = 8;
+struct CheckRanges {
+  unsigned long long lo[kMaxRanges], hi[kMaxRanges];  // [lo, hi)
+  uint32_t n;
+  uint32_t* err;
+  uint32_t* info;
+};
+// an extra parameter (and its argument) of the kernels and launchers that
+// take no argument structure, in the checked build only
+#ifdef LSMC_CHECKED
+#define CHK_PARAM , ::lsmc::CheckRanges chk
+#define CHK_ARG(x) , (x)
+#else
+#define CHK_PARAM
+#define CHK_ARG(x)
+#endif
 
 // ---- forward ------------------------------------------------------------
 struct FwdGroup {
@@ -82,6 +104,9 @@ struct FwdArgs {
   unsigned long long next_job_value;
   uint32_t stream_xor;  // xored into every contract's stream id (pricing paths)
   int32_t store_fmt;    // element type of the E/V rows (kStore*)
+#ifdef LSMC_CHECKED
+  CheckRanges chk;
+#endif
 };
 
 // ---- STAC-A2 multi-asset path reduction --------------------------------------
@@ -96,6 +121,9 @@ struct MultiArgs {        // passed by value (about 4 KB of kernel parameters)
   double T;
   double sqrt_rho, sqrt_1m_rho;  // loadings of the common shock (0, 1: independent)
   void* M;                       // (N + 1) x P values of the working precision
+#ifdef LSMC_CHECKED
+  CheckRanges chk;
+#endif
 };
 
 // ---- backward -------------------------------------------------------------
@@ -164,6 +192,9 @@ struct BwdArgs {
   uint32_t n_rounds, n_inst;
   uint32_t row0;             // date of E/V row index 0 of the instances' rows
   int32_t store_fmt;         // element type of the E/V rows (kStore*)
+#ifdef LSMC_CHECKED
+  CheckRanges chk;
+#endif
 };
 
 // ---- dual upper bound ------------------------------------------------------
@@ -186,6 +217,9 @@ struct DualArgs {
   uint32_t* max_ties;                // n_strikes x n_outer near ties along the outer paths
   double* out;                       // n_strikes x kDualOut: bound, its standard error,
                                      // mean pi_N, its standard error, near ties
+#ifdef LSMC_CHECKED
+  CheckRanges chk;
+#endif
 };
 
 // ---- Greeks ---------------------------------------------------------------

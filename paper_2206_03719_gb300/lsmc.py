@@ -39,6 +39,7 @@ EXPORTS = [
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
     "lsmc_backward_noalloc", "lsmc_device_allocations", "lsmc_set_wait_limit",
     "lsmc_set_backward_shape", "lsmc_plan_fetch_scenarios", "lsmc_measure_peaks",
+    "lsmc_check_report",
 ]
 # scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
 LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
@@ -128,14 +129,18 @@ def library_path() -> str:
     return _build.LIB_PATH
 
 
-def load(build_if_missing: bool = False):
-    """Load liblsmc.so (raises if it is missing and build_if_missing is False)."""
+def load(build_if_missing: bool = False, path: str = None):
+    """Load liblsmc.so (raises if it is missing and build_if_missing is False).
+    path: another build of the library (e.g. the checked build) to load
+    instead, only before the first load of the process."""
     global _lib
     with _lock:
         if _lib is not None:
+            if path is not None and path != _lib._name:
+                raise RuntimeError("another build of liblsmc.so is already loaded")
             return _lib
-        path = _build.LIB_PATH
-        if build_if_missing:
+        path = path or _build.LIB_PATH
+        if build_if_missing and path == _build.LIB_PATH:
             path = _build.build()
         if not os.path.exists(path):
             raise RuntimeError(
@@ -187,6 +192,7 @@ def load(build_if_missing: bool = False):
             "lsmc_set_backward_shape": ([vp, u32, u32], ctypes.c_int),
             "lsmc_plan_fetch_scenarios": ([vp, P(dbl), P(u32), sz], ctypes.c_int),
             "lsmc_measure_peaks": ([i32, P(lsmc_peaks)], ctypes.c_int),
+            "lsmc_check_report": ([P(u32), P(u32), i32], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -261,6 +267,15 @@ def lsmc_measure_peaks(device=0):
     out = lsmc_peaks()
     check(load().lsmc_measure_peaks(device, ctypes.byref(out)), "lsmc_measure_peaks")
     return out.as_dict()
+
+
+def lsmc_check_report(reset=False):
+    """(code, line) of the checked build's first out-of-range access (0, 0:
+    none); LsmcError(LSMC_ENOTIMPL) from the ordinary build."""
+    code, line = ctypes.c_uint32(), ctypes.c_uint32()
+    check(load().lsmc_check_report(ctypes.byref(code), ctypes.byref(line), 1 if reset else 0),
+          "lsmc_check_report")
+    return code.value, line.value
 
 
 def lsmc_set_wait_limit(ctx, seconds):
