@@ -249,11 +249,14 @@ def stepper_roofline(wl, fwd_ms, peaks, hbm_gbs):
     stored = path_steps * groups * value * (2 if wl.basis == "sv2" else 1)
     t = fwd_ms / 1e3
     single = wl.precision == "mixed"
-    fma_peak = peaks.get("fp32_tflops" if single else "fp64_tflops")
+    # float pairs run the same formulas on the FP32 pipes (about ten FP32
+    # instructions per operation), their elementary functions in software
+    fp32 = wl.precision in ("mixed", "df")
+    fma_peak = peaks.get("fp32_tflops" if fp32 else "fp64_tflops")
     out = {"kernel": "forward_kernel", "workload": wl.name, "precision": wl.precision,
            "kernel_ms": fwd_ms, "simulated_path_steps": path_steps * groups,
            "fma": {"achieved": flops / t / 1e12, "peak": fma_peak, "unit": "TFLOP/s",
-                   "pipe": "FP32" if single else "FP64", "flops_per_path_step":
+                   "pipe": "FP32" if fp32 else "FP64", "flops_per_path_step":
                    STEP_SHARED["flops"] + groups * g["flops"]},
            "dram": {"achieved": stored / t / 1e9, "peak": hbm_gbs, "unit": "GB/s",
                     "bytes_per_path_step": stored / path_steps}}

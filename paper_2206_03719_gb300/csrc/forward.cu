@@ -115,9 +115,10 @@ forward_kernel(FwdArgs a) {
           if (rowV[g]) CHK_ST(a.chk, &rowV[g][0], narrow<St>(v[g]));
         }
     }
-    // the time loop, once with every group present and storing v (the full
-    // bump set with the SV2 basis: no per-group or per-store tests in the
-    // loop), once for the general case
+    // the time loop, once with every group present, storing v and with unit
+    // row scale (the full bump set with the SV2 basis in a plan: no per-group
+    // or per-store tests and no scaling in the loop), once for the general
+    // case
     auto time_loop = [&](auto all_groups) {
       constexpr bool kAll = decltype(all_groups)::value;
       size_t off = (size_t)(n0 + 1 - row0) * ld;
@@ -134,7 +135,7 @@ forward_kernel(FwdArgs a) {
             x[g] = xg;
             v[g] = vg;
             if (store_rows) {
-              CHK_ST(a.chk, &rowE[g][off], narrow<St>(os[g] * __expf(xg)));
+              CHK_ST(a.chk, &rowE[g][off], narrow<St>(kAll ? __expf(xg) : os[g] * __expf(xg)));
               if (kAll || rowV[g]) CHK_ST(a.chk, &rowV[g][off], narrow<St>(vg));
             }
             if (save_at(n + 1)) {
@@ -147,7 +148,7 @@ forward_kernel(FwdArgs a) {
     };
     bool all = ng == kMaxGroups;
 #pragma unroll
-    for (int g = 0; g < kMaxGroups; ++g) all = all && rowV[g] != nullptr;
+    for (int g = 0; g < kMaxGroups; ++g) all = all && rowV[g] != nullptr && os[g] == 1.0f;
     if (all) time_loop(std::true_type{});
     else time_loop(std::false_type{});
   } else if constexpr (!kPair) {

@@ -104,8 +104,8 @@ def _run(which):
 
 
 def _same(a, b):
-    if isinstance(a, dict):
-        return a.keys() == b.keys() and all(_same(a[k], b[k]) for k in a)
+    if isinstance(a, dict):  # (the dual pass's device time is a timing, not a result)
+        return a.keys() == b.keys() and all(_same(a[k], b[k]) for k in a if k != "dual_ms")
     if isinstance(a, list):
         return len(a) == len(b) and all(_same(x, y) for x, y in zip(a, b))
     if isinstance(a, float) and math.isnan(a):
