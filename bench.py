@@ -666,7 +666,7 @@ def extra_jobs():
             ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
             ("store16_precision_study", lambda *a: measure_store16(*a)),
             ("dual_upper_bound", lambda *a: measure_dual(*a)),
-            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=4,
+            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2,
                                                           saturation=400),
                                     "mixed": measure_serving(*a, precision="mixed",
                                                              max_inflight=4, saturation=800)}),

@@ -272,6 +272,23 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->fa.next_job_value = 0;
   p->fa.stream_xor = 0;
   p->fa.store_fmt = L.opt.store;
+  // one seed for every contract: the Philox round keys as kernel parameters
+  p->fa.uniform_key = 0;
+  if (!L.contracts.empty()) {
+    const uint64_t seed = L.contracts[0].seed;
+    bool same = true;
+    for (const auto& c : L.contracts) same = same && c.seed == seed;
+    if (same) {
+      uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+      for (int r = 0; r < 10; ++r) {
+        p->fa.rk[2 * r] = k0;
+        p->fa.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;  // the Weyl constants of the key schedule (Salmon et al.)
+        k1 += 0xBB67AE85u;
+      }
+      p->fa.uniform_key = 1;
+    }
+  }
   p->ba.row0 = 1;
   p->ba.store_fmt = L.opt.store;
   p->ba.inst = p->d_inst;

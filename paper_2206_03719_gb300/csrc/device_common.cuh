@@ -26,6 +26,22 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
   return c;
 }
 
+// The same generator with the round keys given: rk[2r], rk[2r + 1] = the
+// key advanced r times.  When every thread of a launch draws under one key,
+// the round keys are kernel parameters, so each xor takes its key from the
+// parameter bank and the key schedule costs no instruction.
+__device__ __forceinline__ uint4 philox4x32_10_rk(uint4 c, const uint32_t (&rk)[20]) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const uint32_t lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ rk[2 * round], lo1, hi0 ^ c.w ^ rk[2 * round + 1], lo0);
+  }
+  return c;
+}
+
 // (m + 1/2) 2^-52, m = top 52 bits of (hi:lo): exact, in (0, 1).
 __device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
   const unsigned long long m =

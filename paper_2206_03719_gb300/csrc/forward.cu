@@ -116,14 +116,15 @@ forward_kernel(FwdArgs a) {
         }
     }
     // the time loop, once with every group present, storing v and with unit
-    // row scale (the full bump set with the SV2 basis in a plan: no per-group
-    // or per-store tests and no scaling in the loop), once for the general
-    // case
+    // row scale, under the launch's one key (the full bump set with the SV2
+    // basis in a plan: no per-group or per-store tests, no scaling and no key
+    // schedule in the loop), once for the general case
     auto time_loop = [&](auto all_groups) {
       constexpr bool kAll = decltype(all_groups)::value;
       size_t off = (size_t)(n0 + 1 - row0) * ld;
       for (uint32_t n = n0; n < n1; ++n, off += ld) {
-        const uint4 w = philox4x32_10(make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u), key);
+        const uint4 ctr = make_uint4(p, n, sc.stream_id ^ a.stream_xor, 0u);
+        const uint4 w = kAll ? philox4x32_10_rk(ctr, a.rk) : philox4x32_10(ctr, key);
         float u, omu, zV, zX;
         Draw<float>::make(w, u, omu, zV, zX, tabs);
 #pragma unroll
@@ -149,6 +150,7 @@ forward_kernel(FwdArgs a) {
     bool all = ng == kMaxGroups;
 #pragma unroll
     for (int g = 0; g < kMaxGroups; ++g) all = all && rowV[g] != nullptr && os[g] == 1.0f;
+    all = all && a.uniform_key != 0;
     if (all) time_loop(std::true_type{});
     else time_loop(std::false_type{});
   } else if constexpr (!kPair) {

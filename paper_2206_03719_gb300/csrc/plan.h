@@ -104,6 +104,10 @@ struct FwdArgs {
   unsigned long long next_job_value;
   uint32_t stream_xor;  // xored into every contract's stream id (pricing paths)
   int32_t store_fmt;    // element type of the E/V rows (kStore*)
+  // every contract of the launch draws under one key: its Philox round keys
+  // (key advanced r times at 2r, 2r + 1); uniform_key = 0 otherwise
+  int32_t uniform_key;
+  uint32_t rk[20];
 #ifdef LSMC_CHECKED
   CheckRanges chk;
 #endif
