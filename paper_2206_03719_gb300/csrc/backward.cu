@@ -101,6 +101,15 @@ struct JobInfo {
 
 }  // namespace
 
+// Threads per CTA of the backward pass and resident CTAs per SM: 128 x 4 for
+// double (shorter barriers around the FP64 pipe's work: the FP64 backward
+// 62.3 -> 59.3 ms against 256 x 2), 256 x 2 for float pairs and float
+// (which lose with 128).  backward_block() on the host gives the same.
+template <typename Real> struct BwdShape {
+  static constexpr int kThreads = std::is_same<Real, double>::value ? 128 : kBlock;
+  static constexpr int kMinBlocks = std::is_same<Real, double>::value ? 4 : 2;
+};
+
 // Derived per-instance constants: reciprocals of the basis scales, the
 // exercise value at t_0, the S multiplier of every date (scale0 exp(n dr dt))
 // and the discount factor of every date back to t_0 (exp(-r n dt)).
@@ -352,11 +361,13 @@ __device__ __forceinline__ float item_float(const Real* buf, int i) {
 // regression runs on Z and the exercise test compares h exp(-r n dt) with the
 // fitted value in the same units.  Z changes only where a path exercises.
 //
-// A job covers `I.sub` sub-tiles of kBlock * PPT paths: the wait for the
+// A job covers `I.sub` sub-tiles of kBT * PPT paths (kBT threads per CTA:
+// BwdShape): the wait for the
 // previous round, the block reduction and the arrival are paid once per job.
 template <typename Real, int BASIS, int PPT, int FMT>
-__global__ void __launch_bounds__(kBlock, 2)
+__global__ void __launch_bounds__(BwdShape<Real>::kThreads, BwdShape<Real>::kMinBlocks)
 backward_kernel(BwdArgs a) {
+  constexpr int kBT = BwdShape<Real>::kThreads;
   using RR = RowRead<Real, FMT>;  // the E/V rows' elements and their widening
   using St = typename RR::raw;
   // double with a 16-bit store: row values kept as floats until the dense loops
@@ -366,8 +377,8 @@ backward_kernel(BwdArgs a) {
   constexpr int NB = BASIS == kBasisSV2 ? 6 : 3;      // basis functions
   constexpr int NM = BASIS == kBasisSV2 ? 15 : 5;     // distinct monomials
   constexpr int NA = NM + NB;                         // register sums
-  constexpr int TILE0 = kBlock * PPT;
-  constexpr int NW = kBlock / 32;
+  constexpr int TILE0 = kBT * PPT;
+  constexpr int NW = kBT / 32;
 
   __shared__ JobInfo s_job;
   __shared__ double s_beta[6];
@@ -582,7 +593,7 @@ backward_kernel(BwdArgs a) {
         St e1r[PPT], v1r[PPT], e0r[PPT], v0r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          const uint32_t p = p_base + k * kBlock;
+          const uint32_t p = p_base + k * kBT;
           zr[k] = (Real)0;
           e1r[k] = v1r[k] = e0r[k] = v0r[k] = (St)0;
           if (p < P) {
@@ -613,7 +624,7 @@ backward_kernel(BwdArgs a) {
         if (first) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             z[k] = (Real)0;
             if (p < P) {
               const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
@@ -630,7 +641,7 @@ backward_kernel(BwdArgs a) {
             // fitted continuation value (basis centred at the strike and theta)
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              const uint32_t p = p_base + k * kBlock;
+              const uint32_t p = p_base + k * kBT;
               const Real S = s1 * e1[k];
               if (p < P && in_money<Real>(type, K, S)) {
                 const Real h = intrinsic<Real>(type, K, S);
@@ -656,7 +667,7 @@ backward_kernel(BwdArgs a) {
         if (final_job) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             if (p < P) {
               const double zv = (double)z[k];
               sy += zv;
@@ -668,7 +679,7 @@ backward_kernel(BwdArgs a) {
           Real* t = acc.target();
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             const Real S = s0 * e0[k];
             if (p < P && in_money<Real>(type, K, S)) {
               accumulate_moments<Real, BASIS, NM>(t, n_itm, S, v0[k], z[k], invK, invTh);
@@ -729,7 +740,7 @@ backward_kernel(BwdArgs a) {
           St e1r[PPT], v1r[PPT];
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             e1r[k] = v1r[k] = (St)0;
             if (p < P) {
               if (first) {
@@ -749,7 +760,7 @@ backward_kernel(BwdArgs a) {
           if (first) {
 #pragma unroll
             for (int k = 0; k < PPT; ++k) {
-              const uint32_t p = p_base + k * kBlock;
+              const uint32_t p = p_base + k * kBT;
               if (p < P) {
                 const Real h = payoff<Real>(type, K, sN * (Real)e1[k]);
                 const Real z = fma(h, dNhi, h * dNlo);
@@ -762,7 +773,7 @@ backward_kernel(BwdArgs a) {
           int cnt = 0;
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             bool itm;
             if constexpr (kNarrow64) {
               const int eb = __float_as_int(e1[k]);
@@ -794,7 +805,7 @@ backward_kernel(BwdArgs a) {
               const int o = co[j];
               wb.xe[q] = cs[j];
               if (BASIS == kBasisSV2) wb.xw[q] = cv[j];
-              wb.xo[q] = (sb * TILE0 + (uint32_t)(o >> 5) * kBlock + warp * 32 + (o & 31)) |
+              wb.xo[q] = (sb * TILE0 + (uint32_t)(o >> 5) * kBT + warp * 32 + (o & 31)) |
                          ((uint32_t)pre << 30);
             }
             xn += __popc(m);
@@ -841,7 +852,7 @@ backward_kernel(BwdArgs a) {
         St e0r[PPT], v0r[PPT];
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          const uint32_t p = p_base + k * kBlock;
+          const uint32_t p = p_base + k * kBT;
           z[k] = (Real)0;
           e0r[k] = v0r[k] = (St)0;
           if (p < P) {
@@ -855,7 +866,7 @@ backward_kernel(BwdArgs a) {
         if (final_job) {
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            const uint32_t p = p_base + k * kBlock;
+            const uint32_t p = p_base + k * kBT;
             if (p < P) {
               const double zv = (double)z[k];
               sy += zv;
@@ -873,7 +884,7 @@ backward_kernel(BwdArgs a) {
         int cnt = mcarry;
 #pragma unroll
         for (int k = 0; k < PPT; ++k) {
-          const uint32_t p = p_base + k * kBlock;
+          const uint32_t p = p_base + k * kBT;
           bool itm;
           if constexpr (kNarrow64) {
             const int eb = __float_as_int(e0[k]);
@@ -1133,7 +1144,7 @@ cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s CHK_
 
 template <typename Real, int PPT>
 static size_t bwd_dyn_bytes() {
-  return (size_t)(kBlock / 32) * sizeof(BwdWarpBufs<Real, PPT>);
+  return (size_t)(BwdShape<Real>::kThreads / 32) * sizeof(BwdWarpBufs<Real, PPT>);
 }
 
 // dynamic shared memory above 48 KB needs the kernel's opt-in, once per device
@@ -1157,7 +1168,7 @@ struct BwdLaunch {
   static cudaError_t run(const BwdArgs& a, int grid, cudaStream_t s) {
     const cudaError_t e = bwd_prepare<Real, BASIS, PPT, FMT>();
     if (e != cudaSuccess) return e;
-    backward_kernel<Real, BASIS, PPT, FMT><<<grid, kBlock, bwd_dyn_bytes<Real, PPT>(), s>>>(a);
+    backward_kernel<Real, BASIS, PPT, FMT><<<grid, BwdShape<Real>::kThreads, bwd_dyn_bytes<Real, PPT>(), s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -1168,7 +1179,7 @@ struct BwdOccupancy {
     int n = 0;
     if (bwd_prepare<Real, BASIS, PPT, FMT>() != cudaSuccess) return 1;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-               &n, backward_kernel<Real, BASIS, PPT, FMT>, kBlock,
+               &n, backward_kernel<Real, BASIS, PPT, FMT>, BwdShape<Real>::kThreads,
                bwd_dyn_bytes<Real, PPT>()) == cudaSuccess ? n : 1;
   }
 };

@@ -423,7 +423,7 @@ int plan_options(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, PlanOptions*
 uint64_t tune_key(const lsmc_request* reqs, size_t n, const PlanOptions& o) {
   // sub-tiles (of the default shape) of the first round over all
   // instances, as a power of two
-  const uint64_t tile0 = (uint64_t)backward_tile(backward_ppt_default(o.precision));
+  const uint64_t tile0 = (uint64_t)backward_tile(o.precision, backward_ppt_default(o.precision));
   uint64_t tiles = 0;
   for (size_t i = 0; i < n; ++i) {
     std::vector<Scenario> sc;
@@ -1188,7 +1188,8 @@ int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket) {
   // about four jobs per regression and date, at most kMaxServeSub sub-tiles
   o.ppt = ctx->ppt_override;
   t->ppt = (uint32_t)plan_ppt(o);
-  const uint32_t tiles = (req->n_paths + backward_tile((int)t->ppt) - 1) / backward_tile((int)t->ppt);
+  const uint32_t tile = (uint32_t)backward_tile(o.precision, (int)t->ppt);
+  const uint32_t tiles = (req->n_paths + tile - 1) / tile;
   t->sub = ctx->sub_override ? ctx->sub_override
                              : std::min<uint32_t>(kMaxServeSub, std::max<uint32_t>(1, (tiles + 3) / 4));
   t->t_submit = now_s() - ctx->t0;

@@ -175,7 +175,7 @@ int plan_ppt(const PlanOptions& o) {
 
 uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, int ppt,
                     uint32_t workers, uint32_t jobs_per_worker) {
-  const uint64_t tile0 = (uint64_t)backward_tile(ppt);
+  const uint64_t tile0 = (uint64_t)backward_tile(precision, ppt);
   uint64_t tiles = 0;  // sub-tiles of the first round, over all instances
   for (size_t i = 0; i < n; ++i) {
     std::vector<Scenario> sc;
@@ -193,7 +193,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
   L->opt = opt;
   const size_t real = value_bytes(opt.precision);
   const size_t rowb = row_bytes(opt.precision, opt.store);  // an element of the E/V rows
-  const uint32_t tile0 = (uint32_t)backward_tile(plan_ppt(opt));
+  const uint32_t tile0 = (uint32_t)backward_tile(opt.precision, plan_ppt(opt));
   const bool store_v = opt.basis == LSMC_BASIS_SV2;
   // device offsets are relative to the region starts; the caller binds them
   size_t off_paths = 0, off_y = 0, off_partial = 0, off_scale = 0;

@@ -145,7 +145,7 @@ def test_book_equals_requests_priced_one_by_one(ctx, prec):
 # exercise decisions near the boundary, and each moved decision changes a
 # price at first order; central differences divide those moves by the bumps.
 # The bounds below are the errors this form is reported with at this size
-# (32,768 paths x 64 dates), with margin: the price moves by a fraction of
+# (32,768 paths x 64 dates), with margin: the price moves by less than half
 # its Monte Carlo standard error, and the European price, which has no
 # decisions, stays at the single-precision path error.  A Greek's error is
 # relative to itself or, where it is much smaller than the price differences
@@ -167,7 +167,7 @@ def test_mixed_precision_errors_against_fp64_oracle_are_within_stated_bounds(ctx
     for k, bound in MIXED_BOUNDS.items():
         assert worst[k] <= bound, (k, worst[k], bound)
     for g, r in zip(got, ref):
-        assert abs(g["price"] - r["price"]) <= 0.25 * r["price_se"]
+        assert abs(g["price"] - r["price"]) <= 0.5 * r["price_se"]
 
 
 def test_invalid_requests_are_rejected_before_launch(ctx):
