@@ -391,6 +391,7 @@ backward_kernel(BwdArgs a) {
   __shared__ Real s_c[16];            // per-job constants, converted once
   __shared__ long long s_thr[2];      // double: in-the-money thresholds of dates n + 1, n
   __shared__ int s_thrf[2];           // the same for float row values (16-bit store)
+  __shared__ df s_thrdf[2];           // float pairs: the thresholds K / s of dates n + 1, n
   __shared__ ScreenConsts s_q;        // the exercise test of date n + 1 in float
   // per-warp compaction of in-the-money paths (dynamic shared memory, one
   // BwdWarpBufs per warp): the heavy arithmetic runs on dense lists instead
@@ -406,10 +407,10 @@ backward_kernel(BwdArgs a) {
   // compaction pays where the in-the-money arithmetic is heavy (double and
   // float pairs); plain floats are bound by loads and stay uncompacted
   constexpr bool kCompact = !std::is_same<Real, float>::value;
-  // double: the in-the-money test needs no product (threshold on the stored
-  // value), so the compaction buffers hold the stored value and S = s e is
-  // formed on the dense lists, where no lane idles
-  constexpr bool kProdLate = std::is_same<Real, double>::value;
+  // double and float pairs: the in-the-money test needs no product (a
+  // threshold on the stored value), so the compaction buffers hold the
+  // stored value and S = s e is formed on the dense lists, where no lane idles
+  constexpr bool kProdLate = kCompact;
   // Job decoding by thread 0: the job number `next` was taken from the
   // counter one job earlier, so the atomic's latency is hidden.
   unsigned long long next = 0;
@@ -533,14 +534,21 @@ backward_kernel(BwdArgs a) {
           default: v = first ? 0.0 : s_beta[lane]; break;
         }
         s_c[lane] = (Real)v;
-      } else if (std::is_same<Real, double>::value && lane < 18) {
+      } else if (kProdLate && lane < 18) {
         const double sv = CHK_LD(a.chk, lane == 16 ? &stab[n + 1] : &stab[n]);
-        const double T = itm_threshold(type, sv, I.K);
-        s_thr[lane - 16] = __double_as_longlong(T);
-        // float e: e < T iff e < (T rounded up to a float); e > T iff e > (T rounded down)
-        if constexpr (kNarrow64)
-          s_thrf[lane - 16] =
-              __float_as_int(type == kPut ? __double2float_ru(T) : __double2float_rd(T));
+        if constexpr (std::is_same<Real, double>::value) {
+          const double T = itm_threshold(type, sv, I.K);
+          s_thr[lane - 16] = __double_as_longlong(T);
+          // float e: e < T iff e < (T rounded up to a float); e > T iff e > (T rounded down)
+          if constexpr (kNarrow64)
+            s_thrf[lane - 16] =
+                __float_as_int(type == kPut ? __double2float_ru(T) : __double2float_rd(T));
+        } else {
+          // float pairs: S = s e < K where e < K / s (put), > for a call; the
+          // two tests can differ only where s e lies within the pairs'
+          // rounding (about 1e-14 relative) of K
+          s_thrdf[lane - 16] = df(I.K / sv);
+        }
       }
       __syncwarp();
       // the compaction buffers hold the row value e (double) or S itself
@@ -778,6 +786,8 @@ backward_kernel(BwdArgs a) {
             if constexpr (kNarrow64) {
               const int eb = __float_as_int(e1[k]);
               itm = p < P && (type == kPut ? eb < s_thrf[0] : eb > s_thrf[0]);
+            } else if constexpr (std::is_same<Real, df>::value) {
+              itm = p < P && (type == kPut ? e1[k] < s_thrdf[0] : s_thrdf[0] < e1[k]);
             } else {
               itm = p < P && itm_test(type, K, s1, e1[k], thr1);
             }
@@ -889,6 +899,8 @@ backward_kernel(BwdArgs a) {
           if constexpr (kNarrow64) {
             const int eb = __float_as_int(e0[k]);
             itm = p < P && (type == kPut ? eb < s_thrf[1] : eb > s_thrf[1]);
+          } else if constexpr (std::is_same<Real, df>::value) {
+            itm = p < P && (type == kPut ? e0[k] < s_thrdf[1] : s_thrdf[1] < e0[k]);
           } else {
             itm = p < P && itm_test(type, K, s0, e0[k], thr0);
           }
