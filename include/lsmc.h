@@ -392,6 +392,15 @@ int lsmc_philox(const uint32_t* d_ctr, uint32_t key_lo, uint32_t key_hi,
 int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
                const uint32_t* d_step, size_t n, int32_t precision,
                void* d_out, void* cuda_stream);
+/* The exponential step of the path generation (Sec. 2.2.1: the stored S is
+ * S0 exp(x) of the log price x) on n values: d_x, d_y (device) of the
+ * precision (double, float, or float pairs hi, lo).  In double, Tang's
+ * table-driven method for |x| < 512 (within one unit in the last place) and
+ * CUDA's exp beyond; float pairs by a Cody-Waite reduction and a 128-entry
+ * table; single precision by CUDA's __expf.  Asynchronous on cuda_stream;
+ * LSMC_EINVAL for NULL arrays (n > 0) or an unknown precision. */
+int lsmc_exp(const void* d_x, void* d_y, size_t n, int32_t precision, void* cuda_stream);
+
 /* Heston paths (Sec. 2.2.1: variance, log price, exponential):
  * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double, float
  * or float pairs by precision; row 0 holds S0 and v0.  V holds max(v, 0) under

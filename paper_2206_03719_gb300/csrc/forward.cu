@@ -356,6 +356,34 @@ cudaError_t launch_multi_max(const MultiArgs& a, int precision, int scheme, cuda
   return cudaGetLastError();
 }
 
+// The exponential of the forward pass (the E rows are S0 exp(x)): exp_f64
+// in double, exp_df on float pairs, __expf in single precision.
+template <typename Real>
+__global__ void exp_kernel(const Real* __restrict__ x, Real* __restrict__ y, size_t n) {
+  constexpr bool kPair = std::is_same<Real, df>::value;
+  __shared__ __align__(16) unsigned char tab_raw[kPair ? sizeof(DfTables) : 16];
+  DfTables* tabs = reinterpret_cast<DfTables*>(tab_raw);
+  if constexpr (kPair) {
+    load_df_tables(tabs);
+    __syncthreads();
+  }
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = Fm<Real>::exp_(x[i], tabs);
+}
+
+cudaError_t launch_exp(const void* x, void* y, size_t n, int precision, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + kBlock - 1) / kBlock;
+  if (blocks > 0x7fffffffu) return cudaErrorInvalidValue;
+  if (precision == kPrecFP64)
+    exp_kernel<double><<<(unsigned)blocks, kBlock, 0, s>>>((const double*)x, (double*)y, n);
+  else if (precision == kPrecDF)
+    exp_kernel<df><<<(unsigned)blocks, kBlock, 0, s>>>((const df*)x, (df*)y, n);
+  else
+    exp_kernel<float><<<(unsigned)blocks, kBlock, 0, s>>>((const float*)x, (float*)y, n);
+  return cudaGetLastError();
+}
+
 __global__ void philox_kernel(const uint4* __restrict__ ctr, uint2 key,
                               uint4* __restrict__ out, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;

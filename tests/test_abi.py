@@ -177,3 +177,8 @@ def test_path_groups_follow_the_bumps_on_host(lib):
     assert groups[()] == groups[("delta", "gamma", "rho")] == 1
     assert groups[("vega",)] == groups[("theta",)] == 3
     assert groups[workloads.ALL_GREEKS] == 5
+
+
+def test_exp_stage_entry_rejects_bad_arguments(lib):
+    assert lib.lsmc_exp(None, None, 4, 0, None) == L.LSMC_EINVAL
+    assert lib.lsmc_exp(None, None, 0, 7, None) == L.LSMC_EINVAL
