@@ -101,13 +101,14 @@ struct JobInfo {
 
 }  // namespace
 
-// Threads per CTA of the backward pass and resident CTAs per SM: 128 x 4 for
-// double (shorter barriers around the FP64 pipe's work: the FP64 backward
-// 62.3 -> 59.3 ms against 256 x 2), 256 x 2 for float pairs and float
-// (which lose with 128).  backward_block() on the host gives the same.
+// Threads per CTA of the backward pass and resident CTAs per SM: 64 x 8 for
+// double (shorter barriers around the FP64 pipe's work: the FP64 backward of
+// the paper-size book 62.3 ms with 256 x 2, 59.4 with 128 x 4, 58.1 with
+// 64 x 8), 256 x 2 for float pairs and float (which lose with 128).
+// backward_block() on the host gives the same.
 template <typename Real> struct BwdShape {
-  static constexpr int kThreads = std::is_same<Real, double>::value ? 128 : kBlock;
-  static constexpr int kMinBlocks = std::is_same<Real, double>::value ? 4 : 2;
+  static constexpr int kThreads = std::is_same<Real, double>::value ? 64 : kBlock;
+  static constexpr int kMinBlocks = std::is_same<Real, double>::value ? 8 : 2;
 };
 
 // Derived per-instance constants: reciprocals of the basis scales, the

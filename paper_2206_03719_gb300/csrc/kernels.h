@@ -33,9 +33,9 @@ cudaError_t launch_greeks(const GreekOut* g, const BwdResult* res, uint32_t n_ou
 // paths): the default for a precision and whether a value is compiled for it.
 int backward_ppt_default(int precision);
 bool backward_ppt_valid(int precision, int ppt);
-// threads per CTA of the backward pass (128 for FP64, kBlock otherwise) and
+// threads per CTA of the backward pass (64 for FP64, kBlock otherwise) and
 // paths per backward sub-tile
-inline int backward_block(int precision) { return precision == kPrecFP64 ? 128 : kBlock; }
+inline int backward_block(int precision) { return precision == kPrecFP64 ? 64 : kBlock; }
 inline int backward_tile(int precision, int ppt) { return backward_block(precision) * ppt; }
 // resident backward CTAs per SM of a kernel variant (fmt: store format)
 int backward_occupancy(int precision, int basis, int ppt, int fmt);
