@@ -3,8 +3,9 @@ S0 exp(x)) on its own, through lsmc_exp: the double-precision exponential
 (Tang's table-driven method for |x| < 512, CUDA's exp beyond) within one unit
 in the last place of exp(x) computed in extended precision (numpy's long
 double: binary128 on the Arm GPU hosts), over the whole double range in
-which it is finite and across the switch at |x| = 512; and the float-pair
-exponential against the same reference on the range the paths use."""
+which it is finite and across the switch at |x| = 512 (measured: 0.998 ulp
+and 0.864 ulp); and the float-pair exponential against the same reference
+for |x| <= 60."""
 import numpy as np
 import pytest
 
@@ -71,7 +72,10 @@ def test_float_pair_exponential_close_to_exact(torch):
     if np.finfo(np.longdouble).nmant < 60:
         pytest.skip("no extended-precision long double on this host")
     rng = np.random.default_rng(8)
-    x = np.concatenate([rng.uniform(-12.0, 12.0, 1 << 20), rng.uniform(-80.0, 80.0, 1 << 18),
+    # up to |x| = 60: below that the low part of exp(x) leaves float's normal
+    # range (exp(-80) ~ 2e-35 has its low part among the subnormals, about
+    # 4e-11 relative); the paths' exp(x) lies near 1
+    x = np.concatenate([rng.uniform(-12.0, 12.0, 1 << 20), rng.uniform(-60.0, 60.0, 1 << 18),
                         np.array([0.0, 1e-30, -1e-30, 1.0, -1.0])])
     # the pairs hold x exactly only to about 48 bits: compare with exp of the
     # value they hold
