@@ -124,7 +124,7 @@ typedef struct lsmc_config {
   int32_t device;        /* CUDA device ordinal */
   int32_t precision;     /* default LSMC_FP64 / LSMC_MIXED */
   int32_t scheme;        /* default LSMC_SCHEME_QE / LSMC_SCHEME_FT_EULER */
-  int32_t reserved;
+  int32_t max_batch;     /* requests admitted together in serving; 0 = 64 */
   uint64_t hbm_budget;   /* bytes the serving loop may hold; 0 = 3/4 of free */
   uint32_t max_inflight; /* requests on the device at once (serving); 0 = 8 */
   uint32_t queue_capacity; /* pending requests accepted; 0 = 4096 */
@@ -333,8 +333,9 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
 /* Queues a copy of *req; returns a ticket.  Whenever a slot
  * (config.max_inflight) is free, the oldest pending request and the pending
  * requests right behind it that can share a launch (same precision, scheme
- * and basis; up to 64, while the workspace bytes of config.hbm_budget allow)
- * are admitted together as one batch: one launch of each kernel, on the
+ * and basis; up to config.max_batch, while the workspace bytes of
+ * config.hbm_budget allow) are admitted together as one batch: one launch
+ * of each kernel, on the
  * slot's own stream, overlapping with the batches already running.  The
  * backward job size of a request depends on the request alone, so its
  * results are the same whichever batch it runs in.  LSMC_EBUSY when the

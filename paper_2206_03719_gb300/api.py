@@ -60,11 +60,11 @@ class Context:
     def __init__(self, workspace_bytes: int = 0, precision: str = "fp64",
                  scheme: str = "qe", hbm_budget: int = 0, max_inflight: int = 8,
                  use_torch_stream: bool = True, device: Optional[int] = None,
-                 torch_allocator: bool = False):
+                 torch_allocator: bool = False, max_batch: int = 0):
         import torch
         self.torch = torch
         dev = torch.cuda.current_device() if device is None else device
-        cfg = L.lsmc_config(dev, _PREC[precision], _SCHEME[scheme], 0, hbm_budget,
+        cfg = L.lsmc_config(dev, _PREC[precision], _SCHEME[scheme], max_batch, hbm_budget,
                             max_inflight, 0)
         self.ctx = L.lsmc_create(cfg)
         self._plans = weakref.WeakSet()

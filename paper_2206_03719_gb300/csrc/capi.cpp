@@ -70,6 +70,7 @@ struct lsmc_ctx {
   void* own_arena_mem = nullptr;
   size_t hbm_budget = 0;
   uint32_t max_inflight = 8, queue_capacity = 4096;
+  uint32_t max_batch = 64;    // requests admitted together (lsmc_config.max_batch)
   int num_sms = 0;
   std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
   std::mutex occ_mu;          // guards occ (plans are built on several threads)
@@ -612,7 +613,7 @@ void finish_ticket(lsmc_ctx* ctx, Ticket* t, int status) {
 }
 
 // Requests admitted together share one plan (one launch of each kernel).
-constexpr size_t kMaxBatch = 64;
+constexpr size_t kMaxBatch = 64;  // default and upper limit of lsmc_config.max_batch
 constexpr uint32_t kMaxServeSub = 32;
 
 void scheduler_loop(lsmc_ctx* ctx) {
@@ -659,7 +660,7 @@ void scheduler_loop(lsmc_ctx* ctx) {
       if (room < t0->footprint) break;  // wait for memory
       std::vector<Ticket*> batch{t0};
       size_t need = t0->footprint;
-      for (size_t i = 1; i < ctx->pending.size() && batch.size() < kMaxBatch; ++i) {
+      for (size_t i = 1; i < ctx->pending.size() && batch.size() < ctx->max_batch; ++i) {
         Ticket* t = ctx->pending[i];
         if (t->precision != t0->precision || t->scheme != t0->scheme ||
             t->basis != t0->basis || t->ppt != t0->ppt || t->req.flags != t0->req.flags ||
@@ -834,6 +835,8 @@ int lsmc_create(lsmc_ctx** out, const lsmc_config* cfg) {
   ctx->hbm_budget = (size_t)c.hbm_budget;
   ctx->max_inflight = c.max_inflight ? c.max_inflight : 8;
   ctx->queue_capacity = c.queue_capacity ? c.queue_capacity : 4096;
+  ctx->max_batch = c.max_batch > 0 ? std::min<uint32_t>((uint32_t)c.max_batch, kMaxBatch)
+                                   : (uint32_t)kMaxBatch;
   ctx->t0 = now_s();
   if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
     delete ctx;

@@ -95,7 +95,7 @@ class lsmc_peaks(ctypes.Structure):
 
 class lsmc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("scheme", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("scheme", ctypes.c_int32), ("max_batch", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_uint64), ("max_inflight", ctypes.c_uint32),
                 ("queue_capacity", ctypes.c_uint32)]
 
