@@ -335,8 +335,8 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
  * requests right behind it that can share a launch (same precision, scheme
  * and basis; up to config.max_batch, while the workspace bytes of
  * config.hbm_budget allow) are admitted together as one batch: one launch
- * of each kernel, on the
- * slot's own stream, overlapping with the batches already running.  The
+ * of each kernel, on the slot's own stream, overlapping with the batches
+ * already running.  The
  * backward job size of a request depends on the request alone, so its
  * results are the same whichever batch it runs in.  LSMC_EBUSY when the
  * queue is full. */
