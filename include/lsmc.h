@@ -398,7 +398,8 @@ int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
  * precision (double, float, or float pairs hi, lo).  In double, Tang's
  * table-driven method for |x| < 512 (within one unit in the last place) and
  * CUDA's exp beyond; float pairs by a Cody-Waite reduction and a 128-entry
- * table; single precision by CUDA's __expf.  Asynchronous on cuda_stream;
+ * table (within 2e-14 relative for |x| <= 70, where the result's low word
+ * stays a normal float); single precision by CUDA's __expf.  Asynchronous on cuda_stream;
  * LSMC_EINVAL for NULL arrays (n > 0) or an unknown precision. */
 int lsmc_exp(const void* d_x, void* d_y, size_t n, int32_t precision, void* cuda_stream);
 

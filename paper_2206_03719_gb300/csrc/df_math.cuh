@@ -30,8 +30,8 @@ __device__ __forceinline__ void load_df_tables(DfTables* t) {
 
 // exp(a).  Reduction a = k L + r with L = ln 2 / kExpTab split into three
 // floats (Cody and Waite: k C1 is exact, k C2 is an exact product pair), so
-// |r| <= L / 2 ~ 0.0027; then exp(a) = 2^n 2^(j / kExpTab) exp(r) with
-// k = n kExpTab + j.  exp(r) - 1 = r + r^2 / 2 + r^3 (1/6 + r / 24 + r^2 / 120):
+// |r| <= L / 2 ~ 0.0027, held to about 2^-56 absolute; then
+// exp(a) = 2^n 2^(j / kExpTab) exp(r) with k = n kExpTab + j.  exp(r) - 1 = r + r^2 / 2 + r^3 (1/6 + r / 24 + r^2 / 120):
 // r^2 is an exact product pair, the cubic tail (< 4e-9) is summed in float.
 __device__ __forceinline__ df exp_df(df a, const float2* tab) {
   if (a.hi > 88.0f) return df(__int_as_float(0x7f800000), 0.0f);
@@ -40,9 +40,12 @@ __device__ __forceinline__ df exp_df(df a, const float2* tab) {
   const int k = (int)kf;
   const float t1 = __fmaf_rn(-kf, kExpC1, a.hi);  // exact (Sterbenz)
   const df p2 = two_prod(kf, kExpC2);
-  df r = two_sum(t1, -p2.hi);
-  r = quick_two_sum(r.hi, __fadd_rn(r.lo, __fsub_rn(__fsub_rn(a.lo, p2.lo),
-                                                     __fmul_rn(kf, kExpC3))));
+  // a.lo (up to half an ulp of a.hi, 2e-6 at |a| = 60) is added by a two-sum:
+  // folded into the low word in float it would cost up to 2^-43 absolute
+  const df d = two_sum(t1, -p2.hi);
+  const df e0 = two_sum(d.hi, a.lo);
+  const df r = quick_two_sum(
+      e0.hi, __fadd_rn(e0.lo, __fsub_rn(d.lo, __fmaf_rn(kf, kExpC3, p2.lo))));
   df r2 = two_prod(r.hi, r.hi);
   r2.lo = __fmaf_rn(__fadd_rn(r.hi, r.hi), r.lo, r2.lo);
   const float tail = __fmul_rn(__fmul_rn(r2.hi, r.hi),

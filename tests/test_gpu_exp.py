@@ -4,8 +4,8 @@ S0 exp(x)) on its own, through lsmc_exp: the double-precision exponential
 in the last place of exp(x) computed in extended precision (numpy's long
 double: binary128 on the Arm GPU hosts), over the whole double range in
 which it is finite and across the switch at |x| = 512 (measured: 0.998 ulp
-and 0.864 ulp); and the float-pair exponential against the same reference
-for |x| <= 60."""
+and 0.864 ulp); and the float-pair exponential within 2e-14 relative of the
+same reference for |x| <= 70 (tests/test_exp_df.py emulates it on the CPU)."""
 import numpy as np
 import pytest
 
@@ -72,11 +72,11 @@ def test_float_pair_exponential_close_to_exact(torch):
     if np.finfo(np.longdouble).nmant < 60:
         pytest.skip("no extended-precision long double on this host")
     rng = np.random.default_rng(8)
-    # up to |x| = 60: below that the low part of exp(x) leaves float's normal
+    # up to |x| = 70: beyond, the low part of exp(x) leaves float's normal
     # range (exp(-80) ~ 2e-35 has its low part among the subnormals, about
     # 4e-11 relative); the paths' exp(x) lies near 1
-    x = np.concatenate([rng.uniform(-12.0, 12.0, 1 << 20), rng.uniform(-60.0, 60.0, 1 << 18),
-                        np.array([0.0, 1e-30, -1e-30, 1.0, -1.0])])
+    x = np.concatenate([rng.uniform(-12.0, 12.0, 1 << 20), rng.uniform(-70.0, 70.0, 1 << 18),
+                        np.array([0.0, 1e-30, -1e-30, 1.0, -1.0, 70.0, -70.0])])
     # the pairs hold x exactly only to about 48 bits: compare with exp of the
     # value they hold
     hi = x.astype(np.float32)
@@ -85,4 +85,4 @@ def test_float_pair_exponential_close_to_exact(torch):
     y = _gpu_exp(torch, x, L.LSMC_DF)
     rel = np.abs(y - np.exp(held)) / np.exp(held)
     print("exp_df: worst relative error %.3g" % rel.max())
-    assert rel.max() <= 5e-14
+    assert rel.max() <= 2e-14
