@@ -93,7 +93,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="paper_fp64",
-                    choices=["paper_fp64", "large_mixed", "paper_mixed", "paper_df"])
+                    choices=["paper_fp64", "large_mixed", "paper_mixed", "paper_df", "small",
+                             "book_subset"],
+                    help="book_subset serves --cpu-full only")
     ap.add_argument("--paths", type=int, default=0,
                     help="override the path count (profiling of a smaller case)")
     ap.add_argument("--sub", type=int, default=0,
@@ -120,6 +122,8 @@ def parse():
 
 
 def pick_workload(name):
+    if name == "small":
+        return workloads.SMALL_FP64
     if name == "paper_fp64":
         return workloads.PAPER_FP64
     if name == "paper_df":
@@ -704,14 +708,30 @@ def within_1e4_summary(line, acc, value):
             "outside_1e-4": out}
 
 
-def run_cpu_full(wl):
+def run_cpu_full(wl, name):
     """The FP64 oracle once on the whole workload (every path, strike and
-    revaluation) on all host cores: a full-size CPU baseline."""
+    revaluation) on all host cores: a full-size CPU baseline.  name
+    "book_subset": the 32 seeded contracts of the uneven book whose oracle
+    values are stored, one after another."""
     import oracle
     sys.path.insert(0, os.path.join(_ROOT, "tests"))
-    from golden.make_golden import run_oracle  # noqa: E402
+    from golden.make_golden import BOOK_SUBSET, run_oracle  # noqa: E402
     oracle.build()
     n = os.cpu_count() or 1
+    if name == "book_subset":
+        book = workloads.book(n_contracts=512)
+        wls = [book[i] for i in BOOK_SUBSET]
+        t0 = time.perf_counter()
+        for w in wls:
+            run_oracle(w.replace(precision="fp64"), n_threads=n)
+        dt = time.perf_counter() - t0
+        print(json.dumps({"cpu_full": {"workload": "book subset (%d contracts)" % len(wls),
+                                       "seconds": dt, "cores": n,
+                                       "greeks_per_s": sum(w.n_greeks for w in wls) / dt,
+                                       "lsmc_path_steps_per_s":
+                                           sum(w.lsmc_path_steps for w in wls) / dt}}),
+              flush=True)
+        return
     t0 = time.perf_counter()
     res, _ = run_oracle(wl.replace(precision="fp64"), n_threads=n)
     dt = time.perf_counter() - t0
@@ -726,6 +746,8 @@ def run_cpu_full(wl):
 
 def main():
     args = parse()
+    if args.workload == "book_subset" and not args.cpu_full:
+        sys.exit("--workload book_subset serves --cpu-full only")
     wl = pick_workload(args.workload)
     if args.paths:
         wl = wl.replace(n_paths=args.paths, name=wl.name + "-paths%d" % args.paths)
@@ -739,7 +761,7 @@ def main():
         run_reference(args, wl)
         return
     if args.cpu_full:
-        run_cpu_full(wl)
+        run_cpu_full(wl, args.workload)
         return
     rank, world, local = dist_env()
     wl = replica_workload(wl, rank)
