@@ -336,10 +336,14 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
  * and basis; up to config.max_batch, while the workspace bytes of
  * config.hbm_budget allow) are admitted together as one batch: one launch
  * of each kernel, on the slot's own stream, overlapping with the batches
- * already running.  The
- * backward job size of a request depends on the request alone, so its
- * results are the same whichever batch it runs in.  LSMC_EBUSY when the
- * queue is full. */
+ * already running.  A request is done as soon as its own revaluations are:
+ * the backward pass forms its prices and Greeks when its last regression
+ * finishes and hands them to the host through page-locked, device-mapped
+ * memory, ahead of the rest of its batch (out-of-sample requests finish with
+ * their batch).  The backward job size of a request depends on the request
+ * alone, so its results are the same whichever batch it runs in, and the
+ * same as lsmc_price_request's under the same backward shape.  LSMC_EBUSY
+ * when the queue is full. */
 int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket);
 /* LSMC_PENDING while in flight; LSMC_OK with outs filled (n_strikes results)
  * once done (the ticket is then released); a negative code on failure. */

@@ -315,6 +315,85 @@ __device__ __forceinline__ void accumulate_moments(Real* t, uint32_t& cnt, Real 
   }
 }
 
+// Price and Greeks of one (request, strike) by central differences of its
+// revaluation prices (the bump layout of the request's scenario table).
+// Every operation rounds once (no contraction), so the Greeks kernel and the
+// backward pass's per-request completion form the same bits.  kCg: the
+// results were stored by other CTAs of the running launch (loads from L2).
+template <bool kCg>
+__device__ __forceinline__ bool form_greeks(const GreekOut& G, const BwdResult* res,
+                                            DevResult& o CHK_PARAM) {
+  for (int k = 0; k < kScCount; ++k)
+    if (G.res[k] >= 0 && !CHK_OK(chk, &res[G.res[k]], sizeof(BwdResult))) return false;
+  auto ld = [](const double* p) { return kCg ? __ldcg(p) : *p; };
+  auto V = [&](int kind) { return ld(&res[G.res[kind]].price); };
+  const double nan = __longlong_as_double(0x7ff8000000000000ll);
+  const BwdResult* base = &res[G.res[kScBase]];
+  o.price = ld(&base->price);
+  o.price_se = ld(&base->se);
+  o.european_price = ld(&base->euro);
+  o.delta = o.gamma = o.vega = o.rho = o.theta = nan;
+  // (V+ - V-) / (2 h): the central difference
+  auto central = [&](int up, int dn, double h2) { return __ddiv_rn(__dsub_rn(V(up), V(dn)), h2); };
+  if ((G.mask & 1u) && G.res[kScSUp] >= 0)
+    o.delta = central(kScSUp, kScSDn, __dmul_rn(__dmul_rn(2.0, G.hS), G.S0));
+  if (G.mask & 2u) {
+    // (V+ - 2 V + V-) / h^2
+    const bool own = G.res[kScSgUp] >= 0;
+    if (own || G.res[kScSUp] >= 0) {
+      const int up = own ? kScSgUp : kScSUp, dn = own ? kScSgDn : kScSDn;
+      const double h = __dmul_rn(own ? G.hG : G.hS, G.S0);
+      o.gamma = __ddiv_rn(__dadd_rn(__dsub_rn(V(up), __dmul_rn(2.0, V(kScBase))), V(dn)),
+                          __dmul_rn(h, h));
+    }
+  }
+  if ((G.mask & 4u) && G.res[kScVUp] >= 0)
+    o.vega = central(kScVUp, kScVDn, __dmul_rn(__dmul_rn(2.0, G.hV), G.v0));
+  if ((G.mask & 8u) && G.res[kScRUp] >= 0) o.rho = central(kScRUp, kScRDn, __dmul_rn(2.0, G.dR));
+  if ((G.mask & 16u) && G.res[kScTDn] >= 0)
+    o.theta = central(kScTDn, kScTUp, __dmul_rn(2.0, G.dT));
+  uint32_t sing = 0, nrev = 0;
+  double ties = 0.0;
+  for (int k = 0; k < kScCount; ++k)
+    if (G.res[k] >= 0) {
+      const BwdResult* r = &res[G.res[k]];
+      sing += kCg ? __ldcg(&r->singular) : r->singular;
+      ties = __dadd_rn(ties, ld(&r->ties));
+      ++nrev;
+    }
+  o.n_singular_solves = sing;
+  o.n_revaluations = nrev;
+  o.status = sing ? 1 : 0;
+  o.n_near_ties = (uint32_t)ties;
+  return true;
+}
+
+// Per-request completion (serving), by thread 0 of a CTA that has stored the
+// final result of one of request q's instances: the request's last instance
+// to finish forms its prices and Greeks, writes them to the host-mapped
+// array and then raises the request's host-mapped flag.  The results of the
+// other instances were stored before their CTAs' fenced arrivals on the
+// counter, so the last arrival reads them all.
+__device__ __forceinline__ void finish_request(const BwdArgs& a, uint32_t q) {
+  const uint32_t* info = a.req_info + 3 * (size_t)q;
+  if (!CHK_OK(a.chk, info, 3 * sizeof(uint32_t)) ||
+      !CHK_OK(a.chk, &a.req_count[q], sizeof(uint32_t)) ||
+      !CHK_OK(a.chk, &a.flag_host[q], sizeof(uint32_t)))
+    return;
+  __threadfence();
+  if (atomicAdd(&a.req_count[q], 1u) + 1u != info[0]) return;
+  __threadfence();
+  for (uint32_t g = info[1]; g < info[1] + info[2]; ++g) {
+    DevResult o;
+    if (!CHK_OK(a.chk, &a.greeks[g], sizeof(GreekOut)) ||
+        !form_greeks<true>(a.greeks[g], a.results, o CHK_ARG(a.chk)))
+      return;
+    CHK_ST(a.chk, &a.out_host[g], o);
+  }
+  __threadfence_system();
+  *(volatile uint32_t*)&a.flag_host[q] = 1u;
+}
+
 // Per-warp buffers of the backward kernel (dynamic shared memory): the row
 // values (e or S, and v) of the in-the-money paths compacted for the
 // exercise test and their origins (k * 32 + lane); the row values and cash
@@ -1071,6 +1150,7 @@ backward_kernel(BwdArgs a) {
         res.singular = __ldcg(&st->singular);
         res.done = 1;
         CHK_ST(a.chk, &a.results[I.out_index], res);
+        if (a.flag_host != nullptr) finish_request(a, I.req);
       } else {
         double beta[6];
         const bool ok = solve_normal_equations(NB, s_sum, s_sum + kSlotRhs, beta);
@@ -1106,47 +1186,8 @@ __global__ void greeks_kernel(const GreekOut* __restrict__ g,
                               DevResult* __restrict__ out CHK_PARAM) {
   const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_out) return;
-  const GreekOut G = CHK_LD(chk, &g[i]);
-  for (int k = 0; k < kScCount; ++k)
-    if (G.res[k] >= 0 && !CHK_OK(chk, &res[G.res[k]], sizeof(BwdResult))) return;
-  const double nan = __longlong_as_double(0x7ff8000000000000ll);
-  auto V = [&](int kind) { return res[G.res[kind]].price; };
   DevResult o;
-  const BwdResult base = res[G.res[kScBase]];
-  o.price = base.price;
-  o.price_se = base.se;
-  o.european_price = base.euro;
-  o.delta = o.gamma = o.vega = o.rho = o.theta = nan;
-  if ((G.mask & 1u) && G.res[kScSUp] >= 0)
-    o.delta = (V(kScSUp) - V(kScSDn)) / (2.0 * G.hS * G.S0);
-  if (G.mask & 2u) {
-    if (G.res[kScSgUp] >= 0) {
-      const double h = G.hG * G.S0;
-      o.gamma = (V(kScSgUp) - 2.0 * V(kScBase) + V(kScSgDn)) / (h * h);
-    } else if (G.res[kScSUp] >= 0) {
-      const double h = G.hS * G.S0;
-      o.gamma = (V(kScSUp) - 2.0 * V(kScBase) + V(kScSDn)) / (h * h);
-    }
-  }
-  if ((G.mask & 4u) && G.res[kScVUp] >= 0)
-    o.vega = (V(kScVUp) - V(kScVDn)) / (2.0 * G.hV * G.v0);
-  if ((G.mask & 8u) && G.res[kScRUp] >= 0)
-    o.rho = (V(kScRUp) - V(kScRDn)) / (2.0 * G.dR);
-  if ((G.mask & 16u) && G.res[kScTDn] >= 0)
-    o.theta = (V(kScTDn) - V(kScTUp)) / (2.0 * G.dT);
-  uint32_t sing = 0, nrev = 0;
-  double ties = 0.0;
-  for (int k = 0; k < kScCount; ++k)
-    if (G.res[k] >= 0) {
-      sing += res[G.res[k]].singular;
-      ties += res[G.res[k]].ties;
-      ++nrev;
-    }
-  o.n_singular_solves = sing;
-  o.n_revaluations = nrev;
-  o.status = sing ? 1 : 0;
-  o.n_near_ties = (uint32_t)ties;
-  CHK_ST(chk, &out[i], o);
+  if (form_greeks<false>(CHK_LD(chk, &g[i]), res, o CHK_ARG(chk))) CHK_ST(chk, &out[i], o);
 }
 
 cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s CHK_PARAM) {

@@ -51,12 +51,18 @@ void count_device_alloc() { g_device_allocs.fetch_add(1, std::memory_order_relax
 struct Ticket;
 
 // A serving slot: one stream and, while busy, one plan pricing a batch of
-// admitted tickets.
+// admitted tickets.  A request whose revaluations have all finished is
+// handed over ahead of the rest of its batch: the backward pass writes its
+// results to the slot's host-mapped array and raises its flag.
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  std::vector<Ticket*> batch;
+  std::vector<Ticket*> batch;  // null once a ticket finished ahead of its batch
+  std::vector<uint32_t> nk;    // strikes of each batch entry
   lsmc_plan* plan = nullptr;
+  DevResult* map_out = nullptr;  // host-mapped: results of the batch's strikes
+  uint32_t* map_flag = nullptr;  // host-mapped: per request, set once its results are in
+  size_t cap_out = 0, cap_req = 0;
 };
 
 }  // namespace
@@ -252,6 +258,7 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   uint32_t zero = 0;
   const uint32_t* dA = (const uint32_t*)(L.active.empty() ? put(&zero, 4) : put(L.active.data(), sizeof(uint32_t) * L.active.size()));
   p->d_greeks = (GreekOut*)put(L.greeks.data(), sizeof(GreekOut) * L.greeks.size());
+  const uint32_t* dQ = (const uint32_t*)put(L.req_info.data(), sizeof(uint32_t) * L.req_info.size());
   off = L.bytes_tables;
   p->d_state = take(L.bytes_state);
   p->state_bytes = L.bytes_state;
@@ -300,6 +307,11 @@ int plan_bind_and_upload(lsmc_plan* p, void* ext_S, void* ext_V, double* beta_hi
   p->ba.active = dA;
   p->ba.ctl = p->d_ctl;
   p->ba.total_jobs = L.total_jobs;
+  p->ba.req_count = (uint32_t*)(p->d_ctl + 1);
+  p->ba.req_info = dQ;
+  p->ba.greeks = p->d_greeks;
+  p->ba.out_host = nullptr;  // per-request completion: set by the serving scheduler
+  p->ba.flag_host = nullptr;
   // bound of each device-side wait: the context's limit (20 s unless set)
   const double limit_s = p->ctx ? p->ctx->wait_limit_s : 20.0;
   p->ba.timeout_ns = (unsigned long long)(limit_s * 1e9);
@@ -616,15 +628,68 @@ void finish_ticket(lsmc_ctx* ctx, Ticket* t, int status) {
 constexpr size_t kMaxBatch = 64;  // default and upper limit of lsmc_config.max_batch
 constexpr uint32_t kMaxServeSub = 32;
 
+// Arms per-request completion for the plan of an idle slot: host-mapped room
+// for the plan's results and its requests' flags (grown when too small), the
+// flags cleared, the backward pass pointed at them.  Out-of-sample plans
+// price after the backward pass and finish with their batch.
+int arm_early_results(Slot& sl, lsmc_plan* p, size_t n_req) {
+  if (p->L.opt.oos) return LSMC_OK;
+  const size_t n_out = p->L.greeks.size();
+  if (n_out > sl.cap_out) {
+    if (sl.map_out) cudaFreeHost(sl.map_out);
+    sl.map_out = nullptr;
+    sl.cap_out = 0;
+    const size_t cap = std::max<size_t>(n_out, 4 * kMaxBatch);
+    LSMC_CUDA(cudaHostAlloc((void**)&sl.map_out, cap * sizeof(DevResult), cudaHostAllocMapped));
+    sl.cap_out = cap;
+  }
+  if (n_req > sl.cap_req) {
+    if (sl.map_flag) cudaFreeHost(sl.map_flag);
+    sl.map_flag = nullptr;
+    sl.cap_req = 0;
+    const size_t cap = std::max<size_t>(n_req, kMaxBatch);
+    LSMC_CUDA(cudaHostAlloc((void**)&sl.map_flag, cap * sizeof(uint32_t), cudaHostAllocMapped));
+    sl.cap_req = cap;
+  }
+  std::memset(sl.map_flag, 0, n_req * sizeof(uint32_t));
+  void* d_out = nullptr;
+  void* d_flag = nullptr;
+  LSMC_CUDA(cudaHostGetDevicePointer(&d_out, sl.map_out, 0));
+  LSMC_CUDA(cudaHostGetDevicePointer(&d_flag, sl.map_flag, 0));
+  p->ba.out_host = (DevResult*)d_out;
+  p->ba.flag_host = (uint32_t*)d_flag;
+#ifdef LSMC_CHECKED
+  add_range(p->ba.chk, d_out, n_out * sizeof(DevResult));
+  add_range(p->ba.chk, d_flag, n_req * sizeof(uint32_t));
+#endif
+  return LSMC_OK;
+}
+
 void scheduler_loop(lsmc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   std::unique_lock<std::mutex> lk(ctx->mu);
   while (!ctx->stop) {
     bool progress = false;
-    // completions: a batch finishes together
     for (size_t s = 0; s < ctx->slots.size(); ++s) {
       Slot& sl = ctx->slots[s];
       if (sl.batch.empty()) continue;
+      // requests whose results the device has handed over already
+      if (sl.plan && sl.plan->ba.flag_host) {
+        size_t off = 0;
+        for (size_t i = 0; i < sl.batch.size(); ++i) {
+          Ticket* t = sl.batch[i];
+          if (t && ((volatile uint32_t*)sl.map_flag)[i] != 0u) {
+            std::atomic_thread_fence(std::memory_order_acquire);
+            t->results.resize(sl.nk[i]);
+            std::memcpy(t->results.data(), sl.map_out + off, sizeof(lsmc_result) * sl.nk[i]);
+            finish_ticket(ctx, t, LSMC_OK);
+            sl.batch[i] = nullptr;
+            progress = true;
+          }
+          off += sl.nk[i];
+        }
+      }
+      // the rest of a batch finishes with its launch
       const cudaError_t q = cudaEventQuery(sl.done);
       if (q == cudaErrorNotReady) continue;
       int rc = q == cudaSuccess ? LSMC_OK : LSMC_ECUDA;
@@ -634,16 +699,20 @@ void scheduler_loop(lsmc_ctx* ctx) {
         rc = plan_collect(sl.plan, all.data());
       }
       size_t off = 0;
-      for (Ticket* t : sl.batch) {
-        const size_t k = t->req.n_strikes;
-        if (rc == LSMC_OK && off + k <= all.size())
-          t->results.assign(all.begin() + off, all.begin() + off + k);
+      for (size_t i = 0; i < sl.batch.size(); ++i) {
+        Ticket* t = sl.batch[i];
+        const size_t k = sl.nk[i];
+        if (t) {
+          if (rc == LSMC_OK && off + k <= all.size())
+            t->results.assign(all.begin() + off, all.begin() + off + k);
+          finish_ticket(ctx, t, rc);
+        }
         off += k;
-        finish_ticket(ctx, t, rc);
       }
       plan_free(sl.plan);
       sl.plan = nullptr;
       sl.batch.clear();
+      sl.nk.clear();
       progress = true;
     }
     // admissions, first come first served: the oldest pending request and
@@ -699,6 +768,11 @@ void scheduler_loop(lsmc_ctx* ctx) {
         if (rc != LSMC_ENOMEM || take == 1) break;
         take /= 2;  // fragmentation: a smaller batch
       }
+      // without host-mapped room the batch's requests finish together
+      if (rc == LSMC_OK && arm_early_results(sl, p, take) != LSMC_OK) {
+        p->ba.out_host = nullptr;
+        p->ba.flag_host = nullptr;
+      }
       if (rc == LSMC_OK) rc = plan_launch(p, false);
       if (rc == LSMC_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = LSMC_ECUDA;
       lk.lock();
@@ -720,6 +794,8 @@ void scheduler_loop(lsmc_ctx* ctx) {
       } else {
         sl.plan = p;
         sl.batch = batch;
+        sl.nk.clear();
+        for (Ticket* t : batch) sl.nk.push_back(t->req.n_strikes);
       }
       progress = true;
     }
@@ -867,6 +943,8 @@ void lsmc_destroy(lsmc_ctx* ctx) {
   for (auto& s : ctx->slots) {
     if (s.done) cudaEventDestroy(s.done);
     if (s.stream) cudaStreamDestroy(s.stream);
+    if (s.map_out) cudaFreeHost(s.map_out);
+    if (s.map_flag) cudaFreeHost(s.map_flag);
   }
   if (ctx->own_stream) {
     cudaStreamSynchronize(ctx->own_stream);

@@ -130,6 +130,25 @@ struct MultiArgs {        // passed by value (about 4 KB of kernel parameters)
 #endif
 };
 
+// ---- Greeks ---------------------------------------------------------------
+// device mirror of lsmc_result (same layout; checked in capi.cpp)
+struct DevResult {
+  double price, price_se, delta, gamma, vega, rho, theta, european_price;
+  uint32_t n_singular_solves, n_revaluations;
+  int32_t status;
+  uint32_t n_near_ties;
+};
+
+struct GreekOut {
+  int32_t res[11];     // result slot per scenario kind (-1 absent)
+  uint32_t mask;
+  double S0, v0, hS, hG, hV, dR, dT;
+};
+
+// scenario kinds (layout order)
+enum : int32_t { kScBase = 0, kScSUp, kScSDn, kScSgUp, kScSgDn, kScVUp, kScVDn,
+                 kScRUp, kScRDn, kScTDn, kScTUp, kScCount };
+
 // ---- backward -------------------------------------------------------------
 struct BwdInstance {
   const void* E;      // group rows 1..N (exp(x) scaled by the group's out_scale)
@@ -149,6 +168,8 @@ struct BwdInstance {
   int32_t type, style, basis;
   uint32_t out_index; // result slot
   uint32_t sub;       // sub-tiles of kBlock * PPT paths per job (a tile)
+  uint32_t req;       // the instance's request (contract) in the launch
+  uint32_t pad_;
   double* beta_z;     // out of sample: N x 8, date n: 6 coefficients (cash flows
                       // discounted to t_0), then 1 if the regression was solved
   double* oos_sum;    // out of sample: per pricing tile of kOosTile paths: sum Z,
@@ -196,6 +217,14 @@ struct BwdArgs {
   uint32_t n_rounds, n_inst;
   uint32_t row0;             // date of E/V row index 0 of the instances' rows
   int32_t store_fmt;         // element type of the E/V rows (kStore*)
+  // Per-request completion (serving): the last instance of a request to
+  // finish forms the request's price and Greeks and hands them to the host
+  // at once, ahead of the rest of the launch; flag_host == nullptr: off.
+  uint32_t* req_count;       // per request: instances finished (zeroed with the state)
+  const uint32_t* req_info;  // per request: instances, first GreekOut, GreekOuts
+  const GreekOut* greeks;
+  DevResult* out_host;       // host-mapped: a DevResult per GreekOut
+  uint32_t* flag_host;       // host-mapped: per request, 1 once its results are there
 #ifdef LSMC_CHECKED
   CheckRanges chk;
 #endif
@@ -225,24 +254,5 @@ struct DualArgs {
   CheckRanges chk;
 #endif
 };
-
-// ---- Greeks ---------------------------------------------------------------
-// device mirror of lsmc_result (same layout; checked in capi.cpp)
-struct DevResult {
-  double price, price_se, delta, gamma, vega, rho, theta, european_price;
-  uint32_t n_singular_solves, n_revaluations;
-  int32_t status;
-  uint32_t n_near_ties;
-};
-
-struct GreekOut {
-  int32_t res[11];     // result slot per scenario kind (-1 absent)
-  uint32_t mask;
-  double S0, v0, hS, hG, hV, dR, dT;
-};
-
-// scenario kinds (layout order)
-enum : int32_t { kScBase = 0, kScSUp, kScSDn, kScSgUp, kScSgDn, kScVUp, kScVDn,
-                 kScRUp, kScRDn, kScTDn, kScTUp, kScCount };
 
 }  // namespace lsmc

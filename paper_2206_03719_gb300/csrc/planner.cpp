@@ -326,11 +326,16 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         I.style = q.style;
         I.basis = opt.basis;
         I.out_index = L->n_results++;
+        I.req = (uint32_t)ci;
         gos[k].res[sc[s].kind] = (int32_t)I.out_index;
         inst.push_back(I);
         offs.push_back(o);
       }
     }
+    // per request: its instances, first GreekOut and GreekOuts
+    L->req_info.push_back((uint32_t)(sc.size() * q.n_strikes));
+    L->req_info.push_back((uint32_t)L->greeks.size());
+    L->req_info.push_back(q.n_strikes);
     for (auto& g : gos) L->greeks.push_back(g);
   }
   // jobs: round-major over instances sorted by generations (stable)
@@ -370,8 +375,11 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
                     round_up(sizeof(unsigned long long) * L->round_off.size(), 256) +
                     round_up(sizeof(uint32_t) * L->cum_tiles.size(), 256) +
                     round_up(sizeof(uint32_t) * std::max<size_t>(1, L->active.size()), 256) +
-                    round_up(sizeof(GreekOut) * L->greeks.size(), 256);
-  L->bytes_state = round_up(sizeof(BwdState) * n_inst + sizeof(Control), 256);
+                    round_up(sizeof(GreekOut) * L->greeks.size(), 256) +
+                    round_up(sizeof(uint32_t) * L->req_info.size(), 256);
+  // state: the instances' states, the control word, the requests' counters
+  L->bytes_state = round_up(sizeof(BwdState) * n_inst + sizeof(Control) +
+                            sizeof(uint32_t) * n, 256);
   L->bytes_results = round_up(sizeof(BwdResult) * L->n_results, 256);
   L->bytes_out = round_up(sizeof(DevResult) * L->greeks.size(), 256);
   L->total_bytes = L->bytes_tables + L->bytes_state + L->bytes_results + L->bytes_out +

@@ -84,6 +84,7 @@ struct PlanLayout {
   std::vector<unsigned long long> round_off;
   std::vector<uint32_t> cum_tiles, active;
   std::vector<GreekOut> greeks;
+  std::vector<uint32_t> req_info;         // per request: instances, first GreekOut, GreekOuts
   // region offsets (bytes) of each group's E and V rows (V: SIZE_MAX if not
   // stored) and of each sorted instance's Y, partials and scale table
   std::vector<size_t> group_E_off, group_V_off;

@@ -1,10 +1,11 @@
 """The checked build (LSMC_CHECKED): every global-memory access of the
-forward, backward, out-of-sample, dual-bound, Greeks and path-reduction
-kernels is tested against the byte ranges its launch owns (the plan's
-allocation, a stage call's arrays); an access outside them would be skipped
-and recorded, never performed.  On small cases of every kernel family the
-checked build must record nothing and give the ordinary build's results bit
-for bit (the checks add branches, not arithmetic).
+forward, backward (with its per-request hand-over to host-mapped memory),
+out-of-sample, dual-bound, Greeks and path-reduction kernels is tested
+against the byte ranges its launch owns (the plan's allocation, a stage
+call's arrays, the serving slot's mapped arrays); an access outside them
+would be skipped and recorded, never performed.  On small cases of every
+kernel family the checked build must record nothing and give the ordinary
+build's results bit for bit (the checks add branches, not arithmetic).
 
 compute-sanitizer is closed on this machine; this build is the library's own
 substitute.  One build of the library per process, so the checked one runs
@@ -59,6 +60,14 @@ with api.Context(workspace_bytes=1 << 30) as ctx:
     report("bounds_fp64")
     out["bounds_df"] = ctx.price_bounds(base.replace(greeks=()), 33, 40, precision="df")
     report("bounds_df")
+# served: results handed over per request through host-mapped memory
+with api.Context(workspace_bytes=1 << 30, max_inflight=1) as srv:
+    ws = [base.replace(n_steps=9), base.replace(n_steps=17, strikes=[95.0]),
+          base.replace(n_steps=5, precision="df")]
+    ts = [srv.submit(w) for w in ws]
+    out["served"] = [[r.as_dict() for r in srv.wait(t, len(w.strikes), 120.0)[1]]
+                     for t, w in zip(ts, ws)]
+report("served")
 # stage calls on caller arrays
 P, N = 2500, 9
 m = L.lsmc_heston(**workloads.HESTON_BASE)

@@ -5,7 +5,7 @@ import time
 
 import pytest
 
-from gpu_common import torch_cuda
+from gpu_common import same_results, torch_cuda
 from paper_2206_03719_gb300 import api, workloads
 from paper_2206_03719_gb300 import lsmc as L
 
@@ -78,3 +78,33 @@ def test_poll_pending_then_done_and_unknown_ticket(setup):
         with pytest.raises(L.LsmcError) as e:
             srv.poll(t, 1)
         assert e.value.status == L.LSMC_ENOTFOUND
+
+
+def test_request_finishes_ahead_of_its_batch(setup):
+    # one slot: while a blocker runs, a short request (8 dates) and a long one
+    # (400 dates) queue and are then admitted together; the backward pass
+    # hands the short one over when its own regressions are done, well before
+    # the batch ends.  Under one fixed backward shape its results equal, bit
+    # for bit, those of the synchronous call (the Greeks kernel's path).
+    base = workloads.SMALL_FP64.replace(precision="df", greeks=workloads.ALL_GREEKS,
+                                        basis="sv2", rel_dS_gamma=0.02)
+    blocker = base.replace(n_paths=65536, n_steps=200)
+    short = base.replace(n_paths=8192, n_steps=8, strikes=[95.0, 105.0])
+    long_ = base.replace(n_paths=65536, n_steps=400)
+    with api.Context(workspace_bytes=4 << 30, max_inflight=1) as srv:
+        srv.set_backward_shape(2, 4)
+        ts = [srv.submit(w) for w in (blocker, short, long_)]
+        got = []
+        for t, w in zip(ts, (blocker, short, long_)):
+            st, res = srv.wait(t, len(w.strikes), 120.0)
+            assert st == L.LSMC_OK
+            got.append([r.as_dict() for r in res])
+        times = [L.lsmc_ticket_times(srv.ctx, t) for t in ts]
+    (_, a_b, d_b), (_, a_s, d_s), (_, a_l, d_l) = times
+    assert a_s == a_l > a_b          # admitted together, after the blocker
+    assert d_s < d_l                 # the short request left its batch early
+    print("short done %.1f ms before the long one" % (1e3 * (d_l - d_s)))
+    with api.Context(workspace_bytes=4 << 30) as sync:
+        sync.set_backward_shape(2, 4)
+        for w, g in zip((short, long_), got[1:]):
+            assert same_results(g, sync.price(w)), w.name
