@@ -674,12 +674,12 @@ def extra_jobs():
             ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2,
                                                           saturation=400),
                                     "mixed": measure_serving(*a, precision="mixed",
-                                                             max_inflight=4, saturation=800)}),
+                                                             max_inflight=2, saturation=800)}),
             # not in the default run: the long window (10 s warm-up, 60 s
             # measured) and the slot counts side by side
             ("serving_long", lambda *a: {
                 "df_%d" % k: measure_serving(*a, precision="df", max_inflight=k, warm_s=10.0,
-                                             window_s=60.0) for k in (2, 4, 8)}))
+                                             window_s=60.0) for k in (2, 3)}))
     return jobs
 
 
