@@ -582,7 +582,7 @@ def measure_stac(api, L, torch, reps=3):
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
-                    precision="mixed", max_inflight=16, saturation=0, max_batch=0):
+                    precision="mixed", max_inflight=16, saturation=0, max_batch=0, share=1.0):
     """Poisson stream of book-distributed requests with continuous batching
     (up to `max_inflight` launches on the device at once, each pricing the
     requests admitted together, admitted by workspace bytes), and the first
@@ -592,6 +592,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
     reqs = workloads.book(n_contracts=len(arrivals), seed=99, precision=precision)
     with api.Context(workspace_bytes=48 << 30, max_inflight=max_inflight,
                      precision=precision, max_batch=max_batch) as srv:
+        srv.set_serving_share(share)
         t0 = time.perf_counter()
         tickets = []
         for t_arr, w in zip(arrivals, reqs):
@@ -619,7 +620,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
               "precision": precision, "max_inflight": max_inflight,
-              "max_batch": max_batch or 64,
+              "max_batch": max_batch or 64, "backward_share": share,
               "error": subset_errors(served_results, GOLDEN_SERVING)}
     if saturation:
         # capacity: a burst far above what the device can serve, all submitted
@@ -628,6 +629,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
         burst = workloads.book(n_contracts=saturation, seed=1234, precision=precision)
         with api.Context(workspace_bytes=48 << 30, max_inflight=max_inflight,
                          precision=precision) as srv:
+            srv.set_serving_share(share)
             srv.price(burst[0])  # module load
             t0 = time.perf_counter()
             ts = [srv.submit(w) for w in burst]

@@ -77,6 +77,7 @@ struct lsmc_ctx {
   size_t hbm_budget = 0;
   uint32_t max_inflight = 8, queue_capacity = 4096;
   uint32_t max_batch = 64;    // requests admitted together (lsmc_config.max_batch)
+  double serve_share = 1.0;   // share of the resident backward CTAs a batch takes
   int num_sms = 0;
   std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
   std::mutex occ_mu;          // guards occ (plans are built on several threads)
@@ -753,6 +754,7 @@ void scheduler_loop(lsmc_ctx* ctx) {
       sl.batch = batch;
       sl.plan = nullptr;
       const uint32_t ppt = t0->ppt;
+      const double share = ctx->serve_share;
       lk.unlock();
       lsmc_plan* p = nullptr;
       int rc = LSMC_ENOMEM;
@@ -767,6 +769,13 @@ void scheduler_loop(lsmc_ctx* ctx) {
         rc = plan_create_on(ctx, reqs.data(), reqs.size(), sl.stream, true, &p, &subs, ppt);
         if (rc != LSMC_ENOMEM || take == 1) break;
         take /= 2;  // fragmentation: a smaller batch
+      }
+      // the batch's persistent backward grid: its share of the device
+      if (rc == LSMC_OK && share < 1.0) {
+        const int occ = occupancy(ctx, p->L.opt.precision, p->L.opt.basis, plan_ppt(p->L.opt),
+                                  p->L.opt.store);
+        const int part = (int)std::ceil(share * occ * sm_count(ctx));
+        p->bwd_grid = std::max(1, std::min(p->bwd_grid, part));
       }
       // without host-mapped room the batch's requests finish together
       if (rc == LSMC_OK && arm_early_results(sl, p, take) != LSMC_OK) {
@@ -988,6 +997,13 @@ int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt) {
   std::lock_guard<std::mutex> g(ctx->mu);
   ctx->sub_override = sub;
   ctx->ppt_override = ppt;
+  return LSMC_OK;
+}
+
+int lsmc_set_serving_share(lsmc_ctx* ctx, double share) {
+  if (!ctx || !(share > 0.0 && share <= 1.0)) return LSMC_EINVAL;
+  std::lock_guard<std::mutex> g(ctx->mu);
+  ctx->serve_share = share;
   return LSMC_OK;
 }
 

@@ -38,8 +38,8 @@ EXPORTS = [
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
     "lsmc_backward_noalloc", "lsmc_device_allocations", "lsmc_set_wait_limit",
-    "lsmc_set_backward_shape", "lsmc_plan_fetch_scenarios", "lsmc_measure_peaks",
-    "lsmc_check_report", "lsmc_exp",
+    "lsmc_set_backward_shape", "lsmc_set_serving_share", "lsmc_plan_fetch_scenarios",
+    "lsmc_measure_peaks", "lsmc_check_report", "lsmc_exp",
 ]
 # scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
 LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
@@ -190,6 +190,7 @@ def load(build_if_missing: bool = False, path: str = None):
             "lsmc_device_allocations": ([P(u64)], ctypes.c_int),
             "lsmc_set_wait_limit": ([vp, dbl], ctypes.c_int),
             "lsmc_set_backward_shape": ([vp, u32, u32], ctypes.c_int),
+            "lsmc_set_serving_share": ([vp, ctypes.c_double], ctypes.c_int),
             "lsmc_plan_fetch_scenarios": ([vp, P(dbl), P(u32), sz], ctypes.c_int),
             "lsmc_measure_peaks": ([i32, P(lsmc_peaks)], ctypes.c_int),
             "lsmc_check_report": ([P(u32), P(u32), i32], ctypes.c_int),
@@ -285,6 +286,10 @@ def lsmc_set_wait_limit(ctx, seconds):
 
 def lsmc_set_backward_shape(ctx, sub, ppt):
     return check(load().lsmc_set_backward_shape(ctx, sub, ppt), "lsmc_set_backward_shape")
+
+
+def lsmc_set_serving_share(ctx, share):
+    return check(load().lsmc_set_serving_share(ctx, share), "lsmc_set_serving_share")
 
 
 def lsmc_set_workspace(ctx, ptr, nbytes):

@@ -133,6 +133,7 @@ def test_option_and_diagnostic_entry_points_on_host(lib):
     # plan; the allocation count needs no device and starts at zero here
     assert lib.lsmc_set_wait_limit(None, 1.0) == L.LSMC_EINVAL
     assert lib.lsmc_set_backward_shape(None, 4, 4) == L.LSMC_EINVAL
+    assert lib.lsmc_set_serving_share(None, 0.5) == L.LSMC_EINVAL
     prices = (ctypes.c_double * L.LSMC_SC_COUNT)()
     assert lib.lsmc_plan_fetch_scenarios(None, prices, None, 1) == L.LSMC_EINVAL
     assert lib.lsmc_device_allocations(None) == L.LSMC_EINVAL

@@ -50,6 +50,23 @@ def test_results_same_alone_and_in_the_mix(setup):
                 assert abs(a["price"] - b["price"]) <= 1e-4 * abs(b["price"])
 
 
+def test_results_same_with_a_share_of_the_device(setup):
+    # four slots, each batch's persistent backward grid a quarter of the
+    # device: batches run side by side and the results do not change
+    mix = _mix()
+    with api.Context(workspace_bytes=4 << 30, max_inflight=4) as solo:
+        alone = [_serve(solo, [w])[0] for w in mix]
+    with api.Context(workspace_bytes=4 << 30, max_inflight=4) as srv:
+        srv.set_serving_share(0.25)
+        got = _serve(srv, mix)
+    assert got == alone
+    with api.Context(workspace_bytes=1 << 30) as ctx:
+        for bad in (0.0, -0.5, 1.5):
+            with pytest.raises(L.LsmcError) as e:
+                ctx.set_serving_share(bad)
+            assert e.value.status == L.LSMC_EINVAL
+
+
 def test_admission_by_memory_budget(setup):
     mix = _mix()[:6]
     need = max(L.lsmc_request_footprint(None, api.Request(w).c) for w in mix)
