@@ -582,7 +582,7 @@ def measure_stac(api, L, torch, reps=3):
 
 
 def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_n=32,
-                    precision="mixed", max_inflight=16, saturation=0, max_batch=0, share=1.0):
+                    precision="mixed", max_inflight=16, saturation=0, max_batch=0, share=0.0):
     """Poisson stream of book-distributed requests with continuous batching
     (up to `max_inflight` launches on the device at once, each pricing the
     requests admitted together, admitted by workspace bytes), and the first
@@ -620,7 +620,7 @@ def measure_serving(api, L, torch, rate=200.0, window_s=8.0, warm_s=2.0, serial_
               "p50_ms": pct(0.50), "p99_ms": pct(0.99), "mean_ms": 1e3 * sum(lat) / max(1, len(lat)),
               "greeks_per_s": sum(w.n_greeks for _, w, _ in tickets) / (last_done - first_done),
               "precision": precision, "max_inflight": max_inflight,
-              "max_batch": max_batch or 64, "backward_share": share,
+              "max_batch": max_batch or 64, "backward_share": share or 1.0 / max_inflight,
               "error": subset_errors(served_results, GOLDEN_SERVING)}
     if saturation:
         # capacity: a burst far above what the device can serve, all submitted
@@ -673,15 +673,15 @@ def extra_jobs():
             ("regenerate_and_out_of_sample", lambda *a: measure_variants(*a)),
             ("store16_precision_study", lambda *a: measure_store16(*a)),
             ("dual_upper_bound", lambda *a: measure_dual(*a)),
-            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=2,
+            ("serving", lambda *a: {"df": measure_serving(*a, precision="df", max_inflight=8,
                                                           saturation=400),
                                     "mixed": measure_serving(*a, precision="mixed",
-                                                             max_inflight=2, saturation=800)}),
+                                                             max_inflight=4, saturation=800)}),
             # not in the default run: the long window (10 s warm-up, 60 s
             # measured) and the slot counts side by side
             ("serving_long", lambda *a: {
                 "df_%d" % k: measure_serving(*a, precision="df", max_inflight=k, warm_s=10.0,
-                                             window_s=60.0) for k in (2, 3)}))
+                                             window_s=60.0) for k in (4, 8)}))
     return jobs
 
 

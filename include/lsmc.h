@@ -235,11 +235,12 @@ int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds);
  * autotuner's result when lsmc_autotune has tuned that kind of plan).
  * LSMC_EINVAL for sub > 64 or ppt not in {0, 2, 4, 8}. */
 int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt);
-/* Share (0, 1] of the device's resident backward CTAs that one serving batch's
- * persistent backward grid takes (default 1: the whole device, so batches
- * on other slots wait for its CTAs to finish).  Applies to batches admitted
- * afterwards.  A serving-policy option (the paper has no serving loop).
- * LSMC_EINVAL outside (0, 1]. */
+/* Share of the device's resident backward CTAs that one serving batch's
+ * persistent backward grid takes, so that batches on different slots run
+ * side by side instead of each waiting for the CTAs of the one before.
+ * share in (0, 1]; 0 (the default) = 1 / config.max_inflight.  Applies to
+ * batches admitted afterwards.  A serving-policy option (the paper has no
+ * serving loop).  LSMC_EINVAL outside [0, 1]. */
 int lsmc_set_serving_share(lsmc_ctx* ctx, double share);
 /* Device memory the context sub-allocates from instead of cudaMalloc
  * (e.g. a PyTorch tensor).  Must be set before any plan exists and stay

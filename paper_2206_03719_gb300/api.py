@@ -115,7 +115,7 @@ class Context:
     def set_backward_shape(self, sub: int = 0, ppt: int = 0):
         L.lsmc_set_backward_shape(self.ctx, sub, ppt)
 
-    def set_serving_share(self, share: float = 1.0):
+    def set_serving_share(self, share: float = 0.0):
         L.lsmc_set_serving_share(self.ctx, share)
 
     # ---- synchronous ------------------------------------------------------

@@ -77,7 +77,7 @@ struct lsmc_ctx {
   size_t hbm_budget = 0;
   uint32_t max_inflight = 8, queue_capacity = 4096;
   uint32_t max_batch = 64;    // requests admitted together (lsmc_config.max_batch)
-  double serve_share = 1.0;   // share of the resident backward CTAs a batch takes
+  double serve_share = 0.0;   // share of the resident backward CTAs a batch takes (0: 1/slots)
   int num_sms = 0;
   std::map<int, int> occ;     // resident backward CTAs per SM by kernel variant
   std::mutex occ_mu;          // guards occ (plans are built on several threads)
@@ -754,7 +754,8 @@ void scheduler_loop(lsmc_ctx* ctx) {
       sl.batch = batch;
       sl.plan = nullptr;
       const uint32_t ppt = t0->ppt;
-      const double share = ctx->serve_share;
+      const double share =
+          ctx->serve_share > 0.0 ? ctx->serve_share : 1.0 / (double)ctx->slots.size();
       lk.unlock();
       lsmc_plan* p = nullptr;
       int rc = LSMC_ENOMEM;
@@ -1001,7 +1002,7 @@ int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt) {
 }
 
 int lsmc_set_serving_share(lsmc_ctx* ctx, double share) {
-  if (!ctx || !(share > 0.0 && share <= 1.0)) return LSMC_EINVAL;
+  if (!ctx || !(share >= 0.0 && share <= 1.0)) return LSMC_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   ctx->serve_share = share;
   return LSMC_OK;

@@ -61,7 +61,8 @@ def test_results_same_with_a_share_of_the_device(setup):
         got = _serve(srv, mix)
     assert got == alone
     with api.Context(workspace_bytes=1 << 30) as ctx:
-        for bad in (0.0, -0.5, 1.5):
+        ctx.set_serving_share(0.0)  # the default: a share of 1 / slots
+        for bad in (-0.5, 1.5):
             with pytest.raises(L.LsmcError) as e:
                 ctx.set_serving_share(bad)
             assert e.value.status == L.LSMC_EINVAL
