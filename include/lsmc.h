@@ -413,6 +413,17 @@ int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
  * stays a normal float); single precision by CUDA's __expf.  Asynchronous on cuda_stream;
  * LSMC_EINVAL for NULL arrays (n > 0) or an unknown precision. */
 int lsmc_exp(const void* d_x, void* d_y, size_t n, int32_t precision, void* cuda_stream);
+/* The Gaussian transform of the random inputs (Sec. 2.2.1: the normal draws
+ * of the Heston step from uniforms) on n uniforms: d_u, d_z (device) double
+ * (LSMC_FP64) or float (LSMC_MIXED); z = Phi^-1(u) with 1 - u formed in the
+ * precision, exact for u on its uniform grid (the points (m + 1/2) 2^-52,
+ * (m + 1/2) 2^-23 that lsmc_draws uses).  Double: w = -log(4 u (1 - u)) by
+ * a table-driven logarithm and polynomials in w or sqrt(w) (Giles'
+ * transformation, own fit), within 6e-16 of Phi^-1(u), max(1, |z|)
+ * relative; float: within 1e-6.  Asynchronous on cuda_stream; LSMC_EINVAL for
+ * NULL arrays (n > 0) or an unknown precision, LSMC_ENOTIMPL for LSMC_DF
+ * (its quantile reads the random words: lsmc_draws). */
+int lsmc_quantile(const void* d_u, void* d_z, size_t n, int32_t precision, void* cuda_stream);
 
 /* Heston paths (Sec. 2.2.1: variance, log price, exponential):
  * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double, float

@@ -1430,6 +1430,13 @@ int lsmc_exp(const void* d_x, void* d_y, size_t n, int32_t precision, void* s) {
   return cuda_status(launch_exp(d_x, d_y, n, precision, (cudaStream_t)s));
 }
 
+int lsmc_quantile(const void* d_u, void* d_z, size_t n, int32_t precision, void* s) {
+  if ((!d_u || !d_z) && n) return LSMC_EINVAL;
+  if (precision == LSMC_DF) return LSMC_ENOTIMPL;
+  if (precision != LSMC_FP64 && precision != LSMC_MIXED) return LSMC_EINVAL;
+  return cuda_status(launch_quantile(d_u, d_z, n, precision, (cudaStream_t)s));
+}
+
 static int stage_plan(const lsmc_heston* m, double T, int32_t scheme, int32_t precision,
                       uint32_t P, uint32_t N, int32_t basis, const lsmc_contract* c,
                       uint64_t seed, uint32_t stream_id, cudaStream_t s, lsmc_plan** out) {

@@ -7,6 +7,7 @@
 
 #include "dfloat.cuh"
 #include "quantile_f32.h"
+#include "quantile_f64.h"
 
 namespace lsmc {
 
@@ -92,6 +93,50 @@ __device__ __forceinline__ float norm_quantile_f32(float u, float omu) {
   return __fmul_rn(x, r);
 }
 
+// log(a) in double for a normal, finite, positive a (Tang's table-driven
+// reduction, tables in quantile_f64.h): a = 2^e m, m in [1, 2),
+// j = round(128 (m - 1)), t = m c_j - 1 by one fused multiply-add
+// (|t| < 0.004), log a = e ln2 - log c_j + log1p(t), log1p by its Taylor
+// series to t^7.  About 15 FP64 operations; other arguments (zero,
+// subnormal, infinite, NaN, negative) go to CUDA's log.  Near a = 1 the
+// ln2 terms cancel exactly and the result keeps full relative accuracy.
+__device__ __forceinline__ double log_f64(double a) {
+  const long long bits = __double_as_longlong(a);
+  if (bits < 0x0010000000000000ll || bits >= 0x7ff0000000000000ll) return log(a);
+  const double e = (double)((int)(bits >> 52) - 1023);
+  const double m = __longlong_as_double((bits & 0x000fffffffffffffll) | 0x3ff0000000000000ll);
+  const int j = ((int)((bits >> 44) & 0xff) + 1) >> 1;  // nearest integer to 128 (m - 1)
+  const double t = fma(m, __ldg(&kLogRecip[j]), -1.0);
+  // log1p(t) = t + t^2 q(t), q = -1/2 + t/3 - t^2/4 + t^3/5 - t^4/6 + t^5/7
+  double q = fma(t, 1.0 / 7.0, -1.0 / 6.0);
+  q = fma(q, t, 1.0 / 5.0);
+  q = fma(q, t, -1.0 / 4.0);
+  q = fma(q, t, 1.0 / 3.0);
+  q = fma(q, t, -0.5);
+  const double lp = fma(t * t, q, t);
+  const double hi = fma(e, kLn2Hi, __ldg(&kLogNegHi[j]));  // e ln2_hi is exact
+  return hi + fma(e, kLn2Lo, __ldg(&kLogNegLo[j]) + lp);
+}
+
+// Standard normal quantile of a point u of the 52-bit grid (omu = 1 - u,
+// exact) in double: Giles' transformation as in norm_quantile_f32, with
+// w = -log(4 u (1 - u)) by log_f64 and polynomials of degree 23 in w - 3.125
+// for w < 6.25, 18 and 16 in sqrt(w) beyond (the tails, about 0.1% of the
+// draws); coefficients in quantile_f64.h (gen_quantile_f64.py), each
+// polynomial within 2.5e-16 of the exact quotient.
+__device__ __forceinline__ double norm_quantile_f64(double u, double omu) {
+  const double w = -log_f64(4.0 * (u * omu));
+  const double x = u - omu;  // 2u - 1
+  double r;
+  if (w < kQdSplitW) {
+    r = qd_central(w - kQdCentreW);
+  } else {
+    const double s = sqrt(w);
+    r = s < kQdSplitS ? qd_tail1(s - kQdCentreS1) : qd_tail2(s - kQdCentreS2);
+  }
+  return x * r;
+}
+
 // Random inputs of one path step from one Philox block: the uniform U_V,
 // 1 - U_V (exact in both grids), Z_V = Phi^-1(U_V) and Z_X.  The float-pair
 // specialisation is in df_math.cuh and uses the tables t stages in shared
@@ -104,8 +149,9 @@ template <> struct Draw<double> {
                                               double& zX, const DfTables*) {
     u = uniform52(w.x, w.y);
     omu = 1.0 - u;
-    zV = normcdfinv(u);
-    zX = normcdfinv(uniform52(w.z, w.w));
+    zV = norm_quantile_f64(u, omu);
+    const double uX = uniform52(w.z, w.w);
+    zX = norm_quantile_f64(uX, 1.0 - uX);
   }
 };
 template <> struct Draw<float> {

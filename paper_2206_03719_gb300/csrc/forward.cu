@@ -262,7 +262,8 @@ template <typename Real>
 __device__ __forceinline__ Real common_shock(uint4 w, const DfTables* t);
 template <>
 __device__ __forceinline__ double common_shock<double>(uint4 w, const DfTables*) {
-  return normcdfinv(uniform52(w.z, w.w));
+  const double u = uniform52(w.z, w.w);
+  return norm_quantile_f64(u, 1.0 - u);
 }
 template <>
 __device__ __forceinline__ float common_shock<float>(uint4 w, const DfTables*) {
@@ -369,6 +370,28 @@ __global__ void exp_kernel(const Real* __restrict__ x, Real* __restrict__ y, siz
   }
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) y[i] = Fm<Real>::exp_(x[i], tabs);
+}
+
+// The normal quantile of the random inputs on n uniforms (1 - u computed;
+// exact on the precision's uniform grid).
+template <typename Real>
+__global__ void quantile_kernel(const Real* __restrict__ u, Real* __restrict__ z, size_t n) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const Real ui = u[i];
+  if constexpr (std::is_same<Real, double>::value) z[i] = norm_quantile_f64(ui, 1.0 - ui);
+  else z[i] = norm_quantile_f32(ui, 1.0f - ui);
+}
+
+cudaError_t launch_quantile(const void* u, void* z, size_t n, int precision, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t blocks = (n + kBlock - 1) / kBlock;
+  if (blocks > 0x7fffffffu) return cudaErrorInvalidValue;
+  if (precision == kPrecFP64)
+    quantile_kernel<double><<<(unsigned)blocks, kBlock, 0, s>>>((const double*)u, (double*)z, n);
+  else
+    quantile_kernel<float><<<(unsigned)blocks, kBlock, 0, s>>>((const float*)u, (float*)z, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_exp(const void* x, void* y, size_t n, int precision, cudaStream_t s) {

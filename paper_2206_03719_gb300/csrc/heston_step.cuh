@@ -20,7 +20,7 @@ template <typename Real> struct Fm;
 template <> struct Fm<double> {
   __device__ static double div(double a, double b) { return a / b; }
   __device__ static double sqrt_(double a) { return sqrt(a); }
-  __device__ static double log_(double a, const DfTables*) { return log(a); }
+  __device__ static double log_(double a, const DfTables*) { return log_f64(a); }
   __device__ static double exp_(double a, const DfTables*) { return exp_f64(a); }
 };
 template <> struct Fm<float> {

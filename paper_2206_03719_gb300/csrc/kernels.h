@@ -17,6 +17,7 @@ cudaError_t launch_draws(uint64_t seed, uint32_t stream_id, const uint32_t* path
 cudaError_t launch_multi_max(const MultiArgs& a, int precision, int scheme, cudaStream_t s);
 // the forward pass's exponential on n values of the precision
 cudaError_t launch_exp(const void* x, void* y, size_t n, int precision, cudaStream_t s);
+cudaError_t launch_quantile(const void* u, void* z, size_t n, int precision, cudaStream_t s);
 cudaError_t launch_setup(BwdInstance* inst, uint32_t n_inst, cudaStream_t s CHK_PARAM);
 cudaError_t launch_backward(const BwdArgs& a, int precision, int basis, int ppt, int grid,
                             cudaStream_t s);

@@ -39,7 +39,7 @@ EXPORTS = [
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
     "lsmc_backward_noalloc", "lsmc_device_allocations", "lsmc_set_wait_limit",
     "lsmc_set_backward_shape", "lsmc_set_serving_share", "lsmc_plan_fetch_scenarios",
-    "lsmc_measure_peaks", "lsmc_check_report", "lsmc_exp",
+    "lsmc_measure_peaks", "lsmc_check_report", "lsmc_exp", "lsmc_quantile",
 ]
 # scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
 LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
@@ -195,6 +195,7 @@ def load(build_if_missing: bool = False, path: str = None):
             "lsmc_measure_peaks": ([i32, P(lsmc_peaks)], ctypes.c_int),
             "lsmc_check_report": ([P(u32), P(u32), i32], ctypes.c_int),
             "lsmc_exp": ([vp, vp, sz, i32, vp], ctypes.c_int),
+            "lsmc_quantile": ([vp, vp, sz, i32, vp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -432,6 +433,10 @@ def lsmc_draws(seed, stream_id, d_path, d_step, n, precision, d_out, stream=None
 
 def lsmc_exp(d_x, d_y, n, precision, stream=None):
     return check(load().lsmc_exp(d_x, d_y, n, precision, stream), "lsmc_exp")
+
+
+def lsmc_quantile(d_u, d_z, n, precision, stream=None):
+    return check(load().lsmc_quantile(d_u, d_z, n, precision, stream), "lsmc_quantile")
 
 
 def lsmc_paths(model, T, scheme, precision, n_paths, n_steps, seed, stream_id, d_S, d_V,

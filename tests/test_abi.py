@@ -183,3 +183,6 @@ def test_path_groups_follow_the_bumps_on_host(lib):
 def test_exp_stage_entry_rejects_bad_arguments(lib):
     assert lib.lsmc_exp(None, None, 4, 0, None) == L.LSMC_EINVAL
     assert lib.lsmc_exp(None, None, 0, 7, None) == L.LSMC_EINVAL
+    assert lib.lsmc_quantile(None, None, 4, 0, None) == L.LSMC_EINVAL
+    assert lib.lsmc_quantile(None, None, 0, 7, None) == L.LSMC_EINVAL
+    assert lib.lsmc_quantile(None, None, 0, L.LSMC_DF, None) == L.LSMC_ENOTIMPL

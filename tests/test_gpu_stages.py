@@ -66,7 +66,8 @@ def test_draws_fp64_grid_exact_quantiles_close(torch):
     ref = oracle.draws(0xABCDEF0123456789, 5, path, step, oracle.GRID_F64)
     assert np.array_equal(got[:, 0], ref[:, 0])
     err = np.abs(got[:, 1:] - ref[:, 1:])
-    # quantile: CUDA's normcdfinv against the oracle's Newton root of erfc
+    # quantile: the table-driven logarithm and polynomial quantile
+    # (norm_quantile_f64) against the oracle's Newton root of erfc
     assert np.all(err <= 4e-15 * np.maximum(1.0, np.abs(ref[:, 1:])))
 
 
