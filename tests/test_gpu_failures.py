@@ -8,6 +8,8 @@ test faults, traps or hangs the device.
   limit of 20 microseconds must make them give up: the kernels record the
   error and return, the call reports LSMC_ETIMEOUT, and the same context then
   prices the request correctly under the default limit.
+* The same expiry in a serving batch: the ticket reports it and the slots
+  serve the next requests.
 * Device memory refused by the caller's allocator (lsmc_set_allocator): the
   call reports LSMC_ENOMEM, every block handed out is handed back, and the
   context works again once the allocator gives memory.
@@ -44,6 +46,30 @@ def test_device_wait_limit_expires_and_the_context_stays_usable(torch):
         with api.Context() as c:
             c.set_wait_limit(-1.0)
     assert e.value.status == L.LSMC_EINVAL
+
+
+def test_served_request_reports_the_expired_wait_and_the_slot_serves_on(torch):
+    # the same chain of dates through the serving loop: the batch's kernels
+    # give up, the ticket reports LSMC_ETIMEOUT (a request that finished its
+    # own regressions before the expiry keeps its results), and the slots
+    # serve the next requests under the default limit
+    long_ = workloads.SMALL_FP64.replace(n_paths=1000, n_steps=500, greeks=(), strikes=[100.0])
+    with api.Context(workspace_bytes=1 << 30, max_inflight=2) as srv:
+        srv.set_backward_shape(2, 4)
+        srv.set_wait_limit(20e-6)
+        t = srv.submit(long_)
+        with pytest.raises(L.LsmcError) as e:
+            srv.wait(t, 1, 60.0)
+        assert e.value.status == L.LSMC_ETIMEOUT
+        srv.set_wait_limit(20.0)
+        ts = [srv.submit(long_) for _ in range(3)]
+        outs = [srv.wait(t, 1, 120.0) for t in ts]
+        assert all(st == L.LSMC_OK for st, _ in outs)
+        with api.Context(workspace_bytes=256 << 20) as sync:
+            sync.set_backward_shape(2, 4)
+            ref = sync.price(long_)
+        for _, res in outs:  # one backward shape: the same bits
+            assert res[0].as_dict()["price"] == ref[0]["price"]
 
 
 def test_allocator_refusals_report_enomem_and_hand_every_block_back(torch):
