@@ -1,5 +1,7 @@
-// device_common.cuh -- counter-based random inputs, uniform grids and the
-// synchronisation primitives shared by the kernels.
+// device_common.cuh -- counter-based random inputs (Philox4x32-10), uniform
+// grids, the normal quantiles of single and double precision with the
+// double-precision logarithm they use, and the synchronisation primitives
+// shared by the kernels.
 #pragma once
 
 #include <cstdint>
