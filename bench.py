@@ -681,7 +681,14 @@ def extra_jobs():
             # measured) and the slot counts side by side
             ("serving_long", lambda *a: {
                 "df_%d" % k: measure_serving(*a, precision="df", max_inflight=k, warm_s=10.0,
-                                             window_s=60.0) for k in (4, 8)}))
+                                             window_s=60.0) for k in (4, 8)}),
+            # not in the default run: latency against offered load (requests/s)
+            ("serving_curve", lambda *a: dict(
+                [("df_%d" % r, measure_serving(*a, rate=float(r), precision="df", max_inflight=8,
+                                               serial_n=1)) for r in (50, 100, 200, 300)] +
+                [("mixed_%d" % r, measure_serving(*a, rate=float(r), precision="mixed",
+                                                  max_inflight=4, serial_n=1))
+                 for r in (200, 400, 800)])))
     return jobs
 
 
