@@ -492,18 +492,17 @@ backward_kernel(BwdArgs a) {
   // threshold on the stored value), so the compaction buffers hold the
   // stored value and S = s e is formed on the dense lists, where no lane idles
   constexpr bool kProdLate = kCompact;
-  // Job decoding by thread 0: the job number `next` was taken from the
-  // counter one job earlier, so the atomic's latency is hidden.
-  unsigned long long next = 0;
+  // Job taking and decoding by thread 0, when the CTA has arrived with its
+  // previous job: a job is taken only once the CTA can start it.
   auto decode = [&]() {
     JobInfo ji;
-    ji.job = next;
     ji.abort = 0;
     ji.round = ji.inst = ji.tile = 0;
-    if (ld_volatile(&a.ctl->error) != 0 || next >= a.total_jobs) {
+    ji.job = ld_volatile(&a.ctl->error) != 0 ? a.total_jobs
+                                             : atomicAdd(&a.ctl->next_job, 1ull);
+    if (ji.job >= a.total_jobs) {
       ji.abort = 1;
     } else {
-      next = atomicAdd(&a.ctl->next_job, 1ull);
       // round: last r with round_off[r] <= job
       uint32_t lo = 0, hi = a.n_rounds;
       while (hi - lo > 1) {
@@ -528,10 +527,7 @@ backward_kernel(BwdArgs a) {
   };
   // the control word (job counter, error word) must lie in the plan
   if (!CHK_OK(a.chk, a.ctl, sizeof(Control))) return;
-  if (tid == 0) {
-    next = atomicAdd(&a.ctl->next_job, 1ull);
-    decode();
-  }
+  if (tid == 0) decode();
   __syncthreads();
 
   for (;;) {
@@ -639,8 +635,6 @@ backward_kernel(BwdArgs a) {
     }
     __syncthreads();
     if (s_last < 0) return;
-    // every thread has read this job: thread 0 decodes the next one now
-    if (tid == 0) decode();
     const int bok = first ? 0 : s_beta_ok;
     Real b[6];
 #pragma unroll
@@ -1114,6 +1108,7 @@ backward_kernel(BwdArgs a) {
         const uint32_t old = atomicAdd(&st->arrive, 1u);
         s_last = (old + 1 == (r + 1) * I.tiles) ? 1 : 0;
         if (s_last) __threadfence();
+        decode();
       }
     }
     __syncthreads();
