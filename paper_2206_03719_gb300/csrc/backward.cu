@@ -56,6 +56,7 @@ __host__ __device__ constexpr int mono(int a, int b) {
 // right-hand sides R.  Returns false (no exercise on this date) when fewer
 // in-the-money paths than basis functions were seen, or when a Cholesky pivot
 // is not above 1e-13 times the largest diagonal entry.
+template <bool kNoDivide>
 __device__ bool solve_normal_equations(int B, const double* M, const double* R,
                                        double beta[6]) {
   const int pa[6] = {0, 1, 2, 0, 1, 0};
@@ -66,12 +67,25 @@ __device__ bool solve_normal_equations(int B, const double* M, const double* R,
   for (int i = 0; i < B; ++i)
     for (int j = 0; j < B; ++j) A[i][j] = M[mono(pa[i] + pa[j], pb[i] + pb[j])];
   for (int i = 0; i < B; ++i) maxdiag = fmax(maxdiag, A[i][i]);
+  // kNoDivide (the double-precision kernel): the solve is the critical path
+  // of its regression's chain of dates and runs on one thread while the other
+  // CTAs keep the FP64 pipe busy, where each dependent operation waits some
+  // 200 cycles; one reciprocal square root per pivot gives both
+  // L_jj = d / sqrt(d) and 1 / L_jj, and the substitutions multiply by the
+  // reciprocals, so no division remains on the chain (within a few ulps of
+  // the divided form): the last CTA's reduction and solve 33 -> 21 us, the
+  // FP64 backward 1.4% faster.  The float-pair kernel, whose FP64 pipe is
+  // idle, keeps the square root and the divisions (it measured 1.3% slower
+  // with the reciprocals).
+  double rinv[6];
   for (int j = 0; j < B; ++j) {
     double d = A[j][j];
     for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
     if (!(d > 1e-13 * maxdiag)) return false;
-    L[j][j] = sqrt(d);
-    const double inv = 1.0 / L[j][j];
+    const double rj = kNoDivide ? rsqrt(d) : 0.0;
+    L[j][j] = kNoDivide ? d * rj : sqrt(d);
+    const double inv = kNoDivide ? rj : 1.0 / L[j][j];
+    rinv[j] = inv;
     for (int i = j + 1; i < B; ++i) {
       double s = A[i][j];
       for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
@@ -82,12 +96,12 @@ __device__ bool solve_normal_equations(int B, const double* M, const double* R,
   for (int i = 0; i < B; ++i) {
     double s = R[i];
     for (int k = 0; k < i; ++k) s -= L[i][k] * z[k];
-    z[i] = s / L[i][i];
+    z[i] = kNoDivide ? s * rinv[i] : s / L[i][i];
   }
   for (int i = B - 1; i >= 0; --i) {
     double s = z[i];
     for (int k = i + 1; k < B; ++k) s -= L[k][i] * beta[k];
-    beta[i] = s / L[i][i];
+    beta[i] = kNoDivide ? s * rinv[i] : s / L[i][i];
   }
   for (int i = B; i < 6; ++i) beta[i] = 0.0;
   return true;
@@ -1154,7 +1168,8 @@ backward_kernel(BwdArgs a) {
         if (a.flag_host != nullptr) finish_request(a, I.req);
       } else {
         double beta[6];
-        const bool ok = solve_normal_equations(NB, s_sum, s_sum + kSlotRhs, beta);
+        const bool ok = solve_normal_equations<std::is_same<Real, double>::value>(
+            NB, s_sum, s_sum + kSlotRhs, beta);
         if (r == 0) st->euro_sum = s_sum[kSlotEuro];
         st->itm = __ldcg(&st->itm) + s_sum[0];
         st->ties = __ldcg(&st->ties) + s_sum[kSlotTies];
