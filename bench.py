@@ -64,12 +64,12 @@ BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
 # DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel at 98,304 paths (3.459872e9 + 0.508091e9 bytes) scaled by the path
+# kernel at 98,304 paths (3.331259e9 + 0.461641e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
 # the kernel source it was taken from: reported as null once the code of
 # backward.cu changes (code_sha256_16).
-BWD_TRAFFIC = {"bytes": (3.459871744e9 + 0.508090880e9) * 131072 / 98304,
-               "source_sha256_16": "d3f1c2f3e7671489",
+BWD_TRAFFIC = {"bytes": (3.331258880e9 + 0.461640960e9) * 131072 / 98304,
+               "source_sha256_16": "9312333d9ec49f23",
                "capture": "profiles/backward_kernel_fp64_98304x252.md (traffic capture), "
                           "scaled by 131072/98304"}
 
