@@ -102,6 +102,8 @@ def parse():
                     help="backward sub-tiles per job; 0 = pick by the autotuner")
     ap.add_argument("--ppt", type=int, default=0,
                     help="backward paths per lane with --sub (0 = the precision's default)")
+    ap.add_argument("--itm-half", action="store_true",
+                    help="with --sub: half the sub-tiles per job for strikes in the money at S0")
     ap.add_argument("--regenerate", action="store_true",
                     help="no path store: regenerate segments from saved states")
     ap.add_argument("--out-of-sample", action="store_true",
@@ -519,7 +521,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
         subs = []
         for ci, c in enumerate(chunks):
             sub, ppt, _ = ctx.autotune(c)
-            subs.append([sub, ppt])
+            subs.append([sub & ~L.LSMC_SUB_ITM_HALF, ppt, bool(sub & L.LSMC_SUB_ITM_HALF)])
             p = ctx.plan(c)
             p.launch(use_graph=True)  # capture and warm
             p.fetch()
@@ -536,7 +538,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
-            "precision": precision, "graph": True, "autotuned_shape_sub_ppt": subs}
+            "precision": precision, "graph": True, "autotuned_shape_sub_ppt_itmhalf": subs}
 
 
 # The paper's STAC-A2 runtimes (Table A1, Alveo U280 multi-kernel, total
@@ -804,8 +806,9 @@ def main():
     ctx = api.Context(workspace_bytes=need + (256 << 20))
     if args.sub:
         # a fixed backward shape (profiling runs) instead of the autotuner's
-        ctx.set_backward_shape(args.sub, args.ppt)
-        tuned_sub, tuned_ppt = args.sub, args.ppt or None
+        tuned_sub = args.sub | (L.LSMC_SUB_ITM_HALF if args.itm_half else 0)
+        ctx.set_backward_shape(tuned_sub, args.ppt)
+        tuned_ppt = args.ppt or None
     else:
         tuned_sub, tuned_ppt, _ = ctx.autotune([wl])
     plan = ctx.plan([wl])
@@ -928,7 +931,8 @@ def main():
                    "strikes": wl.strikes, "greeks": list(wl.greeks),
                    "revaluations": wl.n_scenarios, "scheme": wl.scheme, "basis": wl.basis,
                    "precision": wl.precision, "parallelism": "replicas" if world > 1 else "single",
-                   "backward_subtiles_per_job": tuned_sub,
+                   "backward_subtiles_per_job": tuned_sub & ~L.LSMC_SUB_ITM_HALF,
+                   "backward_itm_strikes_half_subtiles": bool(tuned_sub & L.LSMC_SUB_ITM_HALF),
                    "backward_paths_per_lane": tuned_ppt,
                    "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
         "path_steps_per_s": {"generated": job_throughput(world, wl.generated_path_steps, ms_max),

@@ -85,10 +85,10 @@ struct lsmc_ctx {
   void* (*dev_alloc)(size_t, void*) = nullptr;
   void (*dev_free)(void*, void*) = nullptr;
   void* alloc_user = nullptr;
-  uint32_t sub_override = 0;  // backward sub-tiles per job (0: chosen per plan)
+  uint32_t sub_override = 0;  // backward sub-tiles per job | LSMC_SUB_ITM_HALF (0: chosen per plan)
   uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
   double wait_limit_s = 20.0; // bound of every device-side wait (lsmc_set_wait_limit)
-  // autotuned backward shape (ppt << 16 | sub-tiles per job), keyed by
+  // autotuned backward shape (ppt << 16 | sub-tiles per job | LSMC_SUB_ITM_HALF), keyed by
   // (precision, basis, log2 of the first round's sub-tile count)
   std::map<uint64_t, uint32_t> tuned;
   // serving
@@ -993,7 +993,9 @@ int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds) {
 }
 
 int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt) {
-  if (!ctx || sub > kMaxSub || !(ppt == 0 || ppt == 2 || ppt == 4 || ppt == 8))
+  const uint32_t count = sub & ~LSMC_SUB_ITM_HALF;
+  if (!ctx || count > kMaxSub || (count == 0 && sub != 0) ||
+      !(ppt == 0 || ppt == 2 || ppt == 4 || ppt == 8))
     return LSMC_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
   ctx->sub_override = sub;
@@ -1370,29 +1372,42 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* b
   const uint32_t saved_sub = ctx->sub_override, saved_ppt = ctx->ppt_override;
   uint32_t best = 0;
   double best_t = 1e300;
+  // strikes on both sides of S0 in one request: the in-the-money half tiles
+  // are worth a trial
+  bool mixed_moneyness = false;
+  for (size_t i = 0; i < n; ++i) {
+    bool itm = false, otm = false;
+    for (uint32_t k = 0; k < reqs[i].n_strikes; ++k)
+      (itm_at_spot(reqs[i], k) ? itm : otm) = true;
+    mixed_moneyness = mixed_moneyness || (itm && otm);
+  }
   // each paths-per-lane choice compiled for the precision, and sub-tiles per
-  // job in powers of two while the busiest round keeps >= 8 jobs
+  // job in powers of two while the busiest round keeps >= 8 jobs, uniform
+  // and (from 2 up) with the in-the-money strikes' jobs halved
   for (int ppt = 2; ppt <= 8 && rc == LSMC_OK; ppt *= 2) {
     if (!backward_ppt_valid(o.precision, ppt)) continue;
-    for (uint32_t cand = 1; cand <= kMaxSub; cand *= 2) {
+    for (uint32_t cand = 1; cand <= kMaxSub && rc == LSMC_OK; cand *= 2) {
       if (cand > 1 && (uint64_t)cand * ppt * 8 > tiles0 * dppt) break;
-      ctx->sub_override = cand;
-      ctx->ppt_override = (uint32_t)ppt;
-      lsmc_plan* p = nullptr;
-      rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);
-      if (rc) break;
-      p->timing = true;
-      double ms[4] = {0, 0, 0, 0};
-      uint32_t launches = 0;
-      rc = plan_enqueue(p, true);  // warm-up launch, then the timed one
-      if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
-      if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
-      if (rc == LSMC_OK) rc = plan_enqueue(p, true);
-      if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
-      if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
-      plan_free(p);
-      if (rc) break;
-      if (ms[2] < best_t) { best_t = ms[2]; best = ((uint32_t)ppt << 16) | cand; }
+      for (int half = 0; half < 2 && rc == LSMC_OK; ++half) {
+        if (half && (cand < 2 || !mixed_moneyness)) continue;
+        ctx->sub_override = cand | (half ? LSMC_SUB_ITM_HALF : 0u);
+        ctx->ppt_override = (uint32_t)ppt;
+        lsmc_plan* p = nullptr;
+        rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);
+        if (rc) break;
+        p->timing = true;
+        double ms[4] = {0, 0, 0, 0};
+        uint32_t launches = 0;
+        rc = plan_enqueue(p, true);  // warm-up launch, then the timed one
+        if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+        if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+        if (rc == LSMC_OK) rc = plan_enqueue(p, true);
+        if (rc == LSMC_OK) rc = plan_collect(p, nullptr);
+        if (rc == LSMC_OK) rc = lsmc_plan_kernel_times(p, ms, &launches);
+        plan_free(p);
+        if (rc) break;
+        if (ms[2] < best_t) { best_t = ms[2]; best = ((uint32_t)ppt << 16) | ctx->sub_override; }
+      }
     }
   }
   ctx->sub_override = saved_sub;

@@ -173,6 +173,10 @@ int plan_ppt(const PlanOptions& o) {
                                                              : backward_ppt_default(o.precision);
 }
 
+bool itm_at_spot(const lsmc_request& q, uint32_t k) {
+  return q.type == LSMC_PUT ? q.strikes[k] > q.model.S0 : q.strikes[k] < q.model.S0;
+}
+
 uint32_t choose_sub(const lsmc_request* reqs, size_t n, int precision, int ppt,
                     uint32_t workers, uint32_t jobs_per_worker) {
   const uint64_t tile0 = (uint64_t)backward_tile(precision, ppt);
@@ -267,10 +271,16 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
     L->generated_path_steps += (uint64_t)P * N * sc.size();
     L->lsmc_path_steps += (uint64_t)P * N * sc.size() * q.n_strikes;
 
-    const uint32_t sub = std::max<uint32_t>(1, ci < opt.sub_req.size() ? opt.sub_req[ci] : opt.sub);
-    const uint32_t tile = tile0 * sub;
-    const uint32_t tiles = (P + tile - 1) / tile;
-    if ((uint64_t)tiles * N >= (1ull << 31)) return LSMC_EINVAL;
+    const uint32_t sub_flags = ci < opt.sub_req.size() ? opt.sub_req[ci] : opt.sub;
+    const bool itm_half = (sub_flags & LSMC_SUB_ITM_HALF) != 0 && q.n_strikes > 1;
+    const uint32_t sub = std::max<uint32_t>(1, sub_flags & ~LSMC_SUB_ITM_HALF);
+    // sub-tiles per job and tiles of strike k
+    auto sub_of = [&](uint32_t k) {
+      return itm_half && itm_at_spot(q, k) ? std::max<uint32_t>(1, sub / 2) : sub;
+    };
+    auto tiles_of = [&](uint32_t k) { return (P + tile0 * sub_of(k) - 1) / (tile0 * sub_of(k)); };
+    for (uint32_t k = 0; k < q.n_strikes; ++k)
+      if ((uint64_t)tiles_of(k) * N >= (1ull << 31)) return LSMC_EINVAL;
     std::vector<GreekOut> gos(q.n_strikes);
     for (auto& g : gos) {
       for (int k = 0; k < kScCount; ++k) g.res[k] = -1;
@@ -291,7 +301,7 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         o.y = off_y;
         off_y += round_up((size_t)P * real, 256);
         o.partial = off_partial;
-        off_partial += round_up((size_t)tiles * kNSum * 8, 256);
+        off_partial += round_up((size_t)tiles_of(k) * kNSum * 8, 256);
         o.scale = off_scale;
         off_scale += round_up((size_t)2 * (N + 1) * 8, 256);
         o.beta = SIZE_MAX;
@@ -319,8 +329,8 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
         I.theta = sc[s].model.theta;
         I.P = P;
         I.N = N;
-        I.tiles = tiles;
-        I.sub = sub;
+        I.tiles = tiles_of(k);
+        I.sub = sub_of(k);
         I.gens = q.style == LSMC_EUROPEAN ? 1 : N;
         I.type = q.type;
         I.style = q.style;

@@ -192,6 +192,28 @@ def test_autotuned_plans_still_match_oracle(ctx):
     scenario_parity(wl, got2, scen2, what="fixed shape 3 x 2")
 
 
+def test_in_the_money_strikes_in_half_size_jobs_match_oracle(ctx):
+    # LSMC_SUB_ITM_HALF: the strike in the money at S0 (the 110 put) runs its
+    # regressions in jobs of half the sub-tiles; more jobs, the same results
+    wl = workloads.SMALL_FP64.replace(n_paths=20000, n_steps=20, basis="sv2",
+                                      strikes=[90.0, 100.0, 110.0],
+                                      greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02)
+    jobs = {}
+    for name, sub in (("uniform", 4), ("itm half", 4 | L.LSMC_SUB_ITM_HALF)):
+        with api.Context(workspace_bytes=1 << 30) as c:
+            c.set_backward_shape(sub, 2)
+            p = c.plan([wl])
+            jobs[name] = p.info().backward_jobs
+            p.close()
+            got, scen = c.price_with_scenarios(wl)
+        scenario_parity(wl, got, scen, what=name)
+    assert jobs["itm half"] > jobs["uniform"]
+    for bad in (L.LSMC_SUB_ITM_HALF, 65 | L.LSMC_SUB_ITM_HALF):
+        with pytest.raises(L.LsmcError) as e:
+            ctx.set_backward_shape(bad, 2)
+        assert e.value.status == L.LSMC_EINVAL
+
+
 def test_external_allocator():
     # every plan allocation through callbacks (here PyTorch's caching
     # allocator, counted): the same results as cudaMalloc, every block
