@@ -64,12 +64,14 @@ BWD_FLOPS_ALL = 3
 BWD_FLOPS_ITM = 40 + 15
 # DRAM bytes of one FP64 backward launch on the 131,072-path book, from an
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
-# kernel at 98,304 paths (3.331259e9 + 0.461641e9 bytes) scaled by the path
+# kernel at 98,304 paths (3.110958e9 + 0.348644e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
-# the kernel source it was taken from: reported as null once the code of
-# backward.cu changes (code_sha256_16).
-BWD_TRAFFIC = {"bytes": (3.331258880e9 + 0.461640960e9) * 131072 / 98304,
+# the kernel source and the tile shape it was taken with (sub-tiles per job
+# with LSMC_SUB_ITM_HALF, paths per lane): reported as null once the code of
+# backward.cu changes (code_sha256_16) or the bench runs another shape.
+BWD_TRAFFIC = {"bytes": (3.110957824e9 + 0.348643840e9) * 131072 / 98304,
                "source_sha256_16": "9312333d9ec49f23",
+               "shape": (32 | 0x8000, 2),
                "capture": "profiles/backward_kernel_fp64_98304x252.md (traffic capture), "
                           "scaled by 131072/98304"}
 
@@ -888,7 +890,8 @@ def main():
     traffic = None
     src = os.path.join(_ROOT, "paper_2206_03719_gb300", "csrc", "backward.cu")
     if fp64 and wl.n_paths == workloads.PAPER_FP64.n_paths and os.path.exists(src):
-        if code_sha256_16(src) == BWD_TRAFFIC["source_sha256_16"]:
+        if (code_sha256_16(src) == BWD_TRAFFIC["source_sha256_16"] and
+                (tuned_sub, tuned_ppt) == BWD_TRAFFIC["shape"]):
             traffic = BWD_TRAFFIC["bytes"]
     roofline = {
         "kernel": "backward_kernel (Longstaff-Schwartz moments, solve, exercise)",
