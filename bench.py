@@ -67,21 +67,13 @@ BWD_FLOPS_ITM = 40 + 15
 # kernel at 98,304 paths (3.110958e9 + 0.348644e9 bytes) scaled by the path
 # count (the path store and cash flows grow in proportion).  Valid only for
 # the kernel source and the tile shape it was taken with (sub-tiles per job
-# with its LSMC_SUB_ITM_* flag, paths per lane): reported as null once the code of
+# with LSMC_SUB_ITM_HALF, paths per lane): reported as null once the code of
 # backward.cu changes (code_sha256_16) or the bench runs another shape.
 BWD_TRAFFIC = {"bytes": (3.110957824e9 + 0.348643840e9) * 131072 / 98304,
                "source_sha256_16": "9312333d9ec49f23",
                "shape": (32 | 0x8000, 2),
                "capture": "profiles/backward_kernel_fp64_98304x252.md (traffic capture), "
                           "scaled by 131072/98304"}
-
-
-def split_shape(sub):
-    """(sub-tiles per backward job, the factor by which the strikes in the
-    money at S0 divide it) of a sub-tile count with its LSMC_SUB_ITM_* flag."""
-    from paper_2206_03719_gb300.lsmc import LSMC_SUB_ITM_HALF as HALF, LSMC_SUB_ITM_QUARTER as QUARTER
-    div = 2 if sub & HALF else 4 if sub & QUARTER else 1
-    return sub & ~(HALF | QUARTER), div
 
 
 def code_sha256_16(path):
@@ -114,8 +106,6 @@ def parse():
                     help="backward paths per lane with --sub (0 = the precision's default)")
     ap.add_argument("--itm-half", action="store_true",
                     help="with --sub: half the sub-tiles per job for strikes in the money at S0")
-    ap.add_argument("--itm-quarter", action="store_true",
-                    help="with --sub: a quarter of the sub-tiles per job for those strikes")
     ap.add_argument("--regenerate", action="store_true",
                     help="no path store: regenerate segments from saved states")
     ap.add_argument("--out-of-sample", action="store_true",
@@ -533,7 +523,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
         subs = []
         for ci, c in enumerate(chunks):
             sub, ppt, _ = ctx.autotune(c)
-            subs.append([*split_shape(sub), ppt])
+            subs.append([sub & ~L.LSMC_SUB_ITM_HALF, ppt, bool(sub & L.LSMC_SUB_ITM_HALF)])
             p = ctx.plan(c)
             p.launch(use_graph=True)  # capture and warm
             p.fetch()
@@ -550,7 +540,7 @@ def measure_book(api, L, torch, n_contracts=512, chunk=128, precision="mixed"):
             "greeks_per_s": greeks / (total_ms / 1e3),
             "generated_path_steps_per_s": gen / (total_ms / 1e3),
             "lsmc_path_steps_per_s": lsmc / (total_ms / 1e3),
-            "precision": precision, "graph": True, "autotuned_shape_sub_itmdiv_ppt": subs}
+            "precision": precision, "graph": True, "autotuned_shape_sub_ppt_itmhalf": subs}
 
 
 # The paper's STAC-A2 runtimes (Table A1, Alveo U280 multi-kernel, total
@@ -818,8 +808,7 @@ def main():
     ctx = api.Context(workspace_bytes=need + (256 << 20))
     if args.sub:
         # a fixed backward shape (profiling runs) instead of the autotuner's
-        tuned_sub = args.sub | (L.LSMC_SUB_ITM_HALF if args.itm_half else 0) | \
-            (L.LSMC_SUB_ITM_QUARTER if args.itm_quarter else 0)
+        tuned_sub = args.sub | (L.LSMC_SUB_ITM_HALF if args.itm_half else 0)
         ctx.set_backward_shape(tuned_sub, args.ppt)
         tuned_ppt = args.ppt or None
     else:
@@ -945,8 +934,8 @@ def main():
                    "strikes": wl.strikes, "greeks": list(wl.greeks),
                    "revaluations": wl.n_scenarios, "scheme": wl.scheme, "basis": wl.basis,
                    "precision": wl.precision, "parallelism": "replicas" if world > 1 else "single",
-                   "backward_subtiles_per_job": split_shape(tuned_sub)[0],
-                   "backward_itm_strikes_subtile_divisor": split_shape(tuned_sub)[1],
+                   "backward_subtiles_per_job": tuned_sub & ~L.LSMC_SUB_ITM_HALF,
+                   "backward_itm_strikes_half_subtiles": bool(tuned_sub & L.LSMC_SUB_ITM_HALF),
                    "backward_paths_per_lane": tuned_ppt,
                    "l2": "path store %.2f GB per step exceeds L2" % (info.device_bytes / 1e9)},
         "path_steps_per_s": {"generated": job_throughput(world, wl.generated_path_steps, ms_max),

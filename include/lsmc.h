@@ -228,23 +228,22 @@ int lsmc_set_allocator(lsmc_ctx* ctx, void* (*alloc)(size_t bytes, void* user),
  * 20 s; 0 fails any wait that is not satisfied at once.  LSMC_EINVAL outside
  * [0, 3600].  Bounded waits are a deployment safeguard (the paper has none). */
 int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds);
-/* Flags OR'ed into a count of sub-tiles per backward job (sub of
- * lsmc_set_backward_shape, best_sub of lsmc_autotune), at most one of them:
- * in requests with several strikes, the strikes in the money at the
- * request's S0 (puts struck above it, calls below) take half (a quarter) as
- * many sub-tiles per job (at least one) as the others.  Their regressions
- * have the most in-the-money paths per tile, so smaller jobs shorten their
- * chain of dates, while the larger jobs of the other strikes cost fewer
- * arrivals.  Results differ only by the order of the tile sums. */
+/* Flag OR'ed into a count of sub-tiles per backward job (sub of
+ * lsmc_set_backward_shape, best_sub of lsmc_autotune): in requests with
+ * several strikes, the strikes in the money at the request's S0 (puts
+ * struck above it, calls below) take half as many sub-tiles per job (at
+ * least one) as the others.  Their regressions have the most in-the-money
+ * paths per tile, so smaller jobs shorten their chain of dates, while the
+ * larger jobs of the other strikes cost fewer arrivals.  Results differ only
+ * by the order of the tile sums. */
 #define LSMC_SUB_ITM_HALF 0x8000u
-#define LSMC_SUB_ITM_QUARTER 0x4000u
 /* Tile shape of the backward pass for the context's later plans: sub
- * sub-tiles per job (optionally | LSMC_SUB_ITM_HALF or LSMC_SUB_ITM_QUARTER) and ppt paths per
+ * sub-tiles per job (optionally | LSMC_SUB_ITM_HALF) and ppt paths per
  * thread of a sub-tile (2 or 4 for LSMC_FP64 and LSMC_DF, 4 or 8 for
  * LSMC_MIXED; a value not compiled for a plan's precision falls back to its
  * default).  0, 0: chosen per plan (the autotuner's result when
  * lsmc_autotune has tuned that kind of plan).  LSMC_EINVAL for a count
- * above 64, a flag without a count, both flags, or ppt not in {0, 2, 4, 8}. */
+ * above 64, the flag without a count, or ppt not in {0, 2, 4, 8}. */
 int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt);
 /* Share of the device's resident backward CTAs that one serving batch's
  * persistent backward grid takes, so that batches on different slots run
@@ -321,11 +320,11 @@ int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
 /* Autotuner: times the backward pass of a plan for these requests over its
  * tile shapes -- paths per thread of a sub-tile (2 or 4 for LSMC_FP64 and
  * LSMC_DF, 4 or 8 for LSMC_MIXED) and jobs of 1, 2, 4, ... sub-tiles, each
- * from 2 (4) sub-tiles up also with LSMC_SUB_ITM_HALF (LSMC_SUB_ITM_QUARTER)
- * where a request has strikes on both sides of S0 (one warm-up and one
- * timed launch each) --, remembers the fastest for later plans of the same
- * precision, basis and size class on this context, and returns it
- * (best_sub, best_ppt, best_ms: optional; best_sub may carry a flag). */
+ * from 2 sub-tiles up also with LSMC_SUB_ITM_HALF where a request has
+ * strikes on both sides of S0 (one warm-up and one timed launch each) --,
+ * remembers the fastest for later plans of the same precision, basis and
+ * size class on this context, and returns it (best_sub, best_ppt, best_ms:
+ * optional; best_sub may carry LSMC_SUB_ITM_HALF). */
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                   uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
 /* Destroy every plan before the context it was created on. */

@@ -85,10 +85,10 @@ struct lsmc_ctx {
   void* (*dev_alloc)(size_t, void*) = nullptr;
   void (*dev_free)(void*, void*) = nullptr;
   void* alloc_user = nullptr;
-  uint32_t sub_override = 0;  // backward sub-tiles per job | an LSMC_SUB_ITM_* flag (0: chosen per plan)
+  uint32_t sub_override = 0;  // backward sub-tiles per job | LSMC_SUB_ITM_HALF (0: chosen per plan)
   uint32_t ppt_override = 0;  // backward paths per lane (0: chosen per plan)
   double wait_limit_s = 20.0; // bound of every device-side wait (lsmc_set_wait_limit)
-  // autotuned backward shape (ppt << 16 | sub-tiles per job | an LSMC_SUB_ITM_* flag), keyed by
+  // autotuned backward shape (ppt << 16 | sub-tiles per job | LSMC_SUB_ITM_HALF), keyed by
   // (precision, basis, log2 of the first round's sub-tile count)
   std::map<uint64_t, uint32_t> tuned;
   // serving
@@ -993,10 +993,8 @@ int lsmc_set_wait_limit(lsmc_ctx* ctx, double seconds) {
 }
 
 int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt) {
-  const uint32_t flags = sub & (LSMC_SUB_ITM_HALF | LSMC_SUB_ITM_QUARTER);
-  const uint32_t count = sub & ~flags;
+  const uint32_t count = sub & ~LSMC_SUB_ITM_HALF;
   if (!ctx || count > kMaxSub || (count == 0 && sub != 0) ||
-      flags == (LSMC_SUB_ITM_HALF | LSMC_SUB_ITM_QUARTER) ||
       !(ppt == 0 || ppt == 2 || ppt == 4 || ppt == 8))
     return LSMC_EINVAL;
   std::lock_guard<std::mutex> g(ctx->mu);
@@ -1374,8 +1372,8 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* b
   const uint32_t saved_sub = ctx->sub_override, saved_ppt = ctx->ppt_override;
   uint32_t best = 0;
   double best_t = 1e300;
-  // strikes on both sides of S0 in one request: smaller jobs for the
-  // in-the-money strikes are worth a trial
+  // strikes on both sides of S0 in one request: the in-the-money half tiles
+  // are worth a trial
   bool mixed_moneyness = false;
   for (size_t i = 0; i < n; ++i) {
     bool itm = false, otm = false;
@@ -1385,16 +1383,14 @@ int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t* b
   }
   // each paths-per-lane choice compiled for the precision, and sub-tiles per
   // job in powers of two while the busiest round keeps >= 8 jobs, uniform
-  // and with the in-the-money strikes' jobs halved (from 2 up) or quartered
-  // (from 4 up)
+  // and (from 2 up) with the in-the-money strikes' jobs halved
   for (int ppt = 2; ppt <= 8 && rc == LSMC_OK; ppt *= 2) {
     if (!backward_ppt_valid(o.precision, ppt)) continue;
     for (uint32_t cand = 1; cand <= kMaxSub && rc == LSMC_OK; cand *= 2) {
       if (cand > 1 && (uint64_t)cand * ppt * 8 > tiles0 * dppt) break;
-      for (int div = 1; div <= 4 && rc == LSMC_OK; div *= 2) {
-        if (div > 1 && (cand < (uint32_t)div || !mixed_moneyness)) continue;
-        ctx->sub_override = cand | (div == 2 ? LSMC_SUB_ITM_HALF : 0u) |
-                            (div == 4 ? LSMC_SUB_ITM_QUARTER : 0u);
+      for (int half = 0; half < 2 && rc == LSMC_OK; ++half) {
+        if (half && (cand < 2 || !mixed_moneyness)) continue;
+        ctx->sub_override = cand | (half ? LSMC_SUB_ITM_HALF : 0u);
         ctx->ppt_override = (uint32_t)ppt;
         lsmc_plan* p = nullptr;
         rc = plan_create_on(ctx, reqs, n, ctx->stream, ctx->user_workspace, &p);

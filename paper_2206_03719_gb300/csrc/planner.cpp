@@ -272,15 +272,11 @@ int build_layout(const lsmc_request* reqs, size_t n, const PlanOptions& opt,
     L->lsmc_path_steps += (uint64_t)P * N * sc.size() * q.n_strikes;
 
     const uint32_t sub_flags = ci < opt.sub_req.size() ? opt.sub_req[ci] : opt.sub;
-    // sub-tiles per job of the other strikes over those of the strikes in the money at S0
-    const uint32_t itm_div = q.n_strikes < 2 ? 1u
-                             : (sub_flags & LSMC_SUB_ITM_HALF) ? 2u
-                             : (sub_flags & LSMC_SUB_ITM_QUARTER) ? 4u : 1u;
-    const uint32_t sub =
-        std::max<uint32_t>(1, sub_flags & ~(LSMC_SUB_ITM_HALF | LSMC_SUB_ITM_QUARTER));
+    const bool itm_half = (sub_flags & LSMC_SUB_ITM_HALF) != 0 && q.n_strikes > 1;
+    const uint32_t sub = std::max<uint32_t>(1, sub_flags & ~LSMC_SUB_ITM_HALF);
     // sub-tiles per job and tiles of strike k
     auto sub_of = [&](uint32_t k) {
-      return itm_at_spot(q, k) ? std::max<uint32_t>(1, sub / itm_div) : sub;
+      return itm_half && itm_at_spot(q, k) ? std::max<uint32_t>(1, sub / 2) : sub;
     };
     auto tiles_of = [&](uint32_t k) { return (P + tile0 * sub_of(k) - 1) / (tile0 * sub_of(k)); };
     for (uint32_t k = 0; k < q.n_strikes; ++k)

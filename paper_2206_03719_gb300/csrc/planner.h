@@ -53,7 +53,7 @@ struct PlanOptions {
   int scheme = LSMC_SCHEME_QE;
   int basis = LSMC_BASIS_S2;
   bool raw_paths = false;       // stage entry point: E rows are S itself
-  uint32_t sub = 1;             // sub-tiles per backward job (| LSMC_SUB_ITM_HALF or _QUARTER)
+  uint32_t sub = 1;             // sub-tiles per backward job (| LSMC_SUB_ITM_HALF)
   std::vector<uint32_t> sub_req; // per request (if not empty: overrides sub)
   uint32_t ppt = 0;             // paths per thread of a sub-tile (0: the precision's default)
   // regenerate mode: no path store; states saved every ck_stride dates and
@@ -71,9 +71,8 @@ int plan_ppt(const PlanOptions& o);
 constexpr uint32_t kMaxSub = 64;
 
 // Whether strike K of request q is in the money at the request's S0 (a put
-// struck above it, a call below): with LSMC_SUB_ITM_HALF (_QUARTER) such
-// strikes of a request with several strikes take half (a quarter of) the
-// sub-tiles per job.
+// struck above it, a call below): with LSMC_SUB_ITM_HALF such strikes of a
+// request with several strikes take half the sub-tiles per job.
 bool itm_at_spot(const lsmc_request& q, uint32_t k);
 
 // Sub-tiles per backward job so that the busiest round has about

@@ -25,7 +25,7 @@ LSMC_FLAG_OUT_OF_SAMPLE = 2
 LSMC_FLAG_STORE_FP16 = 4
 LSMC_FLAG_STORE_BF16 = 8
 LSMC_FP64, LSMC_MIXED, LSMC_DF = 0, 1, 2
-LSMC_SUB_ITM_HALF, LSMC_SUB_ITM_QUARTER = 0x8000, 0x4000
+LSMC_SUB_ITM_HALF = 0x8000
 LSMC_GREEK_DELTA, LSMC_GREEK_GAMMA, LSMC_GREEK_VEGA = 1, 2, 4
 LSMC_GREEK_RHO, LSMC_GREEK_THETA, LSMC_GREEK_ALL = 8, 16, 31
 

@@ -192,16 +192,14 @@ def test_autotuned_plans_still_match_oracle(ctx):
     scenario_parity(wl, got2, scen2, what="fixed shape 3 x 2")
 
 
-def test_in_the_money_strikes_in_smaller_jobs_match_oracle(ctx):
-    # LSMC_SUB_ITM_HALF / _QUARTER: the strike in the money at S0 (the 110
-    # put) runs its regressions in jobs of half / a quarter of the sub-tiles;
-    # more jobs, the same results
+def test_in_the_money_strikes_in_half_size_jobs_match_oracle(ctx):
+    # LSMC_SUB_ITM_HALF: the strike in the money at S0 (the 110 put) runs its
+    # regressions in jobs of half the sub-tiles; more jobs, the same results
     wl = workloads.SMALL_FP64.replace(n_paths=20000, n_steps=20, basis="sv2",
                                       strikes=[90.0, 100.0, 110.0],
                                       greeks=workloads.ALL_GREEKS, rel_dS_gamma=0.02)
     jobs = {}
-    for name, sub in (("uniform", 4), ("itm half", 4 | L.LSMC_SUB_ITM_HALF),
-                      ("itm quarter", 4 | L.LSMC_SUB_ITM_QUARTER)):
+    for name, sub in (("uniform", 4), ("itm half", 4 | L.LSMC_SUB_ITM_HALF)):
         with api.Context(workspace_bytes=1 << 30) as c:
             c.set_backward_shape(sub, 2)
             p = c.plan([wl])
@@ -209,9 +207,8 @@ def test_in_the_money_strikes_in_smaller_jobs_match_oracle(ctx):
             p.close()
             got, scen = c.price_with_scenarios(wl)
         scenario_parity(wl, got, scen, what=name)
-    assert jobs["itm quarter"] > jobs["itm half"] > jobs["uniform"]
-    for bad in (L.LSMC_SUB_ITM_HALF, L.LSMC_SUB_ITM_QUARTER, 65 | L.LSMC_SUB_ITM_HALF,
-                4 | L.LSMC_SUB_ITM_HALF | L.LSMC_SUB_ITM_QUARTER):
+    assert jobs["itm half"] > jobs["uniform"]
+    for bad in (L.LSMC_SUB_ITM_HALF, 65 | L.LSMC_SUB_ITM_HALF):
         with pytest.raises(L.LsmcError) as e:
             ctx.set_backward_shape(bad, 2)
         assert e.value.status == L.LSMC_EINVAL
