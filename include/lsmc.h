@@ -310,6 +310,19 @@ typedef struct lsmc_plan_info {
   uint64_t d2h_bytes;      /* bytes read back by each lsmc_plan_fetch */
 } lsmc_plan_info;
 int lsmc_plan_get_info(const lsmc_plan* plan, lsmc_plan_info* info);
+/* The counters of lsmc_plan_get_info that are fixed before any launch, for
+ * the plan lsmc_plan_create would build for these requests with backward
+ * shape (sub sub-tiles per job, optionally | LSMC_SUB_ITM_HALF; ppt paths
+ * per thread of a sub-tile, 0: the precision's default): generated and LSMC
+ * path-steps, backward jobs, device bytes, results, instances, path groups
+ * and table bytes (h2d_bytes); kernels_per_launch = 4, itm_path_steps =
+ * d2h_bytes = 0.  Host only: nothing is allocated and no device is touched;
+ * ctx may be NULL (then the library's default precision and scheme).
+ * LSMC_EINVAL for a sub-tile count outside 1..64, another bit in sub, ppt
+ * not in {0, 2, 4, 8} or an invalid request; LSMC_ENOTIMPL where
+ * lsmc_plan_create would give it. */
+int lsmc_plan_layout_info(const lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
+                          uint32_t sub, uint32_t ppt, lsmc_plan_info* info);
 /* Per-kernel timing of later launches (CUDA events on the plan's stream,
  * recorded between its kernels; no effect on results).  enable = 0 stops. */
 int lsmc_plan_set_timing(lsmc_plan* plan, int32_t enable);

@@ -1032,6 +1032,33 @@ int lsmc_request_footprint(const lsmc_ctx* ctx, const lsmc_request* req, size_t*
   return LSMC_OK;
 }
 
+int lsmc_plan_layout_info(const lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, uint32_t sub,
+                          uint32_t ppt, lsmc_plan_info* info) {
+  const uint32_t count = sub & ~LSMC_SUB_ITM_HALF;
+  if (!reqs || !n || !info || count < 1 || count > kMaxSub ||
+      !(ppt == 0 || ppt == 2 || ppt == 4 || ppt == 8))
+    return LSMC_EINVAL;
+  PlanOptions o;
+  int rc = plan_options(const_cast<lsmc_ctx*>(ctx), reqs, n, &o);
+  if (rc) return rc;
+  o.sub = sub;
+  o.ppt = ppt;
+  PlanLayout L;
+  rc = build_layout(reqs, n, o, &L);
+  if (rc) return rc;
+  *info = lsmc_plan_info{};
+  info->generated_path_steps = L.generated_path_steps;
+  info->lsmc_path_steps = L.lsmc_path_steps;
+  info->backward_jobs = L.total_jobs;
+  info->device_bytes = L.total_bytes;
+  info->kernels_per_launch = 4;
+  info->n_results = (uint32_t)L.greeks.size();
+  info->n_instances = (uint32_t)L.inst.size();
+  info->n_groups = (uint32_t)L.groups.size();
+  info->h2d_bytes = L.bytes_tables;
+  return LSMC_OK;
+}
+
 int lsmc_plan_create(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n, lsmc_plan** out) {
   if (!ctx || !out) return LSMC_EINVAL;
   *out = nullptr;

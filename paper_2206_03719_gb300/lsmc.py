@@ -34,7 +34,7 @@ EXPORTS = [
     "lsmc_set_stream", "lsmc_set_workspace", "lsmc_set_allocator", "lsmc_request_footprint",
     "lsmc_price_greeks", "lsmc_price_request", "lsmc_price_book", "lsmc_price_bounds",
     "lsmc_plan_create", "lsmc_plan_launch", "lsmc_plan_fetch",
-    "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_destroy",
+    "lsmc_plan_device_results", "lsmc_plan_get_info", "lsmc_plan_layout_info", "lsmc_plan_destroy",
     "lsmc_plan_set_timing", "lsmc_plan_kernel_times", "lsmc_autotune",
     "lsmc_submit", "lsmc_poll", "lsmc_wait", "lsmc_ticket_times",
     "lsmc_philox", "lsmc_draws", "lsmc_paths", "lsmc_multi_asset_max", "lsmc_backward",
@@ -170,6 +170,8 @@ def load(build_if_missing: bool = False, path: str = None):
             "lsmc_plan_fetch": ([vp, P(lsmc_result)], ctypes.c_int),
             "lsmc_plan_device_results": ([vp, P(vp), P(sz)], ctypes.c_int),
             "lsmc_plan_get_info": ([vp, P(lsmc_plan_info)], ctypes.c_int),
+            "lsmc_plan_layout_info": ([vp, P(lsmc_request), sz, u32, u32, P(lsmc_plan_info)],
+                                      ctypes.c_int),
             "lsmc_plan_destroy": ([vp], None),
             "lsmc_plan_set_timing": ([vp, i32], ctypes.c_int),
             "lsmc_plan_kernel_times": ([vp, P(dbl), P(u32)], ctypes.c_int),
@@ -371,6 +373,16 @@ def lsmc_plan_device_results(plan):
 def lsmc_plan_get_info(plan):
     info = lsmc_plan_info()
     check(load().lsmc_plan_get_info(plan, ctypes.byref(info)), "lsmc_plan_get_info")
+    return info
+
+
+def lsmc_plan_layout_info(ctx, reqs, sub, ppt=0):
+    """Counters of the plan these requests would get with this backward
+    shape, computed on the host (ctx may be None)."""
+    arr = (lsmc_request * len(reqs))(*reqs)
+    info = lsmc_plan_info()
+    check(load().lsmc_plan_layout_info(ctx, arr, len(reqs), sub, ppt, ctypes.byref(info)),
+          "lsmc_plan_layout_info")
     return info
 
 
