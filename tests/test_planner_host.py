@@ -90,6 +90,28 @@ def test_in_the_money_strikes_take_half_the_sub_tiles(lib):
     assert info.device_bytes > _info(PAPER, 32, 2).device_bytes
 
 
+def test_a_book_plan_is_the_sum_of_its_contracts(lib):
+    # 128 uneven contracts of the 512-contract book in one plan: results,
+    # instances, path-steps and jobs add up over the contracts (each with
+    # its own date count: a regression chain per scenario of every contract)
+    book = workloads.book(n_contracts=128, precision="df")
+    reqs = [api.Request(w).c for w in book]
+    info = L.lsmc_plan_layout_info(None, reqs, 4, 2)
+    assert info.n_results == len(book)
+    assert info.n_instances == sum(w.n_scenarios for w in book)
+    assert info.n_groups == 5 * len(book)
+    assert info.lsmc_path_steps == sum(w.lsmc_path_steps for w in book)
+    assert info.backward_jobs == sum(_expected_jobs(w, [4], 2) for w in book)
+    # single-strike contracts: the in-the-money split changes nothing
+    assert L.lsmc_plan_layout_info(None, reqs, 4 | L.LSMC_SUB_ITM_HALF, 2).backward_jobs == \
+        info.backward_jobs
+    # one plan holds one precision
+    mixed = reqs[:2] + [api.Request(book[2].replace(precision="fp64")).c]
+    with pytest.raises(L.LsmcError) as e:
+        L.lsmc_plan_layout_info(None, mixed, 4, 2)
+    assert e.value.status == L.LSMC_ENOTIMPL
+
+
 def test_layout_bytes_match_the_footprint(lib):
     for wl in (PAPER, PAPER.replace(precision="mixed"), workloads.SMALL_FP64):
         fp = L.lsmc_request_footprint(None, api.Request(wl).c)
