@@ -313,7 +313,8 @@ int lsmc_plan_get_info(const lsmc_plan* plan, lsmc_plan_info* info);
 /* The counters of lsmc_plan_get_info that are fixed before any launch, for
  * the plan lsmc_plan_create would build for these requests with backward
  * shape (sub sub-tiles per job, optionally | LSMC_SUB_ITM_HALF; ppt paths
- * per thread of a sub-tile, 0: the precision's default): generated and LSMC
+ * per thread of a sub-tile, 0 or a value not compiled for the precision:
+ * the precision's default): generated and LSMC
  * path-steps, backward jobs, device bytes, results, instances, path groups
  * and table bytes (h2d_bytes); kernels_per_launch = 4, itm_path_steps =
  * d2h_bytes = 0.  Host only: nothing is allocated and no device is touched;
