@@ -147,6 +147,12 @@ class Context:
         reqs = [Request(w, **kw) for w in wls]
         return [r.as_dict() for r in L.lsmc_price_book(self.ctx, [q.c for q in reqs])]
 
+    def layout(self, wls: Sequence[Workload], sub: int, ppt: int = 0, **kw):
+        """Counters (lsmc_plan_info) of the plan these workloads would get
+        with backward shape (sub | LSMC_SUB_ITM_HALF, ppt), computed on the
+        host without allocating."""
+        return plan_layout(wls, sub, ppt, ctx=self, **kw)
+
     def autotune(self, wls: Sequence[Workload], **kw):
         """(sub-tiles per backward job, paths per lane, backward ms) chosen
         for these requests."""
@@ -166,6 +172,15 @@ class Context:
 
     def poll(self, ticket: int, n_strikes: int):
         return L.lsmc_poll(self.ctx, ticket, n_strikes)
+
+
+def plan_layout(wls: Sequence[Workload], sub: int, ppt: int = 0, ctx: "Context" = None, **kw):
+    """Counters (lsmc_plan_info) of the plan these workloads would get with
+    backward shape (sub | LSMC_SUB_ITM_HALF, ppt); host only, no device
+    needed."""
+    reqs = [Request(w, **kw) for w in wls]
+    return L.lsmc_plan_layout_info(ctx.ctx if ctx is not None else None, [q.c for q in reqs],
+                                   sub, ppt)
 
 
 class Plan:

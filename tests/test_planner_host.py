@@ -22,7 +22,7 @@ def lib():
 
 
 def _info(wl, sub, ppt=0):
-    return L.lsmc_plan_layout_info(None, [api.Request(wl).c], sub, ppt)
+    return api.plan_layout([wl], sub, ppt)
 
 
 def _threads(precision):
