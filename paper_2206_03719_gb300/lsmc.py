@@ -13,6 +13,7 @@ import threading
 
 from . import build as _build
 
+LSMC_ABI_VERSION = 1
 LSMC_OK, LSMC_PENDING = 0, 1
 LSMC_EINVAL, LSMC_ENOMEM, LSMC_EBUSY, LSMC_ETIMEOUT = -1, -2, -3, -4
 LSMC_ECUDA, LSMC_ENOTIMPL, LSMC_ENOTFOUND, LSMC_ENODEV = -5, -6, -7, -8
@@ -44,6 +45,8 @@ EXPORTS = [
 ]
 # scenario kinds of a result's revaluations (lsmc_plan_fetch_scenarios)
 LSMC_SC_KINDS = ("base", "S+", "S-", "Sg+", "Sg-", "v0+", "v0-", "r+", "r-", "T-", "T+")
+(LSMC_SC_BASE, LSMC_SC_S_UP, LSMC_SC_S_DN, LSMC_SC_SG_UP, LSMC_SC_SG_DN, LSMC_SC_V0_UP,
+ LSMC_SC_V0_DN, LSMC_SC_R_UP, LSMC_SC_R_DN, LSMC_SC_T_DN, LSMC_SC_T_UP) = range(11)
 LSMC_SC_COUNT = len(LSMC_SC_KINDS)
 
 

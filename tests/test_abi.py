@@ -37,8 +37,29 @@ def test_every_declared_entry_point_is_exported(lib):
     assert sorted(L.EXPORTS) == declared
 
 
+def test_binding_constants_equal_the_header(tmp_path):
+    # every named constant of the header (enum members and #defines), as the
+    # C compiler evaluates it, equals the binding's constant of that name
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    names = set(re.findall(r"#define (LSMC_[A-Z0-9_]+) \S", text))
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        names |= set(re.findall(r"\b(LSMC_[A-Z0-9_]+)\b(?!\s*\()", body))
+    names = sorted(names)
+    assert {"LSMC_SUB_ITM_HALF", "LSMC_GREEK_ALL", "LSMC_SC_T_UP", "LSMC_SC_COUNT"} <= set(names)
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "lsmc.h"\nint main(void) {\n' +
+                   "".join('  printf("%%s %%lld\\n", "%s", (long long)(%s));\n' % (n, n)
+                           for n in names) + "  return 0;\n}\n")
+    exe = tmp_path / "consts"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    for line in subprocess.check_output([str(exe)]).decode().split("\n"):
+        if line:
+            name, value = line.split()
+            assert getattr(L, name) == int(value), name
+
+
 def test_abi_version_and_strerror(lib):
-    assert L.lsmc_abi_version() == 1
+    assert L.lsmc_abi_version() == L.LSMC_ABI_VERSION == 1
     for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
         assert L.lsmc_strerror(code) not in ("", "unknown status")
     assert L.lsmc_strerror(12345) == "unknown status"
