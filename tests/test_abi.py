@@ -37,6 +37,23 @@ def test_every_declared_entry_point_is_exported(lib):
     assert sorted(L.EXPORTS) == declared
 
 
+def test_every_struct_field_sits_where_the_header_puts_it(tmp_path):
+    # the binding's ctypes structures field by field against the compiler's
+    # offsetof (a swap of two fields of one size keeps every size and would
+    # pass a size check alone)
+    structs = (L.lsmc_heston, L.lsmc_contract, L.lsmc_bumps, L.lsmc_result, L.lsmc_config,
+               L.lsmc_request, L.lsmc_plan_info, L.lsmc_bounds)
+    fields = [(t.__name__, f[0]) for t in structs for f in t._fields_]
+    src = tmp_path / "offsets.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lsmc.h"\nint main(void) {\n' +
+                   "".join('  printf("%%zu\\n", offsetof(%s, %s));\n' % f for f in fields) +
+                   "  return 0;\n}\n")
+    exe = tmp_path / "offsets"
+    subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    offs = [int(x) for x in subprocess.check_output([str(exe)]).decode().split()]
+    assert offs == [getattr(getattr(L, t), f).offset for t, f in fields]
+
+
 def test_binding_constants_equal_the_header(tmp_path):
     # every named constant of the header (enum members and #defines), as the
     # C compiler evaluates it, equals the binding's constant of that name
