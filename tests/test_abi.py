@@ -54,6 +54,57 @@ def test_every_struct_field_sits_where_the_header_puts_it(tmp_path):
     assert offs == [getattr(getattr(L, t), f).offset for t, f in fields]
 
 
+def _prototypes():
+    """{name: (return type, [parameter declarations])} of the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for m in re.finditer(r"(const\s+char\s*\*|int|void)\s+(lsmc_\w+)\s*\(", text):
+        depth, i = 1, m.end()
+        while depth:
+            depth += {"(": 1, ")": -1}.get(text[i], 0)
+            i += 1
+        params, depth, cur = [], 0, ""
+        for ch in text[m.end():i - 1]:
+            if ch == "," and depth == 0:
+                params.append(cur.strip())
+                cur = ""
+                continue
+            depth += {"(": 1, ")": -1}.get(ch, 0)
+            cur += ch
+        params.append(cur.strip())
+        out[m.group(2)] = (m.group(1).replace(" ", ""), [p for p in params if p not in ("", "void")])
+    return out
+
+
+def _c_class(decl):
+    if "*" in decl or "[" in decl or "(" in decl:
+        return "ptr"
+    ty = decl.split()[-2] if len(decl.split()) > 1 else decl
+    return {"int": ("int", 4), "int32_t": ("int", 4), "uint32_t": ("int", 4),
+            "uint64_t": ("int", 8), "int64_t": ("int", 8), "size_t": ("int", 8),
+            "double": ("float", 8), "float": ("float", 4)}[ty]
+
+
+def _ctypes_class(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, (ctypes._Pointer, ctypes._CFuncPtr)):
+        return "ptr"
+    return ("float" if t._type_ in "fd" else "int", ctypes.sizeof(t))
+
+
+def test_every_binding_signature_matches_its_prototype(lib):
+    # argument count, and per argument pointer or scalar of the same kind
+    # and width, of every entry point as the binding declares it to ctypes
+    protos = _prototypes()
+    assert sorted(protos) == sorted(L.EXPORTS)
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        assert len(fn.argtypes) == len(params), name
+        for decl, t in zip(params, fn.argtypes):
+            assert _c_class(decl) == _ctypes_class(t), (name, decl, t)
+        assert {"int": ctypes.c_int, "void": None, "constchar*": ctypes.c_char_p}[ret] == \
+            fn.restype, name
+
+
 def test_binding_constants_equal_the_header(tmp_path):
     # every named constant of the header (enum members and #defines), as the
     # C compiler evaluates it, equals the binding's constant of that name
