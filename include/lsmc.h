@@ -191,7 +191,11 @@ typedef struct lsmc_ctx lsmc_ctx;
 typedef struct lsmc_plan lsmc_plan;
 
 /* ---- library ----------------------------------------------------------- */
+/* Static NUL-terminated name of a status code ("unknown status" for any
+ * other value).  Never fails and needs no device. */
 const char* lsmc_strerror(int status);
+/* LSMC_ABI_VERSION of the library actually loaded (compare it with the
+ * header's to detect a mismatched build).  Never fails. */
 int lsmc_abi_version(void);
 /* Device allocations the library has made in this process: cudaMalloc and
  * cudaMallocAsync calls and successful lsmc_set_allocator callbacks (not the
@@ -203,12 +207,20 @@ int lsmc_device_allocations(uint64_t* count);
 /* ---- context ----------------------------------------------------------- */
 /* Creates a context on config->device (NULL: device 0, FP64, QE).  The
  * context owns a CUDA stream unless one is set, a workspace arena and, after
- * the first lsmc_submit, one scheduler thread.  Thread-safe afterwards. */
+ * the first lsmc_submit, one scheduler thread.  Thread-safe afterwards.
+ * *out (host) receives the context, owned by the caller until lsmc_destroy
+ * (NULL on failure).  LSMC_EINVAL: out NULL, an unknown precision or scheme,
+ * or a device ordinal out of range; LSMC_ENODEV: no CUDA device;
+ * LSMC_ECUDA: the device or the context's stream could not be set up;
+ * LSMC_ENOMEM: host memory. */
 int lsmc_create(lsmc_ctx** out, const lsmc_config* config);
-/* Waits for in-flight work, stops the scheduler, frees everything. */
+/* Waits for in-flight work, stops the scheduler, frees everything; tickets
+ * not yet taken are dropped.  Destroy every plan of the context first.
+ * NULL is ignored. */
 void lsmc_destroy(lsmc_ctx* ctx);
 /* Work of the synchronous calls runs on this CUDA stream (a cudaStream_t; NULL
- * = the context's own stream).  The caller keeps the stream alive. */
+ * = the context's own stream).  The caller keeps the stream alive.
+ * LSMC_EINVAL if ctx is NULL. */
 int lsmc_set_stream(lsmc_ctx* ctx, void* cuda_stream);
 /* Device memory callbacks used instead of cudaMalloc / cudaFree for every
  * allocation the context makes outside a workspace (plans, the serving
@@ -254,19 +266,37 @@ int lsmc_set_backward_shape(lsmc_ctx* ctx, uint32_t sub, uint32_t ppt);
 int lsmc_set_serving_share(lsmc_ctx* ctx, double share);
 /* Device memory the context sub-allocates from instead of cudaMalloc
  * (e.g. a PyTorch tensor).  Must be set before any plan exists and stay
- * valid until lsmc_destroy; 256-byte aligned. */
+ * valid until lsmc_destroy; 256-byte aligned.  The caller keeps ownership
+ * (the library never frees it).  LSMC_EINVAL: ctx or device_ptr NULL, bytes
+ * below 4096 or a misaligned pointer; LSMC_EBUSY while a plan holds part of
+ * the current workspace or once the context has allocated its own arena. */
 int lsmc_set_workspace(lsmc_ctx* ctx, void* device_ptr, size_t bytes);
-/* Bytes of device memory a request needs (paths, regression state, tables). */
+/* Bytes of device memory a request needs (paths, regression state, tables),
+ * written to *bytes (host), for the default backward shape.  Host only; ctx
+ * may be NULL (then the library's default precision and scheme).
+ * LSMC_EINVAL: NULL req or bytes, or an invalid request; LSMC_ENOTIMPL: an
+ * unsupported flag combination. */
 int lsmc_request_footprint(const lsmc_ctx* ctx, const lsmc_request* req,
                            size_t* bytes);
 
 /* ---- synchronous pricing ----------------------------------------------- */
-/* One contract: price + the Greeks of bumps->greek_mask (Sec. 2.2). */
+/* Errors of the pricing calls and plans: LSMC_EINVAL for a NULL pointer or
+ * an invalid request (nothing is launched); LSMC_ENOTIMPL for requests of
+ * one call that differ in precision, scheme, basis or flags; LSMC_ENOMEM
+ * when device memory or the workspace is exhausted; LSMC_ETIMEOUT when a
+ * bounded device wait expired (lsmc_set_wait_limit; the context stays
+ * usable); LSMC_ECUDA for a failed CUDA call.  The pricing calls run on the
+ * context stream and return when the results are in outs. */
+/* One contract: price + the Greeks of bumps->greek_mask (Sec. 2.2), its
+ * paths simulated by the context's scheme (Sec. 2.2.1) under Philox seed
+ * seed; out: host, one result. */
 int lsmc_price_greeks(lsmc_ctx* ctx, const lsmc_heston* model,
                       const lsmc_contract* contract, uint32_t n_paths,
                       uint32_t n_steps, int32_t basis, const lsmc_bumps* bumps,
                       uint64_t seed, lsmc_result* out);
-/* All strikes of one request; outs: host, req->n_strikes results. */
+/* All strikes of one request, on one path set per scenario (Sec. 2.2.1:
+ * the curve fits of every strike read the same paths); outs: host,
+ * req->n_strikes results in strike order. */
 int lsmc_price_request(lsmc_ctx* ctx, const lsmc_request* req,
                        lsmc_result* outs);
 /* A book of requests in one forward and one backward launch (CUDA-graph
@@ -276,13 +306,19 @@ int lsmc_price_book(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
 
 /* ---- plans: build once, launch many times ------------------------------ */
 /* Validates and expands the requests (scenarios, path groups, job tables),
- * uploads the tables and reserves the device memory. */
+ * uploads the tables and reserves the device memory (the batching of paths
+ * of Sec. 4.1, over all scenarios and requests at once).  *out (host)
+ * receives the plan, owned by the caller until lsmc_plan_destroy; errors as
+ * for the pricing calls. */
 int lsmc_plan_create(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                      lsmc_plan** out);
 /* Enqueues the whole path (forward, backward, Greeks) on the context stream;
- * with use_graph != 0 the sequence is captured once and replayed. */
+ * with use_graph != 0 the sequence is captured once and replayed.
+ * Asynchronous.  LSMC_EINVAL for NULL; LSMC_ECUDA if a launch fails. */
 int lsmc_plan_launch(lsmc_plan* plan, int32_t use_graph);
-/* Waits for the last launch and copies its results to outs (host). */
+/* Waits for the last launch and copies its results to outs (host, the
+ * plan's n_results, lsmc_plan_get_info).  LSMC_EINVAL for NULL;
+ * LSMC_ETIMEOUT or LSMC_ECUDA as for the pricing calls. */
 int lsmc_plan_fetch(lsmc_plan* plan, lsmc_result* outs);
 /* Scenario kinds of the bump-and-revalue table (LSMC_SC_*), the index of a
  * revaluation within one result's row of lsmc_plan_fetch_scenarios. */
@@ -298,7 +334,9 @@ enum { LSMC_SC_BASE = 0, LSMC_SC_S_UP, LSMC_SC_S_DN, LSMC_SC_SG_UP, LSMC_SC_SG_D
  * count.  Waits for the last launch. */
 int lsmc_plan_fetch_scenarios(lsmc_plan* plan, double* prices, uint32_t* near_ties,
                               size_t n_results);
-/* Device address of the launch's results (lsmc_result array). */
+/* Device address of the launch's results: *device_ptr (host) receives the
+ * address of *count lsmc_result entries, owned by the plan, rewritten by
+ * every launch and valid until lsmc_plan_destroy.  LSMC_EINVAL for NULL. */
 int lsmc_plan_device_results(lsmc_plan* plan, void** device_ptr, size_t* count);
 /* Counters of the plan: kernels per launch, generated and LSMC path-steps,
  * jobs of the backward pass, device bytes held. */
@@ -309,6 +347,7 @@ typedef struct lsmc_plan_info {
   uint64_t h2d_bytes;      /* table bytes uploaded by lsmc_plan_create */
   uint64_t d2h_bytes;      /* bytes read back by each lsmc_plan_fetch */
 } lsmc_plan_info;
+/* Fills *info (host) with the plan's counters.  LSMC_EINVAL for NULL. */
 int lsmc_plan_get_info(const lsmc_plan* plan, lsmc_plan_info* info);
 /* The counters of lsmc_plan_get_info that are fixed before any launch, for
  * the plan lsmc_plan_create would build for these requests with backward
@@ -325,11 +364,14 @@ int lsmc_plan_get_info(const lsmc_plan* plan, lsmc_plan_info* info);
 int lsmc_plan_layout_info(const lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                           uint32_t sub, uint32_t ppt, lsmc_plan_info* info);
 /* Per-kernel timing of later launches (CUDA events on the plan's stream,
- * recorded between its kernels; no effect on results).  enable = 0 stops. */
+ * recorded between its kernels; no effect on results).  enable = 0 stops.
+ * LSMC_EINVAL for NULL. */
 int lsmc_plan_set_timing(lsmc_plan* plan, int32_t enable);
 /* Device milliseconds summed over the launches since the previous call:
- * ms[0] setup, ms[1] forward (paths), ms[2] backward (LSMC), ms[3] Greeks;
- * *launches = number of launches summed.  Waits for the last launch. */
+ * ms[0] setup, ms[1] forward (paths), ms[2] backward (LSMC), ms[3] Greeks
+ * (host, 4 doubles); *launches (optional) = number of launches summed.
+ * Waits for the last launch.  LSMC_EINVAL for NULL plan or ms; LSMC_ECUDA
+ * if an event cannot be read. */
 int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
 /* Autotuner: times the backward pass of a plan for these requests over its
  * tile shapes -- paths per thread of a sub-tile (2 or 4 for LSMC_FP64 and
@@ -341,7 +383,9 @@ int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
  * optional; best_sub may carry LSMC_SUB_ITM_HALF). */
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                   uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
-/* Destroy every plan before the context it was created on. */
+/* Frees the plan's device memory once its work is done (stream-ordered).
+ * Destroy every plan before the context it was created on.  NULL is
+ * ignored. */
 void lsmc_plan_destroy(lsmc_plan* plan);
 
 /* Lower and upper bounds of the American price of every strike of one
@@ -375,18 +419,28 @@ int lsmc_price_bounds(lsmc_ctx* ctx, const lsmc_request* req, uint32_t n_outer,
  * memory, ahead of the rest of its batch (out-of-sample requests finish with
  * their batch).  The backward job size of a request depends on the request
  * alone, so its results are the same whichever batch it runs in, and the
- * same as lsmc_price_request's under the same backward shape.  LSMC_EBUSY
- * when the queue is full. */
+ * same as lsmc_price_request's under the same backward shape.  *ticket
+ * (host) receives the ticket.  LSMC_EINVAL or LSMC_ENOTIMPL as for
+ * lsmc_request_footprint (nothing is queued); LSMC_ENOMEM when the request
+ * alone exceeds the serving workspace; LSMC_EBUSY when the queue
+ * (config.queue_capacity) is full; LSMC_ECUDA if the scheduler's streams
+ * cannot be created.  (A serving policy: the paper prices one problem at a
+ * time.) */
 int lsmc_submit(lsmc_ctx* ctx, const lsmc_request* req, uint64_t* ticket);
-/* LSMC_PENDING while in flight; LSMC_OK with outs filled (n_strikes results)
- * once done (the ticket is then released); a negative code on failure. */
+/* LSMC_PENDING while in flight; LSMC_OK with outs filled (host, n_strikes
+ * results; NULL takes the ticket without copying) once done, the ticket then
+ * released; the request's own error code if it failed (released too);
+ * LSMC_ENOTFOUND for a ticket never issued or already released; LSMC_EINVAL
+ * if ctx is NULL. */
 int lsmc_poll(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs);
-/* Blocks up to timeout_s (< 0: no limit) for the ticket, then as lsmc_poll. */
+/* Blocks up to timeout_s (< 0: no limit) for the ticket, then as lsmc_poll
+ * (LSMC_PENDING if the time ran out first). */
 int lsmc_wait(lsmc_ctx* ctx, uint64_t ticket, lsmc_result* outs,
               double timeout_s);
 /* Per-ticket timing (seconds since lsmc_create, host steady clock): submit,
- * admission to the device and completion.  Also answers for released
- * tickets (the last 2^20 are remembered). */
+ * admission to the device and completion (each output optional, host).
+ * Also answers for released tickets (the last 2^20 are remembered).
+ * LSMC_ENOTFOUND for other tickets; LSMC_EINVAL if ctx is NULL. */
 int lsmc_ticket_times(lsmc_ctx* ctx, uint64_t ticket, double* submit_s,
                       double* admit_s, double* done_s);
 
@@ -421,12 +475,17 @@ int lsmc_check_report(uint32_t* code, uint32_t* line, int32_t reset);
 
 /* ---- stage entry points (device pointers; for parity tests) ------------- */
 /* Philox4x32-10 of n counters: d_ctr n x 4 uint32 (device), key = (key_lo,
- * key_hi); d_out n x 4 uint32 (device).  (Random inputs of Sec. 2.2.1.) */
+ * key_hi); d_out n x 4 uint32 (device).  (Random inputs of Sec. 2.2.1.)
+ * Asynchronous on cuda_stream (NULL: the default stream); LSMC_EINVAL for
+ * NULL arrays with n > 0, LSMC_ECUDA if the launch fails. */
 int lsmc_philox(const uint32_t* d_ctr, uint32_t key_lo, uint32_t key_hi,
                 uint32_t* d_out, size_t n, void* cuda_stream);
-/* Random inputs of n (path, step) pairs under (seed, stream_id): d_out is
- * n x 3 (U_V, Z_V, Z_X) as double (LSMC_FP64: 52-bit grid), float
- * (LSMC_MIXED: 23-bit grid) or float pairs (LSMC_DF: the FP64 values split). */
+/* Random inputs of n (path, step) pairs under (seed, stream_id), the two
+ * per path and step of Sec. 2.2.1: d_path, d_step (device, n uint32 each);
+ * d_out (device) is n x 3 (U_V, Z_V, Z_X) as double (LSMC_FP64: 52-bit
+ * grid), float (LSMC_MIXED: 23-bit grid) or float pairs (LSMC_DF: the FP64
+ * values split).  Asynchronous on cuda_stream; LSMC_EINVAL for NULL arrays
+ * with n > 0 or an unknown precision, LSMC_ECUDA if the launch fails. */
 int lsmc_draws(uint64_t seed, uint32_t stream_id, const uint32_t* d_path,
                const uint32_t* d_step, size_t n, int32_t precision,
                void* d_out, void* cuda_stream);
@@ -451,10 +510,14 @@ int lsmc_exp(const void* d_x, void* d_y, size_t n, int32_t precision, void* cuda
  * (its quantile reads the random words: lsmc_draws). */
 int lsmc_quantile(const void* d_u, void* d_z, size_t n, int32_t precision, void* cuda_stream);
 
-/* Heston paths (Sec. 2.2.1: variance, log price, exponential):
+/* Heston paths (Sec. 2.2.1: variance, log price, exponential; the
+ * step-major layout of Sec. 4.1):
  * d_S, d_V (device) are (n_steps + 1) x n_paths, step-major, double, float
  * or float pairs by precision; row 0 holds S0 and v0.  V holds max(v, 0) under
- * FT_EULER. */
+ * FT_EULER.  Path p, step n draws Philox counter (p, n, stream_id, 0) under
+ * key seed.  Asynchronous on cuda_stream (its small tables are allocated
+ * and freed stream-ordered); LSMC_EINVAL for NULL pointers or invalid model
+ * parameters, LSMC_ENOMEM, LSMC_ECUDA. */
 int lsmc_paths(const lsmc_heston* model, double T, int32_t scheme,
                int32_t precision, uint32_t n_paths, uint32_t n_steps,
                uint64_t seed, uint32_t stream_id, void* d_S, void* d_V,
@@ -476,11 +539,16 @@ int lsmc_multi_asset_max(const lsmc_heston* models, uint32_t n_assets, double T,
                          uint32_t n_paths, uint32_t n_steps, uint64_t seed,
                          uint32_t stream_id, void* d_M, void* cuda_stream);
 
-/* Longstaff-Schwartz backward pass over given paths (same layout as
- * lsmc_paths output).  d_out (device, 5 doubles): price, price_se,
+/* Longstaff-Schwartz backward pass over given paths (Sec. 2.2.1: the
+ * reduction and the least-squares curve fit of every exercise date; same
+ * layout as lsmc_paths output).  d_out (device, 5 doubles): price, price_se,
  * european_price, continuation value, near-tie decisions (see lsmc_result).  d_beta (device, optional):
  * n_steps x 6 doubles, row n = coefficients at date n (NaN if none).
- * d_n_singular (device, optional): 1 uint32. */
+ * d_n_singular (device, optional): 1 uint32.  Returns after the work has
+ * finished (waits on cuda_stream).  LSMC_EINVAL for NULL d_S, model,
+ * contract or d_out, NULL d_V with LSMC_BASIS_SV2, or invalid parameters;
+ * LSMC_ENOMEM; LSMC_ETIMEOUT when a bounded device wait expired;
+ * LSMC_ECUDA. */
 int lsmc_backward(const void* d_S, const void* d_V, uint32_t n_paths,
                   uint32_t n_steps, int32_t precision, const lsmc_heston* model,
                   const lsmc_contract* contract, int32_t basis, double* d_out,

@@ -175,7 +175,7 @@ int cuda_status(cudaError_t e) {
     if (e__ != cudaSuccess) return cuda_status(e__); \
   } while (0)
 
-int resolve(const lsmc_ctx* ctx, int32_t v, int dflt) { return v < 0 ? (ctx ? dflt : dflt) : v; }
+int resolve(const lsmc_ctx*, int32_t v, int dflt) { return v < 0 ? dflt : v; }
 
 int occupancy(lsmc_ctx* ctx, int precision, int basis, int ppt, int fmt) {
   if (ctx) {
