@@ -331,7 +331,8 @@ enum { LSMC_SC_BASE = 0, LSMC_SC_S_UP, LSMC_SC_S_DN, LSMC_SC_SG_UP, LSMC_SC_SG_D
  * that revaluation at [k * LSMC_SC_COUNT + s], NaN where the request has no
  * such scenario; near_ties (host, optional, same shape) its near-tie
  * decisions (see lsmc_result).  n_results must equal the plan's result
- * count.  Waits for the last launch. */
+ * count.  Waits for the last launch.  LSMC_EINVAL for a NULL plan or prices
+ * or another n_results; LSMC_ECUDA if the copy fails. */
 int lsmc_plan_fetch_scenarios(lsmc_plan* plan, double* prices, uint32_t* near_ties,
                               size_t n_results);
 /* Device address of the launch's results: *device_ptr (host) receives the
@@ -380,7 +381,9 @@ int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
  * strikes on both sides of S0 (one warm-up and one timed launch each) --,
  * remembers the fastest for later plans of the same precision, basis and
  * size class on this context, and returns it (best_sub, best_ppt, best_ms:
- * optional; best_sub may carry LSMC_SUB_ITM_HALF). */
+ * optional; best_sub may carry LSMC_SUB_ITM_HALF).  Synchronous on the
+ * context stream; errors as for lsmc_plan_create and lsmc_plan_fetch (the
+ * first failing trial ends the search). */
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                   uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
 /* Frees the plan's device memory once its work is done (stream-ordered).
