@@ -382,8 +382,9 @@ int lsmc_plan_kernel_times(lsmc_plan* plan, double ms[4], uint32_t* launches);
  * remembers the fastest for later plans of the same precision, basis and
  * size class on this context, and returns it (best_sub, best_ppt, best_ms:
  * optional; best_sub may carry LSMC_SUB_ITM_HALF).  Synchronous on the
- * context stream; errors as for lsmc_plan_create and lsmc_plan_fetch (the
- * first failing trial ends the search). */
+ * context stream.  The first failing trial ends the search: the fastest
+ * shape timed before it is kept and LSMC_OK returned, else that trial's
+ * error (as for lsmc_plan_create and lsmc_plan_fetch). */
 int lsmc_autotune(lsmc_ctx* ctx, const lsmc_request* reqs, size_t n_reqs,
                   uint32_t* best_sub, uint32_t* best_ppt, double* best_ms);
 /* Frees the plan's device memory once its work is done (stream-ordered).
