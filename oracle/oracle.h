@@ -78,38 +78,50 @@ typedef struct {
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
                        uint32_t out[4]);
 
-/* (m + 1/2) 2^-52 with m = the top 52 bits of (hi:lo); never 0 or 1. */
+/* The uniforms behind the random inputs of Sec. 2.2.1 (the paper leaves
+ * their grid open; this one is symmetric, so 1 - u is exact and the
+ * quantile is odd about 1/2): (m + 1/2) 2^-52 with m = the top 52 bits of
+ * (hi:lo); never 0 or 1. */
 double orc_uniform_f64(uint32_t hi, uint32_t lo);
-/* (m + 1/2) 2^-23 with m = the top 23 bits of w; never 0 or 1. */
+/* The same in single precision: (m + 1/2) 2^-23 with m = the top 23 bits
+ * of w; never 0 or 1. */
 double orc_uniform_f32(uint32_t w);
 
-/* Standard normal quantile: the root z of (1/2) erfc(-z / sqrt 2) = u. */
+/* Standard normal quantile, the map from uniforms to the normal draws of
+ * Sec. 2.2.1, by its definition: the root z of (1/2) erfc(-z / sqrt 2) = u
+ * (bracketed Newton iteration). */
 double orc_norm_inv(double u);
 
-/* The random inputs of one path step: Philox of counter
+/* The random inputs of one path step (Sec. 2.2.1: two random numbers per
+ * path, asset and time step): Philox of counter
  * (path, step, stream, 0) under key (seed lo, seed hi) gives (U_V, Z_V, Z_X),
  * Z = quantile(U).  out = {U_V, Z_V, Z_X}. */
 void orc_draws(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
                int grid, double out[3]);
 
-/* orc_draws for asset `asset` of a multi-asset path: counter
- * (path, step, stream, asset); orc_draws is asset 0. */
+/* orc_draws for asset `asset` of a multi-asset path (the STAC-A2 form of
+ * Sec. 2.2.1): counter (path, step, stream, asset); orc_draws is asset 0. */
 void orc_draws_asset(uint64_t seed, uint32_t stream, uint32_t path, uint32_t step,
                      uint32_t asset, int grid, double out[3]);
 
 /* Andersen QE step: out = {x1, v1}. */
 void orc_qe_step(const orc_heston* m, double dt, double x, double v,
                  double uV, double zV, double zX, double out[2]);
-/* Full-truncation Euler step: out = {x1, v1 (raw), max(v1, 0)}. */
+/* Full-truncation Euler step (Lord, Koekkoek and van Dijk, 2010: v+ =
+ * max(v, 0) in drift and diffusion), offered beside the paper's QE scheme
+ * (Sec. 2.2.1): out = {x1, v1 (raw), max(v1, 0)}. */
 void orc_ft_step(const orc_heston* m, double dt, double x, double v,
                  double zV, double zX, double out[3]);
 
-/* Path matrices S[n*P + p], V[n*P + p] for n = 0..N (row 0 = S0, v0). */
+/* Heston paths in the order of Sec. 2.2.1 (per step the variance, then the
+ * log price, then its exponential), stored step-major as in Sec. 4.1: path
+ * matrices S[n*P + p], V[n*P + p] for n = 0..N (row 0 = S0, v0). */
 int orc_paths(const orc_heston* m, double T, int scheme, int grid,
               uint32_t P, uint32_t N, uint64_t seed, uint32_t stream,
               double* S, double* V, int n_threads);
 
-/* One path (index `path`) of orc_paths: S[n], V[n] for n = 0..N. */
+/* One path (index `path`) of orc_paths (Sec. 2.2.1), simulated alone:
+ * S[n], V[n] for n = 0..N. */
 int orc_path_one(const orc_heston* m, double T, int scheme, int grid,
                  uint32_t path, uint32_t N, uint64_t seed, uint32_t stream,
                  double* S, double* V);
@@ -126,8 +138,8 @@ int orc_path_one(const orc_heston* m, double T, int scheme, int grid,
 int orc_multi_max(const orc_heston* models, uint32_t A, double T, int scheme, int grid,
                   double rho_assets, uint32_t P, uint32_t N, uint64_t seed,
                   uint32_t stream, double* M, int n_threads);
-/* The path of one asset of one multi-asset path (same arithmetic as
- * orc_multi_max): S[n] for n = 0..N. */
+/* The path of one asset of one multi-asset path (Sec. 2.2.1; same
+ * arithmetic as orc_multi_max): S[n] for n = 0..N. */
 int orc_asset_path(const orc_heston* m, uint32_t asset, double T, int scheme, int grid,
                    double rho_assets, uint32_t path, uint32_t N, uint64_t seed,
                    uint32_t stream, double* S);
@@ -164,7 +176,8 @@ typedef struct {
   uint32_t n_flips;
 } orc_tie_ctl;
 
-/* orc_lsmc under a tie control (ctl may be NULL). */
+/* orc_lsmc (Sec. 2.2.1's Longstaff-Schwartz stage) under a tie control
+ * (ctl may be NULL: then it is orc_lsmc). */
 int orc_lsmc_tie(const double* S, const double* V, uint32_t P, uint32_t N,
                  double S0, double K, double T, double r, double theta, int type,
                  int style, int basis, double out[4], uint32_t* n_singular,
@@ -180,12 +193,15 @@ int orc_lsmc_oos(const double* SA, const double* VA, const double* SB, const dou
                  double theta, int type, int style, int basis, double out[4],
                  uint32_t* n_singular);
 
-/* Scenario table of a bump specification: fills up to ORC_SC_COUNT models,
+/* Scenario table of a bump specification (the Greeks that Sec. 2.2 names
+ * as the purpose of the run, with no method: here central bump-and-revalue
+ * differences under common random numbers): fills up to ORC_SC_COUNT models,
  * maturities and kinds; returns the number of scenarios or a negative error. */
 int orc_scenarios(const orc_heston* m, double T, const orc_bumps* b,
                   orc_heston* models, double* Ts, int* kinds);
 
-/* Price and Greeks of n_strikes contracts sharing one path set per scenario.
+/* Price and Greeks (Sec. 2.2) of n_strikes contracts sharing one path set
+ * per scenario (Sec. 2.2.1: paths, then the Longstaff-Schwartz stage).
  * scen_prices (optional): n_scen * n_strikes scenario values. */
 int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      const double* strikes, uint32_t n_strikes, uint32_t P,
@@ -193,7 +209,10 @@ int orc_price_greeks(const orc_heston* m, int type, int style, double T,
                      const orc_bumps* b, uint64_t seed, uint32_t stream,
                      int n_threads, orc_result* out, double* scen_prices);
 
-/* orc_price_greeks with out_of_sample != 0: every scenario's price is the
+/* orc_price_greeks (Sec. 2.2) with the path store kept in double (store 0)
+ * or rounded to 16 bits (store 1: binary16, 2: bfloat16; the storage
+ * analogue of the data-type study of Sec. 4.2) and, with out_of_sample != 0,
+ * every scenario's price the
  * out-of-sample estimate, regressions on stream `stream`, pricing paths on
  * stream `stream ^ 0x80000000`. */
 int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
@@ -203,14 +222,16 @@ int orc_price_greeks_ex(const orc_heston* m, int type, int style, double T,
                         int out_of_sample, int store, int n_threads, orc_result* out,
                         double* scen_prices);
 
-/* The Greeks of one strike from its revaluations: vals[s] is the price of
+/* The Greeks of one strike (Sec. 2.2; central differences of the
+ * revaluations) from its revaluations: vals[s] is the price of
  * scenario s of the table orc_scenarios gives (kinds[s] its kind, n_sc
  * scenarios).  Fills price, the Greeks of b->greek_mask (NaN otherwise) and
  * n_revaluations; price_se and european_price are NaN. */
 void orc_greeks_from_values(const orc_heston* m, const orc_bumps* b, const int* kinds,
                             const double* vals, int n_sc, orc_result* out);
 
-/* One revaluation of orc_price_greeks_ex (scenario index sc of the table,
+/* One revaluation (Sec. 2.2.1's Longstaff-Schwartz price of one scenario)
+ * of orc_price_greeks_ex (scenario index sc of the table,
  * strike K) under reversed decisions: out[i] (2^n_keys values) is its price
  * with the decisions whose bit is set in i reversed, bit j standing for the
  * j-th smallest of the n_keys (<= ORC_MAX_ALT_KEYS) keys.  n_ties (optional):
@@ -238,14 +259,17 @@ int orc_dual_bound(const orc_heston* m, int type, double T, const double* strike
                    uint64_t seed, uint32_t stream, uint32_t n_outer, uint32_t n_inner,
                    int n_threads, double* out);
 
-/* Rounding to nearest, ties to even, from a double to IEEE binary16 and to
- * bfloat16 (returned as doubles; overflow gives infinity). */
+/* The 16-bit storage of the data-type study (Sec. 4.2, Table 4): rounding
+ * to nearest, ties to even, from a double to IEEE binary16 (orc_round_f16)
+ * and to bfloat16 (orc_round_bf16), returned as doubles; overflow gives
+ * infinity. */
 double orc_round_f16(double x);
 double orc_round_bf16(double x);
-/* y[i] = x[i] rounded (store 1: binary16, 2: bfloat16). */
+/* y[i] = x[i] rounded as above (store 1: binary16, 2: bfloat16). */
 void orc_round_n(const double* x, double* y, size_t n, int store);
 
-/* Array forms of the scalar functions above (plain loops). */
+/* Array forms of orc_philox4x32_10, orc_norm_inv and orc_draws (Sec. 2.2.1's
+ * random inputs; plain loops over the scalar functions). */
 void orc_philox_n(const uint32_t* ctr, const uint32_t key[2], uint32_t* out,
                   size_t n);
 void orc_norm_inv_n(const double* u, double* z, size_t n);
