@@ -1,7 +1,7 @@
 """The stored expected values of tests/golden/ are what the oracle computes
 now: the cheapest contracts of the book and serving subsets are priced
 again by the script's own oracle call and must give the stored prices and
-Greeks.  A change of the oracle's arithmetic, or of the seeded workload
+Greeks, and one revaluation of each paper-size file its stored price.  A change of the oracle's arithmetic, or of the seeded workload
 generator, that leaves the stored files behind fails here on the CPU
 instead of as a GPU parity failure."""
 import importlib.util
@@ -48,6 +48,26 @@ def test_cheapest_stored_contracts_reproduce(make_golden, subset):
         for k in KEYS:
             if k in want:
                 assert _same(got[k], want[k]), (wls[i].name, k, got[k], want[k])
+
+
+@pytest.mark.parametrize("name, wl, k, kind", [
+    ("paper_fp64", workloads.PAPER_FP64, 2, "base"),
+    ("paper_fp64_ft", workloads.PAPER_FP64.replace(scheme="ft_euler"), 4, "v0+"),
+])
+def test_one_paper_size_revaluation_reproduces(name, wl, k, kind):
+    # one revaluation of one strike of the 131,072 x 252 book, as the
+    # oracle's Greeks use it, against the stored scenario price
+    import oracle
+    from gpu_common import oracle_args
+    stored = json.load(open(os.path.join(HERE, name + ".json")))
+    assert stored["strikes"] == wl.strikes and stored["scheme"] == wl.scheme
+    m, b, kw = oracle_args(wl)
+    kinds = [kd for kd, _, _ in oracle.scenarios(m, wl.T, b)]
+    prices, _ = oracle.scenario_alternatives(
+        m, wl.strikes[k], wl.T, wl.n_paths, wl.n_steps, kinds.index(kind), type_=kw["type_"],
+        style=kw["style"], scheme=kw["scheme"], basis=kw["basis"], b=b, seed=kw["seed"],
+        stream=kw["stream"])
+    assert _same(prices[0], stored["results"][k]["scenarios"][kind])
 
 
 def test_stored_subsets_name_the_generator_contracts(make_golden):
