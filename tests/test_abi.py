@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 import subprocess
+import sys
 import tempfile
 
 import pytest
@@ -124,6 +125,23 @@ def test_binding_constants_equal_the_header(tmp_path):
         if line:
             name, value = line.split()
             assert getattr(L, name) == int(value), name
+
+
+def test_no_cpu_fallback_and_no_oracle_in_the_product():
+    # without its library the binding refuses to load (a fresh interpreter,
+    # so no library is cached) ...
+    code = ("from paper_2206_03719_gb300 import lsmc as L\n"
+            "L.load(path='/nonexistent/liblsmc.so')\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode != 0 and "liblsmc.so is not built" in r.stderr
+    # ... and no file of the package reaches the oracle (test infrastructure)
+    pkg = os.path.join(ROOT, "paper_2206_03719_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cpp", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f), encoding="utf-8").read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|oracle\.h|orc_", text,
+                                     flags=re.M), f
 
 
 def test_abi_version_and_strerror(lib):
