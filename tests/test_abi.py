@@ -142,6 +142,11 @@ def test_no_cpu_fallback_and_no_oracle_in_the_product():
                 text = open(os.path.join(dirpath, f), encoding="utf-8").read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b|oracle\.h|orc_", text,
                                      flags=re.M), f
+    # nor does the oracle reach the package: it shares no code with the CUDA path
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            text = open(os.path.join(ROOT, "oracle", f), encoding="utf-8").read()
+            assert not re.search(r"paper_2206_03719_gb300|lsmc\.h|csrc", text), f
 
 
 def test_abi_version_and_strerror(lib):
