@@ -843,10 +843,11 @@ int start_scheduler(lsmc_ctx* ctx) {
     }
     ctx->arena.reset(ctx->own_arena_mem, budget);
   }
+  // a later call after a failure here keeps what an earlier one created
   ctx->slots.resize(ctx->max_inflight);
   for (auto& s : ctx->slots) {
-    LSMC_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
-    LSMC_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
+    if (!s.stream) LSMC_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking));
+    if (!s.done) LSMC_CUDA(cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming));
   }
   ctx->sched = std::thread(scheduler_loop, ctx);
   ctx->sched_started = true;
